@@ -1,0 +1,176 @@
+"""FP64 CPU oracle for the Gauss-polynomial bilateral filter.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline legs of ``bench.py`` import this package.  It shares no code
+with the CUDA library (``paper_1505_00077_gb300``) and never imports it.
+
+The arithmetic lives in ``bf_oracle.c`` (plain C, double precision, OpenMP over
+independent lines); this module builds it with gcc and wraps it with ctypes.
+
+Functions (each cites the passage of Chaudhury's paper it follows):
+
+* :func:`direct_bf`  -- O1, Eq. (1)-(2) evaluated by brute force on the window
+  [-w, w]^2 (Sec. 1), in-image neighbours only.
+* :func:`gp_bf`      -- O2, Algorithm 1 (GPF) / Eqs. (7)-(11) with the centring
+  of Sec. 2, spatial operator FIR (Eq. (8)) or Deriche's recursive Gaussian.
+* :func:`line_filter`, :func:`deriche_response`, :func:`deriche_coefs` -- the
+  1-D spatial operators and the recursive filter's impulse response.
+* :func:`gp_kernel` -- Eq. (5), the Gauss-polynomial range kernel.
+* :func:`window` -- W = ceil(3 sigma_s) (Sec. 1).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bf_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libbf_oracle.so")
+
+FIR = 1
+IIR = 2
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile bf_oracle.c into oracle/_build/libbf_oracle.so (gcc, -O2, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-Wall", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB_PATH)
+    dp = ctypes.POINTER(ctypes.c_double)
+    i, d = ctypes.c_int, ctypes.c_double
+    lib.bfo_direct.argtypes = [dp, i, i, d, d, i, i, i, i, i, dp]
+    lib.bfo_direct.restype = None
+    lib.bfo_gp.argtypes = [dp, i, i, d, d, i, d, i, i, i, i, i, i, i, dp]
+    lib.bfo_gp.restype = i
+    lib.bfo_line_filter.argtypes = [dp, i, i, d, i, i, i, dp]
+    lib.bfo_line_filter.restype = None
+    lib.bfo_deriche_response.argtypes = [d, i, i, dp]
+    lib.bfo_deriche_response.restype = None
+    lib.bfo_deriche_coefs.argtypes = [d, i, dp]
+    lib.bfo_deriche_coefs.restype = None
+    lib.bfo_max_threads.argtypes = []
+    lib.bfo_max_threads.restype = i
+    lib.bfo_set_threads.argtypes = [i]
+    lib.bfo_set_threads.restype = None
+    lib.bfo_mean.argtypes = [dp, ctypes.c_long]
+    lib.bfo_mean.restype = d
+    lib.bfo_gp_kernel.argtypes = [d, d, d, i]
+    lib.bfo_gp_kernel.restype = d
+    _lib = lib
+    return lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def window(sigma_s: float) -> int:
+    """Half-width of the square window: W = ceil(3 sigma_s) (Sec. 1, 'W = 3 sigma_s')."""
+    return int(math.ceil(3.0 * sigma_s - 1e-12))
+
+
+def max_threads() -> int:
+    return int(_load().bfo_max_threads())
+
+
+def set_threads(n: int) -> None:
+    _load().bfo_set_threads(int(n))
+
+
+def _crop(crop, H, W):
+    if crop is None:
+        return 0, H, 0, W
+    r0, r1, c0, c1 = (int(v) for v in crop)
+    if not (0 <= r0 < r1 <= H and 0 <= c0 < c1 <= W):
+        raise ValueError(f"bad crop {crop} for {H}x{W}")
+    return r0, r1, c0, c1
+
+
+def direct_bf(f, sigma_s, sigma_r, w=None, crop=None):
+    """O1: Eq. (1) by direct summation over the window (in-image neighbours)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    H, W = f.shape
+    w = window(sigma_s) if w is None else int(w)
+    r0, r1, c0, c1 = _crop(crop, H, W)
+    out = np.empty((r1 - r0, c1 - c0), np.float64)
+    _load().bfo_direct(_ptr(f), H, W, float(sigma_s), float(sigma_r), w, r0, r1, c0, c1, _ptr(out))
+    return out
+
+
+def mean(f) -> float:
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    return float(_load().bfo_mean(_ptr(f), f.size))
+
+
+def gp_bf(f, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop=None, round_coef_f32=False):
+    """O2: Algorithm 1 (GPF) in FP64.
+
+    spatial: 'fir' (window sum of Eq. (8), zero extension) or 'iir' (Deriche's
+    recursive Gaussian, causal + anticausal).  t_c: centre (None = image mean,
+    the algorithm's first step).  crop: (r0, r1, c0, c1) output region; the
+    operator still reads every sample it needs from the full image.
+    """
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    H, W = f.shape
+    sp = FIR if spatial == "fir" else IIR
+    w = window(sigma_s) if w is None else int(w)
+    r0, r1, c0, c1 = _crop(crop, H, W)
+    out = np.empty((r1 - r0, c1 - c0), np.float64)
+    tc = float("nan") if t_c is None else float(t_c)
+    rc = _load().bfo_gp(_ptr(f), H, W, float(sigma_s), float(sigma_r), int(N), tc, sp, w,
+                        1 if round_coef_f32 else 0, r0, r1, c0, c1, _ptr(out))
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    return out
+
+
+def line_filter(x, sigma_s, spatial="fir", w=None, round_coef_f32=False):
+    """The 1-D spatial operator applied to each row of x (zero extension)."""
+    x = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
+    count, n = x.shape
+    w = window(sigma_s) if w is None else int(w)
+    y = np.empty_like(x)
+    _load().bfo_line_filter(_ptr(x), count, n, float(sigma_s), FIR if spatial == "fir" else IIR, w,
+                            1 if round_coef_f32 else 0, _ptr(y))
+    return y
+
+
+def deriche_response(sigma_s, n, round_coef_f32=False):
+    """h(d), d = 0..n-1, of the recursive Gaussian at scale sigma_s."""
+    h = np.empty(int(n), np.float64)
+    _load().bfo_deriche_response(float(sigma_s), 1 if round_coef_f32 else 0, int(n), _ptr(h))
+    return h
+
+
+def gp_kernel(t, tau, sigma_r, N):
+    """Eq. (5): degree-N Gauss-polynomial approximation of g_{sigma_r}(t - tau)."""
+    lib = _load()
+    t = np.asarray(t, np.float64)
+    flat = [lib.bfo_gp_kernel(float(v), float(tau), float(sigma_r), int(N)) for v in t.ravel()]
+    return np.array(flat, np.float64).reshape(t.shape)
+
+
+def deriche_coefs(sigma_s, round_coef_f32=False):
+    """(poles[2], residues[2]) as complex numpy arrays."""
+    o = np.empty(8, np.float64)
+    _load().bfo_deriche_coefs(float(sigma_s), 1 if round_coef_f32 else 0, _ptr(o))
+    return o[0:4:2] + 1j * o[1:4:2], o[4:8:2] + 1j * o[5:8:2]

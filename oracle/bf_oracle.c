@@ -1,0 +1,377 @@
+/*
+ * bf_oracle.c -- FP64 CPU oracle for the Gauss-polynomial bilateral filter
+ * (Chaudhury, "Fast and Accurate Bilateral Filtering using Gauss-Polynomial
+ * Decomposition").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the CPU
+ * baseline legs of bench.py load this library.  It shares no code, header,
+ * table or constant generator with the CUDA library; the product path never
+ * calls it.
+ *
+ * Everything here is plain double-precision C with OpenMP over independent
+ * lines or pixels.  No blocking, fusion or reordering beyond what the cited
+ * definitions state.
+ *
+ *   O1  bfo_direct   Eq. (1) with the Gaussian kernels of Eq. (2) on the square
+ *                    window [-w, w]^2 of Sec. 1; neighbours that fall outside
+ *                    the image are skipped (boundary reading: only in-image
+ *                    pixels take part).
+ *   O2  bfo_gp       Algorithm 1 (GPF) in Sec. 3, i.e. Eqs. (7)-(11) with the
+ *                    centring of Sec. 2 (Proposition / Eq. (6)), using either
+ *                      - FIR:  the window sum of Eq. (8), zero extension, or
+ *                      - IIR:  Deriche's recursive Gaussian (cited in Sec. 3)
+ *                              as the sum of a causal and an anticausal
+ *                              recursion on the same input, zero initial
+ *                              state at both line ends.
+ *   line filters     bfo_line_fir / bfo_line_iir: the 1-D spatial operators
+ *                    alone, for pinning them.
+ *   bfo_deriche_response: the recursive filter's impulse response h(d).
+ *
+ * Deriche's 4th-order fit of exp(-x^2/2) (unit sigma) is
+ *   h(x) = (a0 cos(w0 x) + a1 sin(w0 x)) e^{-b0 x} + (c0 cos(w1 x) + c1 sin(w1 x)) e^{-b1 x},  x >= 0,
+ * with the published constants a0 = 1.680, a1 = 3.735, b0 = 1.783, b1 = 1.723,
+ * c0 = -0.6803, c1 = -0.2598, w0 = 0.6318, w1 = 1.997.  At scale sigma, x is
+ * replaced by d/sigma for integer lags d.  Writing each term as the real part
+ * of a complex exponential gives h(d) = Re[A0 p0^d + A1 p1^d] with
+ *   p0 = exp((-b0 + i w0)/sigma), A0 = a0 - i a1,
+ *   p1 = exp((-b1 + i w1)/sigma), A1 = c0 - i c1,
+ * and the symmetric line operator  y[i] = sum_j h(|i - j|) x[j]  over the
+ * in-line samples j is computed by two first-order recursions per pole.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define BFO_FIR 1
+#define BFO_IIR 2
+
+typedef struct {
+    double complex p[2]; /* poles */
+    double complex A[2]; /* residues */
+} deriche_t;
+
+static void deriche_design(double sigma, int round_f32, deriche_t *D)
+{
+    const double a0 = 1.680, a1 = 3.735, b0 = 1.783, b1 = 1.723;
+    const double c0 = -0.6803, c1 = -0.2598, w0 = 0.6318, w1 = 1.997;
+    D->p[0] = cexp((-b0 + I * w0) / sigma);
+    D->p[1] = cexp((-b1 + I * w1) / sigma);
+    D->A[0] = a0 - I * a1;
+    D->A[1] = c0 - I * c1;
+    if (round_f32) {
+        for (int m = 0; m < 2; ++m) {
+            D->p[m] = (double)(float)creal(D->p[m]) + I * (double)(float)cimag(D->p[m]);
+            D->A[m] = (double)(float)creal(D->A[m]) + I * (double)(float)cimag(D->A[m]);
+        }
+    }
+}
+
+/* FIR: y[i] = sum_{d=-w..w} taps[|d|] x[i-d], samples outside [0, n) are zero. */
+static void fir_line(const double *x, long xs, int n, const double *taps, int w,
+                     double *y, long ys)
+{
+    for (int i = 0; i < n; ++i) {
+        double acc = 0.0;
+        for (int d = -w; d <= w; ++d) {
+            int j = i - d;
+            if (j < 0 || j >= n) continue;
+            acc += taps[d < 0 ? -d : d] * x[(long)j * xs];
+        }
+        y[(long)i * ys] = acc;
+    }
+}
+
+/* IIR: causal part  sum_{d>=0} h(d) x[i-d]  and anticausal part
+ * sum_{d>=1} h(d) x[i+d], both with zero state outside the line. */
+static void iir_line(const double *x, long xs, int n, const deriche_t *D,
+                     double *y, long ys)
+{
+    for (int i = 0; i < n; ++i) y[(long)i * ys] = 0.0;
+    for (int m = 0; m < 2; ++m) {
+        double complex z = 0.0;
+        for (int i = 0; i < n; ++i) {
+            z = x[(long)i * xs] + D->p[m] * z;
+            y[(long)i * ys] += creal(D->A[m] * z);
+        }
+        double complex v = 0.0;
+        for (int i = n - 2; i >= 0; --i) {
+            v = D->p[m] * (x[(long)(i + 1) * xs] + v);
+            y[(long)i * ys] += creal(D->A[m] * v);
+        }
+    }
+}
+
+static void make_taps(double sigma_s, int w, double *taps)
+{
+    for (int d = 0; d <= w; ++d) taps[d] = exp(-(double)d * d / (2.0 * sigma_s * sigma_s));
+}
+
+int bfo_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void bfo_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/* Impulse response of the recursive filter: h[d] for d = 0..n-1. */
+void bfo_deriche_response(double sigma, int round_f32, int n, double *h)
+{
+    deriche_t D;
+    deriche_design(sigma, round_f32, &D);
+    for (int d = 0; d < n; ++d) {
+        double acc = 0.0;
+        for (int m = 0; m < 2; ++m) acc += creal(D.A[m] * cpow(D.p[m], (double)d));
+        h[d] = acc;
+    }
+}
+
+/* Poles and residues as (re, im) pairs: out[0..3] = p0, p1; out[4..7] = A0, A1. */
+void bfo_deriche_coefs(double sigma, int round_f32, double *out)
+{
+    deriche_t D;
+    deriche_design(sigma, round_f32, &D);
+    for (int m = 0; m < 2; ++m) {
+        out[2 * m] = creal(D.p[m]);
+        out[2 * m + 1] = cimag(D.p[m]);
+        out[4 + 2 * m] = creal(D.A[m]);
+        out[4 + 2 * m + 1] = cimag(D.A[m]);
+    }
+}
+
+/* 1-D spatial operator on `count` independent lines of length n (row-major). */
+void bfo_line_filter(const double *x, int count, int n, double sigma_s, int spatial,
+                     int w, int round_f32, double *y)
+{
+    if (spatial == BFO_FIR) {
+        double *taps = malloc(sizeof(double) * (size_t)(w + 1));
+        make_taps(sigma_s, w, taps);
+#pragma omp parallel for schedule(static)
+        for (int l = 0; l < count; ++l) fir_line(x + (long)l * n, 1, n, taps, w, y + (long)l * n, 1);
+        free(taps);
+    } else {
+        deriche_t D;
+        deriche_design(sigma_s, round_f32, &D);
+#pragma omp parallel for schedule(static)
+        for (int l = 0; l < count; ++l) iir_line(x + (long)l * n, 1, n, &D, y + (long)l * n, 1);
+    }
+}
+
+/*
+ * O1 -- direct evaluation of Eq. (1).  Output for the crop rows [r0, r1) and
+ * columns [c0, c1) of the H x W image f (row-major, FP64), written densely to
+ * out[(r1-r0) x (c1-c0)].  sigma_r = +inf gives the plain normalised spatial
+ * filter (range kernel identically one).
+ */
+void bfo_direct(const double *f, int H, int W, double sigma_s, double sigma_r, int w,
+                int r0, int r1, int c0, int c1, double *out)
+{
+    const int cw = c1 - c0;
+    const double inv2s2 = 1.0 / (2.0 * sigma_s * sigma_s);
+    const double inv2r2 = isinf(sigma_r) ? 0.0 : 1.0 / (2.0 * sigma_r * sigma_r);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int y = r0; y < r1; ++y) {
+        for (int x = c0; x < c1; ++x) {
+            const double tau = f[(long)y * W + x];
+            double num = 0.0, den = 0.0;
+            for (int dy = -w; dy <= w; ++dy) {
+                const int yy = y - dy;
+                if (yy < 0 || yy >= H) continue;
+                for (int dx = -w; dx <= w; ++dx) {
+                    const int xx = x - dx;
+                    if (xx < 0 || xx >= W) continue;
+                    const double t = f[(long)yy * W + xx];
+                    const double gs = exp(-(double)(dx * dx + dy * dy) * inv2s2);
+                    const double gr = exp(-(t - tau) * (t - tau) * inv2r2);
+                    num += gs * gr * t;
+                    den += gs * gr;
+                }
+            }
+            out[(long)(y - r0) * cw + (x - c0)] = num / den;
+        }
+    }
+}
+
+double bfo_mean(const double *f, long n)
+{
+    double s = 0.0;
+    for (long i = 0; i < n; ++i) s += f[i];
+    return s / (double)n;
+}
+
+/*
+ * Separable spatial operator S applied to the image a, which holds the rows
+ * [ylo, yhi) of a W-wide image (row y at a + (y - ylo) * W), evaluated on the crop
+ * rows [r0, r1) x columns [c0, c1) into out (dense crop layout).  The row
+ * pass filters whole rows; the column pass filters, for each crop column, the
+ * rows [ylo, yhi) of the row-filtered image.  For IIR the caller passes
+ * ylo = 0, yhi = H so every column is filtered over its full length.
+ */
+typedef struct {
+    int spatial, w;
+    const double *taps;
+    const deriche_t *D;
+} spatial_op;
+
+static void apply_S(const spatial_op *S, const double *a, int W, int ylo, int yhi,
+                    int r0, int r1, int c0, int c1, double *rowtmp, double *out)
+{
+    const int cw = c1 - c0;
+    const int nr = yhi - ylo;
+    /* rows: rowtmp[(y - ylo) * cw + (x - c0)] holds the row-filtered image on the crop columns */
+#pragma omp parallel
+    {
+        double *line = malloc(sizeof(double) * (size_t)W);
+#pragma omp for schedule(static)
+        for (int y = ylo; y < yhi; ++y) {
+            const double *src = a + (long)(y - ylo) * W;
+            if (S->spatial == BFO_FIR) fir_line(src, 1, W, S->taps, S->w, line, 1);
+            else iir_line(src, 1, W, S->D, line, 1);
+            memcpy(rowtmp + (long)(y - ylo) * cw, line + c0, sizeof(double) * (size_t)cw);
+        }
+        free(line);
+    }
+    /* columns */
+#pragma omp parallel
+    {
+        double *col = malloc(sizeof(double) * (size_t)nr);
+#pragma omp for schedule(static)
+        for (int x = 0; x < cw; ++x) {
+            if (S->spatial == BFO_FIR) fir_line(rowtmp + x, cw, nr, S->taps, S->w, col, 1);
+            else iir_line(rowtmp + x, cw, nr, S->D, col, 1);
+            for (int y = r0; y < r1; ++y) out[(long)(y - r0) * cw + x] = col[y - ylo];
+        }
+        free(col);
+    }
+}
+
+/*
+ * O2 -- Algorithm 1 (GPF).  f is the full H x W image; the result is produced
+ * on the crop [r0, r1) x [c0, c1).  t_c: the centre of Sec. 2 (NaN selects the
+ * image mean of the algorithm's first step).  spatial: BFO_FIR (window w) or
+ * BFO_IIR.  round_f32 rounds the recursive filter's poles and residues to
+ * single precision before use (the values a single-precision implementation
+ * holds).  Returns 0 on success, -1 on allocation failure.
+ *
+ * sigma_r = +inf is taken as its limit: every G_n, n >= 1, vanishes and the
+ * result is S(h)/S(1) + t_c, the normalised spatial filter.  A pixel whose
+ * denominator Q is not positive (possible only for odd N, where the truncated
+ * exponential has a real root) is returned as NaN.
+ */
+int bfo_gp(const double *f, int H, int W, double sigma_s, double sigma_r, int N,
+           double t_c, int spatial, int w, int round_f32,
+           int r0, int r1, int c0, int c1, double *out)
+{
+    const int cw = c1 - c0, ch = r1 - r0;
+    const long ncrop = (long)cw * ch;
+    int ylo = 0, yhi = H;
+    if (spatial == BFO_FIR) {
+        ylo = r0 - w < 0 ? 0 : r0 - w;
+        yhi = r1 + w > H ? H : r1 + w;
+    }
+    const long nreg = (long)(yhi - ylo) * W;
+
+    double *taps = NULL;
+    deriche_t D;
+    spatial_op S = {spatial, w, NULL, NULL};
+    if (spatial == BFO_FIR) {
+        taps = malloc(sizeof(double) * (size_t)(w + 1));
+        if (!taps) return -1;
+        make_taps(sigma_s, w, taps);
+        S.taps = taps;
+    } else {
+        deriche_design(sigma_s, round_f32, &D);
+        S.D = &D;
+    }
+
+    /* F and Hs live on the full-width rows [ylo, yhi) (offset so that row y is at (y - ylo) * W) */
+    double *F = malloc(sizeof(double) * (size_t)nreg);
+    double *Hs = malloc(sizeof(double) * (size_t)nreg);
+    double *rowtmp = malloc(sizeof(double) * (size_t)((long)(yhi - ylo) * cw));
+    double *Fbar = malloc(sizeof(double) * (size_t)ncrop);
+    double *G = malloc(sizeof(double) * (size_t)ncrop);
+    double *Hc = malloc(sizeof(double) * (size_t)ncrop);
+    double *P = calloc((size_t)ncrop, sizeof(double));
+    double *Q = calloc((size_t)ncrop, sizeof(double));
+    if (!F || !Hs || !rowtmp || !Fbar || !G || !Hc || !P || !Q) {
+        free(F); free(Hs); free(rowtmp); free(Fbar); free(G); free(Hc); free(P); free(Q); free(taps);
+        return -1;
+    }
+
+    /* step 1: centre */
+    if (isnan(t_c)) t_c = bfo_mean(f, (long)H * W);
+
+    if (isinf(sigma_r)) {
+        /* limit sigma_r -> inf: numerator S(h), denominator S(1) */
+        for (long i = 0; i < nreg; ++i) { F[i] = f[(long)ylo * W + i] - t_c; Hs[i] = 1.0; }
+        apply_S(&S, F, W, ylo, yhi, r0, r1, c0, c1, rowtmp, P);
+        apply_S(&S, Hs, W, ylo, yhi, r0, r1, c0, c1, rowtmp, Q);
+        for (long i = 0; i < ncrop; ++i) out[i] = P[i] / Q[i] + t_c;
+        goto done;
+    }
+
+    /* steps 2, 4, 7 on the rows the operator reads; steps 3, 5, 6 on the crop */
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < nreg; ++i) {
+        const double h = f[(long)ylo * W + i] - t_c;
+        F[i] = exp(-h * h / (2.0 * sigma_r * sigma_r));
+        Hs[i] = h / sigma_r;
+    }
+    for (int y = r0; y < r1; ++y)
+        for (int x = c0; x < c1; ++x) {
+            const long k = (long)(y - r0) * cw + (x - c0);
+            Hc[k] = (f[(long)y * W + x] - t_c) / sigma_r;
+            G[k] = 1.0;
+        }
+    /* step 8: filtered F_0 */
+    apply_S(&S, F, W, ylo, yhi, r0, r1, c0, c1, rowtmp, Fbar);
+    double c = 1.0; /* 1/n! */
+    for (int n = 0; n <= N; ++n) {
+        /* Eq. (10): Q += G_n Fbar_n / n! */
+        for (long i = 0; i < ncrop; ++i) Q[i] += c * G[i] * Fbar[i];
+        /* F_{n+1} = H F_n, then Fbar_{n+1} */
+#pragma omp parallel for schedule(static)
+        for (long i = 0; i < nreg; ++i) F[i] *= Hs[i];
+        apply_S(&S, F, W, ylo, yhi, r0, r1, c0, c1, rowtmp, Fbar);
+        /* Eq. (9) without the sigma_r factor: P += G_n Fbar_{n+1} / n! */
+        for (long i = 0; i < ncrop; ++i) P[i] += c * G[i] * Fbar[i];
+        for (long i = 0; i < ncrop; ++i) G[i] *= Hc[i];
+        c /= (double)(n + 1);
+    }
+    /* step 18: Eq. (11) with the sigma_r of Eq. (9), then undo the centring (Eq. (6)) */
+    for (long i = 0; i < ncrop; ++i) out[i] = Q[i] > 0.0 ? sigma_r * (P[i] / Q[i]) + t_c : NAN;
+
+done:
+    free(F); free(Hs); free(rowtmp); free(Fbar); free(G); free(Hc); free(P); free(Q); free(taps);
+    return 0;
+}
+
+/*
+ * Eq. (5): the Gauss-polynomial of degree N that replaces the translated range
+ * kernel g_{sigma_r}(t - tau) of Eq. (3): the two Gaussian factors times the
+ * first N + 1 Taylor terms of exp(tau t / sigma_r^2) (Eq. (4)).
+ */
+double bfo_gp_kernel(double t, double tau, double sigma_r, int N)
+{
+    const double x = tau * t / (sigma_r * sigma_r);
+    double term = 1.0, sum = 0.0;
+    for (int n = 0; n <= N; ++n) {
+        sum += term;
+        term *= x / (double)(n + 1);
+    }
+    return exp(-tau * tau / (2.0 * sigma_r * sigma_r)) * exp(-t * t / (2.0 * sigma_r * sigma_r)) * sum;
+}

@@ -1,0 +1,336 @@
+"""Pins for the FP64 oracle (CPU only, no GPU).
+
+Every test checks the oracle against something other than its own code:
+brute force on tiny images, closed forms, library routines (scipy), exact
+invariants stated or implied by the paper, the Taylor-remainder bound of
+Eq. (4), and the numbers the paper prints (tests/golden/paper_values.json).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.ndimage import correlate1d
+
+import oracle
+import synthetic
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+# Deriche's published 4th-order constants, restated here in his real (cos/sin)
+# form so the oracle's complex-pole form is checked against an independent
+# evaluation.
+_DERICHE = dict(a0=1.680, a1=3.735, b0=1.783, b1=1.723, c0=-0.6803, c1=-0.2598, w0=0.6318, w1=1.997)
+
+
+def deriche_real(d, sigma):
+    k = _DERICHE
+    x = np.abs(np.asarray(d, np.float64)) / sigma
+    return ((k["a0"] * np.cos(k["w0"] * x) + k["a1"] * np.sin(k["w0"] * x)) * np.exp(-k["b0"] * x)
+            + (k["c0"] * np.cos(k["w1"] * x) + k["c1"] * np.sin(k["w1"] * x)) * np.exp(-k["b1"] * x))
+
+
+def brute_bf(f, spatial_weight, sigma_r, w):
+    """Literal Eq. (1): four nested loops, in-image neighbours only."""
+    H, W = f.shape
+    out = np.empty((H, W))
+    for y in range(H):
+        for x in range(W):
+            num = den = 0.0
+            for dy in range(-w, w + 1):
+                for dx in range(-w, w + 1):
+                    yy, xx = y - dy, x - dx
+                    if 0 <= yy < H and 0 <= xx < W:
+                        t = float(f[yy, xx])
+                        rng = 1.0 if math.isinf(sigma_r) else math.exp(-(t - f[y, x]) ** 2 / (2 * sigma_r ** 2))
+                        g = spatial_weight(dx, dy) * rng
+                        num += g * t
+                        den += g
+            out[y, x] = num / den
+    return out
+
+
+def small_image(H, W, seed, n_rect=6, noise=10.0, ramp=0.0):
+    return synthetic.make_image(H, W, n_rect, noise, ramp, seed).astype(np.float64)
+
+
+def gauss_filter_scipy(a, sigma_s, w):
+    taps = np.exp(-np.arange(-w, w + 1) ** 2 / (2.0 * sigma_s ** 2))
+    return correlate1d(correlate1d(a, taps, axis=1, mode="constant"), taps, axis=0, mode="constant")
+
+
+# ------------------------------------------------------------------ O1 direct
+
+
+@pytest.mark.parametrize("ss,sr", [(1.0, 20.0), (1.5, 40.0), (2.0, 10.0)])
+def test_direct_matches_brute_force(ss, sr):
+    f = small_image(11, 9, 11, n_rect=4)
+    w = oracle.window(ss)
+    ref = brute_bf(f, lambda dx, dy: math.exp(-(dx * dx + dy * dy) / (2 * ss * ss)), sr, w)
+    np.testing.assert_allclose(oracle.direct_bf(f, ss, sr), ref, rtol=0, atol=1e-11)
+
+
+def test_direct_crop_is_slice():
+    f = small_image(30, 26, 12)
+    full = oracle.direct_bf(f, 2.0, 25.0)
+    np.testing.assert_array_equal(oracle.direct_bf(f, 2.0, 25.0, crop=(5, 17, 3, 20)), full[5:17, 3:20])
+
+
+def test_direct_shift_equivariance_prop_2_1():
+    """Proposition (Eq. (6)): f_BF(i) = h_BF(i) + t_c for h = f - t_c."""
+    f = small_image(24, 20, 13)
+    tc = 97.25
+    np.testing.assert_allclose(oracle.direct_bf(f - tc, 2.0, 30.0) + tc, oracle.direct_bf(f, 2.0, 30.0),
+                               rtol=0, atol=1e-10)
+
+
+def test_window_rule():
+    """W = 3 sigma_s (Sec. 1), rounded up for non-integer sigma_s."""
+    assert oracle.window(3.0) == 9
+    assert oracle.window(10.0) == 30
+    assert oracle.window(1.2) == 4
+
+
+# --------------------------------------------------------- spatial operators
+
+
+@pytest.mark.parametrize("sigma", [1.5, 3.0, 10.0, 25.0])
+def test_deriche_impulse_response(sigma):
+    d = np.arange(0, int(6 * sigma) + 1)
+    h = oracle.deriche_response(sigma, len(d))
+    # complex-pole form equals Deriche's real form
+    np.testing.assert_allclose(h, deriche_real(d, sigma), rtol=0, atol=1e-12)
+    # the published fit approximates exp(-d^2 / 2 sigma^2) to about 5e-4 of the peak
+    assert np.abs(h - np.exp(-d ** 2 / (2.0 * sigma ** 2))).max() < 6e-4
+
+
+@pytest.mark.parametrize("sigma,n", [(2.0, 17), (5.0, 40), (12.0, 64)])
+def test_iir_line_operator_is_symmetric_toeplitz(sigma, n):
+    """Causal + anticausal recursions with zero state = the matrix h(|i - j|)."""
+    M = oracle.line_filter(np.eye(n), sigma, "iir")  # row l = S e_l
+    i = np.arange(n)
+    ref = deriche_real(i[:, None] - i[None, :], sigma)
+    np.testing.assert_allclose(M, ref, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("sigma", [1.0, 3.0, 4.5])
+def test_fir_line_matches_scipy(sigma):
+    x = np.random.default_rng(5).normal(size=(3, 50))
+    w = oracle.window(sigma)
+    taps = np.exp(-np.arange(-w, w + 1) ** 2 / (2.0 * sigma ** 2))
+    np.testing.assert_allclose(oracle.line_filter(x, sigma, "fir"), correlate1d(x, taps, axis=1, mode="constant"),
+                               rtol=0, atol=1e-12)
+
+
+# ----------------------------------------------------------------- O2 GPF
+
+
+@pytest.mark.parametrize("sr,N", [(30.0, 60), (50.0, 40)])
+def test_gp_fir_converges_to_direct(sr, N):
+    """With enough terms the Taylor series of Eq. (4) is exact, so Algorithm 1
+    with the window sum of Eq. (8) reproduces Eq. (1)."""
+    f = small_image(40, 36, 21, n_rect=8)
+    np.testing.assert_allclose(oracle.gp_bf(f, 2.0, sr, N, "fir"), oracle.direct_bf(f, 2.0, sr), rtol=0, atol=1e-9)
+
+
+def test_gp_iir_converges_to_brute_force_with_recursive_kernel():
+    """Algorithm 1 with the recursive Gaussian = Eq. (1) with the spatial kernel
+    h(|dx|) h(|dy|) over the whole image (brute force, Deriche's real form)."""
+    f = small_image(12, 10, 22, n_rect=4)
+    sigma = 2.5
+    ref = brute_bf(f, lambda dx, dy: float(deriche_real(dx, sigma) * deriche_real(dy, sigma)), 40.0, 12)
+    np.testing.assert_allclose(oracle.gp_bf(f, sigma, 40.0, 50, "iir"), ref, rtol=0, atol=1e-9)
+
+
+def test_gp_equals_explicit_eqs_7_to_11():
+    """Algorithm 1's recursive powers and factorials equal Eqs. (7)-(11) written
+    out with explicit powers, factorials and scipy's separable filter."""
+    f = small_image(32, 28, 23, n_rect=6)
+    ss, sr, N = 2.0, 30.0, 12
+    w = oracle.window(ss)
+    tc = f.mean()
+    h = f - tc
+    G = lambda n: (h / sr) ** n                                  # Eq. (7)
+    F = lambda n: np.exp(-h ** 2 / (2 * sr ** 2)) * G(n)          # Eq. (7)
+    Fb = [gauss_filter_scipy(F(n), ss, w) for n in range(N + 2)]  # Eq. (8)
+    P = sr * sum(G(n) * Fb[n + 1] / math.factorial(n) for n in range(N + 1))  # Eq. (9)
+    Q = sum(G(n) * Fb[n] / math.factorial(n) for n in range(N + 1))           # Eq. (10)
+    ref = P / Q + tc                                              # Eq. (11) + Eq. (6)
+    np.testing.assert_allclose(oracle.gp_bf(f, ss, sr, N, "fir"), ref, rtol=0, atol=1e-10)
+
+
+def _remainder_bound(f, ss, sr, N, w, tc):
+    """Per-pixel bound on |GPF - Eq. (1)| from the Lagrange remainder of Eq. (4):
+    |exp(x) - T_N(x)| <= |x|^{N+1} / (N+1)! * exp(max(x, 0))."""
+    H, W = f.shape
+    h = f - tc
+    bound = np.empty((H, W))
+    for y in range(H):
+        for x in range(W):
+            y0, y1 = max(0, y - w), min(H, y + w + 1)
+            x0, x1 = max(0, x - w), min(W, x + w + 1)
+            t = h[y0:y1, x0:x1]
+            tau = h[y, x]
+            dy = np.arange(y0, y1)[:, None] - y
+            dx = np.arange(x0, x1)[None, :] - x
+            gs = np.exp(-(dx ** 2 + dy ** 2) / (2 * ss ** 2))
+            xx = tau * t / sr ** 2
+            e = np.exp(-(tau ** 2 + t ** 2) / (2 * sr ** 2)) * np.abs(xx) ** (N + 1) / math.factorial(N + 1) \
+                * np.exp(np.maximum(xx, 0))
+            g = np.exp(-(t - tau) ** 2 / (2 * sr ** 2))
+            D = (gs * g).sum()
+            Nn = (gs * g * t).sum()
+            eD = (gs * e).sum()
+            eN = (gs * e * np.abs(t)).sum()
+            bound[y, x] = (eN + abs(Nn / D) * eD) / (D - eD) if D > eD else np.inf
+    return bound
+
+
+@pytest.mark.parametrize("sr,N", [(50.0, 6), (50.0, 10), (35.0, 14), (30.0, 20)])
+def test_gp_error_within_taylor_remainder_bound(sr, N):
+    f = small_image(20, 18, 24, n_rect=5)
+    ss, w = 2.0, oracle.window(2.0)
+    tc = f.mean()
+    err = np.abs(oracle.gp_bf(f, ss, sr, N, "fir") - oracle.direct_bf(f, ss, sr))
+    bound = _remainder_bound(f, ss, sr, N, w, tc)
+    assert np.all(err <= bound * (1 + 1e-9) + 1e-10)
+    assert err.max() > 0  # the truncation is visible at these orders
+
+
+def test_constant_image_is_unchanged():
+    c = 77.25
+    f = np.full((32, 32), c)
+    for sp in ("fir", "iir"):
+        assert np.all(oracle.gp_bf(f, 3.0, 30.0, 20, sp) == c)
+    np.testing.assert_allclose(oracle.direct_bf(f, 3.0, 30.0), c, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("sp", ["fir", "iir"])
+def test_sigma_r_infinite_is_normalised_gaussian(sp):
+    """sigma_r -> inf: the range kernel is 1 and Eq. (1) is the normalised spatial filter."""
+    f = small_image(26, 22, 25)
+    ss = 2.0
+    w = oracle.window(ss)
+    if sp == "fir":
+        ref = gauss_filter_scipy(f, ss, w) / gauss_filter_scipy(np.ones_like(f), ss, w)
+        np.testing.assert_allclose(oracle.direct_bf(f, ss, math.inf), ref, rtol=0, atol=1e-10)
+    else:
+        Srow = lambda a: oracle.line_filter(a, ss, "iir")
+        S = lambda a: Srow(Srow(a).T).T
+        ref = S(f) / S(np.ones_like(f))
+    np.testing.assert_allclose(oracle.gp_bf(f, ss, math.inf, 20, sp), ref, rtol=0, atol=1e-10)
+    # finite but huge sigma_r approaches the limit at rate O((R / sigma_r)^2 R)
+    np.testing.assert_allclose(oracle.gp_bf(f, ss, 1e6, 20, sp), ref, rtol=0, atol=1e-5)
+
+
+@pytest.mark.parametrize("sp", ["fir", "iir"])
+def test_negation_symmetry(sp):
+    f = small_image(30, 24, 26)
+    np.testing.assert_allclose(oracle.gp_bf(-f, 3.0, 30.0, 20, sp), -oracle.gp_bf(f, 3.0, 30.0, 20, sp),
+                               rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("sp", ["fir", "iir"])
+def test_affine_equivariance(sp):
+    """GP with sigma_r scaled by a on a f + b equals a GP(f) + b."""
+    f = small_image(30, 24, 27)
+    a, b = 2.0, 10.0
+    np.testing.assert_allclose(oracle.gp_bf(a * f + b, 3.0, a * 30.0, 20, sp), a * oracle.gp_bf(f, 3.0, 30.0, 20, sp) + b,
+                               rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("sp", ["fir", "iir"])
+def test_transpose_equivariance(sp):
+    f = small_image(30, 22, 28)
+    np.testing.assert_allclose(oracle.gp_bf(f.T.copy(), 2.5, 25.0, 20, sp), oracle.gp_bf(f, 2.5, 25.0, 20, sp).T,
+                               rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("sr", [15.0, 30.0, 60.0])
+def test_even_order_stays_within_local_min_max(sr):
+    """Even N: the truncated exponential is positive, so every weight is positive
+    and the output is a convex combination of the window's intensities."""
+    f = small_image(40, 40, 29, n_rect=8)
+    ss = 2.0
+    w = oracle.window(ss)
+    y = oracle.gp_bf(f, ss, sr, 20, "fir")
+    from scipy.ndimage import maximum_filter, minimum_filter
+    lo = minimum_filter(f, size=2 * w + 1, mode="nearest")
+    hi = maximum_filter(f, size=2 * w + 1, mode="nearest")
+    assert np.all(y >= lo - 1e-9) and np.all(y <= hi + 1e-9)
+
+
+@pytest.mark.parametrize("sr", [30.0, 50.0])
+def test_error_decreases_with_even_order(sr):
+    f = synthetic.make_image(48, 48, 8, 10.0, 0.0, synthetic.seed_for(1, 77)).astype(np.float64)
+    ref = oracle.direct_bf(f, 3.0, sr)
+    mse = [np.mean((oracle.gp_bf(f, 3.0, sr, N, "fir") - ref) ** 2) for N in range(4, 42, 2)]
+    assert all(b <= a for a, b in zip(mse, mse[1:])), mse
+
+
+@pytest.mark.parametrize("sp", ["fir", "iir"])
+def test_crop_equals_full_slice(sp):
+    f = small_image(48, 40, 30)
+    full = oracle.gp_bf(f, 3.0, 25.0, 20, sp)
+    tc = f.mean()
+    part = oracle.gp_bf(f, 3.0, 25.0, 20, sp, t_c=tc, crop=(9, 31, 4, 27))
+    np.testing.assert_allclose(part, full[9:31, 4:27], rtol=0, atol=1e-10)
+
+
+def test_odd_order_can_give_non_positive_denominator():
+    """Odd N: the truncated exponential has a real root; pixels whose Q <= 0 are NaN."""
+    f = np.zeros((16, 16))
+    f[:, 8] = 255.0  # a thin bright line: its pixels see mostly negative weights
+    y = oracle.gp_bf(f, 3.0, 20.0, 5, "fir")
+    assert np.isnan(y[:, 8]).all() and not np.isnan(np.delete(y, 8, axis=1)).any()
+    assert not np.isnan(oracle.gp_bf(f, 3.0, 20.0, 6, "fir")).any()
+
+
+# ------------------------------------------------------- Eq. (5) and Fig. 1-3
+
+
+def test_fig1_scale_factor():
+    g = GOLDEN["fig1_scale_factor"]
+    tau, sr = g["tau"], g["sigma_r"]
+    # at t = 0 the Gauss-polynomial is exactly the scale factor exp(-tau^2 / 2 sigma_r^2)
+    v = float(oracle.gp_kernel(np.array([0.0]), tau, sr, 20)[0])
+    assert float(f"{v:.{g['printed_digits']}g}") == g["printed"]
+    # and the decomposition of Eq. (3) is exact once the series has converged
+    t = np.linspace(0.0, 255.0, 256)
+    np.testing.assert_allclose(oracle.gp_kernel(t, tau, sr, 90), np.exp(-(t - tau) ** 2 / (2 * sr ** 2)),
+                               rtol=0, atol=1e-12)
+
+
+def test_tau_zero_needs_no_approximation():
+    """Sec. 2: for tau = 0 the exponential factor is 1, so any degree is exact."""
+    t = np.linspace(-255.0, 255.0, 101)
+    for N in (0, 1, 5, 20):
+        np.testing.assert_allclose(oracle.gp_kernel(t, 0.0, 30.0, N), np.exp(-t ** 2 / 1800.0), rtol=1e-15, atol=0)
+
+
+def test_centring_reduces_kernel_error():
+    """Sec. 2 / Fig. 3: degree 20 at sigma_r 30.  Over [0, 255] with tau in
+    {0, 10, 50, 120} (Fig. 3(a)) the worst error is far larger than over the
+    centred interval [-127.5, 127.5] with tau in {-100, -50, 0, 10, 50, 100}
+    (Fig. 3(b)); centring shrinks max |tau| (e.g. 255 -> 155 at t_c = 100)."""
+    g = GOLDEN["centring_example"]
+    L, U, tc = g["L"], g["U"], g["t_c"]
+    assert max(abs(L - tc), abs(U - tc)) == g["max_abs_tau_after"]
+    assert max(abs(L), abs(U)) == g["max_abs_tau_before"]
+
+    def worst(t, taus):
+        return max(np.abs(oracle.gp_kernel(t, tau, 30.0, 20) - np.exp(-(t - tau) ** 2 / 1800.0)).max() for tau in taus)
+
+    raw = worst(np.linspace(0.0, 255.0, 256), (0.0, 10.0, 50.0, 120.0))
+    centred = worst(np.linspace(-127.5, 127.5, 256), (-100.0, -50.0, 0.0, 10.0, 50.0, 100.0))
+    assert centred < 0.5 * raw
+    # and for a fixed centre, the worst error shrinks as max |tau| shrinks
+    assert worst(np.linspace(-tc, U - tc, 256), (-tc, U - tc)) < worst(np.linspace(L, U, 256), (L, U))
+
+
+def test_error_grows_with_abs_tau():
+    """Sec. 2 / Fig. 3(a): for fixed degree the error grows with |tau|."""
+    t = np.linspace(0.0, 255.0, 256)
+    errs = [np.abs(oracle.gp_kernel(t, tau, 30.0, 20) - np.exp(-(t - tau) ** 2 / 1800.0)).max() for tau in (0, 10, 50, 120)]
+    assert errs[0] < 1e-15 and errs[1] < errs[2] < errs[3]
