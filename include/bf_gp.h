@@ -1,0 +1,182 @@
+/*
+ * bf_gp.h -- C ABI of the GB300 (sm_103a) Gauss-polynomial bilateral filter.
+ *
+ * Method: K. N. Chaudhury, "Fast and Accurate Bilateral Filtering using
+ * Gauss-Polynomial Decomposition".  The Gaussian bilateral filter of Eq. (1)
+ * (kernels of Eq. (2)) is approximated by replacing the translated range
+ * kernel with its Gauss-polynomial of degree N (Eqs. (3)-(5)).  The filter
+ * then becomes K = N + 2 spatial Gaussian filterings of the auxiliary images
+ * of Eq. (7) (Eq. (8)), a per-pixel combine (Eqs. (9)-(10)) and a division
+ * (Eq. (11)), after centring the intensities at t_c (Sec. 2, Eq. (6)).
+ * Algorithm 1 lists the steps.
+ *
+ * Implementation form (mathematically identical to Eqs. (7)-(11)): with
+ * h = f - t_c, R = max |h|, u = h / R in [-1, 1], s^2 = (R / sigma_r)^2,
+ * E = exp(-s^2 u^2 / 2) and channels Phi_k = E u^k (k = 0..N+1),
+ *     Q = sum_{n=0..N} (s^2 u)^n / n! * S Phi_n,
+ *     P = sum_{n=0..N} (s^2 u)^n / n! * S Phi_{n+1},
+ *     y = t_c + R * P / Q,
+ * where S is the separable spatial Gaussian (truncated FIR on the window
+ * [-w, w], w = ceil(3 sigma_s) by default (Sec. 1), or Deriche's recursive
+ * Gaussian named in Sec. 3), each applied with zero extension at the image
+ * border.  Everything on the device runs in FP32; FP64 is used only for the
+ * expansion coefficients, the centre/scale and the filter coefficients.
+ *
+ * Conventions for every entry point below:
+ *  - Pointers marked "device" must point to device memory of the current
+ *    CUDA device; "host" pointers to host memory.  The caller owns every
+ *    buffer; the library never allocates device memory.
+ *  - Images are FP32, `planes` planes of H rows x W columns, row-major.
+ *    Row r of plane c starts at  base + (c * H + r) * pitch  (elements), so
+ *    planes are stacked with stride H * pitch; pitch >= W.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  All
+ *    device work is enqueued asynchronously on it; the call returns after
+ *    enqueueing.  Argument errors are detected on the host before anything
+ *    is enqueued and returned synchronously.
+ *  - The workspace `ws` (device, 256-byte aligned, size from
+ *    bf_gp_workspace_size) is scratch owned by the caller.  It must not be
+ *    used by two calls that run concurrently.  It also carries the device
+ *    status word of the last call (bf_gp_get_device_status).
+ *  - No entry point synchronises the device unless it says so.
+ */
+#ifndef BF_GP_H
+#define BF_GP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BF_OK = 0,
+    BF_ERR_INVALID_ARG = 1,  /* null pointer, bad size, sigma or order */
+    BF_ERR_WORKSPACE = 2,    /* workspace too small or misaligned */
+    BF_ERR_CUDA = 3,         /* a CUDA runtime call failed (see bf_gp_last_cuda_error) */
+    BF_ERR_UNSUPPORTED = 4,  /* valid request outside what the kernels cover (e.g. a line too long) */
+    BF_ERR_TIMEOUT = 5       /* a bounded device wait gave up (see the device status bits) */
+} bf_status;
+
+/* Bits of the device status word, set by the kernels of the last call. */
+#define BF_DEV_NONPOS_Q 0x1u      /* some pixel had Q <= 0 (only possible for odd N); it was set to NaN */
+#define BF_DEV_NONFINITE_IN 0x2u  /* the input held NaN/Inf; the plane was passed through unchanged */
+#define BF_DEV_RANGE 0x4u         /* (R/sigma_r)^2 / 2 > 80: exp(-s^2 u^2 / 2) underflows FP32 */
+#define BF_DEV_TIMEOUT 0x8u       /* a bounded inter-block wait gave up */
+
+typedef enum {
+    BF_SPATIAL_AUTO = 0, /* FIR for w <= 12, recursive otherwise */
+    BF_SPATIAL_FIR = 1,  /* window sum of Eq. (8), taps exp(-d^2 / 2 sigma_s^2), |d| <= w */
+    BF_SPATIAL_IIR = 2   /* Deriche's 4th-order recursive Gaussian, causal + anticausal */
+} bf_spatial;
+
+typedef enum {
+    BF_CENTRE_MEAN = 0,  /* t_c = mean of the plane (Algorithm 1, first step) */
+    BF_CENTRE_GIVEN = 1  /* t_c = opts.t_c for every plane */
+} bf_centre;
+
+typedef struct {
+    int order;          /* N >= 0, N <= 62 (K = N + 2 channels).  The paper uses N = 20 (Sec. 4). */
+    int spatial;        /* bf_spatial */
+    int centre;         /* bf_centre */
+    int fir_halfwidth;  /* w for FIR; 0 selects ceil(3 sigma_s) (Sec. 1) */
+    double t_c;         /* centre when centre == BF_CENTRE_GIVEN */
+    int reserved[8];    /* must be zero */
+} bf_gp_opts;
+
+/* Fill *opts with the defaults: N = 20, AUTO spatial operator, mean centre. */
+void bf_gp_default_opts(bf_gp_opts *opts);
+
+/* Human-readable name of a status code (static string). */
+const char *bf_status_string(bf_status s);
+
+/* Text of the last CUDA error seen by this thread's calls (static buffer). */
+const char *bf_gp_last_cuda_error(void);
+
+/* Library version, e.g. 100 for 0.1.0. */
+int bf_gp_version(void);
+
+/*
+ * Workspace bytes a forward call on `planes` planes of H x W needs with these
+ * options (sigma_s matters only for the spatial-operator choice; pass the
+ * value you will use).  Returns BF_ERR_INVALID_ARG for bad sizes.
+ */
+bf_status bf_gp_workspace_size(int planes, int H, int W, float sigma_s, const bf_gp_opts *opts,
+                               size_t *bytes);
+
+/*
+ * Forward filter (Algorithm 1 / Eqs. (7)-(11)).
+ *   f     device, input,  planes x H x W at `pitch` (elements)
+ *   y     device, output, same layout and pitch; may not alias f
+ *   sigma_s > 0 (finite), sigma_r > 0 (+inf allowed: plain normalised Gaussian)
+ *   opts  may be NULL (defaults)
+ * Each plane is filtered independently with its own centre t_c and scale R.
+ * A constant plane (R = 0) is copied.  A plane holding NaN/Inf is copied and
+ * BF_DEV_NONFINITE_IN is raised.
+ */
+bf_status bf_gp_forward(const float *f, float *y, int planes, int H, int W, int pitch,
+                        float sigma_s, float sigma_r, const bf_gp_opts *opts,
+                        void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * The three phases of bf_gp_forward as separate calls, for per-kernel timing
+ * and for testing each half of the separable filter.  Same arguments as
+ * bf_gp_forward; calling stats, rows and cols in this order on one stream
+ * with one workspace is exactly bf_gp_forward.
+ *   stats: Algorithm 1 step 1 (centre t_c = mean) plus min/max -> R, s^2 and
+ *          the per-channel scale factors, written into ws.
+ *   rows:  steps 2-4, 7, 12 (channels Phi_k = E u^k generated on the fly) and
+ *          the row half of steps 8 and 13 (Eq. (8)); K row-filtered planes
+ *          are written into ws.
+ *   cols:  the column half of Eq. (8) fused with the sums of Eqs. (9)-(10)
+ *          and the division of Eq. (11) (steps 11, 14-16, 18); writes y.
+ */
+bf_status bf_gp_phase_stats(const float *f, int planes, int H, int W, int pitch, float sigma_s, float sigma_r,
+                            const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream);
+bf_status bf_gp_phase_rows(const float *f, int planes, int H, int W, int pitch, float sigma_s, float sigma_r,
+                           const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream);
+bf_status bf_gp_phase_cols(const float *f, float *y, int planes, int H, int W, int pitch, float sigma_s,
+                           float sigma_r, const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Forward filter on HOST buffers: copies f (host) into the device workspace,
+ * runs bf_gp_forward there and copies the result into y (host), all on
+ * `stream`; returns after the device->host copy has completed (it
+ * synchronises `stream`).  Pinned host memory gives full copy bandwidth.
+ * ws must hold bf_gp_workspace_size(...) + 2 * planes * H * W * 4 bytes
+ * (bf_gp_host_workspace_size).  pitch of the host buffers is W.
+ */
+bf_status bf_gp_host_workspace_size(int planes, int H, int W, float sigma_s, const bf_gp_opts *opts,
+                                    size_t *bytes);
+bf_status bf_gp_forward_host(const float *f_host, float *y_host, int planes, int H, int W,
+                             float sigma_s, float sigma_r, const bf_gp_opts *opts,
+                             void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Read the device status word written by the last call that used `ws`
+ * (BF_DEV_* bits).  Synchronises `stream` first.
+ */
+bf_status bf_gp_get_device_status(const void *ws, void *stream, uint32_t *bits);
+
+/*
+ * Read back, for plane `plane` of the last forward call that used `ws`, the
+ * centre t_c and the scale R the device computed (FP64).  Synchronises
+ * `stream`.
+ */
+bf_status bf_gp_get_plane_stats(const void *ws, int plane, void *stream, double *t_c, double *R);
+
+/*
+ * The order rule offered when the caller wants a kernel accuracy rather than
+ * a fixed N (the paper fixes N = 20 and leaves the choice open, Sec. 4):
+ * the smallest even N such that for all t, tau in [-R, R]
+ *     | g_{sigma_r}(t - tau) - GP_N(t, tau) | <= eps,
+ * with GP_N the Gauss-polynomial of Eq. (5), evaluated in FP64 on a grid of
+ * the interval.  Returns -1 if no N <= 62 reaches eps.  Host only.
+ */
+int bf_gp_order_for_tol(double sigma_r, double R, double eps);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BF_GP_H */

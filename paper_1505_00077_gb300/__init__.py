@@ -1,0 +1,256 @@
+"""GB300 (sm_103a) Gauss-polynomial bilateral filter -- Python binding.
+
+A thin ctypes layer over the C ABI in include/bf_gp.h (libbfgp.so, built
+in-tree by :func:`paper_1505_00077_gb300.build.build`).  Functions named
+``bf_gp_*`` take the same arguments as the C entry points (device pointers
+as integers, a stream handle as an integer); :func:`bilateral_gp` is the
+tensor-level convenience wrapper that allocates the output and a cached
+workspace with PyTorch and calls :func:`bf_gp_forward` on the current stream.
+Every step of the filter runs in the library's CUDA kernels; there is no CPU
+path.
+
+Method: Chaudhury, "Fast and Accurate Bilateral Filtering using
+Gauss-Polynomial Decomposition" (Algorithm 1, Eqs. (7)-(11)).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+from .build import LIB, build  # noqa: F401
+
+BF_OK = 0
+BF_ERR_INVALID_ARG = 1
+BF_ERR_WORKSPACE = 2
+BF_ERR_CUDA = 3
+BF_ERR_UNSUPPORTED = 4
+BF_ERR_TIMEOUT = 5
+
+BF_DEV_NONPOS_Q = 0x1
+BF_DEV_NONFINITE_IN = 0x2
+BF_DEV_RANGE = 0x4
+BF_DEV_TIMEOUT = 0x8
+
+BF_SPATIAL_AUTO = 0
+BF_SPATIAL_FIR = 1
+BF_SPATIAL_IIR = 2
+_SPATIAL = {"auto": BF_SPATIAL_AUTO, "fir": BF_SPATIAL_FIR, "iir": BF_SPATIAL_IIR}
+
+BF_CENTRE_MEAN = 0
+BF_CENTRE_GIVEN = 1
+
+
+class BFError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)}"
+                         + (f" ({last_cuda_error()})" if status == BF_ERR_CUDA else ""))
+
+
+class bf_gp_opts(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("spatial", ctypes.c_int), ("centre", ctypes.c_int),
+                ("fir_halfwidth", ctypes.c_int), ("t_c", ctypes.c_double), ("reserved", ctypes.c_int * 8)]
+
+
+_lib = None
+
+
+def _load():
+    """Load libbfgp.so; fail loudly if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise RuntimeError(f"CUDA library not built ({LIB}); run paper_1505_00077_gb300.build.build()")
+    lib = ctypes.CDLL(LIB)
+    c_int, c_float, c_double, c_size_t, c_void_p = ctypes.c_int, ctypes.c_float, ctypes.c_double, ctypes.c_size_t, ctypes.c_void_p
+    P = ctypes.POINTER
+    sig = {
+        "bf_gp_default_opts": (None, [P(bf_gp_opts)]),
+        "bf_status_string": (ctypes.c_char_p, [c_int]),
+        "bf_gp_last_cuda_error": (ctypes.c_char_p, []),
+        "bf_gp_version": (c_int, []),
+        "bf_gp_workspace_size": (c_int, [c_int, c_int, c_int, c_float, P(bf_gp_opts), P(c_size_t)]),
+        "bf_gp_forward": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_float, c_float, P(bf_gp_opts),
+                                  c_void_p, c_size_t, c_void_p]),
+        "bf_gp_phase_stats": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_float, c_float, P(bf_gp_opts),
+                                      c_void_p, c_size_t, c_void_p]),
+        "bf_gp_phase_rows": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_float, c_float, P(bf_gp_opts),
+                                     c_void_p, c_size_t, c_void_p]),
+        "bf_gp_phase_cols": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_float, c_float,
+                                     P(bf_gp_opts), c_void_p, c_size_t, c_void_p]),
+        "bf_gp_host_workspace_size": (c_int, [c_int, c_int, c_int, c_float, P(bf_gp_opts), P(c_size_t)]),
+        "bf_gp_forward_host": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_float, c_float, P(bf_gp_opts),
+                                       c_void_p, c_size_t, c_void_p]),
+        "bf_gp_get_device_status": (c_int, [c_void_p, c_void_p, P(ctypes.c_uint32)]),
+        "bf_gp_get_plane_stats": (c_int, [c_void_p, c_int, c_void_p, P(c_double), P(c_double)]),
+        "bf_gp_order_for_tol": (c_int, [c_double, c_double, c_double]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names the binding expects the library to export."""
+    return ["bf_gp_default_opts", "bf_status_string", "bf_gp_last_cuda_error", "bf_gp_version",
+            "bf_gp_workspace_size", "bf_gp_forward", "bf_gp_phase_stats", "bf_gp_phase_rows", "bf_gp_phase_cols",
+            "bf_gp_host_workspace_size", "bf_gp_forward_host",
+            "bf_gp_get_device_status", "bf_gp_get_plane_stats", "bf_gp_order_for_tol"]
+
+
+def status_string(status: int) -> str:
+    return _load().bf_status_string(int(status)).decode()
+
+
+def last_cuda_error() -> str:
+    return _load().bf_gp_last_cuda_error().decode()
+
+
+def make_opts(order: int = 20, spatial="auto", t_c=None, fir_halfwidth: int = 0) -> bf_gp_opts:
+    o = bf_gp_opts()
+    _load().bf_gp_default_opts(ctypes.byref(o))
+    o.order = int(order)
+    o.spatial = _SPATIAL[spatial] if isinstance(spatial, str) else int(spatial)
+    o.fir_halfwidth = int(fir_halfwidth)
+    if t_c is not None:
+        o.centre = BF_CENTRE_GIVEN
+        o.t_c = float(t_c)
+    return o
+
+
+def _check(st: int, what: str):
+    if st != BF_OK:
+        raise BFError(st, what)
+
+
+# ------------------------------------------------------- C-ABI mirrors
+
+
+def bf_gp_workspace_size(planes, H, W, sigma_s, opts=None) -> int:
+    n = ctypes.c_size_t(0)
+    _check(_load().bf_gp_workspace_size(int(planes), int(H), int(W), float(sigma_s),
+                                        ctypes.byref(opts) if opts is not None else None, ctypes.byref(n)),
+           "bf_gp_workspace_size")
+    return int(n.value)
+
+
+def bf_gp_forward(f_ptr, y_ptr, planes, H, W, pitch, sigma_s, sigma_r, opts, ws_ptr, ws_bytes, stream=0) -> None:
+    _check(_load().bf_gp_forward(ctypes.c_void_p(int(f_ptr)), ctypes.c_void_p(int(y_ptr)), int(planes), int(H),
+                                 int(W), int(pitch), float(sigma_s), float(sigma_r),
+                                 ctypes.byref(opts) if opts is not None else None,
+                                 ctypes.c_void_p(int(ws_ptr)), int(ws_bytes), ctypes.c_void_p(int(stream))),
+           "bf_gp_forward")
+
+
+def _vp(v):
+    return ctypes.c_void_p(int(v))
+
+
+def _op(opts):
+    return ctypes.byref(opts) if opts is not None else None
+
+
+def bf_gp_phase_stats(f_ptr, planes, H, W, pitch, sigma_s, sigma_r, opts, ws_ptr, ws_bytes, stream=0) -> None:
+    _check(_load().bf_gp_phase_stats(_vp(f_ptr), int(planes), int(H), int(W), int(pitch), float(sigma_s),
+                                     float(sigma_r), _op(opts), _vp(ws_ptr), int(ws_bytes), _vp(stream)),
+           "bf_gp_phase_stats")
+
+
+def bf_gp_phase_rows(f_ptr, planes, H, W, pitch, sigma_s, sigma_r, opts, ws_ptr, ws_bytes, stream=0) -> None:
+    _check(_load().bf_gp_phase_rows(_vp(f_ptr), int(planes), int(H), int(W), int(pitch), float(sigma_s),
+                                    float(sigma_r), _op(opts), _vp(ws_ptr), int(ws_bytes), _vp(stream)),
+           "bf_gp_phase_rows")
+
+
+def bf_gp_phase_cols(f_ptr, y_ptr, planes, H, W, pitch, sigma_s, sigma_r, opts, ws_ptr, ws_bytes, stream=0) -> None:
+    _check(_load().bf_gp_phase_cols(_vp(f_ptr), _vp(y_ptr), int(planes), int(H), int(W), int(pitch),
+                                    float(sigma_s), float(sigma_r), _op(opts), _vp(ws_ptr), int(ws_bytes),
+                                    _vp(stream)), "bf_gp_phase_cols")
+
+
+def bf_gp_host_workspace_size(planes, H, W, sigma_s, opts=None) -> int:
+    n = ctypes.c_size_t(0)
+    _check(_load().bf_gp_host_workspace_size(int(planes), int(H), int(W), float(sigma_s),
+                                             ctypes.byref(opts) if opts is not None else None, ctypes.byref(n)),
+           "bf_gp_host_workspace_size")
+    return int(n.value)
+
+
+def bf_gp_forward_host(f_host_ptr, y_host_ptr, planes, H, W, sigma_s, sigma_r, opts, ws_ptr, ws_bytes,
+                       stream=0) -> None:
+    _check(_load().bf_gp_forward_host(ctypes.c_void_p(int(f_host_ptr)), ctypes.c_void_p(int(y_host_ptr)),
+                                      int(planes), int(H), int(W), float(sigma_s), float(sigma_r),
+                                      ctypes.byref(opts) if opts is not None else None,
+                                      ctypes.c_void_p(int(ws_ptr)), int(ws_bytes), ctypes.c_void_p(int(stream))),
+           "bf_gp_forward_host")
+
+
+def bf_gp_get_device_status(ws_ptr, stream=0) -> int:
+    b = ctypes.c_uint32(0)
+    _check(_load().bf_gp_get_device_status(ctypes.c_void_p(int(ws_ptr)), ctypes.c_void_p(int(stream)), ctypes.byref(b)),
+           "bf_gp_get_device_status")
+    return int(b.value)
+
+
+def bf_gp_get_plane_stats(ws_ptr, plane, stream=0):
+    tc, R = ctypes.c_double(0), ctypes.c_double(0)
+    _check(_load().bf_gp_get_plane_stats(ctypes.c_void_p(int(ws_ptr)), int(plane), ctypes.c_void_p(int(stream)),
+                                         ctypes.byref(tc), ctypes.byref(R)), "bf_gp_get_plane_stats")
+    return tc.value, R.value
+
+
+def bf_gp_order_for_tol(sigma_r, R, eps) -> int:
+    return int(_load().bf_gp_order_for_tol(float(sigma_r), float(R), float(eps)))
+
+
+def bf_gp_version() -> int:
+    return int(_load().bf_gp_version())
+
+
+# ------------------------------------------------------- tensor wrapper
+
+_ws_cache = {}
+
+
+def workspace(nbytes: int, device=None):
+    """A cached uint8 CUDA tensor of at least nbytes (256-byte aligned by the caching allocator)."""
+    import torch
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    key = (dev.type, dev.index if dev.index is not None else torch.cuda.current_device())
+    buf = _ws_cache.get(key)
+    if buf is None or buf.numel() < nbytes:
+        buf = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
+        _ws_cache[key] = buf
+    return buf
+
+
+def bilateral_gp(x, sigma_s: float, sigma_r: float, order: int = 20, spatial="auto", t_c=None,
+                 fir_halfwidth: int = 0, out=None, ws=None):
+    """Filter a float32 CUDA tensor [..., H, W] (leading dims are independent planes).
+
+    Every plane gets its own centre (the plane mean unless t_c is given) and
+    scale.  Runs asynchronously on torch's current stream.
+    """
+    import torch
+    if not (x.is_cuda and x.dtype == torch.float32):
+        raise TypeError("bilateral_gp needs a float32 CUDA tensor")
+    if x.dim() < 2:
+        raise ValueError("need at least [H, W]")
+    xc = x.contiguous()
+    H, W = xc.shape[-2], xc.shape[-1]
+    planes = max(1, xc.numel() // (H * W))
+    opts = make_opts(order, spatial, t_c, fir_halfwidth)
+    need = bf_gp_workspace_size(planes, H, W, sigma_s, opts)
+    buf = ws if ws is not None else workspace(need, xc.device)
+    if buf.numel() < need:
+        raise ValueError(f"workspace too small: {buf.numel()} < {need}")
+    y = torch.empty_like(xc) if out is None else out
+    stream = torch.cuda.current_stream(xc.device).cuda_stream
+    bf_gp_forward(xc.data_ptr(), y.data_ptr(), planes, H, W, W, sigma_s, sigma_r, opts, buf.data_ptr(),
+                  buf.numel(), stream)
+    return y

@@ -1,0 +1,483 @@
+// bf_gp.cu -- host side of the C ABI declared in include/bf_gp.h.
+//
+// Validates arguments, lays out the caller's workspace, derives the spatial
+// filter coefficients in FP64 (rounded once to FP32) and enqueues the kernels
+// of bf_gp_device.cuh on the caller's stream.  Never allocates device memory.
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+
+#include "../../include/bf_gp.h"
+#include "bf_gp_device.cuh"
+
+using namespace bfgp;
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+bf_status cuda_fail(cudaError_t e, const char *where)
+{
+    snprintf(g_cuda_err, sizeof g_cuda_err, "%s: %s", where, cudaGetErrorString(e));
+    return BF_ERR_CUDA;
+}
+
+#define BF_CUDA(call)                                    \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+constexpr int ROW_C = 16;           // samples per thread along a row
+constexpr int COL_C = 16;           // rows per thread along a column
+constexpr int COL_ROWS_PER_CTA = 32 * COL_C;  // 512
+constexpr int COL_MAX_CLUSTER = 8;
+constexpr size_t HDR_BYTES = 4096;  // status word + spare
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int next_pow2(int v)
+{
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+struct Plan {
+    int K, N, Wp, w, spatial;  // spatial: 1 FIR, 2 IIR
+    int nblk, rows_per_block;
+    int T;                     // row threads per row
+    int CL;                    // column cluster size (IIR)
+    size_t off_params, off_part, off_planes, total;
+};
+
+int fir_halfwidth(float sigma_s, const bf_gp_opts *o)
+{
+    if (o->fir_halfwidth > 0) return o->fir_halfwidth;
+    return (int)std::ceil(3.0 * (double)sigma_s - 1e-12);
+}
+
+bf_status check_opts(const bf_gp_opts *o)
+{
+    if (o->order < 0 || o->order > KMAX - 2) return BF_ERR_INVALID_ARG;
+    if (o->spatial < 0 || o->spatial > 2) return BF_ERR_INVALID_ARG;
+    if (o->centre < 0 || o->centre > 1) return BF_ERR_INVALID_ARG;
+    if (o->fir_halfwidth < 0) return BF_ERR_INVALID_ARG;
+    if (o->centre == BF_CENTRE_GIVEN && !std::isfinite(o->t_c)) return BF_ERR_INVALID_ARG;
+    for (int i = 0; i < 8; ++i)
+        if (o->reserved[i] != 0) return BF_ERR_INVALID_ARG;
+    return BF_OK;
+}
+
+bf_status make_plan(int planes, int H, int W, float sigma_s, const bf_gp_opts *o, Plan *p)
+{
+    if (planes < 1 || H < 1 || W < 1) return BF_ERR_INVALID_ARG;
+    if (!(sigma_s > 0.f) || !std::isfinite(sigma_s)) return BF_ERR_INVALID_ARG;
+    bf_status st = check_opts(o);
+    if (st != BF_OK) return st;
+    p->N = o->order;
+    p->K = o->order + 2;
+    p->w = fir_halfwidth(sigma_s, o);
+    int sp = o->spatial;
+    if (sp == BF_SPATIAL_AUTO) sp = (p->w <= FIR_WMAX) ? BF_SPATIAL_FIR : BF_SPATIAL_IIR;
+    if (sp == BF_SPATIAL_FIR && p->w > FIR_WMAX) return BF_ERR_UNSUPPORTED;
+    p->spatial = sp;
+    p->Wp = (int)align_up((size_t)W, 32);
+    p->T = next_pow2((W + ROW_C - 1) / ROW_C);
+    if (p->T < 8) p->T = 8;
+    if (p->T > 512) return BF_ERR_UNSUPPORTED;  // rows longer than 8192 samples
+    p->CL = (H + COL_ROWS_PER_CTA - 1) / COL_ROWS_PER_CTA;
+    if (sp == BF_SPATIAL_IIR && p->CL > COL_MAX_CLUSTER) return BF_ERR_UNSUPPORTED;  // columns longer than 4096
+    // stats partials: ~16K pixels per block
+    const long long px = (long long)H * W;
+    int nblk = (int)std::min<long long>((long long)H, std::max<long long>(1, (px + 16383) / 16384));
+    p->rows_per_block = (H + nblk - 1) / nblk;
+    p->nblk = (H + p->rows_per_block - 1) / p->rows_per_block;
+    size_t off = HDR_BYTES;
+    p->off_params = off;
+    off = align_up(off + sizeof(PlaneParams) * (size_t)planes, 256);
+    p->off_part = off;
+    off = align_up(off + sizeof(StatPartial) * (size_t)planes * p->nblk, 256);
+    p->off_planes = off;
+    off = align_up(off + sizeof(float) * (size_t)planes * p->K * H * p->Wp, 256);
+    p->total = off;
+    return BF_OK;
+}
+
+void deriche_coefs(double sigma, int C, IIRCoef *cf)
+{
+    // Deriche's published 4th-order fit of exp(-x^2/2) (unit scale):
+    //   (a0 cos(w0 x) + a1 sin(w0 x)) e^{-b0 x} + (c0 cos(w1 x) + c1 sin(w1 x)) e^{-b1 x},
+    // i.e. Re[A0 p0^d + A1 p1^d] at x = d/sigma with p = exp((-b + i w)/sigma).
+    const double a0 = 1.680, a1 = 3.735, b0 = 1.783, b1 = 1.723;
+    const double c0 = -0.6803, c1 = -0.2598, w0 = 0.6318, w1 = 1.997;
+    const std::complex<double> p[NP] = {std::exp(std::complex<double>(-b0, w0) / sigma),
+                                        std::exp(std::complex<double>(-b1, w1) / sigma)};
+    const std::complex<double> A[NP] = {{a0, -a1}, {c0, -c1}};
+    std::memset(cf, 0, sizeof *cf);
+    for (int m = 0; m < NP; ++m) {
+        cf->pr[m] = (float)p[m].real();
+        cf->pi[m] = (float)p[m].imag();
+        for (int e = 0; e <= C; ++e) {
+            const std::complex<double> t = A[m] * std::pow(p[m], (double)e);
+            cf->tr[m][e] = (float)t.real();
+            cf->ti[m][e] = (float)t.imag();
+        }
+        for (int i = 0; i < 12; ++i) {
+            const std::complex<double> t = std::pow(p[m], (double)C * (double)(1 << i));
+            cf->Pr[m][i] = (float)t.real();
+            cf->Pi[m][i] = (float)t.imag();
+        }
+    }
+}
+
+void fir_coefs(double sigma, int w, FIRCoef *g)
+{
+    std::memset(g, 0, sizeof *g);
+    for (int d = 0; d <= w && d <= FIR_WMAX; ++d) g->g[d] = (float)std::exp(-(double)d * d / (2.0 * sigma * sigma));
+}
+
+// ---------------------------------------------------------------- launches
+
+template <int WH>
+bf_status launch_row_fir_w(const RowArgs &ra, const FIRCoef &g, int planes, cudaStream_t s)
+{
+    const int T = ra.T;
+    const int block = T > 256 ? T : 256;
+    const int rows_per_cta = block / T;
+    const size_t smem = sizeof(float) * 2 * rows_per_cta * (size_t)(T * ROW_C + 2 * WH);
+    BF_CUDA(cudaFuncSetAttribute(row_fir<ROW_C, WH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((ra.H + rows_per_cta - 1) / rows_per_cta, planes);
+    row_fir<ROW_C, WH><<<grid, block, smem, s>>>(ra, g);
+    return BF_OK;
+}
+
+template <int WH>
+bf_status launch_col_fir_w(const ColArgs &ca, const FIRCoef &g, int planes, cudaStream_t s)
+{
+    dim3 grid((ca.W + 31) / 32, (ca.H + 63) / 64, planes);
+    col_fir<WH><<<grid, 256, 0, s>>>(ca, g);
+    return BF_OK;
+}
+
+}  // namespace
+
+namespace {
+
+struct Call {
+    Plan p;
+    cudaStream_t s;
+    uint32_t *status;
+    PlaneParams *pp;
+    StatPartial *part;
+    float *planesbuf;
+    RowArgs ra;
+    ColArgs ca;
+};
+
+bf_status prepare(const float *f, float *y, int planes, int H, int W, int pitch, float sigma_s, float sigma_r,
+                  const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream, bool need_y, Call *c)
+{
+    if (!f || !ws || (need_y && !y)) return BF_ERR_INVALID_ARG;
+    if (pitch < W) return BF_ERR_INVALID_ARG;
+    if (!(sigma_r > 0.f)) return BF_ERR_INVALID_ARG;  // also rejects NaN; +inf accepted
+    bf_gp_opts d;
+    if (!opts) {
+        bf_gp_default_opts(&d);
+        opts = &d;
+    }
+    bf_status st = make_plan(planes, H, W, sigma_s, opts, &c->p);
+    if (st != BF_OK) return st;
+    if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < c->p.total) return BF_ERR_WORKSPACE;
+    if (need_y) {
+        // input and output must not overlap
+        const char *fb = reinterpret_cast<const char *>(f);
+        const char *yb = reinterpret_cast<const char *>(y);
+        const size_t span = sizeof(float) * ((size_t)planes * H * pitch);
+        if (fb < yb + span && yb < fb + span) return BF_ERR_INVALID_ARG;
+    }
+    c->s = reinterpret_cast<cudaStream_t>(stream);
+    char *wsb = static_cast<char *>(ws);
+    c->status = reinterpret_cast<uint32_t *>(wsb);
+    c->pp = reinterpret_cast<PlaneParams *>(wsb + c->p.off_params);
+    c->part = reinterpret_cast<StatPartial *>(wsb + c->p.off_part);
+    c->planesbuf = reinterpret_cast<float *>(wsb + c->p.off_planes);
+    RowArgs &ra = c->ra;
+    ra.f = f;
+    ra.ws = c->planesbuf;
+    ra.pp = c->pp;
+    ra.H = H;
+    ra.W = W;
+    ra.pitch = pitch;
+    ra.Wp = c->p.Wp;
+    ra.K = c->p.K;
+    ra.T = c->p.T;
+    ColArgs &ca = c->ca;
+    ca.ws = c->planesbuf;
+    ca.f = f;
+    ca.y = y;
+    ca.pp = c->pp;
+    ca.status = c->status;
+    ca.H = H;
+    ca.W = W;
+    ca.pitch = pitch;
+    ca.Wp = c->p.Wp;
+    ca.K = c->p.K;
+    ca.N = c->p.N;
+    return BF_OK;
+}
+
+bf_status run_stats(const Call &c, int planes, int H, int W, int pitch, float sigma_r, const bf_gp_opts *opts)
+{
+    bf_gp_opts d;
+    if (!opts) {
+        bf_gp_default_opts(&d);
+        opts = &d;
+    }
+    stats_partial<<<dim3(c.p.nblk, planes), 256, 0, c.s>>>(c.ra.f, H, W, pitch, c.p.rows_per_block, c.part);
+    stats_finalize<<<1, 256, 0, c.s>>>(c.part, c.p.nblk, planes, (long long)H * W,
+                                       opts->centre == BF_CENTRE_GIVEN ? 1 : 0, opts->t_c, (double)sigma_r, c.p.K,
+                                       c.pp, c.status);
+    BF_CUDA(cudaGetLastError());
+    return BF_OK;
+}
+
+bf_status run_rows(const Call &c, int planes, float sigma_s)
+{
+    const int T = c.ra.T;
+    const int block = T > 256 ? T : 256;
+    const int rows_per_cta = block / T;
+    if (c.p.spatial == BF_SPATIAL_FIR) {
+        FIRCoef g;
+        fir_coefs((double)sigma_s, c.p.w, &g);
+        bf_status st = BF_ERR_UNSUPPORTED;
+        switch (c.p.w) {
+#define BF_CASE(WW) \
+    case WW: st = launch_row_fir_w<WW>(c.ra, g, planes, c.s); break;
+            BF_CASE(1) BF_CASE(2) BF_CASE(3) BF_CASE(4) BF_CASE(5) BF_CASE(6)
+            BF_CASE(7) BF_CASE(8) BF_CASE(9) BF_CASE(10) BF_CASE(11) BF_CASE(12)
+#undef BF_CASE
+        default: break;
+        }
+        if (st != BF_OK) return st;
+    } else {
+        IIRCoef cr;
+        deriche_coefs((double)sigma_s, ROW_C, &cr);
+        dim3 grid((c.ra.H + rows_per_cta - 1) / rows_per_cta, planes);
+        row_iir<ROW_C><<<grid, block, 0, c.s>>>(c.ra, cr);
+    }
+    BF_CUDA(cudaGetLastError());
+    return BF_OK;
+}
+
+bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
+{
+    if (c.p.spatial == BF_SPATIAL_FIR) {
+        FIRCoef g;
+        fir_coefs((double)sigma_s, c.p.w, &g);
+        bf_status st = BF_ERR_UNSUPPORTED;
+        switch (c.p.w) {
+#define BF_CASE(WW) \
+    case WW: st = launch_col_fir_w<WW>(c.ca, g, planes, c.s); break;
+            BF_CASE(1) BF_CASE(2) BF_CASE(3) BF_CASE(4) BF_CASE(5) BF_CASE(6)
+            BF_CASE(7) BF_CASE(8) BF_CASE(9) BF_CASE(10) BF_CASE(11) BF_CASE(12)
+#undef BF_CASE
+        default: break;
+        }
+        if (st != BF_OK) return st;
+    } else {
+        IIRCoef cc;
+        deriche_coefs((double)sigma_s, COL_C, &cc);
+        const int strips = (W + 7) / 8;
+        if (c.p.CL == 1) {
+            dim3 grid(strips, planes);
+            col_iir<COL_C, false><<<grid, 256, 0, c.s>>>(c.ca, cc);
+        } else {
+            cudaLaunchConfig_t cfg;
+            std::memset(&cfg, 0, sizeof cfg);
+            cfg.gridDim = dim3(strips * c.p.CL, planes, 1);
+            cfg.blockDim = dim3(256, 1, 1);
+            cfg.dynamicSmemBytes = 0;
+            cfg.stream = c.s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = (unsigned)c.p.CL;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            BF_CUDA(cudaLaunchKernelEx(&cfg, col_iir<COL_C, true>, c.ca, cc));
+        }
+    }
+    BF_CUDA(cudaGetLastError());
+    return BF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bf_gp_default_opts(bf_gp_opts *opts)
+{
+    if (!opts) return;
+    std::memset(opts, 0, sizeof *opts);
+    opts->order = 20;
+    opts->spatial = BF_SPATIAL_AUTO;
+    opts->centre = BF_CENTRE_MEAN;
+    opts->fir_halfwidth = 0;
+    opts->t_c = 0.0;
+}
+
+const char *bf_status_string(bf_status s)
+{
+    switch (s) {
+    case BF_OK: return "BF_OK";
+    case BF_ERR_INVALID_ARG: return "BF_ERR_INVALID_ARG";
+    case BF_ERR_WORKSPACE: return "BF_ERR_WORKSPACE";
+    case BF_ERR_CUDA: return "BF_ERR_CUDA";
+    case BF_ERR_UNSUPPORTED: return "BF_ERR_UNSUPPORTED";
+    case BF_ERR_TIMEOUT: return "BF_ERR_TIMEOUT";
+    }
+    return "BF_ERR_UNKNOWN";
+}
+
+const char *bf_gp_last_cuda_error(void) { return g_cuda_err; }
+
+int bf_gp_version(void) { return 100; }
+
+bf_status bf_gp_workspace_size(int planes, int H, int W, float sigma_s, const bf_gp_opts *opts, size_t *bytes)
+{
+    if (!bytes) return BF_ERR_INVALID_ARG;
+    bf_gp_opts d;
+    if (!opts) {
+        bf_gp_default_opts(&d);
+        opts = &d;
+    }
+    Plan p;
+    bf_status st = make_plan(planes, H, W, sigma_s, opts, &p);
+    if (st != BF_OK) return st;
+    *bytes = p.total;
+    return BF_OK;
+}
+
+bf_status bf_gp_forward(const float *f, float *y, int planes, int H, int W, int pitch, float sigma_s, float sigma_r,
+                        const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream)
+{
+    Call c;
+    bf_status st = prepare(f, y, planes, H, W, pitch, sigma_s, sigma_r, opts, ws, ws_bytes, stream, true, &c);
+    if (st != BF_OK) return st;
+    st = run_stats(c, planes, H, W, pitch, sigma_r, opts);
+    if (st == BF_OK) st = run_rows(c, planes, sigma_s);
+    if (st == BF_OK) st = run_cols(c, planes, W, sigma_s);
+    return st;
+}
+
+bf_status bf_gp_phase_stats(const float *f, int planes, int H, int W, int pitch, float sigma_s, float sigma_r,
+                            const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream)
+{
+    Call c;
+    bf_status st = prepare(f, nullptr, planes, H, W, pitch, sigma_s, sigma_r, opts, ws, ws_bytes, stream, false, &c);
+    if (st != BF_OK) return st;
+    return run_stats(c, planes, H, W, pitch, sigma_r, opts);
+}
+
+bf_status bf_gp_phase_rows(const float *f, int planes, int H, int W, int pitch, float sigma_s, float sigma_r,
+                           const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream)
+{
+    Call c;
+    bf_status st = prepare(f, nullptr, planes, H, W, pitch, sigma_s, sigma_r, opts, ws, ws_bytes, stream, false, &c);
+    if (st != BF_OK) return st;
+    return run_rows(c, planes, sigma_s);
+}
+
+bf_status bf_gp_phase_cols(const float *f, float *y, int planes, int H, int W, int pitch, float sigma_s,
+                           float sigma_r, const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream)
+{
+    Call c;
+    bf_status st = prepare(f, y, planes, H, W, pitch, sigma_s, sigma_r, opts, ws, ws_bytes, stream, true, &c);
+    if (st != BF_OK) return st;
+    return run_cols(c, planes, W, sigma_s);
+}
+
+bf_status bf_gp_host_workspace_size(int planes, int H, int W, float sigma_s, const bf_gp_opts *opts, size_t *bytes)
+{
+    size_t b = 0;
+    bf_status st = bf_gp_workspace_size(planes, H, W, sigma_s, opts, &b);
+    if (st != BF_OK) return st;
+    *bytes = align_up(b, 256) + 2 * align_up(sizeof(float) * (size_t)planes * H * W, 256);
+    return BF_OK;
+}
+
+bf_status bf_gp_forward_host(const float *f_host, float *y_host, int planes, int H, int W, float sigma_s,
+                             float sigma_r, const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream)
+{
+    if (!f_host || !y_host || !ws) return BF_ERR_INVALID_ARG;
+    size_t need = 0, base = 0;
+    bf_status st = bf_gp_host_workspace_size(planes, H, W, sigma_s, opts, &need);
+    if (st != BF_OK) return st;
+    st = bf_gp_workspace_size(planes, H, W, sigma_s, opts, &base);
+    if (st != BF_OK) return st;
+    if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < need) return BF_ERR_WORKSPACE;
+    const size_t img = sizeof(float) * (size_t)planes * H * W;
+    char *wsb = static_cast<char *>(ws);
+    float *fd = reinterpret_cast<float *>(wsb + align_up(base, 256));
+    float *yd = reinterpret_cast<float *>(wsb + align_up(base, 256) + align_up(img, 256));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    BF_CUDA(cudaMemcpyAsync(fd, f_host, img, cudaMemcpyHostToDevice, s));
+    st = bf_gp_forward(fd, yd, planes, H, W, W, sigma_s, sigma_r, opts, ws, base, stream);
+    if (st != BF_OK) return st;
+    BF_CUDA(cudaMemcpyAsync(y_host, yd, img, cudaMemcpyDeviceToHost, s));
+    BF_CUDA(cudaStreamSynchronize(s));
+    return BF_OK;
+}
+
+bf_status bf_gp_get_device_status(const void *ws, void *stream, uint32_t *bits)
+{
+    if (!ws || !bits) return BF_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    BF_CUDA(cudaStreamSynchronize(s));
+    BF_CUDA(cudaMemcpy(bits, ws, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    return BF_OK;
+}
+
+bf_status bf_gp_get_plane_stats(const void *ws, int plane, void *stream, double *t_c, double *R)
+{
+    if (!ws || plane < 0) return BF_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    BF_CUDA(cudaStreamSynchronize(s));
+    PlaneParams q;
+    const char *src = static_cast<const char *>(ws) + HDR_BYTES + sizeof(PlaneParams) * (size_t)plane;
+    BF_CUDA(cudaMemcpy(&q, src, sizeof q, cudaMemcpyDeviceToHost));
+    if (t_c) *t_c = q.tc_d;
+    if (R) *R = q.R_d;
+    return BF_OK;
+}
+
+int bf_gp_order_for_tol(double sigma_r, double R, double eps)
+{
+    if (!(sigma_r > 0.0) || !(R >= 0.0) || !(eps > 0.0)) return -1;
+    const int G = 257;
+    for (int N = 0; N <= KMAX - 2; N += 2) {
+        double worst = 0.0;
+        for (int a = 0; a < G && worst <= eps; ++a) {
+            const double tau = -R + 2.0 * R * a / (G - 1);
+            for (int b = 0; b < G; ++b) {
+                const double t = -R + 2.0 * R * b / (G - 1);
+                const double x = tau * t / (sigma_r * sigma_r);
+                double term = 1.0, sum = 0.0;
+                for (int n = 0; n <= N; ++n) {
+                    sum += term;
+                    term *= x / (double)(n + 1);
+                }
+                const double gp = std::exp(-(tau * tau + t * t) / (2.0 * sigma_r * sigma_r)) * sum;
+                const double g = std::exp(-(t - tau) * (t - tau) / (2.0 * sigma_r * sigma_r));
+                worst = std::fmax(worst, std::fabs(g - gp));
+            }
+        }
+        if (worst <= eps) return N;
+    }
+    return -1;
+}
+
+}  // extern "C"

@@ -1,0 +1,232 @@
+"""GPU parity of the forward filter against the FP64 oracle (Algorithm 1).
+
+Every case runs the CUDA path through the C ABI (bf_gp_forward) and compares
+element by element with oracle.gp_bf on the same seeded image, with the same
+spatial operator.  Bar: max |GPU - oracle| <= 1e-3 on the 0..255 scale.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def bf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1505_00077_gb300 as m
+    m.build()
+    return m
+
+
+def run_gpu(bf, img, ss, sr, N, spatial, **kw):
+    x = torch.from_numpy(np.ascontiguousarray(img, dtype=np.float32)).cuda()
+    y = bf.bilateral_gp(x, ss, sr, N, spatial, **kw)
+    torch.cuda.synchronize()
+    return y.cpu().numpy().astype(np.float64)
+
+
+def check(gpu, ref, tol=TOL):
+    assert gpu.shape == ref.shape
+    assert np.isfinite(ref).all()
+    err = np.abs(gpu - ref)
+    assert np.isfinite(gpu).all(), "non-finite GPU output"
+    assert err.max() <= tol, f"max err {err.max():.3e} at {np.unravel_index(err.argmax(), err.shape)}"
+    return err.max()
+
+
+# ---------------------------------------------------------------- config 1
+
+@pytest.mark.parametrize("N", [20, 34])
+def test_config1_fir(bf, N):
+    img = synthetic.config1_image()
+    f64 = img.astype(np.float64)
+    ref = oracle.gp_bf(f64, 3.0, 30.0, N, "fir")
+    check(run_gpu(bf, img, 3.0, 30.0, N, "fir"), ref)
+
+
+def test_config1_iir(bf):
+    img = synthetic.config1_image()
+    ref = oracle.gp_bf(img.astype(np.float64), 3.0, 30.0, 20, "iir")
+    check(run_gpu(bf, img, 3.0, 30.0, 20, "iir"), ref)
+
+
+# ---------------------------------------------------------------- ragged shapes
+
+SHAPES = [(1, 1), (1, 7), (5, 1), (2, 3), (17, 33), (31, 64), (65, 129), (300, 260), (517, 37), (1030, 75),
+          (37, 1500), (1600, 200)]
+
+
+@pytest.mark.parametrize("spatial,ss", [("fir", 1.5), ("fir", 4.0), ("iir", 2.5), ("iir", 9.0)])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_ragged_shapes(bf, shape, spatial, ss):
+    H, W = shape
+    img = synthetic.make_image(H, W, 6, 10.0, 0.0, synthetic.seed_for(9, H * 7 + W))
+    ref = oracle.gp_bf(img.astype(np.float64), ss, 30.0, 12, spatial)
+    check(run_gpu(bf, img, ss, 30.0, 12, spatial), ref)
+
+
+@pytest.mark.parametrize("H", [511, 512, 513, 1024, 2047, 2049, 3000, 4096])
+def test_iir_column_cluster_sizes(bf, H):
+    """Columns spanning 1..8 CTAs of the clustered column pass."""
+    img = synthetic.make_image(H, 24, 8, 10.0, 30.0, synthetic.seed_for(9, H))
+    ref = oracle.gp_bf(img.astype(np.float64), 7.0, 40.0, 10, "iir")
+    check(run_gpu(bf, img, 7.0, 40.0, 10, "iir"), ref)
+
+
+@pytest.mark.parametrize("W", [511, 512, 513, 1024, 4095, 4096, 4097, 8192])
+def test_iir_long_rows(bf, W):
+    img = synthetic.make_image(12, W, 8, 10.0, 30.0, synthetic.seed_for(9, W))
+    ref = oracle.gp_bf(img.astype(np.float64), 11.0, 40.0, 10, "iir")
+    check(run_gpu(bf, img, 11.0, 40.0, 10, "iir"), ref)
+
+
+# ---------------------------------------------------------------- config 2 sweep
+
+@pytest.mark.parametrize("ss,sr,N,spatial", [
+    (2.0, 30.0, 20, "fir"), (2.0, 10.0, 20, "fir"), (2.0, 50.0, 8, "fir"),
+    (5.0, 30.0, 20, "iir"), (5.0, 50.0, 4, "iir"), (10.0, 30.0, 20, "iir"), (10.0, 50.0, 12, "iir"),
+    (20.0, 30.0, 20, "iir"), (20.0, 10.0, 20, "iir"), (20.0, 50.0, 16, "iir"),
+])
+def test_config2_sweep(bf, ss, sr, N, spatial):
+    img = synthetic.config2_image()
+    ref = oracle.gp_bf(img.astype(np.float64), ss, sr, N, spatial)
+    check(run_gpu(bf, img, ss, sr, N, spatial), ref)
+
+
+# ---------------------------------------------------------------- config 3
+
+def test_config3_crop(bf):
+    """4096^2, sigma_s 10, sigma_r 20, N 20, recursive filter: a 512^2 crop of the
+    GPU output against the oracle run on full lines of the full image."""
+    img = synthetic.config3_image()
+    f64 = img.astype(np.float64)
+    gpu = run_gpu(bf, img, 10.0, 20.0, 20, "iir")
+    r0, c0 = 1792, 2304
+    ref = oracle.gp_bf(f64, 10.0, 20.0, 20, "iir", crop=(r0, r0 + 512, c0, c0 + 512))
+    check(gpu[r0:r0 + 512, c0:c0 + 512], ref)
+    # border crop (zero-extension path at the image edge)
+    ref2 = oracle.gp_bf(f64, 10.0, 20.0, 20, "iir", crop=(4096 - 64, 4096, 0, 64))
+    check(gpu[4096 - 64:, :64], ref2)
+
+
+# ---------------------------------------------------------------- special cases
+
+def test_constant_image_exact(bf):
+    img = np.full((70, 90), 123.5, np.float32)
+    for sp in ("fir", "iir"):
+        assert np.all(run_gpu(bf, img, 3.0, 30.0, 20, sp) == 123.5)
+
+
+def test_sigma_r_infinite(bf):
+    img = synthetic.make_image(96, 80, 6, 10.0, 0.0, synthetic.seed_for(9, 1))
+    for sp, ss in (("fir", 2.0), ("iir", 6.0)):
+        ref = oracle.gp_bf(img.astype(np.float64), ss, math.inf, 20, sp)
+        check(run_gpu(bf, img, ss, math.inf, 20, sp), ref)
+
+
+def test_given_centre(bf):
+    img = synthetic.make_image(64, 64, 6, 10.0, 0.0, synthetic.seed_for(9, 2))
+    ref = oracle.gp_bf(img.astype(np.float64), 2.0, 30.0, 20, "fir", t_c=127.5)
+    check(run_gpu(bf, img, 2.0, 30.0, 20, "fir", t_c=127.5), ref)
+
+
+def test_multi_plane_independent_centres(bf):
+    imgs = np.stack([synthetic.make_image(50, 70, 5, 10.0, 0.0, synthetic.seed_for(9, 10 + i)) for i in range(3)])
+    imgs[1] *= 0.3
+    gpu = run_gpu(bf, imgs, 2.0, 25.0, 20, "fir")
+    for i in range(3):
+        check(gpu[i], oracle.gp_bf(imgs[i].astype(np.float64), 2.0, 25.0, 20, "fir"))
+
+
+def test_pitched_input(bf):
+    img = synthetic.make_image(40, 50, 5, 10.0, 0.0, synthetic.seed_for(9, 3))
+    big = np.zeros((40, 53), np.float32)
+    big[:, :50] = img
+    x = torch.from_numpy(big).cuda()
+    y = torch.full_like(x, -7.0)
+    o = bf.make_opts(20, "fir")
+    need = bf.bf_gp_workspace_size(1, 40, 50, 2.0, o)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, 40, 50, 53, 2.0, 30.0, o, ws.data_ptr(), need,
+                     torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    out = y.cpu().numpy()
+    check(out[:, :50].astype(np.float64), oracle.gp_bf(img.astype(np.float64), 2.0, 30.0, 20, "fir"))
+    assert np.all(out[:, 50:] == -7.0)  # padding untouched
+
+
+def test_device_stats_readback(bf):
+    img = synthetic.make_image(123, 77, 5, 10.0, 0.0, synthetic.seed_for(9, 4))
+    x = torch.from_numpy(img).cuda()
+    o = bf.make_opts(20, "fir")
+    need = bf.bf_gp_workspace_size(1, 123, 77, 2.0, o)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    y = torch.empty_like(x)
+    s = torch.cuda.current_stream().cuda_stream
+    bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, 123, 77, 77, 2.0, 30.0, o, ws.data_ptr(), need, s)
+    tc, R = bf.bf_gp_get_plane_stats(ws.data_ptr(), 0, s)
+    f64 = img.astype(np.float64)
+    assert abs(tc - f64.mean()) <= 1e-9 * 255
+    assert R == max(f64.max() - tc, tc - f64.min())
+    assert bf.bf_gp_get_device_status(ws.data_ptr(), s) == 0
+
+
+def test_odd_order_flags_nonpositive_denominator(bf):
+    img = np.zeros((16, 16), np.float32)
+    img[:, 8] = 255.0
+    x = torch.from_numpy(img).cuda()
+    o = bf.make_opts(5, "fir")
+    need = bf.bf_gp_workspace_size(1, 16, 16, 3.0, o)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    y = torch.empty_like(x)
+    s = torch.cuda.current_stream().cuda_stream
+    bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, 16, 16, 16, 3.0, 20.0, o, ws.data_ptr(), need, s)
+    bits = bf.bf_gp_get_device_status(ws.data_ptr(), s)
+    assert bits & bf.BF_DEV_NONPOS_Q
+    out = y.cpu().numpy()
+    ref = oracle.gp_bf(img.astype(np.float64), 3.0, 20.0, 5, "fir")
+    assert np.array_equal(np.isnan(out), np.isnan(ref))
+
+
+def test_nonfinite_input_is_passed_through_and_flagged(bf):
+    img = synthetic.make_image(20, 20, 3, 10.0, 0.0, 5)
+    img[3, 4] = np.nan
+    x = torch.from_numpy(img).cuda()
+    o = bf.make_opts(20, "fir")
+    need = bf.bf_gp_workspace_size(1, 20, 20, 3.0, o)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    y = torch.empty_like(x)
+    s = torch.cuda.current_stream().cuda_stream
+    bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, 20, 20, 20, 3.0, 30.0, o, ws.data_ptr(), need, s)
+    assert bf.bf_gp_get_device_status(ws.data_ptr(), s) & bf.BF_DEV_NONFINITE_IN
+    out = y.cpu().numpy()
+    assert np.array_equal(out, img, equal_nan=True)
+
+
+def test_host_entry_point_matches_device_entry_point(bf):
+    img = synthetic.make_image(200, 180, 8, 10.0, 0.0, synthetic.seed_for(9, 6))
+    o = bf.make_opts(20, "iir")
+    need = bf.bf_gp_host_workspace_size(1, 200, 180, 6.0, o)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    fh = torch.from_numpy(img).pin_memory()
+    yh = torch.empty_like(fh).pin_memory()
+    bf.bf_gp_forward_host(fh.data_ptr(), yh.data_ptr(), 1, 200, 180, 6.0, 30.0, o, ws.data_ptr(), need,
+                          torch.cuda.current_stream().cuda_stream)
+    dev = run_gpu(bf, img, 6.0, 30.0, 20, "iir")
+    assert np.array_equal(yh.numpy().astype(np.float64), dev)
+
+
+def test_repeat_calls_are_deterministic(bf):
+    img = synthetic.make_image(300, 300, 8, 10.0, 0.0, synthetic.seed_for(9, 7))
+    a = run_gpu(bf, img, 8.0, 30.0, 20, "iir")
+    b = run_gpu(bf, img, 8.0, 30.0, 20, "iir")
+    assert np.array_equal(a, b)
