@@ -31,7 +31,7 @@ bf_status cuda_fail(cudaError_t e, const char *where)
 
 constexpr int ROW_C = 16;           // samples per thread along a row
 constexpr int COL_C = 16;           // rows per thread along a column
-constexpr int COL_ROWS_PER_CTA = 32 * COL_C;  // 512
+constexpr int COL_ROWS_PER_CTA = COL_ROWS;  // 32 chunks of COL_C rows
 constexpr int COL_MAX_CLUSTER = 8;
 constexpr size_t HDR_BYTES = 4096;  // status word + spare
 
@@ -228,7 +228,8 @@ bf_status prepare(const float *f, float *y, int planes, int H, int W, int pitch,
     return BF_OK;
 }
 
-bf_status run_stats(const Call &c, int planes, int H, int W, int pitch, float sigma_r, const bf_gp_opts *opts)
+bf_status run_stats(const Call &c, int planes, int H, int W, int pitch, float sigma_s, float sigma_r,
+                    const bf_gp_opts *opts)
 {
     bf_gp_opts d;
     if (!opts) {
@@ -236,9 +237,10 @@ bf_status run_stats(const Call &c, int planes, int H, int W, int pitch, float si
         opts = &d;
     }
     stats_partial<<<dim3(c.p.nblk, planes), 256, 0, c.s>>>(c.ra.f, H, W, pitch, c.p.rows_per_block, c.part);
-    stats_finalize<<<1, 256, 0, c.s>>>(c.part, c.p.nblk, planes, (long long)H * W,
-                                       opts->centre == BF_CENTRE_GIVEN ? 1 : 0, opts->t_c, (double)sigma_r, c.p.K,
-                                       c.pp, c.status);
+    stats_finalize<<<planes, 256, 0, c.s>>>(c.part, c.p.nblk, (long long)H * W,
+                                            opts->centre == BF_CENTRE_GIVEN ? 1 : 0, opts->t_c, (double)sigma_r,
+                                            (double)sigma_s, c.p.K, c.pp);
+    stats_status<<<1, 1, 0, c.s>>>(c.pp, planes, c.status);
     BF_CUDA(cudaGetLastError());
     return BF_OK;
 }
@@ -290,15 +292,14 @@ bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
         IIRCoef cc;
         deriche_coefs((double)sigma_s, COL_C, &cc);
         const int strips = (W + 7) / 8;
-        if (c.p.CL == 1) {
-            dim3 grid(strips, planes);
-            col_iir<COL_C, false><<<grid, 256, 0, c.s>>>(c.ca, cc);
-        } else {
+        const size_t smem = sizeof(float) * 2 * COL_TILE_FLOATS;
+        {
+            BF_CUDA(cudaFuncSetAttribute(col_iir<COL_C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             cudaLaunchConfig_t cfg;
             std::memset(&cfg, 0, sizeof cfg);
             cfg.gridDim = dim3(strips * c.p.CL, planes, 1);
             cfg.blockDim = dim3(256, 1, 1);
-            cfg.dynamicSmemBytes = 0;
+            cfg.dynamicSmemBytes = smem;
             cfg.stream = c.s;
             cudaLaunchAttribute attr[1];
             attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -367,7 +368,7 @@ bf_status bf_gp_forward(const float *f, float *y, int planes, int H, int W, int 
     Call c;
     bf_status st = prepare(f, y, planes, H, W, pitch, sigma_s, sigma_r, opts, ws, ws_bytes, stream, true, &c);
     if (st != BF_OK) return st;
-    st = run_stats(c, planes, H, W, pitch, sigma_r, opts);
+    st = run_stats(c, planes, H, W, pitch, sigma_s, sigma_r, opts);
     if (st == BF_OK) st = run_rows(c, planes, sigma_s);
     if (st == BF_OK) st = run_cols(c, planes, W, sigma_s);
     return st;
@@ -379,7 +380,7 @@ bf_status bf_gp_phase_stats(const float *f, int planes, int H, int W, int pitch,
     Call c;
     bf_status st = prepare(f, nullptr, planes, H, W, pitch, sigma_s, sigma_r, opts, ws, ws_bytes, stream, false, &c);
     if (st != BF_OK) return st;
-    return run_stats(c, planes, H, W, pitch, sigma_r, opts);
+    return run_stats(c, planes, H, W, pitch, sigma_s, sigma_r, opts);
 }
 
 bf_status bf_gp_phase_rows(const float *f, int planes, int H, int W, int pitch, float sigma_s, float sigma_r,

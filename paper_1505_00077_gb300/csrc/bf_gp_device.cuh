@@ -6,23 +6,26 @@
 // Per plane, with h = f - t_c, R = max|h|, u = h/R, s^2 = (R/sigma_r)^2,
 // E = exp(-s^2 u^2/2), channels Phi_k = E u^k (k = 0..K-1, K = N+2) and
 // beta_0 = 1, beta_m = s^{2(m-1)}/m! (m >= 1), Psi_k = beta_k * S Phi_k:
-//     P~ = sum_{m=1..N+1} m u^{m-1} Psi_m      (= Eq. (9) / (sigma_r s))
-//     Q~ = Psi_0 + s^2 u sum_{m=1..N} u^{m-1} Psi_m   (= Eq. (10))
-//     y  = t_c + R P~/Q~                        (Eq. (11) + Eq. (6))
-// which is Eqs. (9)-(11) after substituting G_n = (s u)^n and
-// F_n = s^n Phi_n; P~ is the derivative of the polynomial sum_m v^m Psi_m at
-// v = u, so both sums cost 3 FMA per channel and pixel in Horner form.
+//     P~ = sum_{m=1..N+1} m u^{m-1} Psi_m             (Eq. (9) / (sigma_r s))
+//     Q~ = Psi_0 + s^2 u sum_{m=1..N} u^{m-1} Psi_m   (Eq. (10))
+//     y  = t_c + R P~/Q~                               (Eq. (11) + Eq. (6))
+// which is Eqs. (9)-(11) after substituting G_n = (s u)^n and F_n = s^n Phi_n.
+// Both sums are Horner recurrences in u over descending m (3 FP32 ops per
+// channel and pixel).  All channels also carry one per-plane power-of-two
+// factor 2^e0 (cancels in P~/Q~) that keeps exp(-s^2 u^2/2) from underflowing
+// FP32 when s^2 is large.
 //
 // Kernels (all FP32 arithmetic, IEEE expf and division):
 //   stats_partial / stats_finalize : Algorithm 1 step 1 (mean) plus min/max;
-//                                    finalize derives t_c, R, s^2, beta (FP64).
+//                                    finalize derives t_c, R, s^2, beta_k and
+//                                    the scale 2^e0 (FP64).
 //   row_iir / row_fir              : channel generation (steps 2-4, 7, 12) fused
 //                                    with the row half of the separable filter
 //                                    (steps 8, 13), scaled by beta_k, written
 //                                    to the workspace [plane][k][H][Wp].
 //   col_iir / col_fir              : column half of the filter fused with the
-//                                    combine (steps 11, 14-16) and the division
-//                                    (step 18); the column-filtered planes are
+//                                    sums (steps 11, 14-16) and the division
+//                                    (step 18); column-filtered planes are
 //                                    never written.
 //
 // Recursive filter: Deriche's 4th-order Gaussian (cited in Sec. 3) written as
@@ -30,9 +33,9 @@
 // y_i = sum_j h(|i-j|) x_j (zero extension) is the sum of a causal part
 // (states z_i = x_i + p z_{i-1}, output Re(A z_i)) and an anticausal part
 // (states a_i = x_i + p a_{i+1}, output at i: Re(A p a_{i+1})).  A thread owns a
-// chunk of C consecutive samples, runs both recursions from zero state, and
-// the chunk states are combined by a parallel prefix/suffix scan (carry across
-// a chunk = multiply by p^C); the carries enter each output through the
+// chunk of C consecutive samples and runs both recursions from zero state;
+// the chunk states are combined by a parallel prefix / suffix scan (the carry
+// across a chunk is a multiply by p^C) and enter each output through the
 // tables A p^e.
 #pragma once
 #include <cooperative_groups.h>
@@ -55,8 +58,9 @@ struct __align__(16) PlaneParams {
     float half_s2;  // s^2 / 2
     float s2;       // s^2
     float R;        // scale
+    float escale;   // 2^e0, common factor of every channel (cancels in P~/Q~)
     int mode;       // 0 = filter, 1 = copy input to output
-    int pad0, pad1;
+    int pad0;
     double tc_d, R_d;
     float beta[KMAX];
 };
@@ -70,9 +74,9 @@ struct __align__(16) StatPartial {
 
 // Recursive-filter coefficients for one chunk length C (FP64 -> FP32 on the host).
 struct IIRCoef {
-    float pr[NP], pi[NP];                    // poles p_m
-    float tr[NP][CMAX + 1], ti[NP][CMAX + 1];  // A_m p_m^e, e = 0..C  (tr[m][0] = Re A_m)
-    float Pr[NP][12], Pi[NP][12];            // p_m^{C 2^i}
+    float pr[NP], pi[NP];                      // poles p_m
+    float tr[NP][CMAX + 1], ti[NP][CMAX + 1];  // A_m p_m^e, e = 0..C  (e = 0: A_m)
+    float Pr[NP][12], Pi[NP][12];              // p_m^{C 2^i}
 };
 
 struct FIRCoef {
@@ -94,7 +98,7 @@ __device__ __forceinline__ void cmul(float &rr, float &ri, float ar, float ai, f
     ri = fmaf(ar, bi, ai * br);
 }
 
-// p^n by binary powering from the table p^{C 2^i}
+// p^{C n} by binary powering from the table p^{C 2^i}
 __device__ __forceinline__ void cpow_tab(float &rr, float &ri, const IIRCoef &cf, int m, int n)
 {
     rr = 1.f;
@@ -110,9 +114,9 @@ __device__ __forceinline__ void cpow_tab(float &rr, float &ri, const IIRCoef &cf
 }
 
 // Local recursions of one chunk from zero state.
-//   y[j]      = sum_m Re(A_m z_j) + Re(A_m p_m a_{j+1})   (a_C = 0)
-//   e[m]      = z_{C-1}   (causal state at the chunk end)
-//   s[m]      = a_0       (anticausal state at the chunk start)
+//   y[j] = sum_m Re(A_m z_j) + Re(A_m p_m a_{j+1})   (a_C = 0)
+//   e[m] = z_{C-1}   (causal state at the chunk end)
+//   s[m] = a_0       (anticausal state at the chunk start)
 template <int C>
 __device__ __forceinline__ void chunk_local(const float (&x)[C], float (&y)[C], float (&er)[NP], float (&ei)[NP],
                                             float (&sr)[NP], float (&si)[NP], const IIRCoef &cf)
@@ -128,13 +132,11 @@ __device__ __forceinline__ void chunk_local(const float (&x)[C], float (&y)[C], 
         float ar = 0.f, ai = 0.f;
 #pragma unroll
         for (int j = 0; j < C; ++j) {
-            // causal at j
             const float nzr = fmaf(pr, zr, fmaf(-pi, zi, x[j]));
             const float nzi = fmaf(pr, zi, pi * zr);
             zr = nzr;
             zi = nzi;
             y[j] = fmaf(Ar, zr, fmaf(-Ai, zi, y[j]));
-            // anticausal: output at jj uses a_{jj+1}, then a_jj = x_jj + p a_{jj+1}
             const int jj = C - 1 - j;
             y[jj] = fmaf(Br, ar, fmaf(-Bi, ai, y[jj]));
             const float nar = fmaf(pr, ar, fmaf(-pi, ai, x[jj]));
@@ -168,6 +170,14 @@ __device__ __forceinline__ void chunk_correct(float (&y)[C], const float (&cr)[N
     }
 }
 
+// Phi_0 = E * 2^e0 with E = exp(-s^2 u^2 / 2) formed as e1 * (e1 * 2^e0),
+// e1 = exp(-s^2 u^2 / 4), so neither factor leaves the FP32 range.
+__device__ __forceinline__ float envelope(const PlaneParams &P, float u)
+{
+    const float e1 = expf(-0.5f * P.half_s2 * (u * u));
+    return (e1 * P.escale) * e1;
+}
+
 // ------------------------------------------------------------------ stats
 
 // grid (nblk, planes), block 256.  Each block reduces a band of rows.
@@ -183,7 +193,7 @@ __global__ void __launch_bounds__(256) stats_partial(const float *__restrict__ f
     const bool vec = ((pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(f) & 15) == 0);
     for (int r = r0; r < r1; ++r) {
         const float *row = f + ((size_t)plane * H + r) * pitch;
-        float s = 0.f;  // FP32 partial over one row's share (<= W/256*... values of <= 255-ish)
+        float s = 0.f;  // FP32 partial over this thread's share of one row
         if (vec) {
             const int W4 = W >> 2;
             for (int i = threadIdx.x; i < W4; i += blockDim.x) {
@@ -191,7 +201,10 @@ __global__ void __launch_bounds__(256) stats_partial(const float *__restrict__ f
                 const float a[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    if (!isfinite(a[t])) { ++bad; continue; }
+                    if (!isfinite(a[t])) {
+                        ++bad;
+                        continue;
+                    }
                     s += a[t];
                     mn = fminf(mn, a[t]);
                     mx = fmaxf(mx, a[t]);
@@ -199,7 +212,10 @@ __global__ void __launch_bounds__(256) stats_partial(const float *__restrict__ f
             }
             for (int x = (W4 << 2) + threadIdx.x; x < W; x += blockDim.x) {
                 const float a = __ldg(row + x);
-                if (!isfinite(a)) { ++bad; continue; }
+                if (!isfinite(a)) {
+                    ++bad;
+                    continue;
+                }
                 s += a;
                 mn = fminf(mn, a);
                 mx = fmaxf(mx, a);
@@ -207,7 +223,10 @@ __global__ void __launch_bounds__(256) stats_partial(const float *__restrict__ f
         } else {
             for (int x = threadIdx.x; x < W; x += blockDim.x) {
                 const float a = __ldg(row + x);
-                if (!isfinite(a)) { ++bad; continue; }
+                if (!isfinite(a)) {
+                    ++bad;
+                    continue;
+                }
                 s += a;
                 mn = fminf(mn, a);
                 mx = fmaxf(mx, a);
@@ -215,7 +234,6 @@ __global__ void __launch_bounds__(256) stats_partial(const float *__restrict__ f
         }
         sum += (double)s;
     }
-    // block reduction
     __shared__ double ssum[8];
     __shared__ float smn[8], smx[8];
     __shared__ int sbad[8];
@@ -251,80 +269,108 @@ __global__ void __launch_bounds__(256) stats_partial(const float *__restrict__ f
     }
 }
 
-// One block.  Reduces the partials of every plane (FP64) and writes PlaneParams.
-__global__ void __launch_bounds__(256) stats_finalize(const StatPartial *__restrict__ part, int nblk, int planes,
+// grid (planes), block 256.  Reduces one plane's partials (FP64) and writes
+// its PlaneParams; the status word is written by the stats_status kernel.
+__global__ void __launch_bounds__(256) stats_finalize(const StatPartial *__restrict__ part, int nblk,
                                                       long long npix, int centre_given, double tc_given,
-                                                      double sigma_r, int K, PlaneParams *__restrict__ pp,
-                                                      uint32_t *__restrict__ status)
+                                                      double sigma_r, double sigma_s, int K,
+                                                      PlaneParams *__restrict__ pp)
 {
-    __shared__ double ssum[256];
-    __shared__ float smn[256], smx[256];
-    __shared__ int sbad[256];
-    uint32_t bits = 0;
-    for (int c = 0; c < planes; ++c) {
-        double sum = 0.0;
-        float mn = INFINITY, mx = -INFINITY;
-        int bad = 0;
-        for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-            const StatPartial p = part[(size_t)c * nblk + b];
-            sum += p.sum;
-            mn = fminf(mn, p.mn);
-            mx = fmaxf(mx, p.mx);
-            bad += p.nonfinite;
-        }
-        ssum[threadIdx.x] = sum;
-        smn[threadIdx.x] = mn;
-        smx[threadIdx.x] = mx;
-        sbad[threadIdx.x] = bad;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double S = 0.0;
-            float MN = INFINITY, MX = -INFINITY;
-            long long BAD = 0;
-            for (int t = 0; t < (int)blockDim.x; ++t) {
-                S += ssum[t];
-                MN = fminf(MN, smn[t]);
-                MX = fmaxf(MX, smx[t]);
-                BAD += sbad[t];
-            }
-            PlaneParams q;
-            const double mean = S / (double)npix;
-            const double tc = centre_given ? tc_given : mean;
-            double R = fmax((double)MX - tc, tc - (double)MN);
-            int mode = 0;
-            if (BAD > 0) {
-                mode = 1;
-                bits |= 0x2u;
-            }
-            if (!(R > 0.0)) {
-                mode = 1;
-                R = 1.0;
-            }
-            const double s2 = isinf(sigma_r) ? 0.0 : (R / sigma_r) * (R / sigma_r);
-            if (mode == 0 && 0.5 * s2 > 80.0) bits |= 0x4u;
-            q.tc = (float)tc;
-            q.invR = (float)(1.0 / R);
-            q.half_s2 = (float)(0.5 * s2);
-            q.s2 = (float)s2;
-            q.R = (float)R;
-            q.mode = mode;
-            q.pad0 = q.pad1 = 0;
-            q.tc_d = tc;
-            q.R_d = R;
-            double b = 1.0;
-            for (int m = 0; m < KMAX; ++m) {
-                if (m == 0) {
-                    q.beta[0] = 1.f;
-                } else {
-                    b = (m == 1) ? 1.0 : b * s2 / (double)m;  // beta_m = s^{2(m-1)} / m!
-                    q.beta[m] = (m < K) ? (float)b : 0.f;
-                }
-            }
-            pp[c] = q;
-        }
-        __syncthreads();
+    const int c = blockIdx.x;
+    double sum = 0.0;
+    float mn = INFINITY, mx = -INFINITY;
+    int bad = 0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+        const StatPartial p = part[(size_t)c * nblk + b];
+        sum += p.sum;
+        mn = fminf(mn, p.mn);
+        mx = fmaxf(mx, p.mx);
+        bad += p.nonfinite;
     }
-    if (threadIdx.x == 0) *status = bits;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        sum += __shfl_down_sync(0xffffffffu, sum, o);
+        mn = fminf(mn, __shfl_down_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        bad += __shfl_down_sync(0xffffffffu, bad, o);
+    }
+    __shared__ double ssum[8];
+    __shared__ float smn[8], smx[8];
+    __shared__ int sbad[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        ssum[warp] = sum;
+        smn[warp] = mn;
+        smx[warp] = mx;
+        sbad[warp] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double S = 0.0;
+    float MN = INFINITY, MX = -INFINITY;
+    long long BAD = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        S += ssum[w];
+        MN = fminf(MN, smn[w]);
+        MX = fmaxf(MX, smx[w]);
+        BAD += sbad[w];
+    }
+    PlaneParams q;
+    const double mean = S / (double)npix;
+    const double tc = centre_given ? tc_given : mean;
+    double R = fmax((double)MX - tc, tc - (double)MN);
+    int mode = 0;
+    int flags = 0;
+    if (BAD > 0) {
+        mode = 1;
+        flags |= 0x2;
+    }
+    if (!(R > 0.0)) {
+        mode = 1;
+        R = 1.0;
+    }
+    const double s2 = isinf(sigma_r) ? 0.0 : (R / sigma_r) * (R / sigma_r);
+    // power-of-two scale keeping E * 2^e0 >= 2^-120 at u = 1
+    const double log2e = 1.4426950408889634;
+    const double e0 = fmax(0.0, ceil(0.5 * s2 * log2e - 120.0));
+    // largest channel magnitude: beta_k max_u E u^k (log2), times the filter gain and the sums' growth
+    double top = 0.0, lb = 0.0;  // lb = log2 beta_k
+    for (int k = 1; k < K; ++k) {
+        lb += (k == 1) ? 0.0 : log2(s2 / (double)k);
+        const double u2 = s2 > 0.0 ? fmin(1.0, (double)k / s2) : 1.0;
+        const double v = lb - 0.5 * s2 * u2 * log2e + 0.5 * (double)k * log2(u2);
+        top = fmax(top, v);
+    }
+    const double gain = 2.0 * log2(2.6 * sigma_s + 2.0);
+    if (mode == 0 && (0.25 * s2 * log2e > 120.0 || e0 + top + gain + 2.0 * log2((double)K) > 124.0)) flags |= 0x4;
+    q.tc = (float)tc;
+    q.invR = (float)(1.0 / R);
+    q.half_s2 = (float)(0.5 * s2);
+    q.s2 = (float)s2;
+    q.R = (float)R;
+    q.escale = (float)exp2(e0);
+    q.mode = mode;
+    q.pad0 = flags;
+    q.tc_d = tc;
+    q.R_d = R;
+    double b = 1.0;
+    for (int m = 0; m < KMAX; ++m) {
+        if (m == 0) {
+            q.beta[0] = 1.f;
+        } else {
+            b = (m == 1) ? 1.0 : b * s2 / (double)m;  // beta_m = s^{2(m-1)} / m!
+            q.beta[m] = (m < K) ? (float)b : 0.f;
+        }
+    }
+    pp[c] = q;
+}
+
+// One thread: OR the planes' flags into the status word (written fresh each call).
+__global__ void stats_status(const PlaneParams *__restrict__ pp, int planes, uint32_t *__restrict__ status)
+{
+    uint32_t bits = 0;
+    for (int c = 0; c < planes; ++c) bits |= (uint32_t)pp[c].pad0;
+    *status = bits;
 }
 
 // ------------------------------------------------------------------ row pass
@@ -336,7 +382,7 @@ struct RowArgs {
     int H, W, pitch, Wp, K, T;  // T: threads per row (power of two, 8..512)
 };
 
-// Load one chunk of the row and form u and E (zero beyond the row end).
+// Load one chunk of the row and form u and Phi_0 (zero beyond the row end).
 template <int C>
 __device__ __forceinline__ void load_row_chunk(const RowArgs &a, int plane, int row, bool rv, int x0,
                                                const PlaneParams &P, float (&u)[C], float (&phi)[C])
@@ -362,7 +408,7 @@ __device__ __forceinline__ void load_row_chunk(const RowArgs &a, int plane, int 
         const bool in = rv && (x0 + j < a.W);
         const float uu = (v[j] - P.tc) * P.invR;
         u[j] = in ? uu : 0.f;
-        phi[j] = in ? expf(-P.half_s2 * uu * uu) : 0.f;
+        phi[j] = in ? envelope(P, uu) : 0.f;
     }
 }
 
@@ -385,14 +431,17 @@ __device__ __forceinline__ void store_row_chunk(const RowArgs &a, int plane, int
 }
 
 // grid (ceil(H / rows_per_cta), planes); block = max(T, 256) threads.
+// Thread t of a row owns samples [t*C, (t+1)*C).  Carries: Kogge-Stone
+// inside each warp (shuffles), then one warp combines the warp totals of
+// each row sequentially (one lane per row x pole x direction).
 template <int C>
 __global__ void __launch_bounds__(512) row_iir(RowArgs a, IIRCoef cf)
 {
-    // cross-warp totals: [parity][slot = r_local * wpr + warp_in_row][pole] (cr, ci, ar, ai)
-    __shared__ float4 tot[2][16][NP];
+    __shared__ float4 wt[16][NP];    // warp totals [warp slot][pole] (causal re, im, anticausal re, im)
+    __shared__ float4 wcar[16][NP];  // incoming carries of each warp
     const int T = a.T;
     const int tid = threadIdx.x;
-    const int lane = tid & 31;
+    const int lane = tid & 31, warp = tid >> 5;
     const int plane = blockIdx.y;
     const int rows_per_cta = blockDim.x / T;
     const int r_local = tid / T;
@@ -403,19 +452,13 @@ __global__ void __launch_bounds__(512) row_iir(RowArgs a, IIRCoef cf)
     const int L = T < 32 ? T : 32;  // segment width inside a warp
     const int ls = lane & (L - 1);
     const int wpr = T >> 5;         // warps per row (0 if T < 32)
-    const int wr = t >> 5;          // warp index inside the row
     const int x0 = t * C;
-    const int mode = P.mode;
+    if (P.mode != 0) return;  // copy mode: the column pass copies f
 
     float u[C], phi[C];
     load_row_chunk<C>(a, plane, row, rv, x0, P, u, phi);
 
-    if (mode != 0) {
-        // copy mode: the column pass copies f; nothing to filter.
-        return;
-    }
-
-    // per-thread powers for the cross-warp carries: p^{C ls} and p^{C (31 - ls)}
+    // p^{C ls} and p^{C (31 - ls)}: carry of the previous / next warps through this warp's chunks
     float qcr[NP], qci[NP], qar[NP], qai[NP];
 #pragma unroll
     for (int m = 0; m < NP; ++m) {
@@ -433,7 +476,6 @@ __global__ void __launch_bounds__(512) row_iir(RowArgs a, IIRCoef cf)
         float er[NP], ei[NP], sr[NP], si[NP];
         chunk_local<C>(phi, y, er, ei, sr, si, cf);
 
-        // segment scan across the T chunks of the row
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
             const int d = 1 << i;
@@ -461,45 +503,49 @@ __global__ void __launch_bounds__(512) row_iir(RowArgs a, IIRCoef cf)
             ai[m] = ls < L - 1 ? vi : 0.f;
         }
         if (wpr > 1) {
-            const int par = k & 1;
-            const int slot = r_local * wpr + wr;
             if (lane == 31) {
 #pragma unroll
                 for (int m = 0; m < NP; ++m) {
-                    tot[par][slot][m].x = er[m];
-                    tot[par][slot][m].y = ei[m];
+                    wt[warp][m].x = er[m];
+                    wt[warp][m].y = ei[m];
                 }
             }
             if (lane == 0) {
 #pragma unroll
                 for (int m = 0; m < NP; ++m) {
-                    tot[par][slot][m].z = sr[m];
-                    tot[par][slot][m].w = si[m];
+                    wt[warp][m].z = sr[m];
+                    wt[warp][m].w = si[m];
+                }
+            }
+            __syncthreads();
+            if (warp == 0 && lane < rows_per_cta * 4) {
+                // lane = row * 4 + (direction * 2 + pole)
+                const int rr = lane >> 2, dir = (lane >> 1) & 1, m = lane & 1;
+                const float p32r = cf.Pr[m][5], p32i = cf.Pi[m][5];
+                float accr = 0.f, acci = 0.f;
+                for (int s = 0; s < wpr; ++s) {
+                    const int w = dir == 0 ? s : wpr - 1 - s;
+                    const int slot = rr * wpr + w;
+                    const float4 tt = wt[slot][m];
+                    if (dir == 0) {
+                        wcar[slot][m].x = accr;
+                        wcar[slot][m].y = acci;
+                    } else {
+                        wcar[slot][m].z = accr;
+                        wcar[slot][m].w = acci;
+                    }
+                    float nr, ni;
+                    cmul(nr, ni, p32r, p32i, accr, acci);
+                    accr = nr + (dir == 0 ? tt.x : tt.z);
+                    acci = ni + (dir == 0 ? tt.y : tt.w);
                 }
             }
             __syncthreads();
 #pragma unroll
             for (int m = 0; m < NP; ++m) {
-                // P^32 = table index 5
-                const float p32r = cf.Pr[m][5], p32i = cf.Pi[m][5];
-                float Cr = 0.f, Ci = 0.f;
-                for (int w = 0; w < wr; ++w) {
-                    const float4 tt = tot[par][r_local * wpr + w][m];
-                    float nr, ni;
-                    cmul(nr, ni, p32r, p32i, Cr, Ci);
-                    Cr = nr + tt.x;
-                    Ci = ni + tt.y;
-                }
-                float Ar = 0.f, Ai = 0.f;
-                for (int w = wpr - 1; w > wr; --w) {
-                    const float4 tt = tot[par][r_local * wpr + w][m];
-                    float nr, ni;
-                    cmul(nr, ni, p32r, p32i, Ar, Ai);
-                    Ar = nr + tt.z;
-                    Ai = ni + tt.w;
-                }
-                cmadd(cr[m], ci[m], qcr[m], qci[m], Cr, Ci);
-                cmadd(ar[m], ai[m], qar[m], qai[m], Ar, Ai);
+                const float4 cw = wcar[warp][m];
+                cmadd(cr[m], ci[m], qcr[m], qci[m], cw.x, cw.y);
+                cmadd(ar[m], ai[m], qar[m], qai[m], cw.z, cw.w);
             }
         }
         chunk_correct<C>(y, cr, ci, ar, ai, cf);
@@ -528,7 +574,6 @@ __global__ void __launch_bounds__(512) row_fir(RowArgs a, FIRCoef g)
 
     float u[C], phi[C];
     load_row_chunk<C>(a, plane, row, rv, x0, P, u, phi);
-    // zero both halos of both parity buffers
     for (int i = tid; i < 2 * rows_per_cta * 2 * WH; i += blockDim.x) {
         const int par = i / (rows_per_cta * 2 * WH);
         const int rem = i % (rows_per_cta * 2 * WH);
@@ -574,24 +619,7 @@ struct ColArgs {
     int H, W, pitch, Wp, K, N;
 };
 
-// Per-pixel combine state: descending m, d = d u + v; v = v u + Psi_m;
-// q = q u + Psi_m for 1 <= m <= N.
-template <int C>
-__device__ __forceinline__ void combine_step(int m, int N, const float (&u)[C], float (&q)[C], float (&v)[C],
-                                             float (&d)[C], const float (&psi)[C])
-{
-    if (m >= 1 && m <= N) {
-#pragma unroll
-        for (int j = 0; j < C; ++j) q[j] = fmaf(u[j], q[j], psi[j]);
-    }
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-        d[j] = fmaf(u[j], d[j], v[j]);
-        v[j] = fmaf(u[j], v[j], psi[j]);
-    }
-}
-
-__device__ __forceinline__ float finish_pixel(const PlaneParams &P, float f, float u, float q, float d, float psi0,
+__device__ __forceinline__ float finish_pixel(const PlaneParams &P, float f, float u, float p, float q, float psi0,
                                               bool &nonpos)
 {
     if (P.mode != 0) return f;
@@ -600,18 +628,41 @@ __device__ __forceinline__ float finish_pixel(const PlaneParams &P, float f, flo
         nonpos = true;
         return __int_as_float(0x7fc00000);
     }
-    return fmaf(P.R, __fdiv_rn(d, Q), P.tc);
+    return fmaf(P.R, __fdiv_rn(p, Q), P.tc);
 }
 
+constexpr int COL_ROWS = 512;                          // rows per CTA in the recursive column pass
+constexpr int COL_TILE_FLOATS = (COL_ROWS + COL_ROWS / 16) * 8;  // padded [row][8 cols] tile
+
+// Shared-memory tile row r of the 8-column strip starts at (r + r/16) * 8
+// floats: a gap of 8 floats after every 16 rows puts the four chunks a warp
+// reads at once on disjoint banks.
+__device__ __forceinline__ int tile_off(int r) { return (r + (r >> 4)) << 3; }
+
+__device__ __forceinline__ void cp_async16(float *dst, const float *src, bool valid)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // Column pass for the recursive filter.  A cluster of CL CTAs covers the
-// full height of an 8-column strip; CTA rank r owns rows [r*32*C, (r+1)*32*C).
-// Thread (warp w, lane l): column l%8 of the strip, chunk 4w + l/8 of the CTA.
+// full height of an 8-column strip; CTA rank r owns rows [r*512, (r+1)*512).
+// Thread (warp w, lane l): column l%8 of the strip, chunk 4w + l/8 (16 rows).
+// Each channel's 8 x 512 tile is staged in shared memory by cp.async, one
+// channel ahead.  Carries: shuffles between the 4 chunks of a warp, then
+// warp 0 combines the 8 warp totals of each column and the CTA totals of the
+// cluster (DSMEM) with one lane per column x pole x direction.
 // grid (strips * CL, planes), block 256, cluster (CL, 1, 1).
 template <int C, bool CLUSTER>
 __global__ void __launch_bounds__(256, 2) col_iir(ColArgs a, IIRCoef cf)
 {
-    __shared__ float4 wt[2][8][8][NP];  // [parity][warp][col][pole] (causal total, anticausal total)
-    __shared__ float4 ct[2][8][NP];     // [parity][col][pole] CTA totals
+    extern __shared__ __align__(16) float tiles[];  // [2][COL_TILE_FLOATS]
+    __shared__ float4 wt[8][8][NP];    // [warp][col][pole] warp totals (causal re, im, anticausal re, im)
+    __shared__ float4 wcar[8][8][NP];  // [warp][col][pole] incoming carries of each warp
+    __shared__ float4 ct[8][NP];       // [col][pole] CTA totals, read by the other CTAs of the cluster
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int col = lane & 7, l4 = lane >> 3;
@@ -625,11 +676,28 @@ __global__ void __launch_bounds__(256, 2) col_iir(ColArgs a, IIRCoef cf)
     const int strip = blockIdx.x / CL;
     const int x = strip * 8 + col;
     const int chunk_cta = warp * 4 + l4;
-    const int row0 = (rank * 32 + chunk_cta) * C;
+    const int rbase = rank * COL_ROWS;
+    const int row0 = rbase + chunk_cta * C;
     const PlaneParams &P = a.pp[plane];
+    const bool filt = (P.mode == 0);
+    const float *wsp = a.ws + (size_t)plane * a.K * a.H * a.Wp + strip * 8;
 
-    // input pixels of the chunk (for u) and the combine state
-    float u[C], q[C], v[C], d[C];
+    // tile copy: 512 rows x two 16-byte halves; thread copies 4 of them
+    auto issue_tile = [&](int k, int buf) {
+        const float *src = wsp + (size_t)k * a.H * a.Wp;
+        float *dst = tiles + buf * COL_TILE_FLOATS;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int idx = tid + i * 256;
+            const int r = idx >> 1, half = idx & 1;
+            const int gr = rbase + r;
+            const bool ok = filt && gr < a.H;
+            cp_async16(dst + tile_off(r) + half * 4, src + (size_t)(ok ? gr : 0) * a.Wp + half * 4, ok);
+        }
+        cp_async_commit();
+    };
+
+    float u[C], p[C], q[C];
     const float *fcol = a.f + (size_t)plane * a.H * a.pitch;
 #pragma unroll
     for (int j = 0; j < C; ++j) {
@@ -637,35 +705,26 @@ __global__ void __launch_bounds__(256, 2) col_iir(ColArgs a, IIRCoef cf)
         const bool in = (r < a.H) && (x < a.W);
         const float fv = in ? __ldg(fcol + (size_t)r * a.pitch + x) : 0.f;
         u[j] = (fv - P.tc) * P.invR;
-        q[j] = v[j] = d[j] = 0.f;
+        p[j] = q[j] = 0.f;
     }
-    const bool filt = (P.mode == 0);
-
-    // per-thread powers p^{C l4}, p^{C (3 - l4)} and, for the cluster carry,
-    // p^{C 4 warp}, p^{C 4 (7 - warp)}
     float qcr[NP], qci[NP], qar[NP], qai[NP];
-    float wcr[NP], wci[NP], war[NP], wai[NP];
 #pragma unroll
     for (int m = 0; m < NP; ++m) {
         cpow_tab(qcr[m], qci[m], cf, m, l4);
         cpow_tab(qar[m], qai[m], cf, m, 3 - l4);
-        if (CLUSTER) {
-            cpow_tab(wcr[m], wci[m], cf, m, 4 * warp);
-            cpow_tab(war[m], wai[m], cf, m, 4 * (7 - warp));
-        }
     }
 
+    issue_tile(a.K - 1, (a.K - 1) & 1);
     float psi0[C];
-    const float *wsp = a.ws + (size_t)plane * a.K * a.H * a.Wp;
 #pragma unroll 1
     for (int k = a.K - 1; k >= 0; --k) {
+        cp_async_wait_all();
+        __syncthreads();  // tile k visible; every thread is done with the tile of channel k+1
+        if (k > 0) issue_tile(k - 1, (k - 1) & 1);
         float xin[C];
-        const float *src = wsp + (size_t)k * a.H * a.Wp + x;
+        const float *tl = tiles + (k & 1) * COL_TILE_FLOATS + col;
 #pragma unroll
-        for (int j = 0; j < C; ++j) {
-            const int r = row0 + j;
-            xin[j] = (filt && r < a.H) ? __ldg(src + (size_t)r * a.Wp) : 0.f;
-        }
+        for (int j = 0; j < C; ++j) xin[j] = tl[tile_off(chunk_cta * C + j)];
         float y[C];
         float er[NP], ei[NP], sr[NP], si[NP];
         chunk_local<C>(xin, y, er, ei, sr, si, cf);
@@ -696,111 +755,95 @@ __global__ void __launch_bounds__(256, 2) col_iir(ColArgs a, IIRCoef cf)
             ar[m] = l4 < 3 ? vr : 0.f;
             ai[m] = l4 < 3 ? vi : 0.f;
         }
-        // level 2: the 8 warps of the CTA
-        const int par = k & 1;
         if (l4 == 3) {
 #pragma unroll
             for (int m = 0; m < NP; ++m) {
-                wt[par][warp][col][m].x = er[m];
-                wt[par][warp][col][m].y = ei[m];
+                wt[warp][col][m].x = er[m];
+                wt[warp][col][m].y = ei[m];
             }
         }
         if (l4 == 0) {
 #pragma unroll
             for (int m = 0; m < NP; ++m) {
-                wt[par][warp][col][m].z = sr[m];
-                wt[par][warp][col][m].w = si[m];
+                wt[warp][col][m].z = sr[m];
+                wt[warp][col][m].w = si[m];
             }
         }
         __syncthreads();
-        float Cwr[NP], Cwi[NP], Awr[NP], Awi[NP];
+        // level 2 (warp 0): lane = (dir * 2 + pole) * 8 + column; the
+        // exclusive carry of each warp goes straight to wcar
+        const int gcol = lane & 7, gq = lane >> 3, gm = gq & 1, gdir = gq >> 1;
+        if (warp == 0) {
+            const float p4r = cf.Pr[gm][2], p4i = cf.Pi[gm][2];
+            float totr = 0.f, toti = 0.f;
 #pragma unroll
-        for (int m = 0; m < NP; ++m) {
-            const float p4r = cf.Pr[m][2], p4i = cf.Pi[m][2];
-            float Cr = 0.f, Ci = 0.f;
-            for (int w = 0; w < warp; ++w) {
-                const float4 tt = wt[par][w][col][m];
+            for (int s = 0; s < 8; ++s) {
+                const int w = gdir == 0 ? s : 7 - s;
+                const float4 tt = wt[w][gcol][gm];
+                float *dst = gdir == 0 ? &wcar[w][gcol][gm].x : &wcar[w][gcol][gm].z;
+                dst[0] = totr;
+                dst[1] = toti;
                 float nr, ni;
-                cmul(nr, ni, p4r, p4i, Cr, Ci);
-                Cr = nr + tt.x;
-                Ci = ni + tt.y;
+                cmul(nr, ni, p4r, p4i, totr, toti);
+                totr = nr + (gdir == 0 ? tt.x : tt.z);
+                toti = ni + (gdir == 0 ? tt.y : tt.w);
             }
-            float Ar = 0.f, Ai = 0.f;
-            for (int w = 7; w > warp; --w) {
-                const float4 tt = wt[par][w][col][m];
-                float nr, ni;
-                cmul(nr, ni, p4r, p4i, Ar, Ai);
-                Ar = nr + tt.z;
-                Ai = ni + tt.w;
+            if (CLUSTER) {
+                float *dst = gdir == 0 ? &ct[gcol][gm].x : &ct[gcol][gm].z;
+                dst[0] = totr;
+                dst[1] = toti;
             }
-            Cwr[m] = Cr;
-            Cwi[m] = Ci;
-            Awr[m] = Ar;
-            Awi[m] = Ai;
         }
         if (CLUSTER) {
-            // CTA totals: causal from warp 7 (its l4 == 3 lanes), anticausal from warp 0 (l4 == 0)
-            if (warp == 7 && l4 == 3) {
-#pragma unroll
-                for (int m = 0; m < NP; ++m) {
-                    float tr = er[m], ti = ei[m];
-                    cmadd(tr, ti, cf.Pr[m][2], cf.Pi[m][2], Cwr[m], Cwi[m]);
-                    ct[par][col][m].x = tr;
-                    ct[par][col][m].y = ti;
-                }
-            }
-            if (warp == 0 && l4 == 0) {
-#pragma unroll
-                for (int m = 0; m < NP; ++m) {
-                    float tr = sr[m], ti = si[m];
-                    cmadd(tr, ti, cf.Pr[m][2], cf.Pi[m][2], Awr[m], Awi[m]);
-                    ct[par][col][m].z = tr;
-                    ct[par][col][m].w = ti;
-                }
-            }
             cg::cluster_group cl = cg::this_cluster();
-            cl.sync();
-            // level 3: CTAs of the cluster (P^32 = table index 5)
-#pragma unroll
-            for (int m = 0; m < NP; ++m) {
-                const float p32r = cf.Pr[m][5], p32i = cf.Pi[m][5];
+            cl.sync();  // CTA totals of the whole cluster written
+            if (warp == 0) {
+                // level 3: carry entering this CTA from the other CTAs of the column
+                const float p32r = cf.Pr[gm][5], p32i = cf.Pi[gm][5];
                 float Cr = 0.f, Ci = 0.f;
-                for (int r = 0; r < rank; ++r) {
-                    const float4 *rem = cl.map_shared_rank(&ct[par][col][m], r);
-                    const float4 tt = *rem;
+                const int nsteps = gdir == 0 ? rank : CL - 1 - rank;
+                for (int s = 0; s < nsteps; ++s) {
+                    const int r = gdir == 0 ? s : CL - 1 - s;
+                    const float4 tt = *cl.map_shared_rank(&ct[gcol][gm], r);
                     float nr, ni;
                     cmul(nr, ni, p32r, p32i, Cr, Ci);
-                    Cr = nr + tt.x;
-                    Ci = ni + tt.y;
+                    Cr = nr + (gdir == 0 ? tt.x : tt.z);
+                    Ci = ni + (gdir == 0 ? tt.y : tt.w);
                 }
-                float Ar = 0.f, Ai = 0.f;
-                for (int r = CL - 1; r > rank; --r) {
-                    const float4 *rem = cl.map_shared_rank(&ct[par][col][m], r);
-                    const float4 tt = *rem;
+                // propagate it through the warps before (causal) / after (anticausal) each warp
+                const float p4r = cf.Pr[gm][2], p4i = cf.Pi[gm][2];
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    const int w = gdir == 0 ? s : 7 - s;
+                    float *dst = gdir == 0 ? &wcar[w][gcol][gm].x : &wcar[w][gcol][gm].z;
+                    dst[0] += Cr;
+                    dst[1] += Ci;
                     float nr, ni;
-                    cmul(nr, ni, p32r, p32i, Ar, Ai);
-                    Ar = nr + tt.z;
-                    Ai = ni + tt.w;
+                    cmul(nr, ni, p4r, p4i, Cr, Ci);
+                    Cr = nr;
+                    Ci = ni;
                 }
-                // propagate the CTA carry through the 4*warp chunks before this warp
-                cmadd(Cwr[m], Cwi[m], wcr[m], wci[m], Cr, Ci);
-                cmadd(Awr[m], Awi[m], war[m], wai[m], Ar, Ai);
             }
         }
+        __syncthreads();
 #pragma unroll
         for (int m = 0; m < NP; ++m) {
-            cmadd(cr[m], ci[m], qcr[m], qci[m], Cwr[m], Cwi[m]);
-            cmadd(ar[m], ai[m], qar[m], qai[m], Awr[m], Awi[m]);
+            const float4 cw = wcar[warp][col][m];
+            cmadd(cr[m], ci[m], qcr[m], qci[m], cw.x, cw.y);
+            cmadd(ar[m], ai[m], qar[m], qai[m], cw.z, cw.w);
         }
         chunk_correct<C>(y, cr, ci, ar, ai, cf);
         if (k == 0) {
 #pragma unroll
             for (int j = 0; j < C; ++j) psi0[j] = y[j];
-            // P~ needs the final derivative step only
-#pragma unroll
-            for (int j = 0; j < C; ++j) d[j] = fmaf(u[j], d[j], v[j]);
         } else {
-            combine_step<C>(k, a.N, u, q, v, d, y);
+            const float mk = (float)k;
+            if (k <= a.N) {
+#pragma unroll
+                for (int j = 0; j < C; ++j) q[j] = fmaf(u[j], q[j], y[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < C; ++j) p[j] = fmaf(u[j], p[j], mk * y[j]);
         }
     }
     if (CLUSTER) {
@@ -814,7 +857,7 @@ __global__ void __launch_bounds__(256, 2) col_iir(ColArgs a, IIRCoef cf)
         const int r = row0 + j;
         if (r < a.H && x < a.W) {
             const float fv = filt ? 0.f : __ldg(fcol + (size_t)r * a.pitch + x);
-            ycol[(size_t)r * a.pitch + x] = finish_pixel(P, fv, u[j], q[j], d[j], psi0[j], nonpos);
+            ycol[(size_t)r * a.pitch + x] = finish_pixel(P, fv, u[j], p[j], q[j], psi0[j], nonpos);
         }
     }
     if (__any_sync(0xffffffffu, nonpos) && lane == 0) atomicOr(a.status, 0x1u);
@@ -834,15 +877,15 @@ __global__ void __launch_bounds__(256) col_fir(ColArgs a, FIRCoef g)
     const int rbase = blockIdx.y * TH;
     const PlaneParams &P = a.pp[plane];
     const bool filt = (P.mode == 0);
-    float u[RPT], q[RPT], v[RPT], d[RPT], fv[RPT], psi0[RPT];
+    float u[RPT], p[RPT], q[RPT], psi0[RPT];
     const float *fp = a.f + (size_t)plane * a.H * a.pitch;
 #pragma unroll
     for (int j = 0; j < RPT; ++j) {
         const int r = rbase + ty * RPT + j;
         const bool in = (r < a.H) && (x < a.W);
-        fv[j] = in ? __ldg(fp + (size_t)r * a.pitch + x) : 0.f;
-        u[j] = (fv[j] - P.tc) * P.invR;
-        q[j] = v[j] = d[j] = psi0[j] = 0.f;
+        const float fv = in ? __ldg(fp + (size_t)r * a.pitch + x) : 0.f;
+        u[j] = (fv - P.tc) * P.invR;
+        p[j] = q[j] = psi0[j] = 0.f;
     }
     const float *wsp = a.ws + (size_t)plane * a.K * a.H * a.Wp;
     if (filt) {
@@ -868,12 +911,15 @@ __global__ void __launch_bounds__(256) col_fir(ColArgs a, FIRCoef g)
             }
             if (k == 0) {
 #pragma unroll
-                for (int j = 0; j < RPT; ++j) {
-                    psi0[j] = y[j];
-                    d[j] = fmaf(u[j], d[j], v[j]);
-                }
+                for (int j = 0; j < RPT; ++j) psi0[j] = y[j];
             } else {
-                combine_step<RPT>(k, a.N, u, q, v, d, y);
+                const float mk = (float)k;
+                if (k <= a.N) {
+#pragma unroll
+                    for (int j = 0; j < RPT; ++j) q[j] = fmaf(u[j], q[j], y[j]);
+                }
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) p[j] = fmaf(u[j], p[j], mk * y[j]);
             }
         }
     }
@@ -882,7 +928,10 @@ __global__ void __launch_bounds__(256) col_fir(ColArgs a, FIRCoef g)
 #pragma unroll
     for (int j = 0; j < RPT; ++j) {
         const int r = rbase + ty * RPT + j;
-        if (r < a.H && x < a.W) yp[(size_t)r * a.pitch + x] = finish_pixel(P, fv[j], u[j], q[j], d[j], psi0[j], nonpos);
+        if (r < a.H && x < a.W) {
+            const float fv = filt ? 0.f : __ldg(fp + (size_t)r * a.pitch + x);
+            yp[(size_t)r * a.pitch + x] = finish_pixel(P, fv, u[j], p[j], q[j], psi0[j], nonpos);
+        }
     }
     if (__any_sync(0xffffffffu, nonpos) && tx == 0) atomicOr(a.status, 0x1u);
 }

@@ -27,11 +27,17 @@ def bf():
     return m
 
 
-def run_gpu(bf, img, ss, sr, N, spatial, **kw):
+def run_gpu(bf, img, ss, sr, N, spatial, status=False, **kw):
     x = torch.from_numpy(np.ascontiguousarray(img, dtype=np.float32)).cuda()
-    y = bf.bilateral_gp(x, ss, sr, N, spatial, **kw)
-    torch.cuda.synchronize()
-    return y.cpu().numpy().astype(np.float64)
+    H, W = x.shape[-2], x.shape[-1]
+    planes = max(1, x.numel() // (H * W))
+    o = bf.make_opts(N, spatial, kw.get("t_c"), kw.get("fir_halfwidth", 0))
+    need = bf.bf_gp_workspace_size(planes, H, W, ss, o)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    y = bf.bilateral_gp(x, ss, sr, N, spatial, ws=ws, **kw)
+    bits = bf.bf_gp_get_device_status(ws.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    out = y.cpu().numpy().astype(np.float64)
+    return (out, bits) if status else out
 
 
 def check(gpu, ref, tol=TOL):
@@ -99,7 +105,26 @@ def test_iir_long_rows(bf, W):
 def test_config2_sweep(bf, ss, sr, N, spatial):
     img = synthetic.config2_image()
     ref = oracle.gp_bf(img.astype(np.float64), ss, sr, N, spatial)
-    check(run_gpu(bf, img, ss, sr, N, spatial), ref)
+    out, bits = run_gpu(bf, img, ss, sr, N, spatial, status=True)
+    assert bits == 0
+    check(out, ref)
+
+
+def test_large_s2_stays_in_fp32_range(bf):
+    """(R / sigma_r)^2 = 234 on the 1024^2 image (R = 153, sigma_r = 10): exp(-s^2 u^2 / 2)
+    would underflow FP32 at |u| = 1 without the common power-of-two channel scale."""
+    img = synthetic.config2_image()
+    for ss, sp in ((2.0, "fir"), (10.0, "iir")):
+        out, bits = run_gpu(bf, img, ss, 10.0, 20, sp, status=True)
+        assert bits == 0
+        check(out, oracle.gp_bf(img.astype(np.float64), ss, 10.0, 20, sp))
+
+
+def test_range_flag_beyond_fp32(bf):
+    img = np.zeros((64, 64), np.float32)
+    img[:, 32:] = 255.0
+    _, bits = run_gpu(bf, img, 3.0, 3.0, 20, "fir", status=True)  # s^2 = (127.5 / 3)^2 = 1806
+    assert bits & bf.BF_DEV_RANGE
 
 
 # ---------------------------------------------------------------- config 3
