@@ -59,7 +59,7 @@ def _load():
     i, d = ctypes.c_int, ctypes.c_double
     lib.bfo_direct.argtypes = [dp, i, i, d, d, i, i, i, i, i, dp]
     lib.bfo_direct.restype = None
-    lib.bfo_gp.argtypes = [dp, i, i, d, d, i, d, i, i, i, i, i, i, i, dp]
+    lib.bfo_gp.argtypes = [dp, i, i, d, d, i, d, i, i, i, i, i, i, i, dp, dp]
     lib.bfo_gp.restype = i
     lib.bfo_line_filter.argtypes = [dp, i, i, d, i, i, i, dp]
     lib.bfo_line_filter.restype = None
@@ -121,13 +121,17 @@ def mean(f) -> float:
     return float(_load().bfo_mean(_ptr(f), f.size))
 
 
-def gp_bf(f, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop=None, round_coef_f32=False):
+def gp_bf(f, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop=None, round_coef_f32=False,
+          return_kappa=False):
     """O2: Algorithm 1 (GPF) in FP64.
 
     spatial: 'fir' (window sum of Eq. (8), zero extension) or 'iir' (Deriche's
     recursive Gaussian, causal + anticausal).  t_c: centre (None = image mean,
     the algorithm's first step).  crop: (r0, r1, c0, c1) output region; the
     operator still reads every sample it needs from the full image.
+    return_kappa: also return kappa = sigma_r (sum|p_n| + |P/Q| sum|q_n|) / |Q|,
+    the bound on how far relative errors eps in the terms of Eqs. (9)-(10) can
+    move the result (error <= kappa * eps); inf where Q <= 0.
     """
     f = np.ascontiguousarray(f, dtype=np.float64)
     H, W = f.shape
@@ -135,12 +139,14 @@ def gp_bf(f, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop=None, ro
     w = window(sigma_s) if w is None else int(w)
     r0, r1, c0, c1 = _crop(crop, H, W)
     out = np.empty((r1 - r0, c1 - c0), np.float64)
+    kap = np.empty_like(out) if return_kappa else None
     tc = float("nan") if t_c is None else float(t_c)
     rc = _load().bfo_gp(_ptr(f), H, W, float(sigma_s), float(sigma_r), int(N), tc, sp, w,
-                        1 if round_coef_f32 else 0, r0, r1, c0, c1, _ptr(out))
+                        1 if round_coef_f32 else 0, r0, r1, c0, c1, _ptr(out),
+                        _ptr(kap) if kap is not None else None)
     if rc != 0:
         raise MemoryError("oracle allocation failed")
-    return out
+    return (out, kap) if return_kappa else out
 
 
 def line_filter(x, sigma_s, spatial="fir", w=None, round_coef_f32=False):

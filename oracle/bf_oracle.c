@@ -269,12 +269,19 @@ static void apply_S(const spatial_op *S, const double *a, int W, int ylo, int yh
  *
  * sigma_r = +inf is taken as its limit: every G_n, n >= 1, vanishes and the
  * result is S(h)/S(1) + t_c, the normalised spatial filter.  A pixel whose
- * denominator Q is not positive (possible only for odd N, where the truncated
- * exponential has a real root) is returned as NaN.
+ * denominator Q is not positive is returned as NaN (with the window sum this
+ * needs odd N, where the truncated exponential has a real root; the recursive
+ * filter's small negative tail can also do it when (R / sigma_r)^2 is large).
+ *
+ * kappa (may be NULL): per-pixel sensitivity of the result to relative
+ * perturbations of the individual terms of Eqs. (9)-(10),
+ *     kappa = sigma_r (sum_n |p_n| + |P / Q| sum_n |q_n|) / |Q|,
+ * with p_n, q_n the n-th terms of P and Q: a relative error eps in every
+ * term moves the result by at most kappa * eps.
  */
 int bfo_gp(const double *f, int H, int W, double sigma_s, double sigma_r, int N,
            double t_c, int spatial, int w, int round_f32,
-           int r0, int r1, int c0, int c1, double *out)
+           int r0, int r1, int c0, int c1, double *out, double *kappa)
 {
     const int cw = c1 - c0, ch = r1 - r0;
     const long ncrop = (long)cw * ch;
@@ -307,8 +314,11 @@ int bfo_gp(const double *f, int H, int W, double sigma_s, double sigma_r, int N,
     double *Hc = malloc(sizeof(double) * (size_t)ncrop);
     double *P = calloc((size_t)ncrop, sizeof(double));
     double *Q = calloc((size_t)ncrop, sizeof(double));
-    if (!F || !Hs || !rowtmp || !Fbar || !G || !Hc || !P || !Q) {
-        free(F); free(Hs); free(rowtmp); free(Fbar); free(G); free(Hc); free(P); free(Q); free(taps);
+    double *Pa = calloc((size_t)ncrop, sizeof(double));
+    double *Qa = calloc((size_t)ncrop, sizeof(double));
+    if (!F || !Hs || !rowtmp || !Fbar || !G || !Hc || !P || !Q || !Pa || !Qa) {
+        free(F); free(Hs); free(rowtmp); free(Fbar); free(G); free(Hc); free(P); free(Q); free(Pa); free(Qa);
+        free(taps);
         return -1;
     }
 
@@ -320,7 +330,10 @@ int bfo_gp(const double *f, int H, int W, double sigma_s, double sigma_r, int N,
         for (long i = 0; i < nreg; ++i) { F[i] = f[(long)ylo * W + i] - t_c; Hs[i] = 1.0; }
         apply_S(&S, F, W, ylo, yhi, r0, r1, c0, c1, rowtmp, P);
         apply_S(&S, Hs, W, ylo, yhi, r0, r1, c0, c1, rowtmp, Q);
-        for (long i = 0; i < ncrop; ++i) out[i] = P[i] / Q[i] + t_c;
+        for (long i = 0; i < ncrop; ++i) {
+            out[i] = P[i] / Q[i] + t_c;
+            if (kappa) kappa[i] = 2.0 * fabs(P[i] / Q[i]);
+        }
         goto done;
     }
 
@@ -342,21 +355,31 @@ int bfo_gp(const double *f, int H, int W, double sigma_s, double sigma_r, int N,
     double c = 1.0; /* 1/n! */
     for (int n = 0; n <= N; ++n) {
         /* Eq. (10): Q += G_n Fbar_n / n! */
-        for (long i = 0; i < ncrop; ++i) Q[i] += c * G[i] * Fbar[i];
+        for (long i = 0; i < ncrop; ++i) {
+            Q[i] += c * G[i] * Fbar[i];
+            Qa[i] += fabs(c * G[i] * Fbar[i]);
+        }
         /* F_{n+1} = H F_n, then Fbar_{n+1} */
 #pragma omp parallel for schedule(static)
         for (long i = 0; i < nreg; ++i) F[i] *= Hs[i];
         apply_S(&S, F, W, ylo, yhi, r0, r1, c0, c1, rowtmp, Fbar);
         /* Eq. (9) without the sigma_r factor: P += G_n Fbar_{n+1} / n! */
-        for (long i = 0; i < ncrop; ++i) P[i] += c * G[i] * Fbar[i];
+        for (long i = 0; i < ncrop; ++i) {
+            P[i] += c * G[i] * Fbar[i];
+            Pa[i] += fabs(c * G[i] * Fbar[i]);
+        }
         for (long i = 0; i < ncrop; ++i) G[i] *= Hc[i];
         c /= (double)(n + 1);
     }
     /* step 18: Eq. (11) with the sigma_r of Eq. (9), then undo the centring (Eq. (6)) */
-    for (long i = 0; i < ncrop; ++i) out[i] = Q[i] > 0.0 ? sigma_r * (P[i] / Q[i]) + t_c : NAN;
+    for (long i = 0; i < ncrop; ++i) {
+        out[i] = Q[i] > 0.0 ? sigma_r * (P[i] / Q[i]) + t_c : NAN;
+        if (kappa) kappa[i] = Q[i] > 0.0 ? sigma_r * (Pa[i] + fabs(P[i] / Q[i]) * Qa[i]) / Q[i] : INFINITY;
+    }
 
 done:
-    free(F); free(Hs); free(rowtmp); free(Fbar); free(G); free(Hc); free(P); free(Q); free(taps);
+    free(F); free(Hs); free(rowtmp); free(Fbar); free(G); free(Hc); free(P); free(Q); free(Pa); free(Qa);
+    free(taps);
     return 0;
 }
 

@@ -236,11 +236,11 @@ bf_status run_stats(const Call &c, int planes, int H, int W, int pitch, float si
         bf_gp_default_opts(&d);
         opts = &d;
     }
-    stats_partial<<<dim3(c.p.nblk, planes), 256, 0, c.s>>>(c.ra.f, H, W, pitch, c.p.rows_per_block, c.part);
+    stats_partial<<<dim3(c.p.nblk, planes), 256, 0, c.s>>>(c.ra.f, H, W, pitch, c.p.rows_per_block, c.part,
+                                                           c.status);
     stats_finalize<<<planes, 256, 0, c.s>>>(c.part, c.p.nblk, (long long)H * W,
                                             opts->centre == BF_CENTRE_GIVEN ? 1 : 0, opts->t_c, (double)sigma_r,
-                                            (double)sigma_s, c.p.K, c.pp);
-    stats_status<<<1, 1, 0, c.s>>>(c.pp, planes, c.status);
+                                            (double)sigma_s, c.p.K, c.pp, c.status);
     BF_CUDA(cudaGetLastError());
     return BF_OK;
 }

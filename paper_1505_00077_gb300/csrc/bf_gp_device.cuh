@@ -180,11 +180,14 @@ __device__ __forceinline__ float envelope(const PlaneParams &P, float u)
 
 // ------------------------------------------------------------------ stats
 
-// grid (nblk, planes), block 256.  Each block reduces a band of rows.
+// grid (nblk, planes), block 256.  Each block reduces a band of rows.  Block
+// (0, 0) also zeroes the status word of this call.
 __global__ void __launch_bounds__(256) stats_partial(const float *__restrict__ f, int H, int W, int pitch,
-                                                     int rows_per_block, StatPartial *__restrict__ part)
+                                                     int rows_per_block, StatPartial *__restrict__ part,
+                                                     uint32_t *__restrict__ status)
 {
     const int plane = blockIdx.y;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *status = 0u;
     const int r0 = blockIdx.x * rows_per_block;
     const int r1 = min(H, r0 + rows_per_block);
     float mn = INFINITY, mx = -INFINITY;
@@ -269,12 +272,23 @@ __global__ void __launch_bounds__(256) stats_partial(const float *__restrict__ f
     }
 }
 
+// 1/m, m = 0..KMAX (entry 0 unused): the beta recurrence multiplies instead of dividing.
+__constant__ double c_inv[KMAX + 1] = {
+    0.0, 1.0 / 1, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 5, 1.0 / 6, 1.0 / 7, 1.0 / 8, 1.0 / 9, 1.0 / 10, 1.0 / 11,
+    1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15, 1.0 / 16, 1.0 / 17, 1.0 / 18, 1.0 / 19, 1.0 / 20, 1.0 / 21, 1.0 / 22,
+    1.0 / 23, 1.0 / 24, 1.0 / 25, 1.0 / 26, 1.0 / 27, 1.0 / 28, 1.0 / 29, 1.0 / 30, 1.0 / 31, 1.0 / 32, 1.0 / 33,
+    1.0 / 34, 1.0 / 35, 1.0 / 36, 1.0 / 37, 1.0 / 38, 1.0 / 39, 1.0 / 40, 1.0 / 41, 1.0 / 42, 1.0 / 43, 1.0 / 44,
+    1.0 / 45, 1.0 / 46, 1.0 / 47, 1.0 / 48, 1.0 / 49, 1.0 / 50, 1.0 / 51, 1.0 / 52, 1.0 / 53, 1.0 / 54, 1.0 / 55,
+    1.0 / 56, 1.0 / 57, 1.0 / 58, 1.0 / 59, 1.0 / 60, 1.0 / 61, 1.0 / 62, 1.0 / 63, 1.0 / 64};
+
 // grid (planes), block 256.  Reduces one plane's partials (FP64) and writes
-// its PlaneParams; the status word is written by the stats_status kernel.
+// its PlaneParams: t_c, R, s^2, beta_k = s^{2(k-1)}/k! (thread k, FP64
+// product of s^2 / j), the common scale 2^e0 and the range flag.  ORs its
+// flags into the status word (zeroed by stats_partial of the same call).
 __global__ void __launch_bounds__(256) stats_finalize(const StatPartial *__restrict__ part, int nblk,
                                                       long long npix, int centre_given, double tc_given,
                                                       double sigma_r, double sigma_s, int K,
-                                                      PlaneParams *__restrict__ pp)
+                                                      PlaneParams *__restrict__ pp, uint32_t *__restrict__ status)
 {
     const int c = blockIdx.x;
     double sum = 0.0;
@@ -297,6 +311,9 @@ __global__ void __launch_bounds__(256) stats_finalize(const StatPartial *__restr
     __shared__ double ssum[8];
     __shared__ float smn[8], smx[8];
     __shared__ int sbad[8];
+    __shared__ double sh_tc, sh_R, sh_s2;
+    __shared__ int sh_mode;
+    __shared__ float stop[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
         ssum[warp] = sum;
@@ -305,72 +322,72 @@ __global__ void __launch_bounds__(256) stats_finalize(const StatPartial *__restr
         sbad[warp] = bad;
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    double S = 0.0;
-    float MN = INFINITY, MX = -INFINITY;
-    long long BAD = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        S += ssum[w];
-        MN = fminf(MN, smn[w]);
-        MX = fmaxf(MX, smx[w]);
-        BAD += sbad[w];
+    if (threadIdx.x == 0) {
+        double S = 0.0;
+        float MN = INFINITY, MX = -INFINITY;
+        long long BAD = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            S += ssum[w];
+            MN = fminf(MN, smn[w]);
+            MX = fmaxf(MX, smx[w]);
+            BAD += sbad[w];
+        }
+        const double tc = centre_given ? tc_given : S / (double)npix;
+        double R = fmax((double)MX - tc, tc - (double)MN);
+        int mode = BAD > 0 ? 2 : 0;  // 2: non-finite input (copy + flag)
+        if (!(R > 0.0)) {
+            mode = mode ? mode : 1;
+            R = 1.0;
+        }
+        sh_tc = tc;
+        sh_R = R;
+        sh_s2 = isinf(sigma_r) ? 0.0 : (R / sigma_r) * (R / sigma_r);
+        sh_mode = mode;
     }
-    PlaneParams q;
-    const double mean = S / (double)npix;
-    const double tc = centre_given ? tc_given : mean;
-    double R = fmax((double)MX - tc, tc - (double)MN);
-    int mode = 0;
-    int flags = 0;
-    if (BAD > 0) {
-        mode = 1;
-        flags |= 0x2;
-    }
-    if (!(R > 0.0)) {
-        mode = 1;
-        R = 1.0;
-    }
-    const double s2 = isinf(sigma_r) ? 0.0 : (R / sigma_r) * (R / sigma_r);
-    // power-of-two scale keeping E * 2^e0 >= 2^-120 at u = 1
-    const double log2e = 1.4426950408889634;
-    const double e0 = fmax(0.0, ceil(0.5 * s2 * log2e - 120.0));
-    // largest channel magnitude: beta_k max_u E u^k (log2), times the filter gain and the sums' growth
-    double top = 0.0, lb = 0.0;  // lb = log2 beta_k
-    for (int k = 1; k < K; ++k) {
-        lb += (k == 1) ? 0.0 : log2(s2 / (double)k);
-        const double u2 = s2 > 0.0 ? fmin(1.0, (double)k / s2) : 1.0;
-        const double v = lb - 0.5 * s2 * u2 * log2e + 0.5 * (double)k * log2(u2);
-        top = fmax(top, v);
-    }
-    const double gain = 2.0 * log2(2.6 * sigma_s + 2.0);
-    if (mode == 0 && (0.25 * s2 * log2e > 120.0 || e0 + top + gain + 2.0 * log2((double)K) > 124.0)) flags |= 0x4;
-    q.tc = (float)tc;
-    q.invR = (float)(1.0 / R);
-    q.half_s2 = (float)(0.5 * s2);
-    q.s2 = (float)s2;
-    q.R = (float)R;
-    q.escale = (float)exp2(e0);
-    q.mode = mode;
-    q.pad0 = flags;
-    q.tc_d = tc;
-    q.R_d = R;
-    double b = 1.0;
-    for (int m = 0; m < KMAX; ++m) {
-        if (m == 0) {
-            q.beta[0] = 1.f;
+    __syncthreads();
+    const double s2 = sh_s2;
+    // beta_k and the log2 magnitude of the largest value of channel k, beta_k max_u E u^k
+    const int k = threadIdx.x;
+    double beta = 0.0;
+    float lmax = -INFINITY;
+    if (k < K) {
+        beta = 1.0;
+        for (int j = 2; j <= k; ++j) beta *= s2 * c_inv[j];
+        if (k >= 1 && beta > 0.0) {
+            const float s2f = (float)s2;
+            const float u2 = fminf(1.f, (float)k / s2f);
+            lmax = log2f((float)beta) - 0.7213475f * s2f * u2 + 0.5f * (float)k * log2f(u2);
         } else {
-            b = (m == 1) ? 1.0 : b * s2 / (double)m;  // beta_m = s^{2(m-1)} / m!
-            q.beta[m] = (m < K) ? (float)b : 0.f;
+            lmax = 0.f;
         }
     }
-    pp[c] = q;
-}
-
-// One thread: OR the planes' flags into the status word (written fresh each call).
-__global__ void stats_status(const PlaneParams *__restrict__ pp, int planes, uint32_t *__restrict__ status)
-{
-    uint32_t bits = 0;
-    for (int c = 0; c < planes; ++c) bits |= (uint32_t)pp[c].pad0;
-    *status = bits;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) lmax = fmaxf(lmax, __shfl_down_sync(0xffffffffu, lmax, o));
+    if (lane == 0) stop[warp] = lmax;
+    if (k < KMAX) pp[c].beta[k] = (k < K) ? (float)beta : 0.f;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float top = stop[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) top = fmaxf(top, stop[w]);
+        const float s2f = (float)s2;
+        const float e0 = fmaxf(0.f, ceilf(0.7213475f * s2f - 120.f));  // E 2^e0 >= 2^-120 at |u| = 1
+        const float gain = 2.f * log2f(2.6f * (float)sigma_s + 2.f);
+        uint32_t flags = sh_mode == 2 ? 0x2u : 0u;
+        if (sh_mode == 0 && (0.3606738f * s2f > 120.f || e0 + top + gain + 2.f * log2f((float)K) > 124.f))
+            flags |= 0x4u;
+        PlaneParams &q = pp[c];
+        q.tc = (float)sh_tc;
+        q.invR = (float)(1.0 / sh_R);
+        q.half_s2 = (float)(0.5 * s2);
+        q.s2 = s2f;
+        q.R = (float)sh_R;
+        q.escale = exp2f(e0);
+        q.mode = sh_mode ? 1 : 0;
+        q.pad0 = (int)flags;
+        q.tc_d = sh_tc;
+        q.R_d = sh_R;
+        if (flags) atomicOr(status, flags);
+    }
 }
 
 // ------------------------------------------------------------------ row pass

