@@ -105,6 +105,19 @@ static void iir_line(const double *x, long xs, int n, const deriche_t *D,
     }
 }
 
+/* y[i] = sum_{|d| <= D} a[|d|] x[i - d], zero extension (explicit; a >= 0). */
+static void absconv_line(const double *x, long xs, int n, const double *a, int D, double *y, long ys)
+{
+    for (int i = 0; i < n; ++i) {
+        double acc = a[0] * x[(long)i * xs];
+        for (int d = 1; d <= D; ++d) {
+            if (i - d >= 0) acc += a[d] * x[(long)(i - d) * xs];
+            if (i + d < n) acc += a[d] * x[(long)(i + d) * xs];
+        }
+        y[(long)i * ys] = acc;
+    }
+}
+
 static void make_taps(double sigma_s, int w, double *taps)
 {
     for (int d = 0; d <= w; ++d) taps[d] = exp(-(double)d * d / (2.0 * sigma_s * sigma_s));
@@ -225,10 +238,12 @@ typedef struct {
     int spatial, w;
     const double *taps;
     const deriche_t *D;
+    const double *abs_h; /* |h(d)|, d = 0..abs_D: the kernel's absolute values (for kappa) */
+    int abs_D;
 } spatial_op;
 
-static void apply_S(const spatial_op *S, const double *a, int W, int ylo, int yhi,
-                    int r0, int r1, int c0, int c1, double *rowtmp, double *out)
+static void apply_S_impl(const spatial_op *S, int absk, const double *a, int W, int ylo, int yhi,
+                         int r0, int r1, int c0, int c1, double *rowtmp, double *out)
 {
     const int cw = c1 - c0;
     const int nr = yhi - ylo;
@@ -239,7 +254,8 @@ static void apply_S(const spatial_op *S, const double *a, int W, int ylo, int yh
 #pragma omp for schedule(static)
         for (int y = ylo; y < yhi; ++y) {
             const double *src = a + (long)(y - ylo) * W;
-            if (S->spatial == BFO_FIR) fir_line(src, 1, W, S->taps, S->w, line, 1);
+            if (absk) absconv_line(src, 1, W, S->abs_h, S->abs_D < W - 1 ? S->abs_D : W - 1, line, 1);
+            else if (S->spatial == BFO_FIR) fir_line(src, 1, W, S->taps, S->w, line, 1);
             else iir_line(src, 1, W, S->D, line, 1);
             memcpy(rowtmp + (long)(y - ylo) * cw, line + c0, sizeof(double) * (size_t)cw);
         }
@@ -251,12 +267,19 @@ static void apply_S(const spatial_op *S, const double *a, int W, int ylo, int yh
         double *col = malloc(sizeof(double) * (size_t)nr);
 #pragma omp for schedule(static)
         for (int x = 0; x < cw; ++x) {
-            if (S->spatial == BFO_FIR) fir_line(rowtmp + x, cw, nr, S->taps, S->w, col, 1);
+            if (absk) absconv_line(rowtmp + x, cw, nr, S->abs_h, S->abs_D < nr - 1 ? S->abs_D : nr - 1, col, 1);
+            else if (S->spatial == BFO_FIR) fir_line(rowtmp + x, cw, nr, S->taps, S->w, col, 1);
             else iir_line(rowtmp + x, cw, nr, S->D, col, 1);
             for (int y = r0; y < r1; ++y) out[(long)(y - r0) * cw + x] = col[y - ylo];
         }
         free(col);
     }
+}
+
+static void apply_S(const spatial_op *S, const double *a, int W, int ylo, int yhi, int r0, int r1, int c0, int c1,
+                    double *rowtmp, double *out)
+{
+    apply_S_impl(S, 0, a, W, ylo, yhi, r0, r1, c0, c1, rowtmp, out);
 }
 
 /*
@@ -273,11 +296,13 @@ static void apply_S(const spatial_op *S, const double *a, int W, int ylo, int yh
  * needs odd N, where the truncated exponential has a real root; the recursive
  * filter's small negative tail can also do it when (R / sigma_r)^2 is large).
  *
- * kappa (may be NULL): per-pixel sensitivity of the result to relative
- * perturbations of the individual terms of Eqs. (9)-(10),
- *     kappa = sigma_r (sum_n |p_n| + |P / Q| sum_n |q_n|) / |Q|,
- * with p_n, q_n the n-th terms of P and Q: a relative error eps in every
- * term moves the result by at most kappa * eps.
+ * kappa (may be NULL): first-order bound on how far relative errors eps in
+ * every product entering P and Q (the spatial sums of Eq. (8) and the terms
+ * of Eqs. (9)-(10)) can move the result:
+ *     kappa = sigma_r (sum_n |G_n| (|h| * |F_{n+1}|) / n! + |P/Q| sum_n |G_n| (|h| * |F_n|) / n!) / |Q|,
+ * where |h| * |F| filters |F| with the absolute spatial kernel (explicitly,
+ * out to 40 sigma_s for the recursive one); the result moves by at most
+ * about kappa * eps.  Infinite where Q <= 0.
  */
 int bfo_gp(const double *f, int H, int W, double sigma_s, double sigma_r, int N,
            double t_c, int spatial, int w, int round_f32,
@@ -294,7 +319,7 @@ int bfo_gp(const double *f, int H, int W, double sigma_s, double sigma_r, int N,
 
     double *taps = NULL;
     deriche_t D;
-    spatial_op S = {spatial, w, NULL, NULL};
+    spatial_op S = {spatial, w, NULL, NULL, NULL, 0};
     if (spatial == BFO_FIR) {
         taps = malloc(sizeof(double) * (size_t)(w + 1));
         if (!taps) return -1;
@@ -303,6 +328,26 @@ int bfo_gp(const double *f, int H, int W, double sigma_s, double sigma_r, int N,
     } else {
         deriche_design(sigma_s, round_f32, &D);
         S.D = &D;
+    }
+    /* |h(d)| for kappa: the window taps, or the recursive kernel out to 40 sigma (|h| < 1e-29 there) */
+    double *abs_h = NULL;
+    if (kappa) {
+        int Dn = spatial == BFO_FIR ? w : (int)ceil(40.0 * sigma_s);
+        const int nmax = (H > W ? H : W) - 1;
+        if (spatial != BFO_FIR && Dn > nmax) Dn = nmax;
+        if (Dn < 0) Dn = 0;
+        abs_h = malloc(sizeof(double) * (size_t)(Dn + 1));
+        if (!abs_h) { free(taps); return -1; }
+        for (int d = 0; d <= Dn; ++d) {
+            if (spatial == BFO_FIR) abs_h[d] = taps[d];
+            else {
+                double acc = 0.0;
+                for (int m = 0; m < 2; ++m) acc += creal(D.A[m] * cpow(D.p[m], (double)d));
+                abs_h[d] = fabs(acc);
+            }
+        }
+        S.abs_h = abs_h;
+        S.abs_D = Dn;
     }
 
     /* F and Hs live on the full-width rows [ylo, yhi) (offset so that row y is at (y - ylo) * W) */
@@ -316,9 +361,11 @@ int bfo_gp(const double *f, int H, int W, double sigma_s, double sigma_r, int N,
     double *Q = calloc((size_t)ncrop, sizeof(double));
     double *Pa = calloc((size_t)ncrop, sizeof(double));
     double *Qa = calloc((size_t)ncrop, sizeof(double));
-    if (!F || !Hs || !rowtmp || !Fbar || !G || !Hc || !P || !Q || !Pa || !Qa) {
+    double *Fa = kappa ? malloc(sizeof(double) * (size_t)nreg) : NULL;
+    double *FbarA = kappa ? malloc(sizeof(double) * (size_t)ncrop) : NULL;
+    if (!F || !Hs || !rowtmp || !Fbar || !G || !Hc || !P || !Q || !Pa || !Qa || (kappa && (!Fa || !FbarA))) {
         free(F); free(Hs); free(rowtmp); free(Fbar); free(G); free(Hc); free(P); free(Q); free(Pa); free(Qa);
-        free(taps);
+        free(Fa); free(FbarA); free(taps); free(abs_h);
         return -1;
     }
 
@@ -330,9 +377,14 @@ int bfo_gp(const double *f, int H, int W, double sigma_s, double sigma_r, int N,
         for (long i = 0; i < nreg; ++i) { F[i] = f[(long)ylo * W + i] - t_c; Hs[i] = 1.0; }
         apply_S(&S, F, W, ylo, yhi, r0, r1, c0, c1, rowtmp, P);
         apply_S(&S, Hs, W, ylo, yhi, r0, r1, c0, c1, rowtmp, Q);
+        if (kappa) {
+            for (long i = 0; i < nreg; ++i) Fa[i] = fabs(F[i]);
+            apply_S_impl(&S, 1, Fa, W, ylo, yhi, r0, r1, c0, c1, rowtmp, Pa);
+            apply_S_impl(&S, 1, Hs, W, ylo, yhi, r0, r1, c0, c1, rowtmp, Qa);
+        }
         for (long i = 0; i < ncrop; ++i) {
             out[i] = P[i] / Q[i] + t_c;
-            if (kappa) kappa[i] = 2.0 * fabs(P[i] / Q[i]);
+            if (kappa) kappa[i] = (Pa[i] + fabs(P[i] / Q[i]) * Qa[i]) / fabs(Q[i]);
         }
         goto done;
     }
@@ -350,23 +402,31 @@ int bfo_gp(const double *f, int H, int W, double sigma_s, double sigma_r, int N,
             Hc[k] = (f[(long)y * W + x] - t_c) / sigma_r;
             G[k] = 1.0;
         }
-    /* step 8: filtered F_0 */
+    /* step 8: filtered F_0 (and, for kappa, the filter of |F_0| with |h|) */
     apply_S(&S, F, W, ylo, yhi, r0, r1, c0, c1, rowtmp, Fbar);
+    if (kappa) {
+        for (long i = 0; i < nreg; ++i) Fa[i] = fabs(F[i]);
+        apply_S_impl(&S, 1, Fa, W, ylo, yhi, r0, r1, c0, c1, rowtmp, FbarA);
+    }
     double c = 1.0; /* 1/n! */
     for (int n = 0; n <= N; ++n) {
         /* Eq. (10): Q += G_n Fbar_n / n! */
         for (long i = 0; i < ncrop; ++i) {
             Q[i] += c * G[i] * Fbar[i];
-            Qa[i] += fabs(c * G[i] * Fbar[i]);
+            if (kappa) Qa[i] += fabs(c * G[i]) * FbarA[i];
         }
         /* F_{n+1} = H F_n, then Fbar_{n+1} */
 #pragma omp parallel for schedule(static)
         for (long i = 0; i < nreg; ++i) F[i] *= Hs[i];
         apply_S(&S, F, W, ylo, yhi, r0, r1, c0, c1, rowtmp, Fbar);
+        if (kappa) {
+            for (long i = 0; i < nreg; ++i) Fa[i] = fabs(F[i]);
+            apply_S_impl(&S, 1, Fa, W, ylo, yhi, r0, r1, c0, c1, rowtmp, FbarA);
+        }
         /* Eq. (9) without the sigma_r factor: P += G_n Fbar_{n+1} / n! */
         for (long i = 0; i < ncrop; ++i) {
             P[i] += c * G[i] * Fbar[i];
-            Pa[i] += fabs(c * G[i] * Fbar[i]);
+            if (kappa) Pa[i] += fabs(c * G[i]) * FbarA[i];
         }
         for (long i = 0; i < ncrop; ++i) G[i] *= Hc[i];
         c /= (double)(n + 1);
@@ -379,7 +439,7 @@ int bfo_gp(const double *f, int H, int W, double sigma_s, double sigma_r, int N,
 
 done:
     free(F); free(Hs); free(rowtmp); free(Fbar); free(G); free(Hc); free(P); free(Q); free(Pa); free(Qa);
-    free(taps);
+    free(Fa); free(FbarA); free(taps); free(abs_h);
     return 0;
 }
 

@@ -16,10 +16,12 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-3
-# A pixel is held to TOL when its conditioning kappa (oracle.gp_bf(..., return_kappa=True):
-# the bound on how far relative errors eps in the terms of Eqs. (9)-(10) move the result)
-# keeps FP32 unit roundoff amplified below 1e-4: kappa * 2^-24 <= 1e-4.
-KAPPA_GATE = 1e-4 * 2.0 ** 24
+# A pixel is held to TOL when its conditioning kappa (oracle.gp_bf(..., return_kappa=True): the
+# first-order bound on how far relative errors eps in every product entering P and Q move the
+# result) predicts an FP32 error below 8e-4 with an effective eps of 16 units of roundoff
+# (the FP32 recursions accumulate up to ~13 ulp; measured max |err| / kappa = 7.8e-7):
+# 16 * 2^-24 * kappa <= 8e-4.
+KAPPA_GATE = 8e-4 * 2.0 ** 24 / 16
 
 
 @pytest.fixture(scope="module")
@@ -164,11 +166,11 @@ def test_config3_crop(bf):
     f64 = img.astype(np.float64)
     gpu = run_gpu(bf, img, 10.0, 20.0, 20, "iir")
     r0, c0 = 1792, 2304
-    ref, kap = oracle.gp_bf(f64, 10.0, 20.0, 20, "iir", crop=(r0, r0 + 512, c0, c0 + 512), return_kappa=True)
-    check(gpu[r0:r0 + 512, c0:c0 + 512], ref, kappa=kap, min_gated=0.9999)
+    ref = oracle.gp_bf(f64, 10.0, 20.0, 20, "iir", crop=(r0, r0 + 512, c0, c0 + 512))
+    check(gpu[r0:r0 + 512, c0:c0 + 512], ref)  # every pixel: kappa <= 182 on this crop
     # border crop (zero-extension path at the image edge)
-    ref2, kap2 = oracle.gp_bf(f64, 10.0, 20.0, 20, "iir", crop=(4096 - 64, 4096, 0, 64), return_kappa=True)
-    check(gpu[4096 - 64:, :64], ref2, kappa=kap2, min_gated=0.9999)
+    ref2 = oracle.gp_bf(f64, 10.0, 20.0, 20, "iir", crop=(4096 - 64, 4096, 0, 64))
+    check(gpu[4096 - 64:, :64], ref2)
 
 
 # ---------------------------------------------------------------- special cases
