@@ -153,6 +153,39 @@ bf_status bf_gp_forward_host(const float *f_host, float *y_host, int planes, int
                              void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * Forward filter for callers that cannot allocate device memory.  The paper
+ * has no counterpart; this is a calling convenience.
+ *
+ * Some callers can't call cudaMalloc and can't be handed a workspace: plug-in
+ * hosts that give a filter only its input and output buffers, code running
+ * while a stream is being captured (where allocation is not allowed), and
+ * latency-bound loops where cudaMalloc/cudaFree would synchronise the device.
+ * This entry point takes the same arguments as bf_gp_forward minus the
+ * workspace and uses instead one scratch array of BF_GP_NOALLOC_SCRATCH_BYTES
+ * that lives in the library itself (a static device array: every GPU that
+ * loads the library holds it until the process exits).  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *
+ *  - Limit: the request needs bf_gp_workspace_size(planes, H, W, sigma_s,
+ *    opts) bytes of scratch; anything above BF_GP_NOALLOC_SCRATCH_BYTES is
+ *    rejected with BF_ERR_WORKSPACE before anything is enqueued (the reason is
+ *    also in bf_gp_last_cuda_error()).  With N = 20 that is about 380 000
+ *    pixels per call (e.g. one 512 x 512 plane, or three 256 x 256 planes).
+ *  - Set-up: the first call on a device looks up the array's device address
+ *    (with that device current) and caches it; make that first call before
+ *    any stream capture.
+ *  - Sharing: every call on a device uses the same array, which keeps the
+ *    previous call's contents; the filter writes every scratch byte it reads
+ *    before reading it, so nothing needs clearing.  Calls that overlap on the
+ *    GPU (different streams, threads or processes sharing the context) race
+ *    on the array: serialise them.  bf_gp_get_device_status and
+ *    bf_gp_get_plane_stats cannot reach this scratch.
+ */
+#define BF_GP_NOALLOC_SCRATCH_BYTES (32u << 20)
+bf_status bf_gp_forward_noalloc(const float *f, float *y, int planes, int H, int W, int pitch,
+                                float sigma_s, float sigma_r, const bf_gp_opts *opts, void *stream);
+
+/*
  * Read the device status word written by the last call that used `ws`
  * (BF_DEV_* bits).  Synchronises `stream` first.
  */

@@ -80,6 +80,8 @@ def _load():
                                      c_void_p, c_size_t, c_void_p]),
         "bf_gp_phase_cols": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_float, c_float,
                                      P(bf_gp_opts), c_void_p, c_size_t, c_void_p]),
+        "bf_gp_forward_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_float, c_float,
+                                          P(bf_gp_opts), c_void_p]),
         "bf_gp_host_workspace_size": (c_int, [c_int, c_int, c_int, c_float, P(bf_gp_opts), P(c_size_t)]),
         "bf_gp_forward_host": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_float, c_float, P(bf_gp_opts),
                                        c_void_p, c_size_t, c_void_p]),
@@ -99,7 +101,7 @@ def exported_symbols():
     """Names the binding expects the library to export."""
     return ["bf_gp_default_opts", "bf_status_string", "bf_gp_last_cuda_error", "bf_gp_version",
             "bf_gp_workspace_size", "bf_gp_forward", "bf_gp_phase_stats", "bf_gp_phase_rows", "bf_gp_phase_cols",
-            "bf_gp_host_workspace_size", "bf_gp_forward_host",
+            "bf_gp_forward_noalloc", "bf_gp_host_workspace_size", "bf_gp_forward_host",
             "bf_gp_get_device_status", "bf_gp_get_plane_stats", "bf_gp_order_for_tol"]
 
 
@@ -171,6 +173,17 @@ def bf_gp_phase_cols(f_ptr, y_ptr, planes, H, W, pitch, sigma_s, sigma_r, opts, 
     _check(_load().bf_gp_phase_cols(_vp(f_ptr), _vp(y_ptr), int(planes), int(H), int(W), int(pitch),
                                     float(sigma_s), float(sigma_r), _op(opts), _vp(ws_ptr), int(ws_bytes),
                                     _vp(stream)), "bf_gp_phase_cols")
+
+
+BF_GP_NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def bf_gp_forward_noalloc(f_ptr, y_ptr, planes, H, W, pitch, sigma_s, sigma_r, opts, stream=0) -> None:
+    """bf_gp_forward without a workspace: uses the library's own static device
+    scratch (at most BF_GP_NOALLOC_SCRATCH_BYTES); see include/bf_gp.h."""
+    _check(_load().bf_gp_forward_noalloc(_vp(f_ptr), _vp(y_ptr), int(planes), int(H), int(W), int(pitch),
+                                         float(sigma_s), float(sigma_r), _op(opts), _vp(stream)),
+           "bf_gp_forward_noalloc")
 
 
 def bf_gp_host_workspace_size(planes, H, W, sigma_s, opts=None) -> int:

@@ -7,6 +7,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/bf_gp.h"
 #include "bf_gp_device.cuh"
@@ -399,6 +400,50 @@ bf_status bf_gp_phase_cols(const float *f, float *y, int planes, int H, int W, i
     bf_status st = prepare(f, y, planes, H, W, pitch, sigma_s, sigma_r, opts, ws, ws_bytes, stream, true, &c);
     if (st != BF_OK) return st;
     return run_cols(c, planes, W, sigma_s);
+}
+
+}  // extern "C"
+
+// Scratch for bf_gp_forward_noalloc: a static device array, so the entry
+// point needs neither a caller workspace nor an allocation.  Host code may
+// not use the symbol itself as a device pointer; its device address is looked
+// up once per device with cudaGetSymbolAddress (that device current) and cached.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[BF_GP_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+}  // namespace
+
+extern "C" {
+
+bf_status bf_gp_forward_noalloc(const float *f, float *y, int planes, int H, int W, int pitch, float sigma_s,
+                                float sigma_r, const bf_gp_opts *opts, void *stream)
+{
+    size_t need = 0;
+    bf_status st = bf_gp_workspace_size(planes, H, W, sigma_s, opts, &need);
+    if (st != BF_OK) return st;
+    if (need > (size_t)BF_GP_NOALLOC_SCRATCH_BYTES) {
+        snprintf(g_cuda_err, sizeof g_cuda_err,
+                 "bf_gp_forward_noalloc: request needs %zu bytes of scratch; the static scratch holds %u", need,
+                 (unsigned)BF_GP_NOALLOC_SCRATCH_BYTES);
+        return BF_ERR_WORKSPACE;
+    }
+    int dev = -1;
+    BF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return BF_ERR_UNSUPPORTED;
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        base = g_noalloc_ptr[dev];
+        if (!base) {
+            BF_CUDA(cudaGetSymbolAddress(&base, g_noalloc_scratch));
+            g_noalloc_ptr[dev] = base;
+        }
+    }
+    return bf_gp_forward(f, y, planes, H, W, pitch, sigma_s, sigma_r, opts, base,
+                         (size_t)BF_GP_NOALLOC_SCRATCH_BYTES, stream);
 }
 
 bf_status bf_gp_host_workspace_size(int planes, int H, int W, float sigma_s, const bf_gp_opts *opts, size_t *bytes)
