@@ -15,6 +15,7 @@ Functions (each cites the passage of Chaudhury's paper it follows):
   of Sec. 2, spatial operator FIR (Eq. (8)) or Deriche's recursive Gaussian.
 * :func:`line_filter`, :func:`deriche_response`, :func:`deriche_coefs` -- the
   1-D spatial operators and the recursive filter's impulse response.
+* :func:`gp_adjoint` -- O3, the reverse-mode derivative of O2 (w.r.t. f and sigma_r).
 * :func:`gp_kernel` -- Eq. (5), the Gauss-polynomial range kernel.
 * :func:`window` -- W = ceil(3 sigma_s) (Sec. 1).
 """
@@ -73,6 +74,8 @@ def _load():
     lib.bfo_set_threads.restype = None
     lib.bfo_mean.argtypes = [dp, ctypes.c_long]
     lib.bfo_mean.restype = d
+    lib.bfo_gp_adjoint.argtypes = [dp, i, i, d, d, i, d, i, i, dp, dp, dp]
+    lib.bfo_gp_adjoint.restype = i
     lib.bfo_gp_kernel.argtypes = [d, d, d, i]
     lib.bfo_gp_kernel.restype = d
     _lib = lib
@@ -147,6 +150,28 @@ def gp_bf(f, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop=None, ro
     if rc != 0:
         raise MemoryError("oracle allocation failed")
     return (out, kap) if return_kappa else out
+
+
+def gp_adjoint(f, sigma_s, sigma_r, N, ybar, spatial="fir", t_c=None, w=None):
+    """O3: reverse-mode derivative of gp_bf (Algorithm 1) on the full image.
+
+    Returns (dL/df, dL/dsigma_r) for L = sum(ybar * gp_bf(f, ...)).  t_c=None is
+    the mean centre of the algorithm's first step (its derivative included);
+    a given t_c is held fixed.
+    """
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    H, W = f.shape
+    yb = np.ascontiguousarray(ybar, dtype=np.float64)
+    assert yb.shape == f.shape
+    w = window(sigma_s) if w is None else int(w)
+    fb = np.empty_like(f)
+    srb = np.zeros(1)
+    tc = float("nan") if t_c is None else float(t_c)
+    rc = _load().bfo_gp_adjoint(_ptr(f), H, W, float(sigma_s), float(sigma_r), int(N), tc,
+                                FIR if spatial == "fir" else IIR, w, _ptr(yb), _ptr(fb), _ptr(srb))
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    return fb, float(srb[0])
 
 
 def line_filter(x, sigma_s, spatial="fir", w=None, round_coef_f32=False):

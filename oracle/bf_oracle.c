@@ -458,3 +458,131 @@ double bfo_gp_kernel(double t, double tau, double sigma_r, int N)
     }
     return exp(-tau * tau / (2.0 * sigma_r * sigma_r)) * exp(-t * t / (2.0 * sigma_r * sigma_r)) * sum;
 }
+
+/*
+ * O3 -- reverse-mode derivative of O2 (Algorithm 1) on the full image, in the
+ * paper's own variables.  With H = h / sigma_r, E = exp(-h^2 / 2 sigma_r^2),
+ * G_n = H^n, F_n = E H^n, Fbar_n = S F_n, c_n = 1/n!:
+ *     P = sum_{n<=N} c_n G_n Fbar_{n+1},  Q = sum_{n<=N} c_n G_n Fbar_n,
+ *     y = sigma_r P / Q + t_c   (Eqs. (9)-(11), Eq. (6)).
+ * Given ybar = dL/dy, with Pbar = ybar sigma_r / Q and Qbar = -ybar sigma_r P / Q^2:
+ *   direct:   Hbar_i = sum_n c_n n H_i^{n-1} (Pbar_i Fbar_{n+1} + Qbar_i Fbar_n)
+ *   through S (S is symmetric, so its adjoint is S itself):
+ *             lambda_k = Pbar c_{k-1} G_{k-1} [k >= 1] + Qbar c_k G_k [k <= N],  mu_k = S lambda_k,
+ *             dF_k/dh = E (k H^{k-1} / sigma_r - h H^k / sigma_r^2)
+ *   hbar = sum_k mu_k dF_k/dh + Hbar / sigma_r,
+ *   fbar = hbar + (sum ybar - sum hbar) / |I|  when t_c is the mean (Algorithm 1, step 1),
+ *          hbar                                 when t_c is given.
+ *   sigma_r: y depends on it through the explicit factor, H (dH/dsigma_r = -H/sigma_r)
+ *   and E (dE/dsigma_r = E h^2 / sigma_r^3).
+ * Full image only (no crop).  Returns 0, or -1 on allocation failure.
+ */
+int bfo_gp_adjoint(const double *f, int H_, int W, double sigma_s, double sigma_r, int N, double t_c_given,
+                   int spatial, int w, const double *ybar, double *fbar, double *sigma_r_bar)
+{
+    const long n = (long)H_ * W;
+    const int K = N + 2;
+    double *taps = NULL;
+    deriche_t D;
+    spatial_op S = {spatial, w, NULL, NULL, NULL, 0};
+    if (spatial == BFO_FIR) {
+        taps = malloc(sizeof(double) * (size_t)(w + 1));
+        if (!taps) return -1;
+        make_taps(sigma_s, w, taps);
+        S.taps = taps;
+    } else {
+        deriche_design(sigma_s, 0, &D);
+        S.D = &D;
+    }
+    double *h = malloc(sizeof(double) * (size_t)n);
+    double *Hh = malloc(sizeof(double) * (size_t)n);
+    double *E = malloc(sizeof(double) * (size_t)n);
+    double *Fb = malloc(sizeof(double) * (size_t)n * K);   /* Fbar_k, k = 0..N+1 */
+    double *tmp = malloc(sizeof(double) * (size_t)n);
+    double *rowtmp = malloc(sizeof(double) * (size_t)n);
+    double *P = calloc((size_t)n, sizeof(double));
+    double *Q = calloc((size_t)n, sizeof(double));
+    double *Pb = malloc(sizeof(double) * (size_t)n);
+    double *Qb = malloc(sizeof(double) * (size_t)n);
+    double *hb = calloc((size_t)n, sizeof(double));
+    double *lam = malloc(sizeof(double) * (size_t)n);
+    double *mu = malloc(sizeof(double) * (size_t)n);
+    if (!h || !Hh || !E || !Fb || !tmp || !rowtmp || !P || !Q || !Pb || !Qb || !hb || !lam || !mu) {
+        free(h); free(Hh); free(E); free(Fb); free(tmp); free(rowtmp); free(P); free(Q); free(Pb); free(Qb);
+        free(hb); free(lam); free(mu); free(taps);
+        return -1;
+    }
+    const int centre_mean = isnan(t_c_given);
+    const double t_c = centre_mean ? bfo_mean(f, n) : t_c_given;
+    for (long i = 0; i < n; ++i) {
+        h[i] = f[i] - t_c;
+        Hh[i] = h[i] / sigma_r;
+        E[i] = exp(-h[i] * h[i] / (2.0 * sigma_r * sigma_r));
+    }
+    /* forward: Fbar_k = S(E H^k) for k = 0..N+1 */
+    for (long i = 0; i < n; ++i) tmp[i] = E[i];
+    for (int k = 0; k < K; ++k) {
+        apply_S(&S, tmp, W, 0, H_, 0, H_, 0, W, rowtmp, Fb + (long)k * n);
+        for (long i = 0; i < n; ++i) tmp[i] *= Hh[i];
+    }
+    double sr_bar = 0.0;
+    for (long i = 0; i < n; ++i) {
+        double g = 1.0, c = 1.0;
+        for (int k = 0; k <= N; ++k) {
+            P[i] += c * g * Fb[(long)(k + 1) * n + i];
+            Q[i] += c * g * Fb[(long)k * n + i];
+            g *= Hh[i];
+            c /= (double)(k + 1);
+        }
+        Pb[i] = ybar[i] * sigma_r / Q[i];
+        Qb[i] = -ybar[i] * sigma_r * P[i] / (Q[i] * Q[i]);
+        sr_bar += ybar[i] * P[i] / Q[i]; /* explicit sigma_r factor */
+        /* direct dependence on H_i through G_n(i) */
+        double Hbar = 0.0, Gsr = 0.0, gm1 = 0.0; /* gm1 = H^{n-1} */
+        c = 1.0;
+        g = 1.0;
+        for (int k = 0; k <= N; ++k) {
+            const double term = Pb[i] * Fb[(long)(k + 1) * n + i] + Qb[i] * Fb[(long)k * n + i];
+            if (k >= 1) Hbar += c * k * gm1 * term;
+            Gsr += c * (-(double)k / sigma_r) * g * term; /* dG_k/dsigma_r = -k G_k / sigma_r */
+            gm1 = g;
+            g *= Hh[i];
+            c /= (double)(k + 1);
+        }
+        hb[i] += Hbar / sigma_r;
+        sr_bar += Gsr;
+    }
+    /* through S: lambda_k, mu_k = S lambda_k, then dF_k/dh and dF_k/dsigma_r */
+    double c_k = 1.0;          /* 1/k! */
+    double c_km1 = 0.0;        /* 1/(k-1)! */
+    for (int k = 0; k < K; ++k) {
+        for (long i = 0; i < n; ++i) {
+            double l = 0.0;
+            const double Gk = pow(Hh[i], (double)k);
+            if (k >= 1) l += Pb[i] * c_km1 * pow(Hh[i], (double)(k - 1));
+            if (k <= N) l += Qb[i] * c_k * Gk;
+            lam[i] = l;
+        }
+        apply_S(&S, lam, W, 0, H_, 0, H_, 0, W, rowtmp, mu);
+        for (long i = 0; i < n; ++i) {
+            const double Hk = pow(Hh[i], (double)k);
+            const double Hkm1 = k >= 1 ? pow(Hh[i], (double)(k - 1)) : 0.0;
+            const double dFdh = E[i] * ((double)k * Hkm1 / sigma_r - h[i] * Hk / (sigma_r * sigma_r));
+            hb[i] += mu[i] * dFdh;
+            const double Fk = E[i] * Hk;
+            sr_bar += mu[i] * Fk * (h[i] * h[i] / (sigma_r * sigma_r * sigma_r) - (double)k / sigma_r);
+        }
+        c_km1 = c_k;
+        c_k /= (double)(k + 1);
+    }
+    double sy = 0.0, sh = 0.0;
+    for (long i = 0; i < n; ++i) {
+        sy += ybar[i];
+        sh += hb[i];
+    }
+    for (long i = 0; i < n; ++i) fbar[i] = hb[i] + (centre_mean ? (sy - sh) / (double)n : 0.0);
+    *sigma_r_bar = sr_bar;
+    free(h); free(Hh); free(E); free(Fb); free(tmp); free(rowtmp); free(P); free(Q); free(Pb); free(Qb);
+    free(hb); free(lam); free(mu); free(taps);
+    return 0;
+}

@@ -347,3 +347,48 @@ def test_kappa_lower_bound_and_equality(sp):
     if sp == "fir":
         y0, k0 = oracle.gp_bf(f, 2.0, 30.0, 20, sp, t_c=0.0, return_kappa=True)
         np.testing.assert_allclose(k0, 2 * np.abs(y0), rtol=1e-12)
+
+
+# --------------------------------------------------------------- O3 adjoint
+
+@pytest.mark.parametrize("sp,ss", [("fir", 1.5), ("iir", 2.0)])
+def test_spatial_operator_is_self_adjoint(sp, ss):
+    """<S x, z> = <x, S z>: the backward pass filters the adjoint channels with S itself."""
+    rng = np.random.default_rng(3)
+    x, z = rng.normal(size=(2, 5, 41))
+    Sx, Sz = oracle.line_filter(x, ss, sp), oracle.line_filter(z, ss, sp)
+    np.testing.assert_allclose((Sx * z).sum(axis=1), (x * Sz).sum(axis=1), rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("sp,ss", [("fir", 1.5), ("iir", 2.0)])
+@pytest.mark.parametrize("tc", [None, 110.0])
+def test_adjoint_matches_central_differences_every_pixel(sp, ss, tc):
+    """O3 against central differences of O2 in FP64, pixel by pixel on a tiny image,
+    for the mean centre (its derivative included) and a fixed centre."""
+    f = small_image(9, 8, 41, n_rect=3)
+    yb = np.random.default_rng(4).normal(size=f.shape)
+    g, gs = oracle.gp_adjoint(f, ss, 25.0, 10, yb, sp, t_c=tc)
+    L = lambda ff, sr=25.0: float((yb * oracle.gp_bf(ff, ss, sr, 10, sp, t_c=tc)).sum())
+    eps = 1e-4
+    fd = np.empty_like(f)
+    for idx in np.ndindex(f.shape):
+        e = np.zeros_like(f)
+        e[idx] = eps
+        fd[idx] = (L(f + e) - L(f - e)) / (2 * eps)
+    np.testing.assert_allclose(g, fd, rtol=0, atol=1e-7 * max(1.0, np.abs(fd).max()))
+    fds = (L(f, 25.0 + 1e-4) - L(f, 25.0 - 1e-4)) / 2e-4
+    assert abs(gs - fds) <= 1e-7 * max(1.0, abs(fds))
+
+
+@pytest.mark.parametrize("sp,ss", [("fir", 3.0), ("iir", 5.0)])
+def test_adjoint_directional_derivatives(sp, ss):
+    """Random directions on a 48 x 40 image: <grad, v> = d/dt L(f + t v)."""
+    f = small_image(48, 40, 42, n_rect=8)
+    rng = np.random.default_rng(5)
+    yb = rng.normal(size=f.shape)
+    g, _ = oracle.gp_adjoint(f, ss, 25.0, 20, yb, sp)
+    L = lambda ff: float((yb * oracle.gp_bf(ff, ss, 25.0, 20, sp)).sum())
+    for _ in range(6):
+        v = rng.normal(size=f.shape)
+        fd = (L(f + 1e-4 * v) - L(f - 1e-4 * v)) / 2e-4
+        assert abs((g * v).sum() - fd) <= 1e-6 * max(1.0, abs(fd))
