@@ -139,6 +139,35 @@ bf_status bf_gp_phase_cols(const float *f, float *y, int planes, int H, int W, i
                            float sigma_r, const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * Training support (no counterpart in the paper, which has no derivative):
+ * reverse-mode derivative of bf_gp_forward with respect to the image and
+ * sigma_r.
+ *
+ * bf_gp_forward_train: bf_gp_forward that also writes, per pixel, the four
+ *   sums the backward pass needs into `saved` (device, 4 * planes * H * W
+ *   floats, layout [planes][4][H][W], dense).  A constant plane is filtered
+ *   (result equal to its value) instead of copied, so its derivative exists.
+ *
+ * bf_gp_backward: given grad_y = dL/dy (device, layout and pitch of f),
+ *   writes grad_f = dL/df (device, same layout; may not alias f) and, if
+ *   grad_sigma_r is not NULL, dL/dsigma_r per plane (device, planes floats).
+ *   f, saved, sigma_s, sigma_r and opts must be those of the matching
+ *   bf_gp_forward_train call; ws needs bf_gp_workspace_size bytes (it may be
+ *   the forward's workspace; its contents are not needed).  The derivative of
+ *   the centre t_c (the plane mean, Algorithm 1 step 1) is included; a given
+ *   centre is held fixed.  R gets no derivative (the result does not depend
+ *   on it).  Pixels whose forward result was NaN (Q <= 0) pass no gradient.
+ *   Enqueues four kernels: stats, adjoint row pass, adjoint column pass
+ *   (the same spatial operator, which is symmetric), finish.
+ */
+bf_status bf_gp_forward_train(const float *f, float *y, float *saved, int planes, int H, int W, int pitch,
+                              float sigma_s, float sigma_r, const bf_gp_opts *opts, void *ws, size_t ws_bytes,
+                              void *stream);
+bf_status bf_gp_backward(const float *f, const float *grad_y, const float *saved, float *grad_f,
+                         float *grad_sigma_r, int planes, int H, int W, int pitch, float sigma_s, float sigma_r,
+                         const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream);
+
+/*
  * Forward filter on HOST buffers: copies f (host) into the device workspace,
  * runs bf_gp_forward there and copies the result into y (host), all on
  * `stream`; returns after the device->host copy has completed (it

@@ -80,6 +80,10 @@ def _load():
                                      c_void_p, c_size_t, c_void_p]),
         "bf_gp_phase_cols": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_float, c_float,
                                      P(bf_gp_opts), c_void_p, c_size_t, c_void_p]),
+        "bf_gp_forward_train": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_float, c_float,
+                                        P(bf_gp_opts), c_void_p, c_size_t, c_void_p]),
+        "bf_gp_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int,
+                                   c_float, c_float, P(bf_gp_opts), c_void_p, c_size_t, c_void_p]),
         "bf_gp_forward_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_float, c_float,
                                           P(bf_gp_opts), c_void_p]),
         "bf_gp_host_workspace_size": (c_int, [c_int, c_int, c_int, c_float, P(bf_gp_opts), P(c_size_t)]),
@@ -101,7 +105,7 @@ def exported_symbols():
     """Names the binding expects the library to export."""
     return ["bf_gp_default_opts", "bf_status_string", "bf_gp_last_cuda_error", "bf_gp_version",
             "bf_gp_workspace_size", "bf_gp_forward", "bf_gp_phase_stats", "bf_gp_phase_rows", "bf_gp_phase_cols",
-            "bf_gp_forward_noalloc", "bf_gp_host_workspace_size", "bf_gp_forward_host",
+            "bf_gp_forward_train", "bf_gp_backward", "bf_gp_forward_noalloc", "bf_gp_host_workspace_size", "bf_gp_forward_host",
             "bf_gp_get_device_status", "bf_gp_get_plane_stats", "bf_gp_order_for_tol"]
 
 
@@ -173,6 +177,20 @@ def bf_gp_phase_cols(f_ptr, y_ptr, planes, H, W, pitch, sigma_s, sigma_r, opts, 
     _check(_load().bf_gp_phase_cols(_vp(f_ptr), _vp(y_ptr), int(planes), int(H), int(W), int(pitch),
                                     float(sigma_s), float(sigma_r), _op(opts), _vp(ws_ptr), int(ws_bytes),
                                     _vp(stream)), "bf_gp_phase_cols")
+
+
+def bf_gp_forward_train(f_ptr, y_ptr, saved_ptr, planes, H, W, pitch, sigma_s, sigma_r, opts, ws_ptr, ws_bytes,
+                        stream=0) -> None:
+    _check(_load().bf_gp_forward_train(_vp(f_ptr), _vp(y_ptr), _vp(saved_ptr), int(planes), int(H), int(W),
+                                       int(pitch), float(sigma_s), float(sigma_r), _op(opts), _vp(ws_ptr),
+                                       int(ws_bytes), _vp(stream)), "bf_gp_forward_train")
+
+
+def bf_gp_backward(f_ptr, gy_ptr, saved_ptr, gf_ptr, gsr_ptr, planes, H, W, pitch, sigma_s, sigma_r, opts, ws_ptr,
+                   ws_bytes, stream=0) -> None:
+    _check(_load().bf_gp_backward(_vp(f_ptr), _vp(gy_ptr), _vp(saved_ptr), _vp(gf_ptr), _vp(gsr_ptr or 0),
+                                  int(planes), int(H), int(W), int(pitch), float(sigma_s), float(sigma_r),
+                                  _op(opts), _vp(ws_ptr), int(ws_bytes), _vp(stream)), "bf_gp_backward")
 
 
 BF_GP_NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -267,3 +285,61 @@ def bilateral_gp(x, sigma_s: float, sigma_r: float, order: int = 20, spatial="au
     bf_gp_forward(xc.data_ptr(), y.data_ptr(), planes, H, W, W, sigma_s, sigma_r, opts, buf.data_ptr(),
                   buf.numel(), stream)
     return y
+
+
+# ------------------------------------------------------- autograd
+
+def _autograd_function():
+    import torch
+
+    class BilateralGPFunction(torch.autograd.Function):
+        """y = bilateral_gp(x, sigma_s, sigma_r, order) with the hand-written
+        adjoint (bf_gp_backward) as its backward: gradients w.r.t. the image
+        and sigma_r (summed over planes when sigma_r is shared)."""
+
+        @staticmethod
+        def forward(ctx, x, sigma_r, sigma_s, order, spatial, t_c):
+            xc = x.contiguous()
+            H, W = xc.shape[-2], xc.shape[-1]
+            planes = max(1, xc.numel() // (H * W))
+            sr = float(sigma_r)
+            opts = make_opts(order, spatial, t_c)
+            need = bf_gp_workspace_size(planes, H, W, sigma_s, opts)
+            ws = workspace(need, xc.device)
+            y = torch.empty_like(xc)
+            saved = torch.empty((planes, 4, H, W), dtype=torch.float32, device=xc.device)
+            stream = torch.cuda.current_stream(xc.device).cuda_stream
+            bf_gp_forward_train(xc.data_ptr(), y.data_ptr(), saved.data_ptr(), planes, H, W, W, sigma_s, sr, opts,
+                                ws.data_ptr(), ws.numel(), stream)
+            ctx.save_for_backward(xc, saved)
+            ctx.cfg = (planes, H, W, float(sigma_s), sr, int(order), spatial, t_c)
+            return y
+
+        @staticmethod
+        def backward(ctx, gy):
+            xc, saved = ctx.saved_tensors
+            planes, H, W, ss, sr, order, spatial, t_c = ctx.cfg
+            opts = make_opts(order, spatial, t_c)
+            need = bf_gp_workspace_size(planes, H, W, ss, opts)
+            ws = workspace(need, xc.device)
+            gyc = gy.contiguous()
+            gx = torch.empty_like(xc)
+            gsr = torch.empty(planes, dtype=torch.float32, device=xc.device)
+            stream = torch.cuda.current_stream(xc.device).cuda_stream
+            bf_gp_backward(xc.data_ptr(), gyc.data_ptr(), saved.data_ptr(), gx.data_ptr(), gsr.data_ptr(), planes, H,
+                           W, W, ss, sr, opts, ws.data_ptr(), ws.numel(), stream)
+            gsig = gsr.sum() if ctx.needs_input_grad[1] else None
+            return gx, gsig, None, None, None, None
+
+    return BilateralGPFunction
+
+
+_fn = None
+
+
+def bilateral_gp_autograd(x, sigma_s: float, sigma_r, order: int = 20, spatial="auto", t_c=None):
+    """Differentiable filter: gradients flow to x and (if it is a tensor) sigma_r."""
+    global _fn
+    if _fn is None:
+        _fn = _autograd_function()
+    return _fn.apply(x, sigma_r, sigma_s, order, spatial, t_c)

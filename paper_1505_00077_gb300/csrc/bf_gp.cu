@@ -50,7 +50,7 @@ struct Plan {
     int nblk, rows_per_block;
     int T;                     // row threads per row
     int CL;                    // column cluster size (IIR)
-    size_t off_params, off_part, off_planes, total;
+    size_t off_params, off_part, off_acc, off_planes, total;
 };
 
 int fir_halfwidth(float sigma_s, const bf_gp_opts *o)
@@ -100,6 +100,8 @@ bf_status make_plan(int planes, int H, int W, float sigma_s, const bf_gp_opts *o
     off = align_up(off + sizeof(PlaneParams) * (size_t)planes, 256);
     p->off_part = off;
     off = align_up(off + sizeof(StatPartial) * (size_t)planes * p->nblk, 256);
+    p->off_acc = off;
+    off = align_up(off + sizeof(double) * NACC * (size_t)planes, 256);
     p->off_planes = off;
     off = align_up(off + sizeof(float) * (size_t)planes * p->K * H * p->Wp, 256);
     p->total = off;
@@ -141,24 +143,24 @@ void fir_coefs(double sigma, int w, FIRCoef *g)
 
 // ---------------------------------------------------------------- launches
 
-template <int WH>
+template <int WH, int MODE>
 bf_status launch_row_fir_w(const RowArgs &ra, const FIRCoef &g, int planes, cudaStream_t s)
 {
     const int T = ra.T;
     const int block = T > 256 ? T : 256;
     const int rows_per_cta = block / T;
     const size_t smem = sizeof(float) * 2 * rows_per_cta * (size_t)(T * ROW_C + 2 * WH);
-    BF_CUDA(cudaFuncSetAttribute(row_fir<ROW_C, WH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BF_CUDA(cudaFuncSetAttribute(row_fir<ROW_C, WH, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((ra.H + rows_per_cta - 1) / rows_per_cta, planes);
-    row_fir<ROW_C, WH><<<grid, block, smem, s>>>(ra, g);
+    row_fir<ROW_C, WH, MODE><<<grid, block, smem, s>>>(ra, g);
     return BF_OK;
 }
 
-template <int WH>
+template <int WH, int MODE>
 bf_status launch_col_fir_w(const ColArgs &ca, const FIRCoef &g, int planes, cudaStream_t s)
 {
     dim3 grid((ca.W + 31) / 32, (ca.H + 63) / 64, planes);
-    col_fir<WH><<<grid, 256, 0, s>>>(ca, g);
+    col_fir<WH, MODE><<<grid, 256, 0, s>>>(ca, g);
     return BF_OK;
 }
 
@@ -172,15 +174,18 @@ struct Call {
     uint32_t *status;
     PlaneParams *pp;
     StatPartial *part;
+    double *acc;
     float *planesbuf;
     RowArgs ra;
     ColArgs ca;
 };
 
-bf_status prepare(const float *f, float *y, int planes, int H, int W, int pitch, float sigma_s, float sigma_r,
-                  const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream, bool need_y, Call *c)
+// Validates the common arguments and lays out the workspace.  out: y for the
+// forward, grad_f for the backward (may be null for the stats/rows phases).
+bf_status prepare(const float *f, float *out, int planes, int H, int W, int pitch, float sigma_s, float sigma_r,
+                  const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream, bool need_out, Call *c)
 {
-    if (!f || !ws || (need_y && !y)) return BF_ERR_INVALID_ARG;
+    if (!f || !ws || (need_out && !out)) return BF_ERR_INVALID_ARG;
     if (pitch < W) return BF_ERR_INVALID_ARG;
     if (!(sigma_r > 0.f)) return BF_ERR_INVALID_ARG;  // also rejects NaN; +inf accepted
     bf_gp_opts d;
@@ -191,10 +196,10 @@ bf_status prepare(const float *f, float *y, int planes, int H, int W, int pitch,
     bf_status st = make_plan(planes, H, W, sigma_s, opts, &c->p);
     if (st != BF_OK) return st;
     if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < c->p.total) return BF_ERR_WORKSPACE;
-    if (need_y) {
+    if (need_out) {
         // input and output must not overlap
         const char *fb = reinterpret_cast<const char *>(f);
-        const char *yb = reinterpret_cast<const char *>(y);
+        const char *yb = reinterpret_cast<const char *>(out);
         const size_t span = sizeof(float) * ((size_t)planes * H * pitch);
         if (fb < yb + span && yb < fb + span) return BF_ERR_INVALID_ARG;
     }
@@ -203,23 +208,29 @@ bf_status prepare(const float *f, float *y, int planes, int H, int W, int pitch,
     c->status = reinterpret_cast<uint32_t *>(wsb);
     c->pp = reinterpret_cast<PlaneParams *>(wsb + c->p.off_params);
     c->part = reinterpret_cast<StatPartial *>(wsb + c->p.off_part);
+    c->acc = reinterpret_cast<double *>(wsb + c->p.off_acc);
     c->planesbuf = reinterpret_cast<float *>(wsb + c->p.off_planes);
     RowArgs &ra = c->ra;
+    std::memset(&ra, 0, sizeof ra);
     ra.f = f;
     ra.ws = c->planesbuf;
     ra.pp = c->pp;
+    ra.acc = c->acc;
     ra.H = H;
     ra.W = W;
     ra.pitch = pitch;
     ra.Wp = c->p.Wp;
     ra.K = c->p.K;
     ra.T = c->p.T;
+    ra.N = c->p.N;
     ColArgs &ca = c->ca;
+    std::memset(&ca, 0, sizeof ca);
     ca.ws = c->planesbuf;
     ca.f = f;
-    ca.y = y;
+    ca.y = out;
     ca.pp = c->pp;
     ca.status = c->status;
+    ca.acc = c->acc;
     ca.H = H;
     ca.W = W;
     ca.pitch = pitch;
@@ -230,7 +241,7 @@ bf_status prepare(const float *f, float *y, int planes, int H, int W, int pitch,
 }
 
 bf_status run_stats(const Call &c, int planes, int H, int W, int pitch, float sigma_s, float sigma_r,
-                    const bf_gp_opts *opts)
+                    const bf_gp_opts *opts, int for_backward)
 {
     bf_gp_opts d;
     if (!opts) {
@@ -241,11 +252,12 @@ bf_status run_stats(const Call &c, int planes, int H, int W, int pitch, float si
                                                            c.status);
     stats_finalize<<<planes, 256, 0, c.s>>>(c.part, c.p.nblk, (long long)H * W,
                                             opts->centre == BF_CENTRE_GIVEN ? 1 : 0, opts->t_c, (double)sigma_r,
-                                            (double)sigma_s, c.p.K, c.pp, c.status);
+                                            (double)sigma_s, c.p.K, for_backward, c.pp, c.status);
     BF_CUDA(cudaGetLastError());
     return BF_OK;
 }
 
+template <int MODE>
 bf_status run_rows(const Call &c, int planes, float sigma_s)
 {
     const int T = c.ra.T;
@@ -257,7 +269,7 @@ bf_status run_rows(const Call &c, int planes, float sigma_s)
         bf_status st = BF_ERR_UNSUPPORTED;
         switch (c.p.w) {
 #define BF_CASE(WW) \
-    case WW: st = launch_row_fir_w<WW>(c.ra, g, planes, c.s); break;
+    case WW: st = launch_row_fir_w<WW, MODE>(c.ra, g, planes, c.s); break;
             BF_CASE(1) BF_CASE(2) BF_CASE(3) BF_CASE(4) BF_CASE(5) BF_CASE(6)
             BF_CASE(7) BF_CASE(8) BF_CASE(9) BF_CASE(10) BF_CASE(11) BF_CASE(12)
 #undef BF_CASE
@@ -268,12 +280,13 @@ bf_status run_rows(const Call &c, int planes, float sigma_s)
         IIRCoef cr;
         deriche_coefs((double)sigma_s, ROW_C, &cr);
         dim3 grid((c.ra.H + rows_per_cta - 1) / rows_per_cta, planes);
-        row_iir<ROW_C><<<grid, block, 0, c.s>>>(c.ra, cr);
+        row_iir<ROW_C, MODE><<<grid, block, 0, c.s>>>(c.ra, cr);
     }
     BF_CUDA(cudaGetLastError());
     return BF_OK;
 }
 
+template <int MODE>
 bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
 {
     if (c.p.spatial == BF_SPATIAL_FIR) {
@@ -282,7 +295,7 @@ bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
         bf_status st = BF_ERR_UNSUPPORTED;
         switch (c.p.w) {
 #define BF_CASE(WW) \
-    case WW: st = launch_col_fir_w<WW>(c.ca, g, planes, c.s); break;
+    case WW: st = launch_col_fir_w<WW, MODE>(c.ca, g, planes, c.s); break;
             BF_CASE(1) BF_CASE(2) BF_CASE(3) BF_CASE(4) BF_CASE(5) BF_CASE(6)
             BF_CASE(7) BF_CASE(8) BF_CASE(9) BF_CASE(10) BF_CASE(11) BF_CASE(12)
 #undef BF_CASE
@@ -294,23 +307,21 @@ bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
         deriche_coefs((double)sigma_s, COL_C, &cc);
         const int strips = (W + 7) / 8;
         const size_t smem = sizeof(float) * 2 * COL_TILE_FLOATS;
-        {
-            BF_CUDA(cudaFuncSetAttribute(col_iir<COL_C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            cudaLaunchConfig_t cfg;
-            std::memset(&cfg, 0, sizeof cfg);
-            cfg.gridDim = dim3(strips * c.p.CL, planes, 1);
-            cfg.blockDim = dim3(256, 1, 1);
-            cfg.dynamicSmemBytes = smem;
-            cfg.stream = c.s;
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeClusterDimension;
-            attr[0].val.clusterDim.x = (unsigned)c.p.CL;
-            attr[0].val.clusterDim.y = 1;
-            attr[0].val.clusterDim.z = 1;
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            BF_CUDA(cudaLaunchKernelEx(&cfg, col_iir<COL_C, true>, c.ca, cc));
-        }
+        BF_CUDA(cudaFuncSetAttribute(col_iir<COL_C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        cudaLaunchConfig_t cfg;
+        std::memset(&cfg, 0, sizeof cfg);
+        cfg.gridDim = dim3(strips * c.p.CL, planes, 1);
+        cfg.blockDim = dim3(256, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = c.s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)c.p.CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        BF_CUDA(cudaLaunchKernelEx(&cfg, col_iir<COL_C, MODE>, c.ca, cc));
     }
     BF_CUDA(cudaGetLastError());
     return BF_OK;
@@ -369,9 +380,9 @@ bf_status bf_gp_forward(const float *f, float *y, int planes, int H, int W, int 
     Call c;
     bf_status st = prepare(f, y, planes, H, W, pitch, sigma_s, sigma_r, opts, ws, ws_bytes, stream, true, &c);
     if (st != BF_OK) return st;
-    st = run_stats(c, planes, H, W, pitch, sigma_s, sigma_r, opts);
-    if (st == BF_OK) st = run_rows(c, planes, sigma_s);
-    if (st == BF_OK) st = run_cols(c, planes, W, sigma_s);
+    st = run_stats(c, planes, H, W, pitch, sigma_s, sigma_r, opts, 0);
+    if (st == BF_OK) st = run_rows<MODE_FWD>(c, planes, sigma_s);
+    if (st == BF_OK) st = run_cols<MODE_FWD>(c, planes, W, sigma_s);
     return st;
 }
 
@@ -381,7 +392,7 @@ bf_status bf_gp_phase_stats(const float *f, int planes, int H, int W, int pitch,
     Call c;
     bf_status st = prepare(f, nullptr, planes, H, W, pitch, sigma_s, sigma_r, opts, ws, ws_bytes, stream, false, &c);
     if (st != BF_OK) return st;
-    return run_stats(c, planes, H, W, pitch, sigma_s, sigma_r, opts);
+    return run_stats(c, planes, H, W, pitch, sigma_s, sigma_r, opts, 0);
 }
 
 bf_status bf_gp_phase_rows(const float *f, int planes, int H, int W, int pitch, float sigma_s, float sigma_r,
@@ -390,7 +401,7 @@ bf_status bf_gp_phase_rows(const float *f, int planes, int H, int W, int pitch, 
     Call c;
     bf_status st = prepare(f, nullptr, planes, H, W, pitch, sigma_s, sigma_r, opts, ws, ws_bytes, stream, false, &c);
     if (st != BF_OK) return st;
-    return run_rows(c, planes, sigma_s);
+    return run_rows<MODE_FWD>(c, planes, sigma_s);
 }
 
 bf_status bf_gp_phase_cols(const float *f, float *y, int planes, int H, int W, int pitch, float sigma_s,
@@ -399,7 +410,51 @@ bf_status bf_gp_phase_cols(const float *f, float *y, int planes, int H, int W, i
     Call c;
     bf_status st = prepare(f, y, planes, H, W, pitch, sigma_s, sigma_r, opts, ws, ws_bytes, stream, true, &c);
     if (st != BF_OK) return st;
-    return run_cols(c, planes, W, sigma_s);
+    return run_cols<MODE_FWD>(c, planes, W, sigma_s);
+}
+
+bf_status bf_gp_forward_train(const float *f, float *y, float *saved, int planes, int H, int W, int pitch,
+                              float sigma_s, float sigma_r, const bf_gp_opts *opts, void *ws, size_t ws_bytes,
+                              void *stream)
+{
+    if (!saved) return BF_ERR_INVALID_ARG;
+    Call c;
+    bf_status st = prepare(f, y, planes, H, W, pitch, sigma_s, sigma_r, opts, ws, ws_bytes, stream, true, &c);
+    if (st != BF_OK) return st;
+    c.ca.saved = saved;
+    st = run_stats(c, planes, H, W, pitch, sigma_s, sigma_r, opts, 1);
+    if (st == BF_OK) st = run_rows<MODE_FWD>(c, planes, sigma_s);
+    if (st == BF_OK) st = run_cols<MODE_SAVE>(c, planes, W, sigma_s);
+    return st;
+}
+
+bf_status bf_gp_backward(const float *f, const float *grad_y, const float *saved, float *grad_f,
+                         float *grad_sigma_r, int planes, int H, int W, int pitch, float sigma_s, float sigma_r,
+                         const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream)
+{
+    if (!grad_y || !saved) return BF_ERR_INVALID_ARG;
+    Call c;
+    bf_status st = prepare(f, grad_f, planes, H, W, pitch, sigma_s, sigma_r, opts, ws, ws_bytes, stream, true, &c);
+    if (st != BF_OK) return st;
+    bf_gp_opts d;
+    if (!opts) {
+        bf_gp_default_opts(&d);
+        opts = &d;
+    }
+    c.ra.gy = grad_y;
+    c.ra.saved = saved;
+    c.ca.gy = grad_y;
+    c.ca.saved = const_cast<float *>(saved);
+    st = run_stats(c, planes, H, W, pitch, sigma_s, sigma_r, opts, 1);
+    if (st == BF_OK) st = run_rows<MODE_ADJ>(c, planes, sigma_s);
+    if (st == BF_OK) st = run_cols<MODE_ADJ>(c, planes, W, sigma_s);
+    if (st != BF_OK) return st;
+    const long long n = (long long)H * W;
+    dim3 grid((unsigned)((n + 255) / 256), planes);
+    grad_finish<<<grid, 256, 0, c.s>>>(grad_f, c.acc, c.pp, H, W, pitch, opts->centre == BF_CENTRE_MEAN ? 1 : 0,
+                                       (double)sigma_r, grad_sigma_r);
+    BF_CUDA(cudaGetLastError());
+    return BF_OK;
 }
 
 }  // extern "C"

@@ -285,9 +285,10 @@ __constant__ double c_inv[KMAX + 1] = {
 // its PlaneParams: t_c, R, s^2, beta_k = s^{2(k-1)}/k! (thread k, FP64
 // product of s^2 / j), the common scale 2^e0 and the range flag.  ORs its
 // flags into the status word (zeroed by stats_partial of the same call).
+// for_backward: a constant plane is filtered (R := 1) instead of copied.
 __global__ void __launch_bounds__(256) stats_finalize(const StatPartial *__restrict__ part, int nblk,
                                                       long long npix, int centre_given, double tc_given,
-                                                      double sigma_r, double sigma_s, int K,
+                                                      double sigma_r, double sigma_s, int K, int for_backward,
                                                       PlaneParams *__restrict__ pp, uint32_t *__restrict__ status)
 {
     const int c = blockIdx.x;
@@ -336,7 +337,10 @@ __global__ void __launch_bounds__(256) stats_finalize(const StatPartial *__restr
         double R = fmax((double)MX - tc, tc - (double)MN);
         int mode = BAD > 0 ? 2 : 0;  // 2: non-finite input (copy + flag)
         if (!(R > 0.0)) {
-            mode = mode ? mode : 1;
+            // constant plane: the forward copies it; for training the filter runs
+            // with R = 1 (the result is independent of R), which gives y = t_c = f
+            // exactly and a defined derivative
+            if (!for_backward) mode = mode ? mode : 1;
             R = 1.0;
         }
         sh_tc = tc;
@@ -390,44 +394,121 @@ __global__ void __launch_bounds__(256) stats_finalize(const StatPartial *__restr
     }
 }
 
-// ------------------------------------------------------------------ row pass
+// ------------------------------------------------------------------ modes
+
+// MODE_FWD: forward.  MODE_SAVE: forward that also writes, per pixel, the
+// four sums the backward pass needs.  MODE_ADJ: backward (adjoint) pass.
+enum { MODE_FWD = 0, MODE_SAVE = 1, MODE_ADJ = 2 };
+
+// Saved per pixel by MODE_SAVE, layout [planes][4][H][W]:
+//   0: P~   1: Q~   2: dp = sum_{m>=2} m (m-1) u^{m-2} Psi_m  (= dP~/du)
+//   3: dq = sum_{1<=m<=N} m u^{m-1} Psi_m  (dQ~/du = s^2 dq)
+// Backward accumulators per plane (FP64, in the workspace): [0] sum of dL/dy,
+// [1] sum of dL/dh, [2] dL/d(s^2); zeroed by the adjoint row pass.
+constexpr int NACC = 4;
 
 struct RowArgs {
     const float *f;
-    float *ws;  // [planes][K][H][Wp]
+    const float *gy;     // MODE_ADJ: dL/dy, same layout as f
+    const float *saved;  // MODE_ADJ: the MODE_SAVE sums
+    float *ws;           // [planes][K][H][Wp]
     const PlaneParams *pp;
-    int H, W, pitch, Wp, K, T;  // T: threads per row (power of two, 8..512)
+    double *acc;         // MODE_ADJ: [planes][NACC]
+    int H, W, pitch, Wp, K, T, N;  // T: threads per row (power of two, 8..512)
 };
 
-// Load one chunk of the row and form u and Phi_0 (zero beyond the row end).
-template <int C>
-__device__ __forceinline__ void load_row_chunk(const RowArgs &a, int plane, int row, bool rv, int x0,
-                                               const PlaneParams &P, float (&u)[C], float (&phi)[C])
+__device__ __forceinline__ size_t saved_idx(int plane, int which, int H, int W, int r, int x)
 {
-    const float *frow = a.f + ((size_t)plane * a.H + (rv ? row : 0)) * a.pitch;
-    float v[C];
-    const bool vec = ((a.pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.f) & 15) == 0) && (x0 + C <= a.W);
-    if (rv && vec) {
-#pragma unroll
-        for (int j = 0; j < C; j += 4) {
-            const float4 t = __ldg(reinterpret_cast<const float4 *>(frow + x0 + j));
-            v[j] = t.x;
-            v[j + 1] = t.y;
-            v[j + 2] = t.z;
-            v[j + 3] = t.w;
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < C; ++j) v[j] = (rv && x0 + j < a.W) ? __ldg(frow + x0 + j) : P.tc;
-    }
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-        const bool in = rv && (x0 + j < a.W);
-        const float uu = (v[j] - P.tc) * P.invR;
-        u[j] = in ? uu : 0.f;
-        phi[j] = in ? envelope(P, uu) : 0.f;
-    }
+    return (((size_t)plane * 4 + which) * H + r) * W + x;
 }
+
+// Channel generator of the row pass for one chunk.
+//   forward: Phi_k = 2^e0 E u^k (k = 0..K-1), E = exp(-s^2 u^2/2)
+//   adjoint: with alpha = dL/dy R / Q~ and rho = P~ / Q~ at the pixel,
+//            lambda_0 = -alpha rho,  lambda_m = alpha u^{m-1} (m - rho s^2 u) (1 <= m <= N),
+//            lambda_{N+1} = alpha (N+1) u^N
+//   (the adjoint of Psi_m in P~ = sum m u^{m-1} Psi_m and Q~ = Psi_0 + s^2 u sum u^{m-1} Psi_m)
+template <int C, int MODE>
+struct RowGen {
+    // forward: v = current channel.  adjoint: v = alpha u^{m-1}; t = rho until
+    // channel 0 has been formed, rho s^2 u afterwards.
+    float u[C], v[C], t[C];
+    float s2;
+    __device__ __forceinline__ void init(const RowArgs &a, int plane, int row, bool rv, int x0, const PlaneParams &P)
+    {
+        s2 = P.s2;
+        const float *frow = a.f + ((size_t)plane * a.H + (rv ? row : 0)) * a.pitch;
+        float fv[C];
+        const bool vec = ((a.pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.f) & 15) == 0) && (x0 + C <= a.W);
+        if (rv && vec) {
+#pragma unroll
+            for (int j = 0; j < C; j += 4) {
+                const float4 q = __ldg(reinterpret_cast<const float4 *>(frow + x0 + j));
+                fv[j] = q.x;
+                fv[j + 1] = q.y;
+                fv[j + 2] = q.z;
+                fv[j + 3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < C; ++j) fv[j] = (rv && x0 + j < a.W) ? __ldg(frow + x0 + j) : P.tc;
+        }
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            const bool in = rv && (x0 + j < a.W);
+            const float uu = (fv[j] - P.tc) * P.invR;
+            u[j] = in ? uu : 0.f;
+            if (MODE != MODE_ADJ) {
+                v[j] = in ? envelope(P, uu) : 0.f;
+                t[j] = 0.f;
+            } else {
+                float al = 0.f, rho = 0.f;
+                if (in) {
+                    const float g = __ldg(a.gy + ((size_t)plane * a.H + row) * a.pitch + x0 + j);
+                    const float Pt = __ldg(a.saved + saved_idx(plane, 0, a.H, a.W, row, x0 + j));
+                    const float Qt = __ldg(a.saved + saved_idx(plane, 1, a.H, a.W, row, x0 + j));
+                    if (Qt > 0.f && isfinite(g)) {
+                        al = __fdiv_rn(g * P.R, Qt);
+                        rho = __fdiv_rn(Pt, Qt);
+                    }
+                }
+                v[j] = al;
+                t[j] = rho;
+            }
+        }
+    }
+    // channel k into x (k increasing from 0)
+    __device__ __forceinline__ void channel(int k, int N, float (&x)[C])
+    {
+        if (MODE != MODE_ADJ) {
+            if (k > 0) {
+#pragma unroll
+                for (int j = 0; j < C; ++j) v[j] *= u[j];
+            }
+#pragma unroll
+            for (int j = 0; j < C; ++j) x[j] = v[j];
+            return;
+        }
+        if (k == 0) {
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+                x[j] = -v[j] * t[j];      // lambda_0 = -alpha rho
+                t[j] = t[j] * s2 * u[j];  // rho s^2 u from here on
+            }
+            return;
+        }
+        const float mk = (float)k;
+        if (k <= N) {
+#pragma unroll
+            for (int j = 0; j < C; ++j) x[j] = v[j] * (mk - t[j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < C; ++j) x[j] = v[j] * mk;
+        }
+#pragma unroll
+        for (int j = 0; j < C; ++j) v[j] *= u[j];
+    }
+};
 
 template <int C>
 __device__ __forceinline__ void store_row_chunk(const RowArgs &a, int plane, int k, int row, bool rv, int x0,
@@ -447,11 +528,16 @@ __device__ __forceinline__ void store_row_chunk(const RowArgs &a, int plane, int
     }
 }
 
+__device__ __forceinline__ void zero_acc(const RowArgs &a, int plane)
+{
+    if (blockIdx.x == 0 && threadIdx.x < NACC) a.acc[plane * NACC + threadIdx.x] = 0.0;
+}
+
 // grid (ceil(H / rows_per_cta), planes); block = max(T, 256) threads.
 // Thread t of a row owns samples [t*C, (t+1)*C).  Carries: Kogge-Stone
 // inside each warp (shuffles), then one warp combines the warp totals of
 // each row sequentially (one lane per row x pole x direction).
-template <int C>
+template <int C, int MODE>
 __global__ void __launch_bounds__(512) row_iir(RowArgs a, IIRCoef cf)
 {
     __shared__ float4 wt[16][NP];    // warp totals [warp slot][pole] (causal re, im, anticausal re, im)
@@ -470,10 +556,11 @@ __global__ void __launch_bounds__(512) row_iir(RowArgs a, IIRCoef cf)
     const int ls = lane & (L - 1);
     const int wpr = T >> 5;         // warps per row (0 if T < 32)
     const int x0 = t * C;
-    if (P.mode != 0) return;  // copy mode: the column pass copies f
+    if (MODE == MODE_ADJ) zero_acc(a, plane);
+    if (P.mode != 0) return;  // copy mode: the column pass copies f (or dL/dy)
 
-    float u[C], phi[C];
-    load_row_chunk<C>(a, plane, row, rv, x0, P, u, phi);
+    RowGen<C, MODE> gen;
+    gen.init(a, plane, row, rv, x0, P);
 
     // p^{C ls} and p^{C (31 - ls)}: carry of the previous / next warps through this warp's chunks
     float qcr[NP], qci[NP], qar[NP], qai[NP];
@@ -485,13 +572,11 @@ __global__ void __launch_bounds__(512) row_iir(RowArgs a, IIRCoef cf)
 
 #pragma unroll 1
     for (int k = 0; k < a.K; ++k) {
-        if (k > 0) {
-#pragma unroll
-            for (int j = 0; j < C; ++j) phi[j] *= u[j];
-        }
+        float x[C];
+        gen.channel(k, a.N, x);
         float y[C];
         float er[NP], ei[NP], sr[NP], si[NP];
-        chunk_local<C>(phi, y, er, ei, sr, si, cf);
+        chunk_local<C>(x, y, er, ei, sr, si, cf);
 
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
@@ -572,7 +657,7 @@ __global__ void __launch_bounds__(512) row_iir(RowArgs a, IIRCoef cf)
 
 // FIR row pass: the row's channel is staged in shared memory with zero halos.
 // grid (ceil(H / rows_per_cta), planes); block = max(T, 256) threads.
-template <int C, int WH>
+template <int C, int WH, int MODE>
 __global__ void __launch_bounds__(512) row_fir(RowArgs a, FIRCoef g)
 {
     extern __shared__ float srow[];  // [2][rows_per_cta][T*C + 2*WH]
@@ -587,10 +672,11 @@ __global__ void __launch_bounds__(512) row_fir(RowArgs a, FIRCoef g)
     const PlaneParams &P = a.pp[plane];
     const int x0 = t * C;
     const int span = T * C + 2 * WH;
+    if (MODE == MODE_ADJ) zero_acc(a, plane);
     if (P.mode != 0) return;
 
-    float u[C], phi[C];
-    load_row_chunk<C>(a, plane, row, rv, x0, P, u, phi);
+    RowGen<C, MODE> gen;
+    gen.init(a, plane, row, rv, x0, P);
     for (int i = tid; i < 2 * rows_per_cta * 2 * WH; i += blockDim.x) {
         const int par = i / (rows_per_cta * 2 * WH);
         const int rem = i % (rows_per_cta * 2 * WH);
@@ -602,13 +688,11 @@ __global__ void __launch_bounds__(512) row_fir(RowArgs a, FIRCoef g)
 
 #pragma unroll 1
     for (int k = 0; k < a.K; ++k) {
-        if (k > 0) {
-#pragma unroll
-            for (int j = 0; j < C; ++j) phi[j] *= u[j];
-        }
+        float x[C];
+        gen.channel(k, a.N, x);
         float *buf = srow + ((k & 1) * rows_per_cta + r_local) * span;
 #pragma unroll
-        for (int j = 0; j < C; ++j) buf[WH + x0 + j] = phi[j];
+        for (int j = 0; j < C; ++j) buf[WH + x0 + j] = x[j];
         __syncthreads();
         float win[C + 2 * WH];
 #pragma unroll
@@ -630,25 +714,154 @@ __global__ void __launch_bounds__(512) row_fir(RowArgs a, FIRCoef g)
 struct ColArgs {
     const float *ws;  // [planes][K][H][Wp]
     const float *f;
-    float *y;
+    float *y;         // forward: output image; adjoint: dL/dh (dL/df after the finish kernel)
+    const float *gy;  // MODE_ADJ: dL/dy
+    float *saved;     // MODE_SAVE: written; MODE_ADJ: read
     const PlaneParams *pp;
     uint32_t *status;
+    double *acc;      // MODE_ADJ
     int H, W, pitch, Wp, K, N;
 };
 
-__device__ __forceinline__ float finish_pixel(const PlaneParams &P, float f, float u, float p, float q, float psi0,
-                                              bool &nonpos)
+// Per-pixel combine over descending channel m for RPT pixels.
+//   forward: p = sum m u^{m-1} Psi_m (P~); q = sum_{1..N} u^{m-1} Psi_m, which
+//            the last channel (m = 0) turns into Q~ = Psi_0 + s^2 u q
+//   save:    also dp = sum_{m>=2} m(m-1) u^{m-2} Psi_m, dq = sum_{1..N} m u^{m-1} Psi_m
+//   adjoint: with c_m the filtered adjoint channel, p = A = sum m c_m u^{m-1}, q = B = sum c_m u^m
+template <int RPT, int MODE>
+struct Combine {
+    float u[RPT], p[RPT], q[RPT], dp[MODE == MODE_SAVE ? RPT : 1], dq[MODE == MODE_SAVE ? RPT : 1];
+    __device__ __forceinline__ void init(float uu, int j)
+    {
+        u[j] = uu;
+        p[j] = q[j] = 0.f;
+        if (MODE == MODE_SAVE) dp[j] = dq[j] = 0.f;
+    }
+    __device__ __forceinline__ void step(int m, int N, float s2, const float (&y)[RPT])
+    {
+        const float mk = (float)m;
+        if (MODE == MODE_ADJ) {
+#pragma unroll
+            for (int j = 0; j < RPT; ++j) {
+                p[j] = fmaf(u[j], p[j], mk * y[j]);
+                q[j] = fmaf(u[j], q[j], y[j]);
+            }
+            return;
+        }
+        if (m == 0) {
+#pragma unroll
+            for (int j = 0; j < RPT; ++j) q[j] = fmaf(s2 * u[j], q[j], y[j]);  // Q~
+            return;
+        }
+        if (MODE == MODE_SAVE) {
+            const float mm1 = mk * (float)(m - 1);
+#pragma unroll
+            for (int j = 0; j < RPT; ++j) dp[j] = fmaf(u[j], dp[j], mm1 * y[j]);
+            if (m <= N) {
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) dq[j] = fmaf(u[j], dq[j], mk * y[j]);
+            }
+        }
+        if (m <= N) {
+#pragma unroll
+            for (int j = 0; j < RPT; ++j) q[j] = fmaf(u[j], q[j], y[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) p[j] = fmaf(u[j], p[j], mk * y[j]);
+    }
+};
+
+struct AdjSums {
+    float gy, gh, s2g;
+};
+
+// Writes the result for one pixel (r, x) of the plane.
+template <int RPT, int MODE>
+__device__ __forceinline__ void finish_pixel(const ColArgs &a, const PlaneParams &P, int plane, int r, int x,
+                                             const Combine<RPT, MODE> &cb, int j, bool &nonpos, AdjSums &sums)
 {
-    if (P.mode != 0) return f;
-    const float Q = fmaf(P.s2 * u, q, psi0);
+    const size_t pix = ((size_t)plane * a.H + r) * a.pitch + x;
+    if (MODE == MODE_ADJ) {
+        const float g = __ldg(a.gy + pix);
+        if (P.mode != 0) {  // the forward copied this plane: dL/df = dL/dy
+            a.y[pix] = g;
+            sums.gy += g;
+            sums.gh += g;
+            return;
+        }
+        const float Pt = __ldg(a.saved + saved_idx(plane, 0, a.H, a.W, r, x));
+        const float Qt = __ldg(a.saved + saved_idx(plane, 1, a.H, a.W, r, x));
+        const float dpv = __ldg(a.saved + saved_idx(plane, 2, a.H, a.W, r, x));
+        const float dqv = __ldg(a.saved + saved_idx(plane, 3, a.H, a.W, r, x));
+        const float u = cb.u[j];
+        float gdir = 0.f;
+        if (Qt > 0.f && isfinite(g)) {
+            const float al = __fdiv_rn(g * P.R, Qt);
+            const float rho = __fdiv_rn(Pt, Qt);
+            gdir = al * fmaf(-rho * P.s2, dqv, dpv);
+        }
+        const float E = envelope(P, u);
+        const float gind = E * fmaf(-P.s2 * u, cb.q[j], cb.p[j]);
+        const float gu = gind + gdir;
+        const float gh = gu * P.invR;
+        a.y[pix] = gh;
+        sums.gy += isfinite(g) ? g : 0.f;
+        sums.gh += gh;
+        if (P.s2 > 0.f) sums.s2g += __fdiv_rn(u, P.s2) * gdir - 0.5f * u * u * E * cb.q[j];
+        return;
+    }
+    if (P.mode != 0) {
+        a.y[pix] = __ldg(a.f + pix);
+        return;
+    }
+    const float Q = cb.q[j];
+    float out;
     if (!(Q > 0.f)) {
         nonpos = true;
-        return __int_as_float(0x7fc00000);
+        out = __int_as_float(0x7fc00000);
+    } else {
+        out = fmaf(P.R, __fdiv_rn(cb.p[j], Q), P.tc);
     }
-    return fmaf(P.R, __fdiv_rn(p, Q), P.tc);
+    a.y[pix] = out;
+    if (MODE == MODE_SAVE) {
+        a.saved[saved_idx(plane, 0, a.H, a.W, r, x)] = cb.p[j];
+        a.saved[saved_idx(plane, 1, a.H, a.W, r, x)] = Q;
+        a.saved[saved_idx(plane, 2, a.H, a.W, r, x)] = cb.dp[j];
+        a.saved[saved_idx(plane, 3, a.H, a.W, r, x)] = cb.dq[j];
+    }
 }
 
-constexpr int COL_ROWS = 512;                          // rows per CTA in the recursive column pass
+// Block-wide sum of the adjoint partials, then one FP64 atomic per quantity.
+__device__ __forceinline__ void flush_sums(const ColArgs &a, int plane, AdjSums s)
+{
+    __shared__ float red[3][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        s.gy += __shfl_down_sync(0xffffffffu, s.gy, o);
+        s.gh += __shfl_down_sync(0xffffffffu, s.gh, o);
+        s.s2g += __shfl_down_sync(0xffffffffu, s.s2g, o);
+    }
+    if (lane == 0) {
+        red[0][warp] = s.gy;
+        red[1][warp] = s.gh;
+        red[2][warp] = s.s2g;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t0 += red[0][w];
+            t1 += red[1][w];
+            t2 += red[2][w];
+        }
+        atomicAdd(a.acc + plane * NACC + 0, t0);
+        atomicAdd(a.acc + plane * NACC + 1, t1);
+        atomicAdd(a.acc + plane * NACC + 2, t2);
+    }
+}
+
+constexpr int COL_ROWS = 512;                                    // rows per CTA in the recursive column pass
 constexpr int COL_TILE_FLOATS = (COL_ROWS + COL_ROWS / 16) * 8;  // padded [row][8 cols] tile
 
 // Shared-memory tile row r of the 8-column strip starts at (r + r/16) * 8
@@ -673,8 +886,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // warp 0 combines the 8 warp totals of each column and the CTA totals of the
 // cluster (DSMEM) with one lane per column x pole x direction.
 // grid (strips * CL, planes), block 256, cluster (CL, 1, 1).
-template <int C, bool CLUSTER>
-__global__ void __launch_bounds__(256, 2) col_iir(ColArgs a, IIRCoef cf)
+template <int C, int MODE>
+__global__ void __launch_bounds__(256, MODE == MODE_SAVE ? 1 : 2) col_iir(ColArgs a, IIRCoef cf)
 {
     extern __shared__ __align__(16) float tiles[];  // [2][COL_TILE_FLOATS]
     __shared__ float4 wt[8][8][NP];    // [warp][col][pole] warp totals (causal re, im, anticausal re, im)
@@ -684,12 +897,9 @@ __global__ void __launch_bounds__(256, 2) col_iir(ColArgs a, IIRCoef cf)
     const int lane = tid & 31, warp = tid >> 5;
     const int col = lane & 7, l4 = lane >> 3;
     const int plane = blockIdx.y;
-    int rank = 0, CL = 1;
-    if (CLUSTER) {
-        cg::cluster_group cl = cg::this_cluster();
-        rank = (int)cl.block_rank();
-        CL = (int)cl.num_blocks();
-    }
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int CL = (int)cl.num_blocks();
     const int strip = blockIdx.x / CL;
     const int x = strip * 8 + col;
     const int chunk_cta = warp * 4 + l4;
@@ -714,15 +924,14 @@ __global__ void __launch_bounds__(256, 2) col_iir(ColArgs a, IIRCoef cf)
         cp_async_commit();
     };
 
-    float u[C], p[C], q[C];
+    Combine<C, MODE> cb;
     const float *fcol = a.f + (size_t)plane * a.H * a.pitch;
 #pragma unroll
     for (int j = 0; j < C; ++j) {
         const int r = row0 + j;
         const bool in = (r < a.H) && (x < a.W);
         const float fv = in ? __ldg(fcol + (size_t)r * a.pitch + x) : 0.f;
-        u[j] = (fv - P.tc) * P.invR;
-        p[j] = q[j] = 0.f;
+        cb.init((fv - P.tc) * P.invR, j);
     }
     float qcr[NP], qci[NP], qar[NP], qai[NP];
 #pragma unroll
@@ -732,7 +941,6 @@ __global__ void __launch_bounds__(256, 2) col_iir(ColArgs a, IIRCoef cf)
     }
 
     issue_tile(a.K - 1, (a.K - 1) & 1);
-    float psi0[C];
 #pragma unroll 1
     for (int k = a.K - 1; k >= 0; --k) {
         cp_async_wait_all();
@@ -805,41 +1013,36 @@ __global__ void __launch_bounds__(256, 2) col_iir(ColArgs a, IIRCoef cf)
                 totr = nr + (gdir == 0 ? tt.x : tt.z);
                 toti = ni + (gdir == 0 ? tt.y : tt.w);
             }
-            if (CLUSTER) {
-                float *dst = gdir == 0 ? &ct[gcol][gm].x : &ct[gcol][gm].z;
-                dst[0] = totr;
-                dst[1] = toti;
-            }
+            float *dst = gdir == 0 ? &ct[gcol][gm].x : &ct[gcol][gm].z;
+            dst[0] = totr;
+            dst[1] = toti;
         }
-        if (CLUSTER) {
-            cg::cluster_group cl = cg::this_cluster();
-            cl.sync();  // CTA totals of the whole cluster written
-            if (warp == 0) {
-                // level 3: carry entering this CTA from the other CTAs of the column
-                const float p32r = cf.Pr[gm][5], p32i = cf.Pi[gm][5];
-                float Cr = 0.f, Ci = 0.f;
-                const int nsteps = gdir == 0 ? rank : CL - 1 - rank;
-                for (int s = 0; s < nsteps; ++s) {
-                    const int r = gdir == 0 ? s : CL - 1 - s;
-                    const float4 tt = *cl.map_shared_rank(&ct[gcol][gm], r);
-                    float nr, ni;
-                    cmul(nr, ni, p32r, p32i, Cr, Ci);
-                    Cr = nr + (gdir == 0 ? tt.x : tt.z);
-                    Ci = ni + (gdir == 0 ? tt.y : tt.w);
-                }
-                // propagate it through the warps before (causal) / after (anticausal) each warp
-                const float p4r = cf.Pr[gm][2], p4i = cf.Pi[gm][2];
+        cl.sync();  // CTA totals of the whole cluster written
+        if (warp == 0) {
+            // level 3: carry entering this CTA from the other CTAs of the column
+            const float p32r = cf.Pr[gm][5], p32i = cf.Pi[gm][5];
+            float Cr = 0.f, Ci = 0.f;
+            const int nsteps = gdir == 0 ? rank : CL - 1 - rank;
+            for (int s = 0; s < nsteps; ++s) {
+                const int r = gdir == 0 ? s : CL - 1 - s;
+                const float4 tt = *cl.map_shared_rank(&ct[gcol][gm], r);
+                float nr, ni;
+                cmul(nr, ni, p32r, p32i, Cr, Ci);
+                Cr = nr + (gdir == 0 ? tt.x : tt.z);
+                Ci = ni + (gdir == 0 ? tt.y : tt.w);
+            }
+            // propagate it through the warps before (causal) / after (anticausal) each warp
+            const float p4r = cf.Pr[gm][2], p4i = cf.Pi[gm][2];
 #pragma unroll
-                for (int s = 0; s < 8; ++s) {
-                    const int w = gdir == 0 ? s : 7 - s;
-                    float *dst = gdir == 0 ? &wcar[w][gcol][gm].x : &wcar[w][gcol][gm].z;
-                    dst[0] += Cr;
-                    dst[1] += Ci;
-                    float nr, ni;
-                    cmul(nr, ni, p4r, p4i, Cr, Ci);
-                    Cr = nr;
-                    Ci = ni;
-                }
+            for (int s = 0; s < 8; ++s) {
+                const int w = gdir == 0 ? s : 7 - s;
+                float *dst = gdir == 0 ? &wcar[w][gcol][gm].x : &wcar[w][gcol][gm].z;
+                dst[0] += Cr;
+                dst[1] += Ci;
+                float nr, ni;
+                cmul(nr, ni, p4r, p4i, Cr, Ci);
+                Cr = nr;
+                Ci = ni;
             }
         }
         __syncthreads();
@@ -850,40 +1053,28 @@ __global__ void __launch_bounds__(256, 2) col_iir(ColArgs a, IIRCoef cf)
             cmadd(ar[m], ai[m], qar[m], qai[m], cw.z, cw.w);
         }
         chunk_correct<C>(y, cr, ci, ar, ai, cf);
-        if (k == 0) {
-#pragma unroll
-            for (int j = 0; j < C; ++j) psi0[j] = y[j];
-        } else {
-            const float mk = (float)k;
-            if (k <= a.N) {
-#pragma unroll
-                for (int j = 0; j < C; ++j) q[j] = fmaf(u[j], q[j], y[j]);
-            }
-#pragma unroll
-            for (int j = 0; j < C; ++j) p[j] = fmaf(u[j], p[j], mk * y[j]);
-        }
+        cb.step(k, a.N, P.s2, y);
     }
-    if (CLUSTER) {
-        // no CTA may leave while a peer can still read its shared memory
-        cg::this_cluster().sync();
-    }
+    // no CTA may leave while a peer can still read its shared memory
+    cl.sync();
     bool nonpos = false;
-    float *ycol = a.y + (size_t)plane * a.H * a.pitch;
+    AdjSums sums = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int j = 0; j < C; ++j) {
         const int r = row0 + j;
-        if (r < a.H && x < a.W) {
-            const float fv = filt ? 0.f : __ldg(fcol + (size_t)r * a.pitch + x);
-            ycol[(size_t)r * a.pitch + x] = finish_pixel(P, fv, u[j], p[j], q[j], psi0[j], nonpos);
-        }
+        if (r < a.H && x < a.W) finish_pixel<C, MODE>(a, P, plane, r, x, cb, j, nonpos, sums);
     }
-    if (__any_sync(0xffffffffu, nonpos) && lane == 0) atomicOr(a.status, 0x1u);
+    if (MODE == MODE_ADJ) {
+        flush_sums(a, plane, sums);
+    } else if (__any_sync(0xffffffffu, nonpos) && lane == 0) {
+        atomicOr(a.status, 0x1u);
+    }
 }
 
 // Column pass for the FIR filter: 2-D tiles of 32 columns x 64 rows; the
 // channel's tile plus a WH-row halo is staged in shared memory.
 // grid (ceil(W/32), ceil(H/64), planes), block 256 (32 columns x 8 row groups of 8).
-template <int WH>
+template <int WH, int MODE>
 __global__ void __launch_bounds__(256) col_fir(ColArgs a, FIRCoef g)
 {
     constexpr int TH = 64, RPT = 8;
@@ -894,15 +1085,14 @@ __global__ void __launch_bounds__(256) col_fir(ColArgs a, FIRCoef g)
     const int rbase = blockIdx.y * TH;
     const PlaneParams &P = a.pp[plane];
     const bool filt = (P.mode == 0);
-    float u[RPT], p[RPT], q[RPT], psi0[RPT];
+    Combine<RPT, MODE> cb;
     const float *fp = a.f + (size_t)plane * a.H * a.pitch;
 #pragma unroll
     for (int j = 0; j < RPT; ++j) {
         const int r = rbase + ty * RPT + j;
         const bool in = (r < a.H) && (x < a.W);
         const float fv = in ? __ldg(fp + (size_t)r * a.pitch + x) : 0.f;
-        u[j] = (fv - P.tc) * P.invR;
-        p[j] = q[j] = psi0[j] = 0.f;
+        cb.init((fv - P.tc) * P.invR, j);
     }
     const float *wsp = a.ws + (size_t)plane * a.K * a.H * a.Wp;
     if (filt) {
@@ -926,31 +1116,46 @@ __global__ void __launch_bounds__(256) col_fir(ColArgs a, FIRCoef g)
                 for (int dd = 1; dd <= WH; ++dd) acc = fmaf(g.g[dd], win[j + WH - dd] + win[j + WH + dd], acc);
                 y[j] = acc;
             }
-            if (k == 0) {
-#pragma unroll
-                for (int j = 0; j < RPT; ++j) psi0[j] = y[j];
-            } else {
-                const float mk = (float)k;
-                if (k <= a.N) {
-#pragma unroll
-                    for (int j = 0; j < RPT; ++j) q[j] = fmaf(u[j], q[j], y[j]);
-                }
-#pragma unroll
-                for (int j = 0; j < RPT; ++j) p[j] = fmaf(u[j], p[j], mk * y[j]);
-            }
+            cb.step(k, a.N, P.s2, y);
         }
     }
     bool nonpos = false;
-    float *yp = a.y + (size_t)plane * a.H * a.pitch;
+    AdjSums sums = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int j = 0; j < RPT; ++j) {
         const int r = rbase + ty * RPT + j;
-        if (r < a.H && x < a.W) {
-            const float fv = filt ? 0.f : __ldg(fp + (size_t)r * a.pitch + x);
-            yp[(size_t)r * a.pitch + x] = finish_pixel(P, fv, u[j], p[j], q[j], psi0[j], nonpos);
-        }
+        if (r < a.H && x < a.W) finish_pixel<RPT, MODE>(a, P, plane, r, x, cb, j, nonpos, sums);
     }
-    if (__any_sync(0xffffffffu, nonpos) && tx == 0) atomicOr(a.status, 0x1u);
+    if (MODE == MODE_ADJ) {
+        flush_sums(a, plane, sums);
+    } else if (__any_sync(0xffffffffu, nonpos) && tx == 0) {
+        atomicOr(a.status, 0x1u);
+    }
+}
+
+// Backward finish: dL/df = dL/dh + (sum dL/dy - sum dL/dh) / |I| when the
+// centre is the plane mean (Algorithm 1 step 1), and dL/dsigma_r per plane
+// = dL/d(s^2) * d(s^2)/dsigma_r = dL/d(s^2) * (-2 s^2 / sigma_r).
+// grid (ceil(H*W / 256), planes), block 256.
+__global__ void __launch_bounds__(256) grad_finish(float *__restrict__ grad, const double *__restrict__ acc,
+                                                   const PlaneParams *__restrict__ pp, int H, int W, int pitch,
+                                                   int centre_mean, double sigma_r, float *__restrict__ grad_sigma_r)
+{
+    const int plane = blockIdx.y;
+    const double *ac = acc + plane * NACC;
+    const long long n = (long long)H * W;
+    const float shift = centre_mean ? (float)((ac[0] - ac[1]) / (double)n) : 0.f;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const int r = (int)(i / W), c = (int)(i % W);
+        grad[((size_t)plane * H + r) * pitch + c] += shift;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && grad_sigma_r) {
+        const double s2 = (double)pp[plane].s2;
+        grad_sigma_r[plane] = (s2 > 0.0 && pp[plane].mode == 0 && !isinf(sigma_r))
+                                  ? (float)(ac[2] * (-2.0 * s2 / sigma_r))
+                                  : 0.f;
+    }
 }
 
 }  // namespace bfgp
