@@ -741,11 +741,13 @@ struct Combine {
     {
         const float mk = (float)m;
         if (MODE == MODE_ADJ) {
+            // A's lowest term is m = 1 (power u^0): channel 0 does not enter it
+            if (m >= 1) {
 #pragma unroll
-            for (int j = 0; j < RPT; ++j) {
-                p[j] = fmaf(u[j], p[j], mk * y[j]);
-                q[j] = fmaf(u[j], q[j], y[j]);
+                for (int j = 0; j < RPT; ++j) p[j] = fmaf(u[j], p[j], mk * y[j]);
             }
+#pragma unroll
+            for (int j = 0; j < RPT; ++j) q[j] = fmaf(u[j], q[j], y[j]);
             return;
         }
         if (m == 0) {
@@ -755,8 +757,10 @@ struct Combine {
         }
         if (MODE == MODE_SAVE) {
             const float mm1 = mk * (float)(m - 1);
+            if (m >= 2) {  // dp's lowest term is m = 2 (power u^0)
 #pragma unroll
-            for (int j = 0; j < RPT; ++j) dp[j] = fmaf(u[j], dp[j], mm1 * y[j]);
+                for (int j = 0; j < RPT; ++j) dp[j] = fmaf(u[j], dp[j], mm1 * y[j]);
+            }
             if (m <= N) {
 #pragma unroll
                 for (int j = 0; j < RPT; ++j) dq[j] = fmaf(u[j], dq[j], mk * y[j]);
