@@ -215,6 +215,45 @@ bf_status bf_gp_forward_noalloc(const float *f, float *y, int planes, int H, int
                                 float sigma_s, float sigma_r, const bf_gp_opts *opts, void *stream);
 
 /*
+ * Batched filtering: many planes of different sizes, each with its own
+ * sigma_s, sigma_r and order, filtered by four launches over all planes
+ * (stats, finalize, rows, columns), with the recursive Gaussian for every
+ * plane.  Same method and per-plane result as bf_gp_forward with
+ * BF_SPATIAL_IIR (the paper filters one image at a time; batching is an
+ * implementation choice).
+ *
+ *   bf_gp_batched_plan_create: validates the planes (H, W <= 4096; pitch >= W;
+ *     f, y device pointers that stay valid while the plan is used) and builds
+ *     the per-plane tables on the host (filter coefficients in FP64 rounded
+ *     to FP32).  opts.spatial must be AUTO or IIR; opts.order is ignored (each
+ *     plane's own order is used); the centre option applies to every plane.
+ *     The plan owns host memory only.
+ *   bf_gp_batched_plan_workspace: device bytes the plan needs (tables and
+ *     every plane's K row-filtered planes).
+ *   bf_gp_batched_plan_upload: copies the tables into ws (synchronises
+ *     `stream`); must be called once per workspace before bf_gp_batched.
+ *   bf_gp_batched: enqueues the four launches on `stream` and nothing else
+ *     (no copies, no host synchronisation), so it can be captured into a
+ *     CUDA graph and replayed.  ws must be the uploaded workspace.
+ *   bf_gp_batched_plan_destroy: frees the plan.
+ */
+typedef struct {
+    const float *f;  /* device input plane */
+    float *y;        /* device output plane (may not alias f) */
+    int H, W, pitch;
+    float sigma_s, sigma_r;
+    int order;
+} bf_gp_plane;
+
+typedef struct bf_gp_plan bf_gp_plan;
+
+bf_status bf_gp_batched_plan_create(const bf_gp_plane *planes, int n, const bf_gp_opts *opts, bf_gp_plan **out);
+bf_status bf_gp_batched_plan_workspace(const bf_gp_plan *plan, size_t *bytes);
+bf_status bf_gp_batched_plan_upload(bf_gp_plan *plan, void *ws, size_t ws_bytes, void *stream);
+bf_status bf_gp_batched(const bf_gp_plan *plan, void *ws, size_t ws_bytes, void *stream);
+void bf_gp_batched_plan_destroy(bf_gp_plan *plan);
+
+/*
  * Read the device status word written by the last call that used `ws`
  * (BF_DEV_* bits).  Synchronises `stream` first.
  */

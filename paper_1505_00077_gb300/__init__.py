@@ -53,6 +53,12 @@ class bf_gp_opts(ctypes.Structure):
                 ("fir_halfwidth", ctypes.c_int), ("t_c", ctypes.c_double), ("reserved", ctypes.c_int * 8)]
 
 
+class bf_gp_plane(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_void_p), ("y", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("pitch", ctypes.c_int), ("sigma_s", ctypes.c_float), ("sigma_r", ctypes.c_float),
+                ("order", ctypes.c_int)]
+
+
 _lib = None
 
 
@@ -84,6 +90,11 @@ def _load():
                                         P(bf_gp_opts), c_void_p, c_size_t, c_void_p]),
         "bf_gp_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int,
                                    c_float, c_float, P(bf_gp_opts), c_void_p, c_size_t, c_void_p]),
+        "bf_gp_batched_plan_create": (c_int, [P(bf_gp_plane), c_int, P(bf_gp_opts), P(c_void_p)]),
+        "bf_gp_batched_plan_workspace": (c_int, [c_void_p, P(c_size_t)]),
+        "bf_gp_batched_plan_upload": (c_int, [c_void_p, c_void_p, c_size_t, c_void_p]),
+        "bf_gp_batched": (c_int, [c_void_p, c_void_p, c_size_t, c_void_p]),
+        "bf_gp_batched_plan_destroy": (None, [c_void_p]),
         "bf_gp_forward_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_float, c_float,
                                           P(bf_gp_opts), c_void_p]),
         "bf_gp_host_workspace_size": (c_int, [c_int, c_int, c_int, c_float, P(bf_gp_opts), P(c_size_t)]),
@@ -105,7 +116,8 @@ def exported_symbols():
     """Names the binding expects the library to export."""
     return ["bf_gp_default_opts", "bf_status_string", "bf_gp_last_cuda_error", "bf_gp_version",
             "bf_gp_workspace_size", "bf_gp_forward", "bf_gp_phase_stats", "bf_gp_phase_rows", "bf_gp_phase_cols",
-            "bf_gp_forward_train", "bf_gp_backward", "bf_gp_forward_noalloc", "bf_gp_host_workspace_size", "bf_gp_forward_host",
+            "bf_gp_forward_train", "bf_gp_backward", "bf_gp_batched_plan_create", "bf_gp_batched_plan_workspace",
+            "bf_gp_batched_plan_upload", "bf_gp_batched", "bf_gp_batched_plan_destroy", "bf_gp_forward_noalloc", "bf_gp_host_workspace_size", "bf_gp_forward_host",
             "bf_gp_get_device_status", "bf_gp_get_plane_stats", "bf_gp_order_for_tol"]
 
 
@@ -191,6 +203,76 @@ def bf_gp_backward(f_ptr, gy_ptr, saved_ptr, gf_ptr, gsr_ptr, planes, H, W, pitc
     _check(_load().bf_gp_backward(_vp(f_ptr), _vp(gy_ptr), _vp(saved_ptr), _vp(gf_ptr), _vp(gsr_ptr or 0),
                                   int(planes), int(H), int(W), int(pitch), float(sigma_s), float(sigma_r),
                                   _op(opts), _vp(ws_ptr), int(ws_bytes), _vp(stream)), "bf_gp_backward")
+
+
+def bf_gp_batched_plan_create(planes, opts=None) -> int:
+    """planes: list of (f_ptr, y_ptr, H, W, pitch, sigma_s, sigma_r, order).  Returns the plan handle."""
+    arr = (bf_gp_plane * len(planes))()
+    for i, (f, y, H, W, pitch, ss, sr, order) in enumerate(planes):
+        arr[i] = bf_gp_plane(f, y, H, W, pitch, ss, sr, order)
+    h = ctypes.c_void_p(0)
+    _check(_load().bf_gp_batched_plan_create(arr, len(planes), _op(opts), ctypes.byref(h)), "bf_gp_batched_plan_create")
+    return int(h.value)
+
+
+def bf_gp_batched_plan_workspace(plan) -> int:
+    n = ctypes.c_size_t(0)
+    _check(_load().bf_gp_batched_plan_workspace(_vp(plan), ctypes.byref(n)), "bf_gp_batched_plan_workspace")
+    return int(n.value)
+
+
+def bf_gp_batched_plan_upload(plan, ws_ptr, ws_bytes, stream=0) -> None:
+    _check(_load().bf_gp_batched_plan_upload(_vp(plan), _vp(ws_ptr), int(ws_bytes), _vp(stream)),
+           "bf_gp_batched_plan_upload")
+
+
+def bf_gp_batched(plan, ws_ptr, ws_bytes, stream=0) -> None:
+    _check(_load().bf_gp_batched(_vp(plan), _vp(ws_ptr), int(ws_bytes), _vp(stream)), "bf_gp_batched")
+
+
+def bf_gp_batched_plan_destroy(plan) -> None:
+    _load().bf_gp_batched_plan_destroy(_vp(plan))
+
+
+class BatchedFilter:
+    """Owns a batched plan and its workspace for a fixed list of (input, output,
+    sigma_s, sigma_r, order) planes (float32 CUDA tensors [H, W]).  run()
+    enqueues the four batched launches on the current stream; it is safe to
+    capture in a CUDA graph."""
+
+    def __init__(self, planes, order_default=20, t_c=None):
+        import torch
+        self._keep = []
+        spec = []
+        for item in planes:
+            x, y, ss, sr = item[:4]
+            order = item[4] if len(item) > 4 else order_default
+            assert x.is_cuda and x.dtype == torch.float32 and x.dim() == 2 and x.is_contiguous()
+            assert y.shape == x.shape and y.is_contiguous()
+            self._keep.append((x, y))
+            spec.append((x.data_ptr(), y.data_ptr(), x.shape[0], x.shape[1], x.shape[1], float(ss), float(sr), int(order)))
+        self.plan = bf_gp_batched_plan_create(spec, make_opts(order_default, "iir", t_c))
+        self.ws_bytes = bf_gp_batched_plan_workspace(self.plan)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
+        bf_gp_batched_plan_upload(self.plan, self.ws.data_ptr(), self.ws_bytes,
+                                  torch.cuda.current_stream().cuda_stream)
+
+    def run(self, stream=None):
+        import torch
+        s = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        bf_gp_batched(self.plan, self.ws.data_ptr(), self.ws_bytes, s)
+
+    def status(self):
+        import torch
+        return bf_gp_get_device_status(self.ws.data_ptr(), torch.cuda.current_stream().cuda_stream)
+
+    def __del__(self):
+        try:
+            if getattr(self, "plan", None):
+                bf_gp_batched_plan_destroy(self.plan)
+                self.plan = None
+        except Exception:
+            pass
 
 
 BF_GP_NOALLOC_SCRATCH_BYTES = 32 << 20

@@ -6,8 +6,11 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
+#include <new>
 #include <mutex>
+#include <vector>
 
 #include "../../include/bf_gp.h"
 #include "bf_gp_device.cuh"
@@ -580,5 +583,180 @@ int bf_gp_order_for_tol(double sigma_r, double R, double eps)
     }
     return -1;
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batched
+
+struct bf_gp_plan {
+    std::vector<BatchPlane> bp;  // device pointers to ws filled at upload
+    std::vector<IIRCoef> coef;
+    std::vector<int> pre_stats, pre_rows, pre_cols;
+    std::vector<size_t> plane_off;  // byte offset of each plane's channel planes
+    int n = 0, CLmax = 1, total_stats = 0, total_rows = 0, total_strips = 0;
+    int centre_given = 0;
+    double tc_given = 0.0;
+    size_t off_params = 0, off_part = 0, off_tables = 0, off_planes = 0, total = 0;
+    size_t tables_bytes = 0;
+    const void *uploaded_ws = nullptr;
+};
+
+extern "C" {
+
+bf_status bf_gp_batched_plan_create(const bf_gp_plane *planes, int n, const bf_gp_opts *opts, bf_gp_plan **out)
+{
+    if (!planes || n < 1 || !out) return BF_ERR_INVALID_ARG;
+    bf_gp_opts d;
+    if (!opts) {
+        bf_gp_default_opts(&d);
+        opts = &d;
+    }
+    bf_status st = check_opts(opts);
+    if (st != BF_OK) return st;
+    if (opts->spatial == BF_SPATIAL_FIR) return BF_ERR_UNSUPPORTED;  // batched planes use the recursive filter
+    bf_gp_plan *pl = new (std::nothrow) bf_gp_plan;
+    if (!pl) return BF_ERR_INVALID_ARG;
+    pl->n = n;
+    pl->centre_given = opts->centre == BF_CENTRE_GIVEN ? 1 : 0;
+    pl->tc_given = opts->t_c;
+    pl->bp.resize(n);
+    pl->coef.resize(n);
+    pl->pre_stats.assign(n + 1, 0);
+    pl->pre_rows.assign(n + 1, 0);
+    pl->pre_cols.assign(n + 1, 0);
+    pl->plane_off.resize(n);
+    size_t planes_bytes = 0;
+    for (int i = 0; i < n; ++i) {
+        const bf_gp_plane &q = planes[i];
+        bf_gp_opts o = *opts;
+        o.order = q.order;
+        o.spatial = BF_SPATIAL_IIR;
+        Plan pp;
+        st = (q.f && q.y && q.pitch >= q.W && q.sigma_r > 0.f) ? make_plan(1, q.H, q.W, q.sigma_s, &o, &pp)
+                                                                  : BF_ERR_INVALID_ARG;
+        if (st == BF_OK && pp.T > 256) st = BF_ERR_UNSUPPORTED;  // rows up to 4096 samples in batched mode
+        if (st != BF_OK) {
+            delete pl;
+            return st;
+        }
+        BatchPlane &b = pl->bp[i];
+        std::memset(&b, 0, sizeof b);
+        b.f = q.f;
+        b.y = q.y;
+        b.H = q.H;
+        b.W = q.W;
+        b.pitch = q.pitch;
+        b.Wp = pp.Wp;
+        b.K = pp.K;
+        b.N = pp.N;
+        b.T = pp.T;
+        b.nblk = pp.nblk;
+        b.rows_per_block = pp.rows_per_block;
+        b.sigma_s = q.sigma_s;
+        b.sigma_r = q.sigma_r;
+        deriche_coefs((double)q.sigma_s, ROW_C, &pl->coef[i]);
+        const int rows_per_cta = 256 / pp.T;
+        pl->pre_stats[i + 1] = pl->pre_stats[i] + pp.nblk;
+        pl->pre_rows[i + 1] = pl->pre_rows[i] + (q.H + rows_per_cta - 1) / rows_per_cta;
+        pl->pre_cols[i + 1] = pl->pre_cols[i] + (q.W + 7) / 8;
+        pl->CLmax = std::max(pl->CLmax, pp.CL);
+        pl->plane_off[i] = planes_bytes;
+        planes_bytes = align_up(planes_bytes + sizeof(float) * (size_t)pp.K * q.H * pp.Wp, 256);
+    }
+    pl->total_stats = pl->pre_stats[n];
+    pl->total_rows = pl->pre_rows[n];
+    pl->total_strips = pl->pre_cols[n];
+    size_t off = HDR_BYTES;
+    pl->off_params = off;
+    off = align_up(off + sizeof(PlaneParams) * (size_t)n, 256);
+    pl->off_part = off;
+    off = align_up(off + sizeof(StatPartial) * (size_t)pl->total_stats, 256);
+    pl->off_tables = off;
+    pl->tables_bytes = sizeof(BatchPlane) * n + sizeof(IIRCoef) * n + sizeof(int) * 3 * (n + 1);
+    off = align_up(off + pl->tables_bytes, 256);
+    pl->off_planes = off;
+    pl->total = off + planes_bytes;
+    *out = pl;
+    return BF_OK;
+}
+
+bf_status bf_gp_batched_plan_workspace(const bf_gp_plan *plan, size_t *bytes)
+{
+    if (!plan || !bytes) return BF_ERR_INVALID_ARG;
+    *bytes = plan->total;
+    return BF_OK;
+}
+
+bf_status bf_gp_batched_plan_upload(bf_gp_plan *plan, void *ws, size_t ws_bytes, void *stream)
+{
+    if (!plan || !ws) return BF_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < plan->total) return BF_ERR_WORKSPACE;
+    const int n = plan->n;
+    char *wsb = static_cast<char *>(ws);
+    std::vector<char> img(plan->tables_bytes);
+    std::vector<BatchPlane> bp = plan->bp;
+    for (int i = 0; i < n; ++i) bp[i].ws = reinterpret_cast<float *>(wsb + plan->off_planes + plan->plane_off[i]);
+    size_t o = 0;
+    std::memcpy(img.data() + o, bp.data(), sizeof(BatchPlane) * n);
+    o += sizeof(BatchPlane) * n;
+    std::memcpy(img.data() + o, plan->coef.data(), sizeof(IIRCoef) * n);
+    o += sizeof(IIRCoef) * n;
+    std::memcpy(img.data() + o, plan->pre_stats.data(), sizeof(int) * (n + 1));
+    o += sizeof(int) * (n + 1);
+    std::memcpy(img.data() + o, plan->pre_rows.data(), sizeof(int) * (n + 1));
+    o += sizeof(int) * (n + 1);
+    std::memcpy(img.data() + o, plan->pre_cols.data(), sizeof(int) * (n + 1));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    BF_CUDA(cudaMemcpyAsync(wsb + plan->off_tables, img.data(), plan->tables_bytes, cudaMemcpyHostToDevice, s));
+    BF_CUDA(cudaStreamSynchronize(s));
+    const size_t smem = sizeof(float) * 2 * COL_TILE_FLOATS;
+    BF_CUDA(cudaFuncSetAttribute(batched_col_iir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    plan->uploaded_ws = ws;
+    return BF_OK;
+}
+
+bf_status bf_gp_batched(const bf_gp_plan *plan, void *ws, size_t ws_bytes, void *stream)
+{
+    if (!plan || !ws) return BF_ERR_INVALID_ARG;
+    if (ws != plan->uploaded_ws || ws_bytes < plan->total) return BF_ERR_WORKSPACE;
+    const int n = plan->n;
+    char *wsb = static_cast<char *>(ws);
+    const char *tb = wsb + plan->off_tables;
+    BatchArgs b;
+    b.bp = reinterpret_cast<const BatchPlane *>(tb);
+    b.coef = reinterpret_cast<const IIRCoef *>(tb + sizeof(BatchPlane) * n);
+    const int *pre = reinterpret_cast<const int *>(tb + sizeof(BatchPlane) * n + sizeof(IIRCoef) * n);
+    b.pre_stats = pre;
+    b.pre_rows = pre + (n + 1);
+    b.pre_cols = pre + 2 * (n + 1);
+    b.pp = reinterpret_cast<PlaneParams *>(wsb + plan->off_params);
+    b.part = reinterpret_cast<StatPartial *>(wsb + plan->off_part);
+    b.status = reinterpret_cast<uint32_t *>(wsb);
+    b.n = n;
+    b.centre_given = plan->centre_given;
+    b.tc_given = plan->tc_given;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    batched_stats_partial<<<plan->total_stats, 256, 0, s>>>(b);
+    batched_stats_finalize<<<n, 256, 0, s>>>(b);
+    batched_row_iir<<<plan->total_rows, 256, 0, s>>>(b);
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3((unsigned)(plan->total_strips * plan->CLmax), 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = sizeof(float) * 2 * COL_TILE_FLOATS;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)plan->CLmax;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    BF_CUDA(cudaLaunchKernelEx(&cfg, batched_col_iir, b));
+    BF_CUDA(cudaGetLastError());
+    return BF_OK;
+}
+
+void bf_gp_batched_plan_destroy(bf_gp_plan *plan) { delete plan; }
 
 }  // extern "C"

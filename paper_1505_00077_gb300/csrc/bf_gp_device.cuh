@@ -182,13 +182,11 @@ __device__ __forceinline__ float envelope(const PlaneParams &P, float u)
 
 // grid (nblk, planes), block 256.  Each block reduces a band of rows.  Block
 // (0, 0) also zeroes the status word of this call.
-__global__ void __launch_bounds__(256) stats_partial(const float *__restrict__ f, int H, int W, int pitch,
-                                                     int rows_per_block, StatPartial *__restrict__ part,
-                                                     uint32_t *__restrict__ status)
+__device__ __forceinline__ void stats_partial_body(const float *__restrict__ f, int H, int W, int pitch,
+                                                   int rows_per_block, int blk, StatPartial *__restrict__ out)
 {
-    const int plane = blockIdx.y;
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *status = 0u;
-    const int r0 = blockIdx.x * rows_per_block;
+    const int plane = 0;
+    const int r0 = blk * rows_per_block;
     const int r1 = min(H, r0 + rows_per_block);
     float mn = INFINITY, mx = -INFINITY;
     double sum = 0.0;
@@ -268,8 +266,17 @@ __global__ void __launch_bounds__(256) stats_partial(const float *__restrict__ f
             p.mx = fmaxf(p.mx, smx[w]);
             p.nonfinite += sbad[w];
         }
-        part[(size_t)plane * gridDim.x + blockIdx.x] = p;
+        *out = p;
     }
+}
+
+__global__ void __launch_bounds__(256) stats_partial(const float *__restrict__ f, int H, int W, int pitch,
+                                                     int rows_per_block, StatPartial *__restrict__ part,
+                                                     uint32_t *__restrict__ status)
+{
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *status = 0u;
+    stats_partial_body(f + (size_t)blockIdx.y * H * pitch, H, W, pitch, rows_per_block, blockIdx.x,
+                       part + (size_t)blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // 1/m, m = 0..KMAX (entry 0 unused): the beta recurrence multiplies instead of dividing.
@@ -286,12 +293,11 @@ __constant__ double c_inv[KMAX + 1] = {
 // product of s^2 / j), the common scale 2^e0 and the range flag.  ORs its
 // flags into the status word (zeroed by stats_partial of the same call).
 // for_backward: a constant plane is filtered (R := 1) instead of copied.
-__global__ void __launch_bounds__(256) stats_finalize(const StatPartial *__restrict__ part, int nblk,
-                                                      long long npix, int centre_given, double tc_given,
-                                                      double sigma_r, double sigma_s, int K, int for_backward,
-                                                      PlaneParams *__restrict__ pp, uint32_t *__restrict__ status)
+__device__ __forceinline__ void stats_finalize_body(const StatPartial *__restrict__ part, int nblk, long long npix,
+                                                    int centre_given, double tc_given, double sigma_r,
+                                                    double sigma_s, int K, int for_backward, int c,
+                                                    PlaneParams *__restrict__ pp, uint32_t *__restrict__ status)
 {
-    const int c = blockIdx.x;
     double sum = 0.0;
     float mn = INFINITY, mx = -INFINITY;
     int bad = 0;
@@ -392,6 +398,15 @@ __global__ void __launch_bounds__(256) stats_finalize(const StatPartial *__restr
         q.R_d = sh_R;
         if (flags) atomicOr(status, flags);
     }
+}
+
+__global__ void __launch_bounds__(256) stats_finalize(const StatPartial *__restrict__ part, int nblk,
+                                                      long long npix, int centre_given, double tc_given,
+                                                      double sigma_r, double sigma_s, int K, int for_backward,
+                                                      PlaneParams *__restrict__ pp, uint32_t *__restrict__ status)
+{
+    stats_finalize_body(part, nblk, npix, centre_given, tc_given, sigma_r, sigma_s, K, for_backward, blockIdx.x,
+                        pp, status);
 }
 
 // ------------------------------------------------------------------ modes
@@ -530,7 +545,7 @@ __device__ __forceinline__ void store_row_chunk(const RowArgs &a, int plane, int
 
 __device__ __forceinline__ void zero_acc(const RowArgs &a, int plane)
 {
-    if (blockIdx.x == 0 && threadIdx.x < NACC) a.acc[plane * NACC + threadIdx.x] = 0.0;
+    if (threadIdx.x < NACC) a.acc[plane * NACC + threadIdx.x] = 0.0;
 }
 
 // grid (ceil(H / rows_per_cta), planes); block = max(T, 256) threads.
@@ -538,25 +553,24 @@ __device__ __forceinline__ void zero_acc(const RowArgs &a, int plane)
 // inside each warp (shuffles), then one warp combines the warp totals of
 // each row sequentially (one lane per row x pole x direction).
 template <int C, int MODE>
-__global__ void __launch_bounds__(512) row_iir(RowArgs a, IIRCoef cf)
+__device__ __forceinline__ void row_iir_body(const RowArgs &a, const IIRCoef &cf, int grp, int plane)
 {
     __shared__ float4 wt[16][NP];    // warp totals [warp slot][pole] (causal re, im, anticausal re, im)
     __shared__ float4 wcar[16][NP];  // incoming carries of each warp
     const int T = a.T;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const int plane = blockIdx.y;
     const int rows_per_cta = blockDim.x / T;
     const int r_local = tid / T;
     const int t = tid % T;
-    const int row = blockIdx.x * rows_per_cta + r_local;
+    const int row = grp * rows_per_cta + r_local;
     const bool rv = row < a.H;
     const PlaneParams &P = a.pp[plane];
     const int L = T < 32 ? T : 32;  // segment width inside a warp
     const int ls = lane & (L - 1);
     const int wpr = T >> 5;         // warps per row (0 if T < 32)
     const int x0 = t * C;
-    if (MODE == MODE_ADJ) zero_acc(a, plane);
+    if (MODE == MODE_ADJ && grp == 0) zero_acc(a, plane);
     if (P.mode != 0) return;  // copy mode: the column pass copies f (or dL/dy)
 
     RowGen<C, MODE> gen;
@@ -655,6 +669,12 @@ __global__ void __launch_bounds__(512) row_iir(RowArgs a, IIRCoef cf)
     }
 }
 
+template <int C, int MODE>
+__global__ void __launch_bounds__(512) row_iir(RowArgs a, IIRCoef cf)
+{
+    row_iir_body<C, MODE>(a, cf, blockIdx.x, blockIdx.y);
+}
+
 // FIR row pass: the row's channel is staged in shared memory with zero halos.
 // grid (ceil(H / rows_per_cta), planes); block = max(T, 256) threads.
 template <int C, int WH, int MODE>
@@ -672,7 +692,7 @@ __global__ void __launch_bounds__(512) row_fir(RowArgs a, FIRCoef g)
     const PlaneParams &P = a.pp[plane];
     const int x0 = t * C;
     const int span = T * C + 2 * WH;
-    if (MODE == MODE_ADJ) zero_acc(a, plane);
+    if (MODE == MODE_ADJ && blockIdx.x == 0) zero_acc(a, plane);
     if (P.mode != 0) return;
 
     RowGen<C, MODE> gen;
@@ -891,7 +911,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // cluster (DSMEM) with one lane per column x pole x direction.
 // grid (strips * CL, planes), block 256, cluster (CL, 1, 1).
 template <int C, int MODE>
-__global__ void __launch_bounds__(256, MODE == MODE_SAVE ? 1 : 2) col_iir(ColArgs a, IIRCoef cf)
+__device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf, int strip, int plane)
 {
     extern __shared__ __align__(16) float tiles[];  // [2][COL_TILE_FLOATS]
     __shared__ float4 wt[8][8][NP];    // [warp][col][pole] warp totals (causal re, im, anticausal re, im)
@@ -900,11 +920,9 @@ __global__ void __launch_bounds__(256, MODE == MODE_SAVE ? 1 : 2) col_iir(ColArg
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int col = lane & 7, l4 = lane >> 3;
-    const int plane = blockIdx.y;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int CL = (int)cl.num_blocks();
-    const int strip = blockIdx.x / CL;
     const int x = strip * 8 + col;
     const int chunk_cta = warp * 4 + l4;
     const int rbase = rank * COL_ROWS;
@@ -1075,6 +1093,12 @@ __global__ void __launch_bounds__(256, MODE == MODE_SAVE ? 1 : 2) col_iir(ColArg
     }
 }
 
+template <int C, int MODE>
+__global__ void __launch_bounds__(256, MODE == MODE_SAVE ? 1 : 2) col_iir(ColArgs a, IIRCoef cf)
+{
+    col_iir_body<C, MODE>(a, cf, blockIdx.x / (int)cg::this_cluster().num_blocks(), blockIdx.y);
+}
+
 // Column pass for the FIR filter: 2-D tiles of 32 columns x 64 rows; the
 // channel's tile plus a WH-row halo is staged in shared memory.
 // grid (ceil(W/32), ceil(H/64), planes), block 256 (32 columns x 8 row groups of 8).
@@ -1160,6 +1184,106 @@ __global__ void __launch_bounds__(256) grad_finish(float *__restrict__ grad, con
                                   ? (float)(ac[2] * (-2.0 * s2 / sigma_r))
                                   : 0.f;
     }
+}
+
+// ------------------------------------------------------------------ batched
+
+// Many planes of different sizes, each with its own sigma_s, sigma_r and
+// order, in four launches (stats, finalize, rows, columns), every one of them
+// over all planes at once.  The tables below live in the caller's workspace
+// (written once by bf_gp_batched_plan_upload); blocks find their plane by a
+// binary search over exclusive prefix sums of the planes' work-item counts.
+// The recursive filter is used for every plane.
+struct BatchPlane {
+    const float *f;
+    float *y;
+    float *ws;  // this plane's K row-filtered planes [K][H][Wp]
+    int H, W, pitch, Wp, K, N, T, nblk, rows_per_block, pad;
+    double sigma_s, sigma_r;
+};
+
+struct BatchArgs {
+    const BatchPlane *bp;
+    const IIRCoef *coef;  // per plane (chunk length 16 for rows and columns)
+    PlaneParams *pp;
+    StatPartial *part;
+    const int *pre_stats, *pre_rows, *pre_cols;  // n + 1 entries each
+    uint32_t *status;
+    int n, centre_given;
+    double tc_given;
+};
+
+__device__ __forceinline__ int find_plane(const int *__restrict__ pre, int n, int id)
+{
+    int lo = 0, hi = n - 1;  // largest p with pre[p] <= id
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(pre + mid) <= id) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) batched_stats_partial(BatchArgs b)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) *b.status = 0u;
+    const int p = find_plane(b.pre_stats, b.n, blockIdx.x);
+    const BatchPlane &d = b.bp[p];
+    stats_partial_body(d.f, d.H, d.W, d.pitch, d.rows_per_block, blockIdx.x - b.pre_stats[p], b.part + blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256) batched_stats_finalize(BatchArgs b)
+{
+    const int p = blockIdx.x;
+    const BatchPlane &d = b.bp[p];
+    stats_finalize_body(b.part + b.pre_stats[p], d.nblk, (long long)d.H * d.W, b.centre_given, b.tc_given,
+                        d.sigma_r, d.sigma_s, d.K, 0, p, b.pp, b.status);
+}
+
+__global__ void __launch_bounds__(256) batched_row_iir(BatchArgs b)
+{
+    const int p = find_plane(b.pre_rows, b.n, blockIdx.x);
+    const BatchPlane &d = b.bp[p];
+    RowArgs a;
+    a.f = d.f;
+    a.gy = nullptr;
+    a.saved = nullptr;
+    a.ws = d.ws;
+    a.pp = b.pp + p;
+    a.acc = nullptr;
+    a.H = d.H;
+    a.W = d.W;
+    a.pitch = d.pitch;
+    a.Wp = d.Wp;
+    a.K = d.K;
+    a.T = d.T;
+    a.N = d.N;
+    row_iir_body<CMAX, MODE_FWD>(a, b.coef[p], blockIdx.x - b.pre_rows[p], 0);
+}
+
+// cluster (CLmax, 1, 1): one cluster per (plane, 8-column strip); CTAs below
+// a shorter plane's last row take part in the carries with empty tiles.
+__global__ void __launch_bounds__(256, 2) batched_col_iir(BatchArgs b)
+{
+    const int cid = blockIdx.x / (int)cg::this_cluster().num_blocks();
+    const int p = find_plane(b.pre_cols, b.n, cid);
+    const BatchPlane &d = b.bp[p];
+    ColArgs a;
+    a.ws = d.ws;
+    a.f = d.f;
+    a.y = d.y;
+    a.gy = nullptr;
+    a.saved = nullptr;
+    a.pp = b.pp + p;
+    a.status = b.status;
+    a.acc = nullptr;
+    a.H = d.H;
+    a.W = d.W;
+    a.pitch = d.pitch;
+    a.Wp = d.Wp;
+    a.K = d.K;
+    a.N = d.N;
+    col_iir_body<CMAX, MODE_FWD>(a, b.coef[p], cid - b.pre_cols[p], 0);
 }
 
 }  // namespace bfgp
