@@ -302,7 +302,7 @@ __device__ __forceinline__ void stats_finalize_body(const StatPartial *__restric
     float mn = INFINITY, mx = -INFINITY;
     int bad = 0;
     for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-        const StatPartial p = part[(size_t)c * nblk + b];
+        const StatPartial p = part[b];  // this plane's partials
         sum += p.sum;
         mn = fminf(mn, p.mn);
         mx = fmaxf(mx, p.mx);
@@ -405,8 +405,8 @@ __global__ void __launch_bounds__(256) stats_finalize(const StatPartial *__restr
                                                       double sigma_r, double sigma_s, int K, int for_backward,
                                                       PlaneParams *__restrict__ pp, uint32_t *__restrict__ status)
 {
-    stats_finalize_body(part, nblk, npix, centre_given, tc_given, sigma_r, sigma_s, K, for_backward, blockIdx.x,
-                        pp, status);
+    stats_finalize_body(part + (size_t)blockIdx.x * nblk, nblk, npix, centre_given, tc_given, sigma_r, sigma_s, K,
+                        for_backward, blockIdx.x, pp, status);
 }
 
 // ------------------------------------------------------------------ modes
