@@ -30,6 +30,13 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+EXTRA_WORKLOADS = {
+    # batched: 64 images, sides U{256..2048}, 3 planes each, per-image sigma_s in [1, 16], sigma_r in [10, 60]
+    "gpf-batched-64img-3ch-N20-iir": "config4",
+    # differentiation: 16 x 512^2, sigma_s 5, sigma_r 25, N 20, forward + hand-written backward
+    "gpf-16x512x512-ss5-sr25-N20-fwdbwd": "config5",
+}
+
 WORKLOADS = {
     # name: (H, W, sigma_s, sigma_r, order, spatial, generator)
     "gpf-4096x4096-ss10-sr20-N20-iir": (4096, 4096, 10.0, 20.0, 20, "iir", "config3"),
@@ -222,7 +229,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(EXTRA_WORKLOADS), default=DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -233,7 +240,12 @@ def main():
         args.warmup = 3
     rank, world, local = dist_env()
     if args.impl == "reference":
+        if args.workload in EXTRA_WORKLOADS:
+            print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle arm covers the single-image workloads"}))
+            return 0
         return run_reference(args, rank, world)
+    if args.workload in EXTRA_WORKLOADS:
+        return run_extra(args, rank, world, local)
 
     import numpy as np
     import torch
@@ -370,6 +382,146 @@ def main():
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+def _clock_wrap(local, fn):
+    sampler = ClockSampler(local)
+    sampler.start()
+    sampler.mark("t0")
+    out = fn()
+    sampler.mark("t1")
+    return out, sampler.stop()
+
+
+def run_extra(args, rank, world, local):
+    """Batched (config 4) and forward + backward (config 5) workloads, one GPU."""
+    import numpy as np
+    import torch
+
+    import paper_1505_00077_gb300 as bf
+    import synthetic
+
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    bf.build()
+    peak, peak_kind = measured_peaks()
+    kind = EXTRA_WORKLOADS[args.workload]
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    def timed(fn, steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    if kind == "config4":
+        specs = synthetic.config4_specs()
+        planes = []
+        K = 22
+        for spec in specs:
+            img = synthetic.config4_image(spec)
+            for c in range(3):
+                x = torch.from_numpy(np.ascontiguousarray(img[c])).cuda()
+                planes.append((x, torch.empty_like(x), spec[3], spec[4], 20))
+        px = sum(x.numel() for x, *_ in planes)
+        bfilt = bf.BatchedFilter(planes)
+        for _ in range(args.warmup):
+            bfilt.run()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            bfilt.run()
+        steps = max(1, min(args.steps, 50))
+        for _ in range(2):
+            g.replay()
+        ms, clocks = _clock_wrap(local, lambda: timed(g.replay, steps))
+        status = bfilt.status()
+        # plain form: the single-image path plane by plane (same kernels, 4 launches per plane)
+        maxws = max(bf.bf_gp_workspace_size(1, x.shape[0], x.shape[1], ss, bf.make_opts(o, "iir"))
+                    for x, y, ss, sr, o in planes)
+        ws = torch.empty(maxws, dtype=torch.uint8, device="cuda")
+
+        def plain():
+            for x, y, ss, sr, o in planes:
+                bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, x.shape[0], x.shape[1], x.shape[1], ss, sr,
+                                 bf.make_opts(o, "iir"), ws.data_ptr(), maxws, sp)
+        plain()
+        ms_plain = timed(plain, max(1, min(args.steps, 5)))
+        bytes_step = (8 * K + 16) * px
+        line = {"metric": "Mpixel/s", "value": px / (ms / 1e3) / 1e6, "unit": "Mpixel/s", "n_gpus": 1,
+                "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": args.workload, "planes": len(planes), "pixels": px, "order": 20,
+                           "spatial": "iir", "how": "CUDA graph of the four batched launches, replayed"},
+                "plain_loop": {"value": px / (ms_plain / 1e3) / 1e6, "unit": "Mpixel/s", "ms_per_step": ms_plain,
+                               "how": "bf_gp_forward plane by plane, same kernels, no graph"},
+                "step_roofline": {"bound": "hbm", "algorithmic_bytes_per_step": bytes_step,
+                                  "achieved": bytes_step / (ms / 1e3) / 1e9, "peak": peak,
+                                  "frac": bytes_step / (ms / 1e3) / 1e9 / peak, "peak_kind": peak_kind},
+                "gpu_launches": 4 * steps, "device_status": status}
+        if clocks:
+            line["clocks"] = clocks
+        print(json.dumps(line), flush=True)
+        return 0
+
+    # config 5: forward + backward on a 16 x 512^2 batch (planes in one call)
+    xb = synthetic.config5_batch(16)[:, 0]
+    B, H, W = xb.shape
+    K = 22
+    x = torch.from_numpy(np.ascontiguousarray(xb)).cuda()
+    gy = torch.from_numpy(np.random.default_rng(5).normal(size=xb.shape).astype(np.float32)).cuda()
+    opts = bf.make_opts(20, "iir")
+    need = bf.bf_gp_workspace_size(B, H, W, 5.0, opts)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    y = torch.empty_like(x)
+    saved = torch.empty((B, 4, H, W), dtype=torch.float32, device="cuda")
+    gx = torch.empty_like(x)
+    gsr = torch.empty(B, dtype=torch.float32, device="cuda")
+
+    def fwd():
+        bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), B, H, W, W, 5.0, 25.0, opts, ws.data_ptr(), need, sp)
+
+    def fwdbwd():
+        bf.bf_gp_forward_train(x.data_ptr(), y.data_ptr(), saved.data_ptr(), B, H, W, W, 5.0, 25.0, opts,
+                               ws.data_ptr(), need, sp)
+        bf.bf_gp_backward(x.data_ptr(), gy.data_ptr(), saved.data_ptr(), gx.data_ptr(), gsr.data_ptr(), B, H, W, W,
+                          5.0, 25.0, opts, ws.data_ptr(), need, sp)
+
+    def plain_fwd():  # the single-image form: one call per image
+        for i in range(B):
+            bf.bf_gp_forward(x[i].data_ptr(), y[i].data_ptr(), 1, H, W, W, 5.0, 25.0, opts, ws.data_ptr(), need, sp)
+
+    for _ in range(args.warmup):
+        fwdbwd()
+        fwd()
+        plain_fwd()
+    steps = max(1, args.steps)
+    ms, clocks = _clock_wrap(local, lambda: timed(fwdbwd, steps))
+    ms_fwd = timed(fwd, steps)
+    ms_plain = timed(plain_fwd, steps)
+    px = B * H * W
+    bytes_step = ((8 * K + 32) + (8 * K + 60)) * px  # forward with saves + backward (see DESIGN)
+    line = {"metric": "Mpixel/s", "value": px / (ms / 1e3) / 1e6, "unit": "Mpixel/s", "n_gpus": 1, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "batch": B, "H": H, "W": W, "sigma_s": 5.0, "sigma_r": 25.0,
+                       "order": 20, "spatial": "iir", "step": "bf_gp_forward_train + bf_gp_backward"},
+            "fwd_only": {"value": px / (ms_fwd / 1e3) / 1e6, "unit": "Mpixel/s", "ms_per_step": ms_fwd},
+            "plain_single_image_fwd": {"value": px / (ms_plain / 1e3) / 1e6, "unit": "Mpixel/s",
+                                       "ms_per_step": ms_plain},
+            "step_roofline": {"bound": "hbm", "algorithmic_bytes_per_step": bytes_step,
+                              "achieved": bytes_step / (ms / 1e3) / 1e9, "peak": peak,
+                              "frac": bytes_step / (ms / 1e3) / 1e9 / peak, "peak_kind": peak_kind},
+            "gpu_launches": 8 * steps}
+    if clocks:
+        line["clocks"] = clocks
+    print(json.dumps(line), flush=True)
     return 0
 
 
