@@ -81,7 +81,9 @@ typedef struct {
     int centre;         /* bf_centre */
     int fir_halfwidth;  /* w for FIR; 0 selects ceil(3 sigma_s) (Sec. 1) */
     double t_c;         /* centre when centre == BF_CENTRE_GIVEN */
-    int reserved[8];    /* must be zero */
+    int engine;         /* recursive filter only: 0 = tensor cores (chunk-local products on mma.sync,
+                           TF32 x 3), 1 = FP32 CUDA cores (sequential recursions in each chunk) */
+    int reserved[7];    /* must be zero */
 } bf_gp_opts;
 
 /* Fill *opts with the defaults: N = 20, AUTO spatial operator, mean centre. */

@@ -50,7 +50,8 @@ class BFError(RuntimeError):
 
 class bf_gp_opts(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("spatial", ctypes.c_int), ("centre", ctypes.c_int),
-                ("fir_halfwidth", ctypes.c_int), ("t_c", ctypes.c_double), ("reserved", ctypes.c_int * 8)]
+                ("fir_halfwidth", ctypes.c_int), ("t_c", ctypes.c_double), ("engine", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
 
 
 class bf_gp_plane(ctypes.Structure):
@@ -129,10 +130,15 @@ def last_cuda_error() -> str:
     return _load().bf_gp_last_cuda_error().decode()
 
 
-def make_opts(order: int = 20, spatial="auto", t_c=None, fir_halfwidth: int = 0) -> bf_gp_opts:
+ENGINE_TENSOR = 0
+ENGINE_CUDA_CORE = 1
+
+
+def make_opts(order: int = 20, spatial="auto", t_c=None, fir_halfwidth: int = 0, engine: int = ENGINE_TENSOR) -> bf_gp_opts:
     o = bf_gp_opts()
     _load().bf_gp_default_opts(ctypes.byref(o))
     o.order = int(order)
+    o.engine = int(engine)
     o.spatial = _SPATIAL[spatial] if isinstance(spatial, str) else int(spatial)
     o.fir_halfwidth = int(fir_halfwidth)
     if t_c is not None:

@@ -53,6 +53,8 @@ struct Plan {
     int nblk, rows_per_block;
     int T;                     // row threads per row
     int CL;                    // column cluster size (IIR)
+    int engine;                // 0 tensor cores, 1 CUDA cores (IIR)
+    int wpr;                   // tensor-core row pass: warps per row (512 samples each)
     size_t off_params, off_part, off_acc, off_planes, total;
 };
 
@@ -69,7 +71,8 @@ bf_status check_opts(const bf_gp_opts *o)
     if (o->centre < 0 || o->centre > 1) return BF_ERR_INVALID_ARG;
     if (o->fir_halfwidth < 0) return BF_ERR_INVALID_ARG;
     if (o->centre == BF_CENTRE_GIVEN && !std::isfinite(o->t_c)) return BF_ERR_INVALID_ARG;
-    for (int i = 0; i < 8; ++i)
+    if (o->engine < 0 || o->engine > 1) return BF_ERR_INVALID_ARG;
+    for (int i = 0; i < 7; ++i)
         if (o->reserved[i] != 0) return BF_ERR_INVALID_ARG;
     return BF_OK;
 }
@@ -92,6 +95,9 @@ bf_status make_plan(int planes, int H, int W, float sigma_s, const bf_gp_opts *o
     if (p->T < 8) p->T = 8;
     if (p->T > 512) return BF_ERR_UNSUPPORTED;  // rows longer than 8192 samples
     p->CL = (H + COL_ROWS_PER_CTA - 1) / COL_ROWS_PER_CTA;
+    p->engine = o->engine;
+    p->wpr = next_pow2((W + 511) / 512);
+    if (sp == BF_SPATIAL_IIR && p->engine == 0 && p->wpr > 16) return BF_ERR_UNSUPPORTED;
     if (sp == BF_SPATIAL_IIR && p->CL > COL_MAX_CLUSTER) return BF_ERR_UNSUPPORTED;  // columns longer than 4096
     // stats partials: ~16K pixels per block
     const long long px = (long long)H * W;
@@ -134,6 +140,41 @@ void deriche_coefs(double sigma, int C, IIRCoef *cf)
             const std::complex<double> t = std::pow(p[m], (double)C * (double)(1 << i));
             cf->Pr[m][i] = (float)t.real();
             cf->Pi[m][i] = (float)t.imag();
+        }
+    }
+}
+
+// The three 8 x 8 matrices of the tensor-core passes (chunk length 8), FP64 -> FP32:
+//   loc[k][n] = h(|n - k|);  sum[k][2c + ri]: chunk end states of combo c (c = 0, 1 causal pole c:
+//   p^{7-k}; c = 2, 3 anticausal pole c - 2: p^k), ri = 0 real, 1 imaginary part;
+//   cor[c][n] = Re(B), cor[c + 4][n] = -Im(B) with B = A p^{n+1} (causal) or A p^{8-n} (anticausal).
+void tc_mats(double sigma, TCMat *tm)
+{
+    const double a0 = 1.680, a1 = 3.735, b0 = 1.783, b1 = 1.723;
+    const double c0 = -0.6803, c1 = -0.2598, w0 = 0.6318, w1 = 1.997;
+    const std::complex<double> p[NP] = {std::exp(std::complex<double>(-b0, w0) / sigma),
+                                        std::exp(std::complex<double>(-b1, w1) / sigma)};
+    const std::complex<double> A[NP] = {{a0, -a1}, {c0, -c1}};
+    std::memset(tm, 0, sizeof *tm);
+    for (int k = 0; k < 8; ++k)
+        for (int n = 0; n < 8; ++n) {
+            double h = 0.0;
+            for (int m = 0; m < NP; ++m) h += (A[m] * std::pow(p[m], (double)std::abs(n - k))).real();
+            tm->loc[k][n] = (float)h;
+        }
+    for (int k = 0; k < 8; ++k)
+        for (int c = 0; c < 4; ++c) {
+            const int m = c & 1;
+            const std::complex<double> v = c < 2 ? std::pow(p[m], (double)(7 - k)) : std::pow(p[m], (double)k);
+            tm->sum[k][2 * c] = (float)v.real();
+            tm->sum[k][2 * c + 1] = (float)v.imag();
+        }
+    for (int c = 0; c < 4; ++c) {
+        const int m = c & 1;
+        for (int n = 0; n < 8; ++n) {
+            const std::complex<double> B = c < 2 ? A[m] * std::pow(p[m], (double)(n + 1)) : A[m] * std::pow(p[m], (double)(8 - n));
+            tm->cor[c][n] = (float)B.real();
+            tm->cor[c + 4][n] = (float)(-B.imag());
         }
     }
 }
@@ -279,6 +320,17 @@ bf_status run_rows(const Call &c, int planes, float sigma_s)
         default: break;
         }
         if (st != BF_OK) return st;
+    } else if (c.p.engine == 0) {
+        IIRCoef cr;
+        deriche_coefs((double)sigma_s, TC_C, &cr);
+        TCMat tm;
+        tc_mats((double)sigma_s, &tm);
+        RowArgs ra = c.ra;
+        ra.T = c.p.wpr;  // warps per row
+        const int tblock = 32 * c.p.wpr > 256 ? 32 * c.p.wpr : 256;
+        const int trows = (tblock / 32) / c.p.wpr;
+        dim3 grid((c.ra.H + trows - 1) / trows, planes);
+        row_tc<MODE><<<grid, tblock, 0, c.s>>>(ra, cr, tm);
     } else {
         IIRCoef cr;
         deriche_coefs((double)sigma_s, ROW_C, &cr);
@@ -306,11 +358,17 @@ bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
         }
         if (st != BF_OK) return st;
     } else {
-        IIRCoef cc;
-        deriche_coefs((double)sigma_s, COL_C, &cc);
         const int strips = (W + 7) / 8;
-        const size_t smem = sizeof(float) * 2 * COL_TILE_FLOATS;
-        BF_CUDA(cudaFuncSetAttribute(col_iir<COL_C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const bool tcore = c.p.engine == 0;
+        IIRCoef cc;
+        deriche_coefs((double)sigma_s, tcore ? TC_C : COL_C, &cc);
+        TCMat tm;
+        if (tcore) tc_mats((double)sigma_s, &tm);
+        const size_t smem = tcore ? sizeof(float) * 2 * 512 * 8 : sizeof(float) * 2 * COL_TILE_FLOATS;
+        if (tcore)
+            BF_CUDA(cudaFuncSetAttribute(col_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        else
+            BF_CUDA(cudaFuncSetAttribute(col_iir<COL_C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         cudaLaunchConfig_t cfg;
         std::memset(&cfg, 0, sizeof cfg);
         cfg.gridDim = dim3(strips * c.p.CL, planes, 1);
@@ -324,7 +382,8 @@ bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        BF_CUDA(cudaLaunchKernelEx(&cfg, col_iir<COL_C, MODE>, c.ca, cc));
+        if (tcore) BF_CUDA(cudaLaunchKernelEx(&cfg, col_tc<MODE>, c.ca, cc, tm));
+        else BF_CUDA(cudaLaunchKernelEx(&cfg, col_iir<COL_C, MODE>, c.ca, cc));
     }
     BF_CUDA(cudaGetLastError());
     return BF_OK;

@@ -916,7 +916,7 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
     extern __shared__ __align__(16) float tiles[];  // [2][COL_TILE_FLOATS]
     __shared__ float4 wt[8][8][NP];    // [warp][col][pole] warp totals (causal re, im, anticausal re, im)
     __shared__ float4 wcar[8][8][NP];  // [warp][col][pole] incoming carries of each warp
-    __shared__ float4 ct[8][NP];       // [col][pole] CTA totals, read by the other CTAs of the cluster
+    __shared__ float4 ct[2][8][NP];    // [channel parity][col][pole] CTA totals, read by the other CTAs
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int col = lane & 7, l4 = lane >> 3;
@@ -1035,7 +1035,7 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
                 totr = nr + (gdir == 0 ? tt.x : tt.z);
                 toti = ni + (gdir == 0 ? tt.y : tt.w);
             }
-            float *dst = gdir == 0 ? &ct[gcol][gm].x : &ct[gcol][gm].z;
+            float *dst = gdir == 0 ? &ct[k & 1][gcol][gm].x : &ct[k & 1][gcol][gm].z;
             dst[0] = totr;
             dst[1] = toti;
         }
@@ -1047,7 +1047,7 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
             const int nsteps = gdir == 0 ? rank : CL - 1 - rank;
             for (int s = 0; s < nsteps; ++s) {
                 const int r = gdir == 0 ? s : CL - 1 - s;
-                const float4 tt = *cl.map_shared_rank(&ct[gcol][gm], r);
+                const float4 tt = *cl.map_shared_rank(&ct[k & 1][gcol][gm], r);
                 float nr, ni;
                 cmul(nr, ni, p32r, p32i, Cr, Ci);
                 Cr = nr + (gdir == 0 ? tt.x : tt.z);
@@ -1184,6 +1184,504 @@ __global__ void __launch_bounds__(256) grad_finish(float *__restrict__ grad, con
                                   ? (float)(ac[2] * (-2.0 * s2 / sigma_r))
                                   : 0.f;
     }
+}
+
+// ------------------------------------------------------------------ tensor-core passes
+//
+// The same recursive filter with the chunk-local work done by warp-level
+// tensor-core products (mma.sync m16n8k8, TF32 inputs, FP32 accumulation).
+// Chunks are C = 8 samples.  For a group of 16 chunks X (16 x 8, one chunk per
+// row):
+//   Y  = X Mloc        Mloc[k][n] = h(|n - k|)          (both recursions inside the chunk)
+//   S  = X Msum        chunk end states, 4 combos x (re, im): combo 0/1 causal
+//                      pole 0/1 (sum_k p^{7-k} x_k), combo 2/3 anticausal
+//                      pole 0/1 (sum_k p^k x_k); column 2c + {0 re, 1 im}
+//   Y += Cr Mcor       Cr = incoming states (16 x 8: entry c = Re, c + 4 = Im of
+//                      combo c), Mcor[c][n] = Re(A p^{n+1}), Mcor[c+4][n] = -Im(A p^{n+1})
+//                      for causal combos and A p^{8-n} for anticausal ones
+// Each product runs as three TF32 products (hi*hi + lo*hi + hi*lo, the data
+// and the matrices split into a TF32 high part and the TF32 rounding of the
+// remainder), which keeps FP32-level accuracy.  The states between chunks are
+// combined with the modal scan as before (carry across a chunk = p^8).
+// In the fragment layout, thread (g = lane/4, t = lane%4) holds, for the
+// chunks of MMA rows g and g + 8, exactly the (Re, Im) of combo t in S and
+// the entries t, t + 4 of Cr: the scan of combo t runs in the thread that
+// needs its result.
+
+constexpr int TC_C = 8;
+
+struct TCMat {
+    float loc[8][8];  // [k][n]
+    float sum[8][8];  // [k][s]
+    float cor[8][8];  // [e][n]
+};
+
+__device__ __forceinline__ unsigned tf32_rna(float x)
+{
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void tf32_split(float x, unsigned &hi, unsigned &lo)
+{
+    hi = tf32_rna(x);
+    lo = tf32_rna(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// B fragment of an 8 x 8 matrix for this lane, split: b0 = B[t][g], b1 = B[t+4][g]
+struct BFrag {
+    unsigned h0, h1, l0, l1;
+    __device__ __forceinline__ void load(const float (&B)[8][8], int g, int t)
+    {
+        tf32_split(B[t][g], h0, l0);
+        tf32_split(B[t + 4][g], h1, l1);
+    }
+};
+
+// d += A B in three TF32 products; A given as four FP32 values (fragment order)
+__device__ __forceinline__ void mma3(float (&d)[4], float a0, float a1, float a2, float a3, const BFrag &b)
+{
+    unsigned h0, h1, h2, h3, l0, l1, l2, l3;
+    tf32_split(a0, h0, l0);
+    tf32_split(a1, h1, l1);
+    tf32_split(a2, h2, l2);
+    tf32_split(a3, h3, l3);
+    mma_tf32(d, l0, l1, l2, l3, b.h0, b.h1);
+    mma_tf32(d, h0, h1, h2, h3, b.l0, b.l1);
+    mma_tf32(d, h0, h1, h2, h3, b.h0, b.h1);
+}
+
+// the (complex) multiplier p^{8 n} of this lane's combo, from the table p^{8 2^i}
+__device__ __forceinline__ void tc_pow(float &rr, float &ri, const IIRCoef &cf, int m, int n)
+{
+    cpow_tab(rr, ri, cf, m, n);
+}
+
+// Row pass, tensor cores.  Each warp filters 512 consecutive samples (64
+// chunks, four groups of 16) of one row; a row of W samples uses
+// wpr = ceil(W / 512) warps (a power of two), a CTA holds 256 / (32 wpr) rows
+// (or one row of 512 threads when wpr = 16).  Group q of a warp covers
+// samples [128 q, 128 q + 128); MMA row g is chunk 2g, row g + 8 chunk 2g + 1.
+// grid (ceil(H / rows_per_cta), planes).
+template <int MODE>
+__device__ __forceinline__ void row_tc_body(const RowArgs &a, const IIRCoef &cf, const TCMat &tm, int grp,
+                                            int plane)
+{
+    __shared__ float2 wtot[16][4];  // [warp][combo] warp totals
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int wpr = a.T;  // warps per row
+    const int rows_per_cta = (blockDim.x >> 5) / wpr;
+    const int r_local = warp / wpr, wr = warp % wpr;
+    const int row = grp * rows_per_cta + r_local;
+    const bool rv = row < a.H;
+    const PlaneParams &P = a.pp[plane];
+    if (MODE == MODE_ADJ && grp == 0) zero_acc(a, plane);
+    if (P.mode != 0) return;
+
+    // sample positions of this lane: group q, fragment slot i (a0: 16g+t, a1: 16g+8+t, a2: 16g+t+4, a3: 16g+12+t)
+    const int xw = wr * 512;
+    auto pos = [&](int q, int i) { return xw + 128 * q + 16 * g + t + (i == 1 ? 8 : i == 2 ? 4 : i == 3 ? 12 : 0); };
+    RowGen<16, MODE> gen;
+    {
+        // load the 16 samples through the generator (positions are not contiguous)
+        const float *frow = a.f + ((size_t)plane * a.H + (rv ? row : 0)) * a.pitch;
+        gen.s2 = P.s2;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int x = pos(q, i);
+                const int j = q * 4 + i;
+                const bool in = rv && x < a.W;
+                const float fv = in ? __ldg(frow + x) : P.tc;
+                const float uu = (fv - P.tc) * P.invR;
+                gen.u[j] = in ? uu : 0.f;
+                if (MODE != MODE_ADJ) {
+                    gen.v[j] = in ? envelope(P, uu) : 0.f;
+                    gen.t[j] = 0.f;
+                } else {
+                    float al = 0.f, rho = 0.f;
+                    if (in) {
+                        const float gyv = __ldg(a.gy + ((size_t)plane * a.H + row) * a.pitch + x);
+                        const float Pt = __ldg(a.saved + saved_idx(plane, 0, a.H, a.W, row, x));
+                        const float Qt = __ldg(a.saved + saved_idx(plane, 1, a.H, a.W, row, x));
+                        if (Qt > 0.f && isfinite(gyv)) {
+                            al = __fdiv_rn(gyv * P.R, Qt);
+                            rho = __fdiv_rn(Pt, Qt);
+                        }
+                    }
+                    gen.v[j] = al;
+                    gen.t[j] = rho;
+                }
+            }
+    }
+    BFrag bl, bs, bc;
+    bl.load(tm.loc, g, t);
+    bs.load(tm.sum, g, t);
+    bc.load(tm.cor, g, t);
+    const int m = t & 1, dir = t >> 1;  // this lane's combo: pole m, causal (0) or anticausal (1)
+    const float P1r = cf.Pr[m][0], P1i = cf.Pi[m][0];    // p^8: one chunk
+    const float P16r = cf.Pr[m][4], P16i = cf.Pi[m][4];  // p^128: one group of 16 chunks
+    float Pgr, Pgi;                                      // p^{8 * 2g} or p^{8 * 2(7-g)}: pairs before / after
+    tc_pow(Pgr, Pgi, cf, m, dir == 0 ? 2 * g : 2 * (7 - g));
+    float *orow = a.ws + ((size_t)plane * a.K * a.H + (rv ? row : 0)) * a.Wp;
+
+#pragma unroll 1
+    for (int k = 0; k < a.K; ++k) {
+        float x16[16];
+        gen.channel(k, a.N, x16);
+        float D[4][4], S[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) D[q][i] = S[q][i] = 0.f;
+            mma3(D[q], x16[4 * q], x16[4 * q + 1], x16[4 * q + 2], x16[4 * q + 3], bl);
+            mma3(S[q], x16[4 * q], x16[4 * q + 1], x16[4 * q + 2], x16[4 * q + 3], bs);
+        }
+        // per group: pair value and the 8-pair scan over g (lane stride 4)
+        float Tr[4], Ti[4], Er[4], Ei[4];  // group totals, exclusive carry within the group
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            // S[q] = (re, im) of combo t for chunk 2g (0, 1) and chunk 2g + 1 (2, 3)
+            float vr, vi;
+            if (dir == 0) {  // inclusive over the pair: e(2g+1) + p^8 e(2g)
+                vr = S[q][2];
+                vi = S[q][3];
+                cmadd(vr, vi, P1r, P1i, S[q][0], S[q][1]);
+            } else {  // s(2g) + p^8 s(2g+1)
+                vr = S[q][0];
+                vi = S[q][1];
+                cmadd(vr, vi, P1r, P1i, S[q][2], S[q][3]);
+            }
+#pragma unroll
+            for (int st = 0; st < 3; ++st) {
+                const int d = 1 << st;
+                const float mr = cf.Pr[m][st + 1], mi = cf.Pi[m][st + 1];  // p^{8 * 2d}
+                const float ur = __shfl_up_sync(0xffffffffu, vr, 4 * d);
+                const float ui = __shfl_up_sync(0xffffffffu, vi, 4 * d);
+                const float dr = __shfl_down_sync(0xffffffffu, vr, 4 * d);
+                const float di = __shfl_down_sync(0xffffffffu, vi, 4 * d);
+                if (dir == 0 && g >= d) cmadd(vr, vi, mr, mi, ur, ui);
+                if (dir == 1 && g + d <= 7) cmadd(vr, vi, mr, mi, dr, di);
+            }
+            const float xr = __shfl_up_sync(0xffffffffu, vr, 4), xi = __shfl_up_sync(0xffffffffu, vi, 4);
+            const float yr = __shfl_down_sync(0xffffffffu, vr, 4), yi = __shfl_down_sync(0xffffffffu, vi, 4);
+            Er[q] = dir == 0 ? (g > 0 ? xr : 0.f) : (g < 7 ? yr : 0.f);
+            Ei[q] = dir == 0 ? (g > 0 ? xi : 0.f) : (g < 7 ? yi : 0.f);
+            Tr[q] = __shfl_sync(0xffffffffu, vr, dir == 0 ? 28 + t : t);
+            Ti[q] = __shfl_sync(0xffffffffu, vi, dir == 0 ? 28 + t : t);
+        }
+        // groups of the warp in order, then the warp total
+        float Cr[4], Ci[4];  // carry entering each group (from this warp's data)
+        float accr = 0.f, acci = 0.f;
+        if (dir == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                Cr[q] = accr;
+                Ci[q] = acci;
+                float nr, ni;
+                cmul(nr, ni, P16r, P16i, accr, acci);
+                accr = nr + Tr[q];
+                acci = ni + Ti[q];
+            }
+        } else {
+#pragma unroll
+            for (int q = 3; q >= 0; --q) {
+                Cr[q] = accr;
+                Ci[q] = acci;
+                float nr, ni;
+                cmul(nr, ni, P16r, P16i, accr, acci);
+                accr = nr + Tr[q];
+                acci = ni + Ti[q];
+            }
+        }
+        if (wpr > 1) {
+            if (g == 0) wtot[warp][t] = make_float2(accr, acci);
+            __syncthreads();
+            // carry entering this warp from the other warps of the row (p^512 per warp)
+            const float pwr = cf.Pr[m][6], pwi = cf.Pi[m][6];
+            float Wr = 0.f, Wi = 0.f;
+            const int w0 = r_local * wpr;
+            for (int s = 0; s < wpr; ++s) {
+                const int w = dir == 0 ? s : wpr - 1 - s;
+                if ((dir == 0 && w >= wr) || (dir == 1 && w <= wr)) continue;
+                const float2 tt = wtot[w0 + w][t];
+                float nr, ni;
+                cmul(nr, ni, pwr, pwi, Wr, Wi);
+                Wr = nr + tt.x;
+                Wi = ni + tt.y;
+            }
+            // propagate through the groups before (causal) / after (anticausal) group q
+            if (dir == 0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    Cr[q] += Wr;
+                    Ci[q] += Wi;
+                    float nr, ni;
+                    cmul(nr, ni, P16r, P16i, Wr, Wi);
+                    Wr = nr;
+                    Wi = ni;
+                }
+            } else {
+#pragma unroll
+                for (int q = 3; q >= 0; --q) {
+                    Cr[q] += Wr;
+                    Ci[q] += Wi;
+                    float nr, ni;
+                    cmul(nr, ni, P16r, P16i, Wr, Wi);
+                    Wr = nr;
+                    Wi = ni;
+                }
+            }
+            __syncthreads();  // wtot reused by the next channel
+        }
+        const float beta = P.beta[k];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            // incoming state of chunk 2g (causal: pairs before + group carry) and of chunk 2g+1
+            float c0r = Er[q], c0i = Ei[q];
+            cmadd(c0r, c0i, Pgr, Pgi, Cr[q], Ci[q]);
+            float c1r, c1i;
+            if (dir == 0) {  // chunk 2g+1 gets e(2g) + p^8 cin(2g)
+                c1r = S[q][0];
+                c1i = S[q][1];
+                cmadd(c1r, c1i, P1r, P1i, c0r, c0i);
+            } else {  // anticausal: c0 is the state entering chunk 2g+1; chunk 2g gets s(2g+1) + p^8 that
+                c1r = c0r;
+                c1i = c0i;
+                c0r = S[q][2];
+                c0i = S[q][3];
+                cmadd(c0r, c0i, P1r, P1i, c1r, c1i);
+            }
+            // Cr fragment: a0 = Re chunk 2g, a1 = Re chunk 2g+1, a2 = Im chunk 2g, a3 = Im chunk 2g+1
+            mma3(D[q], c0r, c1r, c0i, c1i, bc);
+            // D: chunk 2g samples 2t, 2t+1 (d0, d1); chunk 2g+1 samples 2t, 2t+1 (d2, d3)
+            if (rv) {
+                const int xa = xw + 128 * q + 16 * g + 2 * t, xb = xa + 8;
+                float *o = orow + (size_t)k * a.H * a.Wp;
+                if (xa + 1 < a.Wp) *reinterpret_cast<float2 *>(o + xa) = make_float2(D[q][0] * beta, D[q][1] * beta);
+                if (xb + 1 < a.Wp) *reinterpret_cast<float2 *>(o + xb) = make_float2(D[q][2] * beta, D[q][3] * beta);
+            }
+        }
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(512) row_tc(RowArgs a, IIRCoef cf, TCMat tm)
+{
+    row_tc_body<MODE>(a, cf, tm, blockIdx.x, blockIdx.y);
+}
+
+// Column pass, tensor cores.  A cluster of CL CTAs covers an 8-column strip's
+// full height; CTA rank r owns rows [512 r, 512 r + 512) = 64 chunks of 8 rows
+// per column; warp w owns chunks [8 w, 8 w + 8) of every column; its group q
+// has MMA row g = (column g, chunk 8w + 2q), row g + 8 = (column g, chunk
+// 8w + 2q + 1).  Thread (g, t) thus holds combo t of column g for 8
+// consecutive chunks: the chunk scan runs in registers.
+template <int MODE>
+__device__ __forceinline__ void col_tc_body(const ColArgs &a, const IIRCoef &cf, const TCMat &tm, int strip,
+                                            int plane)
+{
+    extern __shared__ __align__(16) float tiles[];  // [2][512][8]
+    __shared__ float2 wtot[8][8][4];                 // [warp][column][combo]
+    __shared__ float2 ctot[2][8][4];                 // [channel parity][column][combo] CTA totals for the cluster
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int CL = (int)cl.num_blocks();
+    const int x = strip * 8 + g;
+    const int rbase = rank * 512;
+    const PlaneParams &P = a.pp[plane];
+    const bool filt = (P.mode == 0);
+    const float *wsp = a.ws + (size_t)plane * a.K * a.H * a.Wp + strip * 8;
+    constexpr int TILE = 512 * 8;
+
+    auto issue_tile = [&](int k, int buf) {
+        const float *src = wsp + (size_t)k * a.H * a.Wp;
+        float *dst = tiles + buf * TILE;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int idx = tid + i * 256;
+            const int r = idx >> 1, half = idx & 1;
+            const int gr = rbase + r;
+            const bool ok = filt && gr < a.H;
+            cp_async16(dst + r * 8 + half * 4, src + (size_t)(ok ? gr : 0) * a.Wp + half * 4, ok);
+        }
+        cp_async_commit();
+    };
+
+    // pixel j = 4 q + i of this lane: group q, D slot i
+    auto prow = [&](int q, int i) { return rbase + 8 * (8 * warp + 2 * q + (i >> 1)) + 2 * t + (i & 1); };
+    Combine<16, MODE> cb;
+    const float *fcol = a.f + (size_t)plane * a.H * a.pitch;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = prow(q, i);
+            const bool in = (r < a.H) && (x < a.W);
+            const float fv = in ? __ldg(fcol + (size_t)r * a.pitch + x) : 0.f;
+            cb.init((fv - P.tc) * P.invR, q * 4 + i);
+        }
+    BFrag bl, bs, bc;
+    bl.load(tm.loc, g, t);
+    bs.load(tm.sum, g, t);
+    bc.load(tm.cor, g, t);
+    const int m = t & 1, dir = t >> 1;
+    const float P1r = cf.Pr[m][0], P1i = cf.Pi[m][0];  // p^8: one chunk
+    const float P8r = cf.Pr[m][3], P8i = cf.Pi[m][3];  // p^64: one warp (8 chunks)
+    const float P64r = cf.Pr[m][6], P64i = cf.Pi[m][6];  // p^512: one CTA
+
+    issue_tile(a.K - 1, (a.K - 1) & 1);
+#pragma unroll 1
+    for (int k = a.K - 1; k >= 0; --k) {
+        cp_async_wait_all();
+        __syncthreads();  // tile k visible; all threads done with the tile of channel k+1
+        if (k > 0) issue_tile(k - 1, (k - 1) & 1);
+        const float *tl = tiles + (k & 1) * TILE + g;
+        float D[4][4], S[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r0 = 8 * (8 * warp + 2 * q) + t, r1 = r0 + 8;
+            const float a0 = tl[r0 * 8], a1 = tl[r1 * 8], a2 = tl[(r0 + 4) * 8], a3 = tl[(r1 + 4) * 8];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) D[q][i] = S[q][i] = 0.f;
+            mma3(D[q], a0, a1, a2, a3, bl);
+            mma3(S[q], a0, a1, a2, a3, bs);
+        }
+        // this lane's combo over the warp's 8 chunks (c = 2q + half), from zero state
+        float totr = 0.f, toti = 0.f;
+        if (dir == 0) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                float nr, ni;
+                cmul(nr, ni, P1r, P1i, totr, toti);
+                totr = nr + S[c >> 1][2 * (c & 1)];
+                toti = ni + S[c >> 1][2 * (c & 1) + 1];
+            }
+        } else {
+#pragma unroll
+            for (int c = 7; c >= 0; --c) {
+                float nr, ni;
+                cmul(nr, ni, P1r, P1i, totr, toti);
+                totr = nr + S[c >> 1][2 * (c & 1)];
+                toti = ni + S[c >> 1][2 * (c & 1) + 1];
+            }
+        }
+        wtot[warp][g][t] = make_float2(totr, toti);
+        __syncthreads();
+        // carry entering this warp from the other warps of the CTA (p^64 per warp)
+        float Wr = 0.f, Wi = 0.f;
+        for (int s = 0; s < 8; ++s) {
+            const int w = dir == 0 ? s : 7 - s;
+            if ((dir == 0 && w >= warp) || (dir == 1 && w <= warp)) continue;
+            const float2 tt = wtot[w][g][t];
+            float nr, ni;
+            cmul(nr, ni, P8r, P8i, Wr, Wi);
+            Wr = nr + tt.x;
+            Wi = ni + tt.y;
+        }
+        // CTA total: the last warp in scan order extends its incoming carry by its own total
+        if ((dir == 0 && warp == 7) || (dir == 1 && warp == 0)) {
+            float cr2 = totr, ci2 = toti;
+            cmadd(cr2, ci2, P8r, P8i, Wr, Wi);
+            ctot[k & 1][g][t] = make_float2(cr2, ci2);
+        }
+        // CTA totals of the cluster written.  ctot is double-buffered by channel parity: a
+        // peer may still read this channel's totals until it reaches the next cluster barrier.
+        cl.sync();
+        if (CL > 1) {
+            float Xr = 0.f, Xi = 0.f;
+            const int nsteps = dir == 0 ? rank : CL - 1 - rank;
+            for (int s = 0; s < nsteps; ++s) {
+                const int r = dir == 0 ? s : CL - 1 - s;
+                const float2 tt = *cl.map_shared_rank(&ctot[k & 1][g][t], r);
+                float nr, ni;
+                cmul(nr, ni, P64r, P64i, Xr, Xi);
+                Xr = nr + tt.x;
+                Xi = ni + tt.y;
+            }
+            // through the warps before (causal) / after (anticausal) this one
+            const int hops = dir == 0 ? warp : 7 - warp;
+            for (int s = 0; s < hops; ++s) {
+                float nr, ni;
+                cmul(nr, ni, P8r, P8i, Xr, Xi);
+                Xr = nr;
+                Xi = ni;
+            }
+            Wr += Xr;
+            Wi += Xi;
+        }
+        // incoming state of every chunk, in scan order, and the correction products
+        float inr[8], ini[8];
+        {
+            float cr2 = Wr, ci2 = Wi;
+            if (dir == 0) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    inr[c] = cr2;
+                    ini[c] = ci2;
+                    float nr, ni;
+                    cmul(nr, ni, P1r, P1i, cr2, ci2);
+                    cr2 = nr + S[c >> 1][2 * (c & 1)];
+                    ci2 = ni + S[c >> 1][2 * (c & 1) + 1];
+                }
+            } else {
+#pragma unroll
+                for (int c = 7; c >= 0; --c) {
+                    inr[c] = cr2;
+                    ini[c] = ci2;
+                    float nr, ni;
+                    cmul(nr, ni, P1r, P1i, cr2, ci2);
+                    cr2 = nr + S[c >> 1][2 * (c & 1)];
+                    ci2 = ni + S[c >> 1][2 * (c & 1) + 1];
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) mma3(D[q], inr[2 * q], inr[2 * q + 1], ini[2 * q], ini[2 * q + 1], bc);
+        float y16[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) y16[4 * q + i] = D[q][i];
+        cb.step(k, a.N, P.s2, y16);
+    }
+    cl.sync();  // no CTA may leave while a peer can still read its shared memory
+    bool nonpos = false;
+    AdjSums sums = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = prow(q, i);
+            if (r < a.H && x < a.W) finish_pixel<16, MODE>(a, P, plane, r, x, cb, 4 * q + i, nonpos, sums);
+        }
+    if (MODE == MODE_ADJ) {
+        flush_sums(a, plane, sums);
+    } else if (__any_sync(0xffffffffu, nonpos) && lane == 0) {
+        atomicOr(a.status, 0x1u);
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256, MODE == MODE_SAVE ? 1 : 2) col_tc(ColArgs a, IIRCoef cf, TCMat tm)
+{
+    col_tc_body<MODE>(a, cf, tm, blockIdx.x / (int)cg::this_cluster().num_blocks(), blockIdx.y);
 }
 
 // ------------------------------------------------------------------ batched
