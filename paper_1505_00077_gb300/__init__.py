@@ -130,11 +130,12 @@ def last_cuda_error() -> str:
     return _load().bf_gp_last_cuda_error().decode()
 
 
-ENGINE_TENSOR = 0
+ENGINE_AUTO = 0        # tensor-core row pass, CUDA-core column pass
 ENGINE_CUDA_CORE = 1
+ENGINE_TENSOR = 2
 
 
-def make_opts(order: int = 20, spatial="auto", t_c=None, fir_halfwidth: int = 0, engine: int = ENGINE_TENSOR) -> bf_gp_opts:
+def make_opts(order: int = 20, spatial="auto", t_c=None, fir_halfwidth: int = 0, engine: int = ENGINE_AUTO) -> bf_gp_opts:
     o = bf_gp_opts()
     _load().bf_gp_default_opts(ctypes.byref(o))
     o.order = int(order)

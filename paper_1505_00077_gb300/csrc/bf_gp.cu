@@ -53,7 +53,7 @@ struct Plan {
     int nblk, rows_per_block;
     int T;                     // row threads per row
     int CL;                    // column cluster size (IIR)
-    int engine;                // 0 tensor cores, 1 CUDA cores (IIR)
+    int row_tc, col_tc;        // recursive filter: tensor-core row / column pass
     int wpr;                   // tensor-core row pass: warps per row (512 samples each)
     size_t off_params, off_part, off_acc, off_planes, total;
 };
@@ -71,7 +71,7 @@ bf_status check_opts(const bf_gp_opts *o)
     if (o->centre < 0 || o->centre > 1) return BF_ERR_INVALID_ARG;
     if (o->fir_halfwidth < 0) return BF_ERR_INVALID_ARG;
     if (o->centre == BF_CENTRE_GIVEN && !std::isfinite(o->t_c)) return BF_ERR_INVALID_ARG;
-    if (o->engine < 0 || o->engine > 1) return BF_ERR_INVALID_ARG;
+    if (o->engine < 0 || o->engine > 2) return BF_ERR_INVALID_ARG;
     for (int i = 0; i < 7; ++i)
         if (o->reserved[i] != 0) return BF_ERR_INVALID_ARG;
     return BF_OK;
@@ -95,9 +95,10 @@ bf_status make_plan(int planes, int H, int W, float sigma_s, const bf_gp_opts *o
     if (p->T < 8) p->T = 8;
     if (p->T > 512) return BF_ERR_UNSUPPORTED;  // rows longer than 8192 samples
     p->CL = (H + COL_ROWS_PER_CTA - 1) / COL_ROWS_PER_CTA;
-    p->engine = o->engine;
+    p->row_tc = o->engine == 0 || o->engine == 2;
+    p->col_tc = o->engine == 2;
     p->wpr = next_pow2((W + 511) / 512);
-    if (sp == BF_SPATIAL_IIR && p->engine == 0 && p->wpr > 16) return BF_ERR_UNSUPPORTED;
+    if (sp == BF_SPATIAL_IIR && p->row_tc && p->wpr > 16) return BF_ERR_UNSUPPORTED;
     if (sp == BF_SPATIAL_IIR && p->CL > COL_MAX_CLUSTER) return BF_ERR_UNSUPPORTED;  // columns longer than 4096
     // stats partials: ~16K pixels per block
     const long long px = (long long)H * W;
@@ -320,7 +321,7 @@ bf_status run_rows(const Call &c, int planes, float sigma_s)
         default: break;
         }
         if (st != BF_OK) return st;
-    } else if (c.p.engine == 0) {
+    } else if (c.p.row_tc) {
         IIRCoef cr;
         deriche_coefs((double)sigma_s, TC_C, &cr);
         TCMat tm;
@@ -359,7 +360,7 @@ bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
         if (st != BF_OK) return st;
     } else {
         const int strips = (W + 7) / 8;
-        const bool tcore = c.p.engine == 0;
+        const bool tcore = c.p.col_tc != 0;
         IIRCoef cc;
         deriche_coefs((double)sigma_s, tcore ? TC_C : COL_C, &cc);
         TCMat tm;

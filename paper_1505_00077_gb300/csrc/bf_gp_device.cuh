@@ -1262,17 +1262,51 @@ __device__ __forceinline__ void mma3(float (&d)[4], float a0, float a1, float a2
     mma_tf32(d, h0, h1, h2, h3, b.h0, b.h1);
 }
 
-// the (complex) multiplier p^{8 n} of this lane's combo, from the table p^{8 2^i}
-__device__ __forceinline__ void tc_pow(float &rr, float &ri, const IIRCoef &cf, int m, int n)
+// A fragment split once into TF32 high and low parts, reused by several products
+struct AFrag {
+    unsigned h0, h1, h2, h3, l0, l1, l2, l3;
+    __device__ __forceinline__ void set(float a0, float a1, float a2, float a3)
+    {
+        tf32_split(a0, h0, l0);
+        tf32_split(a1, h1, l1);
+        tf32_split(a2, h2, l2);
+        tf32_split(a3, h3, l3);
+    }
+};
+
+// d += A B as three TF32 products (lo*hi, hi*lo, hi*hi)
+__device__ __forceinline__ void mma3f(float (&d)[4], const AFrag &a, const BFrag &b)
 {
-    cpow_tab(rr, ri, cf, m, n);
+    mma_tf32(d, a.l0, a.l1, a.l2, a.l3, b.h0, b.h1);
+    mma_tf32(d, a.h0, a.h1, a.h2, a.h3, b.l0, b.l1);
+    mma_tf32(d, a.h0, a.h1, a.h2, a.h3, b.h0, b.h1);
 }
 
+// The lane's combo walks its 8 chunks forwards (causal) or backwards
+// (anticausal).  To keep every lane on the same instructions, the 8 (Re, Im)
+// chunk values are first copied into scan order with selects (compile-time
+// register indices on both sides), scanned forwards, and copied back.
+//   S[q][2h], S[q][2h+1]: Re, Im of chunk c = 2q + h.
+struct Seq8 {
+    float r[8], i[8];
+    __device__ __forceinline__ void from_chunks(const float (&S)[4][4], bool rev)
+    {
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int c = s, cr = 7 - s;
+            r[s] = rev ? S[cr >> 1][2 * (cr & 1)] : S[c >> 1][2 * (c & 1)];
+            i[s] = rev ? S[cr >> 1][2 * (cr & 1) + 1] : S[c >> 1][2 * (c & 1) + 1];
+        }
+    }
+};
+
 // Row pass, tensor cores.  Each warp filters 512 consecutive samples (64
-// chunks, four groups of 16) of one row; a row of W samples uses
-// wpr = ceil(W / 512) warps (a power of two), a CTA holds 256 / (32 wpr) rows
-// (or one row of 512 threads when wpr = 16).  Group q of a warp covers
-// samples [128 q, 128 q + 128); MMA row g is chunk 2g, row g + 8 chunk 2g + 1.
+// chunks) of one row; a row of W samples uses wpr = next_pow2(ceil(W/512))
+// warps, a CTA holds 256 / (32 wpr) rows (one row of 512 threads when
+// wpr = 16).  Thread (g, t) owns chunks 8g .. 8g+7 of its warp: in group q
+// the MMA row g is chunk 8g + 2q and row g + 8 chunk 8g + 2q + 1.  The chunk
+// scan of combo t runs in registers over those 8 chunks, then across the 8
+// threads g of the warp (shuffles), then across the warps of the row.
 // grid (ceil(H / rows_per_cta), planes).
 template <int MODE>
 __device__ __forceinline__ void row_tc_body(const RowArgs &a, const IIRCoef &cf, const TCMat &tm, int grp,
@@ -1290,12 +1324,12 @@ __device__ __forceinline__ void row_tc_body(const RowArgs &a, const IIRCoef &cf,
     if (MODE == MODE_ADJ && grp == 0) zero_acc(a, plane);
     if (P.mode != 0) return;
 
-    // sample positions of this lane: group q, fragment slot i (a0: 16g+t, a1: 16g+8+t, a2: 16g+t+4, a3: 16g+12+t)
-    const int xw = wr * 512;
-    auto pos = [&](int q, int i) { return xw + 128 * q + 16 * g + t + (i == 1 ? 8 : i == 2 ? 4 : i == 3 ? 12 : 0); };
+    // sample of group q, fragment slot i: a0 = chunk 8g+2q sample t, a1 = chunk 8g+2q+1 sample t,
+    // a2 = chunk 8g+2q sample t+4, a3 = chunk 8g+2q+1 sample t+4
+    const int xw = wr * 512 + 64 * g;
+    auto pos = [&](int q, int i) { return xw + 16 * q + t + (i == 1 ? 8 : i == 2 ? 4 : i == 3 ? 12 : 0); };
     RowGen<16, MODE> gen;
     {
-        // load the 16 samples through the generator (positions are not contiguous)
         const float *frow = a.f + ((size_t)plane * a.H + (rv ? row : 0)) * a.pitch;
         gen.s2 = P.s2;
 #pragma unroll
@@ -1331,11 +1365,12 @@ __device__ __forceinline__ void row_tc_body(const RowArgs &a, const IIRCoef &cf,
     bl.load(tm.loc, g, t);
     bs.load(tm.sum, g, t);
     bc.load(tm.cor, g, t);
-    const int m = t & 1, dir = t >> 1;  // this lane's combo: pole m, causal (0) or anticausal (1)
-    const float P1r = cf.Pr[m][0], P1i = cf.Pi[m][0];    // p^8: one chunk
-    const float P16r = cf.Pr[m][4], P16i = cf.Pi[m][4];  // p^128: one group of 16 chunks
-    float Pgr, Pgi;                                      // p^{8 * 2g} or p^{8 * 2(7-g)}: pairs before / after
-    tc_pow(Pgr, Pgi, cf, m, dir == 0 ? 2 * g : 2 * (7 - g));
+    const int m = t & 1;
+    const bool rev = (t >> 1) != 0;  // anticausal combo: scan order reversed
+    const int jpos = rev ? 7 - g : g;  // this thread's place in the warp's scan order
+    const float P1r = cf.Pr[m][0], P1i = cf.Pi[m][0];  // p^8: one chunk
+    float Pjr, Pji;                                    // p^{64 jpos}: the warp carry reaches this thread
+    cpow_tab(Pjr, Pji, cf, m, 8 * jpos);
     float *orow = a.ws + ((size_t)plane * a.K * a.H + (rv ? row : 0)) * a.Wp;
 
 #pragma unroll 1
@@ -1347,130 +1382,78 @@ __device__ __forceinline__ void row_tc_body(const RowArgs &a, const IIRCoef &cf,
         for (int q = 0; q < 4; ++q) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) D[q][i] = S[q][i] = 0.f;
-            mma3(D[q], x16[4 * q], x16[4 * q + 1], x16[4 * q + 2], x16[4 * q + 3], bl);
-            mma3(S[q], x16[4 * q], x16[4 * q + 1], x16[4 * q + 2], x16[4 * q + 3], bs);
+            AFrag af;
+            af.set(x16[4 * q], x16[4 * q + 1], x16[4 * q + 2], x16[4 * q + 3]);
+            mma3f(D[q], af, bl);
+            mma3f(S[q], af, bs);
         }
-        // per group: pair value and the 8-pair scan over g (lane stride 4)
-        float Tr[4], Ti[4], Er[4], Ei[4];  // group totals, exclusive carry within the group
+        Seq8 sq;
+        sq.from_chunks(S, rev);
+        // the thread's 8 chunks from zero state
+        float vr = 0.f, vi = 0.f;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            // S[q] = (re, im) of combo t for chunk 2g (0, 1) and chunk 2g + 1 (2, 3)
-            float vr, vi;
-            if (dir == 0) {  // inclusive over the pair: e(2g+1) + p^8 e(2g)
-                vr = S[q][2];
-                vi = S[q][3];
-                cmadd(vr, vi, P1r, P1i, S[q][0], S[q][1]);
-            } else {  // s(2g) + p^8 s(2g+1)
-                vr = S[q][0];
-                vi = S[q][1];
-                cmadd(vr, vi, P1r, P1i, S[q][2], S[q][3]);
-            }
-#pragma unroll
-            for (int st = 0; st < 3; ++st) {
-                const int d = 1 << st;
-                const float mr = cf.Pr[m][st + 1], mi = cf.Pi[m][st + 1];  // p^{8 * 2d}
-                const float ur = __shfl_up_sync(0xffffffffu, vr, 4 * d);
-                const float ui = __shfl_up_sync(0xffffffffu, vi, 4 * d);
-                const float dr = __shfl_down_sync(0xffffffffu, vr, 4 * d);
-                const float di = __shfl_down_sync(0xffffffffu, vi, 4 * d);
-                if (dir == 0 && g >= d) cmadd(vr, vi, mr, mi, ur, ui);
-                if (dir == 1 && g + d <= 7) cmadd(vr, vi, mr, mi, dr, di);
-            }
-            const float xr = __shfl_up_sync(0xffffffffu, vr, 4), xi = __shfl_up_sync(0xffffffffu, vi, 4);
-            const float yr = __shfl_down_sync(0xffffffffu, vr, 4), yi = __shfl_down_sync(0xffffffffu, vi, 4);
-            Er[q] = dir == 0 ? (g > 0 ? xr : 0.f) : (g < 7 ? yr : 0.f);
-            Ei[q] = dir == 0 ? (g > 0 ? xi : 0.f) : (g < 7 ? yi : 0.f);
-            Tr[q] = __shfl_sync(0xffffffffu, vr, dir == 0 ? 28 + t : t);
-            Ti[q] = __shfl_sync(0xffffffffu, vi, dir == 0 ? 28 + t : t);
+        for (int s = 0; s < 8; ++s) {
+            float nr, ni;
+            cmul(nr, ni, P1r, P1i, vr, vi);
+            vr = nr + sq.r[s];
+            vi = ni + sq.i[s];
         }
-        // groups of the warp in order, then the warp total
-        float Cr[4], Ci[4];  // carry entering each group (from this warp's data)
-        float accr = 0.f, acci = 0.f;
-        if (dir == 0) {
+        // across the 8 threads g of the warp, in scan order (p^{64 d} per d threads)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                Cr[q] = accr;
-                Ci[q] = acci;
-                float nr, ni;
-                cmul(nr, ni, P16r, P16i, accr, acci);
-                accr = nr + Tr[q];
-                acci = ni + Ti[q];
-            }
-        } else {
-#pragma unroll
-            for (int q = 3; q >= 0; --q) {
-                Cr[q] = accr;
-                Ci[q] = acci;
-                float nr, ni;
-                cmul(nr, ni, P16r, P16i, accr, acci);
-                accr = nr + Tr[q];
-                acci = ni + Ti[q];
-            }
+        for (int st = 0; st < 3; ++st) {
+            const int d = 1 << st;
+            const int src = 4 * (rev ? g + d : g - d) + t;
+            const float ur = __shfl_sync(0xffffffffu, vr, src & 31);
+            const float ui = __shfl_sync(0xffffffffu, vi, src & 31);
+            if (jpos >= d) cmadd(vr, vi, cf.Pr[m][st + 3], cf.Pi[m][st + 3], ur, ui);
         }
+        const int srcx = 4 * (rev ? g + 1 : g - 1) + t;
+        float er = __shfl_sync(0xffffffffu, vr, srcx & 31);
+        float ei = __shfl_sync(0xffffffffu, vi, srcx & 31);
+        if (jpos == 0) er = ei = 0.f;
         if (wpr > 1) {
-            if (g == 0) wtot[warp][t] = make_float2(accr, acci);
+            const int last = 4 * (rev ? 0 : 7) + t;
+            const float wtr = __shfl_sync(0xffffffffu, vr, last), wti = __shfl_sync(0xffffffffu, vi, last);
+            if (g == 0) wtot[warp][t] = make_float2(wtr, wti);
             __syncthreads();
-            // carry entering this warp from the other warps of the row (p^512 per warp)
-            const float pwr = cf.Pr[m][6], pwi = cf.Pi[m][6];
+            const float pwr = cf.Pr[m][6], pwi = cf.Pi[m][6];  // p^512: one warp
             float Wr = 0.f, Wi = 0.f;
             const int w0 = r_local * wpr;
             for (int s = 0; s < wpr; ++s) {
-                const int w = dir == 0 ? s : wpr - 1 - s;
-                if ((dir == 0 && w >= wr) || (dir == 1 && w <= wr)) continue;
+                const int w = rev ? wpr - 1 - s : s;
+                if ((!rev && w >= wr) || (rev && w <= wr)) continue;
                 const float2 tt = wtot[w0 + w][t];
                 float nr, ni;
                 cmul(nr, ni, pwr, pwi, Wr, Wi);
                 Wr = nr + tt.x;
                 Wi = ni + tt.y;
             }
-            // propagate through the groups before (causal) / after (anticausal) group q
-            if (dir == 0) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    Cr[q] += Wr;
-                    Ci[q] += Wi;
-                    float nr, ni;
-                    cmul(nr, ni, P16r, P16i, Wr, Wi);
-                    Wr = nr;
-                    Wi = ni;
-                }
-            } else {
-#pragma unroll
-                for (int q = 3; q >= 0; --q) {
-                    Cr[q] += Wr;
-                    Ci[q] += Wi;
-                    float nr, ni;
-                    cmul(nr, ni, P16r, P16i, Wr, Wi);
-                    Wr = nr;
-                    Wi = ni;
-                }
-            }
+            cmadd(er, ei, Pjr, Pji, Wr, Wi);
             __syncthreads();  // wtot reused by the next channel
         }
+        // incoming state of each chunk, in scan order, then back to chunk order
+        float inr_s[8], ini_s[8];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            inr_s[s] = er;
+            ini_s[s] = ei;
+            float nr, ni;
+            cmul(nr, ni, P1r, P1i, er, ei);
+            er = nr + sq.r[s];
+            ei = ni + sq.i[s];
+        }
         const float beta = P.beta[k];
+        float *o = orow + (size_t)k * a.H * a.Wp;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            // incoming state of chunk 2g (causal: pairs before + group carry) and of chunk 2g+1
-            float c0r = Er[q], c0i = Ei[q];
-            cmadd(c0r, c0i, Pgr, Pgi, Cr[q], Ci[q]);
-            float c1r, c1i;
-            if (dir == 0) {  // chunk 2g+1 gets e(2g) + p^8 cin(2g)
-                c1r = S[q][0];
-                c1i = S[q][1];
-                cmadd(c1r, c1i, P1r, P1i, c0r, c0i);
-            } else {  // anticausal: c0 is the state entering chunk 2g+1; chunk 2g gets s(2g+1) + p^8 that
-                c1r = c0r;
-                c1i = c0i;
-                c0r = S[q][2];
-                c0i = S[q][3];
-                cmadd(c0r, c0i, P1r, P1i, c1r, c1i);
-            }
-            // Cr fragment: a0 = Re chunk 2g, a1 = Re chunk 2g+1, a2 = Im chunk 2g, a3 = Im chunk 2g+1
-            mma3(D[q], c0r, c1r, c0i, c1i, bc);
-            // D: chunk 2g samples 2t, 2t+1 (d0, d1); chunk 2g+1 samples 2t, 2t+1 (d2, d3)
+            const int c0 = 2 * q, c1 = 2 * q + 1;
+            const float r0 = rev ? inr_s[7 - c0] : inr_s[c0], i0 = rev ? ini_s[7 - c0] : ini_s[c0];
+            const float r1 = rev ? inr_s[7 - c1] : inr_s[c1], i1 = rev ? ini_s[7 - c1] : ini_s[c1];
+            AFrag cfr;
+            cfr.set(r0, r1, i0, i1);
+            mma3f(D[q], cfr, bc);
             if (rv) {
-                const int xa = xw + 128 * q + 16 * g + 2 * t, xb = xa + 8;
-                float *o = orow + (size_t)k * a.H * a.Wp;
+                const int xa = xw + 16 * q + 2 * t, xb = xa + 8;
                 if (xa + 1 < a.Wp) *reinterpret_cast<float2 *>(o + xa) = make_float2(D[q][0] * beta, D[q][1] * beta);
                 if (xb + 1 < a.Wp) *reinterpret_cast<float2 *>(o + xb) = make_float2(D[q][2] * beta, D[q][3] * beta);
             }
@@ -1496,7 +1479,7 @@ __device__ __forceinline__ void col_tc_body(const ColArgs &a, const IIRCoef &cf,
 {
     extern __shared__ __align__(16) float tiles[];  // [2][512][8]
     __shared__ float2 wtot[8][8][4];                 // [warp][column][combo]
-    __shared__ float2 ctot[2][8][4];                 // [channel parity][column][combo] CTA totals for the cluster
+    __shared__ float2 ctot[2][8][4];                 // [channel parity][column][combo] CTA totals
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t = lane & 3;
@@ -1541,10 +1524,13 @@ __device__ __forceinline__ void col_tc_body(const ColArgs &a, const IIRCoef &cf,
     bl.load(tm.loc, g, t);
     bs.load(tm.sum, g, t);
     bc.load(tm.cor, g, t);
-    const int m = t & 1, dir = t >> 1;
-    const float P1r = cf.Pr[m][0], P1i = cf.Pi[m][0];  // p^8: one chunk
-    const float P8r = cf.Pr[m][3], P8i = cf.Pi[m][3];  // p^64: one warp (8 chunks)
+    const int m = t & 1;
+    const bool rev = (t >> 1) != 0;
+    const float P1r = cf.Pr[m][0], P1i = cf.Pi[m][0];    // p^8: one chunk
+    const float P8r = cf.Pr[m][3], P8i = cf.Pi[m][3];    // p^64: one warp (8 chunks)
     const float P64r = cf.Pr[m][6], P64i = cf.Pi[m][6];  // p^512: one CTA
+    float Phr, Phi;  // p^{64 hops}: the CTA carry crosses the warps before (causal) / after (anticausal) this one
+    cpow_tab(Phr, Phi, cf, m, 8 * (rev ? 7 - warp : warp));
 
     issue_tile(a.K - 1, (a.K - 1) & 1);
 #pragma unroll 1
@@ -1557,38 +1543,30 @@ __device__ __forceinline__ void col_tc_body(const ColArgs &a, const IIRCoef &cf,
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int r0 = 8 * (8 * warp + 2 * q) + t, r1 = r0 + 8;
-            const float a0 = tl[r0 * 8], a1 = tl[r1 * 8], a2 = tl[(r0 + 4) * 8], a3 = tl[(r1 + 4) * 8];
 #pragma unroll
             for (int i = 0; i < 4; ++i) D[q][i] = S[q][i] = 0.f;
-            mma3(D[q], a0, a1, a2, a3, bl);
-            mma3(S[q], a0, a1, a2, a3, bs);
+            AFrag af;
+            af.set(tl[r0 * 8], tl[r1 * 8], tl[(r0 + 4) * 8], tl[(r1 + 4) * 8]);
+            mma3f(D[q], af, bl);
+            mma3f(S[q], af, bs);
         }
-        // this lane's combo over the warp's 8 chunks (c = 2q + half), from zero state
+        Seq8 sq;
+        sq.from_chunks(S, rev);
         float totr = 0.f, toti = 0.f;
-        if (dir == 0) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                float nr, ni;
-                cmul(nr, ni, P1r, P1i, totr, toti);
-                totr = nr + S[c >> 1][2 * (c & 1)];
-                toti = ni + S[c >> 1][2 * (c & 1) + 1];
-            }
-        } else {
-#pragma unroll
-            for (int c = 7; c >= 0; --c) {
-                float nr, ni;
-                cmul(nr, ni, P1r, P1i, totr, toti);
-                totr = nr + S[c >> 1][2 * (c & 1)];
-                toti = ni + S[c >> 1][2 * (c & 1) + 1];
-            }
+        for (int s = 0; s < 8; ++s) {
+            float nr, ni;
+            cmul(nr, ni, P1r, P1i, totr, toti);
+            totr = nr + sq.r[s];
+            toti = ni + sq.i[s];
         }
         wtot[warp][g][t] = make_float2(totr, toti);
         __syncthreads();
         // carry entering this warp from the other warps of the CTA (p^64 per warp)
         float Wr = 0.f, Wi = 0.f;
         for (int s = 0; s < 8; ++s) {
-            const int w = dir == 0 ? s : 7 - s;
-            if ((dir == 0 && w >= warp) || (dir == 1 && w <= warp)) continue;
+            const int w = rev ? 7 - s : s;
+            if ((!rev && w >= warp) || (rev && w <= warp)) continue;
             const float2 tt = wtot[w][g][t];
             float nr, ni;
             cmul(nr, ni, P8r, P8i, Wr, Wi);
@@ -1596,7 +1574,7 @@ __device__ __forceinline__ void col_tc_body(const ColArgs &a, const IIRCoef &cf,
             Wi = ni + tt.y;
         }
         // CTA total: the last warp in scan order extends its incoming carry by its own total
-        if ((dir == 0 && warp == 7) || (dir == 1 && warp == 0)) {
+        if ((!rev && warp == 7) || (rev && warp == 0)) {
             float cr2 = totr, ci2 = toti;
             cmadd(cr2, ci2, P8r, P8i, Wr, Wi);
             ctot[k & 1][g][t] = make_float2(cr2, ci2);
@@ -1606,54 +1584,37 @@ __device__ __forceinline__ void col_tc_body(const ColArgs &a, const IIRCoef &cf,
         cl.sync();
         if (CL > 1) {
             float Xr = 0.f, Xi = 0.f;
-            const int nsteps = dir == 0 ? rank : CL - 1 - rank;
+            const int nsteps = rev ? CL - 1 - rank : rank;
             for (int s = 0; s < nsteps; ++s) {
-                const int r = dir == 0 ? s : CL - 1 - s;
+                const int r = rev ? CL - 1 - s : s;
                 const float2 tt = *cl.map_shared_rank(&ctot[k & 1][g][t], r);
                 float nr, ni;
                 cmul(nr, ni, P64r, P64i, Xr, Xi);
                 Xr = nr + tt.x;
                 Xi = ni + tt.y;
             }
-            // through the warps before (causal) / after (anticausal) this one
-            const int hops = dir == 0 ? warp : 7 - warp;
-            for (int s = 0; s < hops; ++s) {
-                float nr, ni;
-                cmul(nr, ni, P8r, P8i, Xr, Xi);
-                Xr = nr;
-                Xi = ni;
-            }
-            Wr += Xr;
-            Wi += Xi;
+            cmadd(Wr, Wi, Phr, Phi, Xr, Xi);
         }
-        // incoming state of every chunk, in scan order, and the correction products
-        float inr[8], ini[8];
-        {
-            float cr2 = Wr, ci2 = Wi;
-            if (dir == 0) {
+        // incoming state of each chunk in scan order, the correction products in chunk order
+        float inr_s[8], ini_s[8];
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    inr[c] = cr2;
-                    ini[c] = ci2;
-                    float nr, ni;
-                    cmul(nr, ni, P1r, P1i, cr2, ci2);
-                    cr2 = nr + S[c >> 1][2 * (c & 1)];
-                    ci2 = ni + S[c >> 1][2 * (c & 1) + 1];
-                }
-            } else {
-#pragma unroll
-                for (int c = 7; c >= 0; --c) {
-                    inr[c] = cr2;
-                    ini[c] = ci2;
-                    float nr, ni;
-                    cmul(nr, ni, P1r, P1i, cr2, ci2);
-                    cr2 = nr + S[c >> 1][2 * (c & 1)];
-                    ci2 = ni + S[c >> 1][2 * (c & 1) + 1];
-                }
-            }
+        for (int s = 0; s < 8; ++s) {
+            inr_s[s] = Wr;
+            ini_s[s] = Wi;
+            float nr, ni;
+            cmul(nr, ni, P1r, P1i, Wr, Wi);
+            Wr = nr + sq.r[s];
+            Wi = ni + sq.i[s];
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) mma3(D[q], inr[2 * q], inr[2 * q + 1], ini[2 * q], ini[2 * q + 1], bc);
+        for (int q = 0; q < 4; ++q) {
+            const int c0 = 2 * q, c1 = 2 * q + 1;
+            const float r0 = rev ? inr_s[7 - c0] : inr_s[c0], i0 = rev ? ini_s[7 - c0] : ini_s[c0];
+            const float r1 = rev ? inr_s[7 - c1] : inr_s[c1], i1 = rev ? ini_s[7 - c1] : ini_s[c1];
+            AFrag cfr;
+            cfr.set(r0, r1, i0, i1);
+            mma3f(D[q], cfr, bc);
+        }
         float y16[16];
 #pragma unroll
         for (int q = 0; q < 4; ++q)

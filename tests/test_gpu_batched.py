@@ -57,7 +57,13 @@ def test_batched_graph_matches_single_and_oracle(bf):
     torch.cuda.synchronize()
     assert (bfilt.status() & ~bf.BF_DEV_NONPOS_Q) == 0
     for i, (x, y, ss, sr, order) in enumerate(planes):
-        single = bf.bilateral_gp(x, ss, sr, order, "iir")
+        # the batched launches use the CUDA-core recursive kernels: same arithmetic as that engine
+        o = bf.make_opts(order, "iir", engine=bf.ENGINE_CUDA_CORE)
+        need = bf.bf_gp_workspace_size(1, x.shape[0], x.shape[1], ss, o)
+        wsb = torch.empty(need, dtype=torch.uint8, device="cuda")
+        single = torch.empty_like(x)
+        bf.bf_gp_forward(x.data_ptr(), single.data_ptr(), 1, x.shape[0], x.shape[1], x.shape[1], ss, sr, o,
+                         wsb.data_ptr(), need, torch.cuda.current_stream().cuda_stream)
         torch.cuda.synchronize()
         a, b = y.cpu().numpy(), single.cpu().numpy()
         assert np.array_equal(np.isnan(a), np.isnan(b))

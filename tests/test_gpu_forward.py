@@ -295,3 +295,21 @@ def test_repeat_calls_are_deterministic(bf):
     a = run_gpu(bf, img, 8.0, 30.0, 20, "iir")
     b = run_gpu(bf, img, 8.0, 30.0, 20, "iir")
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("engine", [0, 1, 2])
+@pytest.mark.parametrize("shape,ss", [((300, 260), 6.0), ((1030, 600), 12.0), ((2049, 75), 20.0)])
+def test_engines_agree_with_oracle(bf, engine, shape, ss):
+    """Recursive filter on tensor cores (rows and/or columns) and on CUDA cores."""
+    H, W = shape
+    img = synthetic.make_image(H, W, 8, 10.0, 20.0, synthetic.seed_for(9, 5000 + H + W))
+    x = torch.from_numpy(img).cuda()
+    o = bf.make_opts(20, "iir", engine=engine)
+    need = bf.bf_gp_workspace_size(1, H, W, ss, o)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    y = torch.empty_like(x)
+    s = torch.cuda.current_stream().cuda_stream
+    bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, 30.0, o, ws.data_ptr(), need, s)
+    assert bf.bf_gp_get_device_status(ws.data_ptr(), s) == 0
+    ref, kap = oracle.gp_bf(img.astype(np.float64), ss, 30.0, 20, "iir", return_kappa=True)
+    check(y.cpu().numpy().astype(np.float64), ref, kappa=kap, min_gated=0.9999)
