@@ -236,7 +236,8 @@ bf_status bf_gp_forward_noalloc(const float *f, float *y, int planes, int H, int
  *     every plane's K row-filtered planes).
  *   bf_gp_batched_plan_upload: copies the tables into ws (synchronises
  *     `stream`); must be called once per workspace before bf_gp_batched.
- *   bf_gp_batched: enqueues the four launches on `stream` and nothing else
+ *   bf_gp_batched: enqueues the launches on `stream` (stats, finalize, rows, one
+ *     column launch per cluster size present) and nothing else
  *     (no copies, no host synchronisation), so it can be captured into a
  *     CUDA graph and replayed.  ws must be the uploaded workspace.
  *   bf_gp_batched_plan_destroy: frees the plan.

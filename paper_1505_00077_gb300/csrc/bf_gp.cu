@@ -651,7 +651,9 @@ int bf_gp_order_for_tol(double sigma_r, double R, double eps)
 struct bf_gp_plan {
     std::vector<BatchPlane> bp;  // device pointers to ws filled at upload
     std::vector<IIRCoef> coef;
-    std::vector<int> pre_stats, pre_rows, pre_cols;
+    std::vector<int> pre_stats, pre_rows, pre_cols;  // pre_cols over col_order
+    std::vector<int> col_order;                      // planes sorted by column cluster size
+    std::vector<int> grp_cl, grp_start, grp_count;   // column launches: cluster size, first item, items
     std::vector<size_t> plane_off;  // byte offset of each plane's channel planes
     int n = 0, CLmax = 1, total_stats = 0, total_rows = 0, total_strips = 0;
     int centre_given = 0;
@@ -718,10 +720,24 @@ bf_status bf_gp_batched_plan_create(const bf_gp_plane *planes, int n, const bf_g
         const int rows_per_cta = 256 / pp.T;
         pl->pre_stats[i + 1] = pl->pre_stats[i] + pp.nblk;
         pl->pre_rows[i + 1] = pl->pre_rows[i] + (q.H + rows_per_cta - 1) / rows_per_cta;
-        pl->pre_cols[i + 1] = pl->pre_cols[i] + (q.W + 7) / 8;
         pl->CLmax = std::max(pl->CLmax, pp.CL);
         pl->plane_off[i] = planes_bytes;
         planes_bytes = align_up(planes_bytes + sizeof(float) * (size_t)pp.K * q.H * pp.Wp, 256);
+    }
+    // column work: planes sorted by cluster size, one launch per size
+    pl->col_order.resize(n);
+    for (int i = 0; i < n; ++i) pl->col_order[i] = i;
+    auto cl_of = [&](int i) { return (planes[i].H + COL_ROWS_PER_CTA - 1) / COL_ROWS_PER_CTA; };
+    std::stable_sort(pl->col_order.begin(), pl->col_order.end(), [&](int x, int y) { return cl_of(x) < cl_of(y); });
+    for (int j = 0; j < n; ++j) {
+        const int i = pl->col_order[j];
+        pl->pre_cols[j + 1] = pl->pre_cols[j] + (planes[i].W + 7) / 8;
+        if (pl->grp_cl.empty() || pl->grp_cl.back() != cl_of(i)) {
+            pl->grp_cl.push_back(cl_of(i));
+            pl->grp_start.push_back(pl->pre_cols[j]);
+            pl->grp_count.push_back(0);
+        }
+        pl->grp_count.back() += (planes[i].W + 7) / 8;
     }
     pl->total_stats = pl->pre_stats[n];
     pl->total_rows = pl->pre_rows[n];
@@ -732,7 +748,7 @@ bf_status bf_gp_batched_plan_create(const bf_gp_plane *planes, int n, const bf_g
     pl->off_part = off;
     off = align_up(off + sizeof(StatPartial) * (size_t)pl->total_stats, 256);
     pl->off_tables = off;
-    pl->tables_bytes = sizeof(BatchPlane) * n + sizeof(IIRCoef) * n + sizeof(int) * 3 * (n + 1);
+    pl->tables_bytes = sizeof(BatchPlane) * n + sizeof(IIRCoef) * n + sizeof(int) * (3 * (n + 1) + n);
     off = align_up(off + pl->tables_bytes, 256);
     pl->off_planes = off;
     pl->total = off + planes_bytes;
@@ -766,6 +782,8 @@ bf_status bf_gp_batched_plan_upload(bf_gp_plan *plan, void *ws, size_t ws_bytes,
     std::memcpy(img.data() + o, plan->pre_rows.data(), sizeof(int) * (n + 1));
     o += sizeof(int) * (n + 1);
     std::memcpy(img.data() + o, plan->pre_cols.data(), sizeof(int) * (n + 1));
+    o += sizeof(int) * (n + 1);
+    std::memcpy(img.data() + o, plan->col_order.data(), sizeof(int) * n);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     BF_CUDA(cudaMemcpyAsync(wsb + plan->off_tables, img.data(), plan->tables_bytes, cudaMemcpyHostToDevice, s));
     BF_CUDA(cudaStreamSynchronize(s));
@@ -789,6 +807,9 @@ bf_status bf_gp_batched(const bf_gp_plan *plan, void *ws, size_t ws_bytes, void 
     b.pre_stats = pre;
     b.pre_rows = pre + (n + 1);
     b.pre_cols = pre + 2 * (n + 1);
+    b.col_order = pre + 3 * (n + 1);
+    b.cid0 = 0;
+    b.pad = 0;
     b.pp = reinterpret_cast<PlaneParams *>(wsb + plan->off_params);
     b.part = reinterpret_cast<StatPartial *>(wsb + plan->off_part);
     b.status = reinterpret_cast<uint32_t *>(wsb);
@@ -799,20 +820,23 @@ bf_status bf_gp_batched(const bf_gp_plan *plan, void *ws, size_t ws_bytes, void 
     batched_stats_partial<<<plan->total_stats, 256, 0, s>>>(b);
     batched_stats_finalize<<<n, 256, 0, s>>>(b);
     batched_row_iir<<<plan->total_rows, 256, 0, s>>>(b);
-    cudaLaunchConfig_t cfg;
-    std::memset(&cfg, 0, sizeof cfg);
-    cfg.gridDim = dim3((unsigned)(plan->total_strips * plan->CLmax), 1, 1);
-    cfg.blockDim = dim3(256, 1, 1);
-    cfg.dynamicSmemBytes = sizeof(float) * 2 * COL_TILE_FLOATS;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)plan->CLmax;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    BF_CUDA(cudaLaunchKernelEx(&cfg, batched_col_iir, b));
+    for (size_t gi = 0; gi < plan->grp_cl.size(); ++gi) {
+        cudaLaunchConfig_t cfg;
+        std::memset(&cfg, 0, sizeof cfg);
+        cfg.gridDim = dim3((unsigned)(plan->grp_count[gi] * plan->grp_cl[gi]), 1, 1);
+        cfg.blockDim = dim3(256, 1, 1);
+        cfg.dynamicSmemBytes = sizeof(float) * 2 * COL_TILE_FLOATS;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)plan->grp_cl[gi];
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        b.cid0 = plan->grp_start[gi];
+        BF_CUDA(cudaLaunchKernelEx(&cfg, batched_col_iir, b));
+    }
     BF_CUDA(cudaGetLastError());
     return BF_OK;
 }

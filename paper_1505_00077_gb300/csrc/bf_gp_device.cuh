@@ -914,8 +914,7 @@ template <int C, int MODE>
 __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf, int strip, int plane)
 {
     extern __shared__ __align__(16) float tiles[];  // [2][COL_TILE_FLOATS]
-    __shared__ float4 wt[8][8][NP];    // [warp][col][pole] warp totals (causal re, im, anticausal re, im)
-    __shared__ float4 wcar[8][8][NP];  // [warp][col][pole] incoming carries of each warp
+    __shared__ float4 wt[2][8][8][NP];  // [channel parity][warp][col][pole] warp totals (causal re, im, anticausal re, im)
     __shared__ float4 ct[2][8][NP];    // [channel parity][col][pole] CTA totals, read by the other CTAs
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -961,6 +960,10 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
         cpow_tab(qcr[m], qci[m], cf, m, l4);
         cpow_tab(qar[m], qai[m], cf, m, 3 - l4);
     }
+    // cross-warp roles: lane = (dir * 2 + pole) * 8 + column
+    const int gcol = lane & 7, gq = lane >> 3, gm = gq & 1, gdir = gq >> 1;
+    float Phr, Phi;  // p^{C 4 hops}: the CTA carry crosses the warps before (causal) / after (anticausal) this one
+    cpow_tab(Phr, Phi, cf, gm, 4 * (gdir == 0 ? warp : 7 - warp));
 
     issue_tile(a.K - 1, (a.K - 1) & 1);
 #pragma unroll 1
@@ -1002,77 +1005,71 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
             ar[m] = l4 < 3 ? vr : 0.f;
             ai[m] = l4 < 3 ? vi : 0.f;
         }
+        const int par = k & 1;
         if (l4 == 3) {
 #pragma unroll
             for (int m = 0; m < NP; ++m) {
-                wt[warp][col][m].x = er[m];
-                wt[warp][col][m].y = ei[m];
+                wt[par][warp][col][m].x = er[m];
+                wt[par][warp][col][m].y = ei[m];
             }
         }
         if (l4 == 0) {
 #pragma unroll
             for (int m = 0; m < NP; ++m) {
-                wt[warp][col][m].z = sr[m];
-                wt[warp][col][m].w = si[m];
+                wt[par][warp][col][m].z = sr[m];
+                wt[par][warp][col][m].w = si[m];
             }
         }
         __syncthreads();
-        // level 2 (warp 0): lane = (dir * 2 + pole) * 8 + column; the
-        // exclusive carry of each warp goes straight to wcar
-        const int gcol = lane & 7, gq = lane >> 3, gm = gq & 1, gdir = gq >> 1;
-        if (warp == 0) {
+        // every warp: the carry entering it from the other warps of the CTA (lane = combo x column)
+        float Wr = 0.f, Wi = 0.f;
+        {
             const float p4r = cf.Pr[gm][2], p4i = cf.Pi[gm][2];
-            float totr = 0.f, toti = 0.f;
-#pragma unroll
             for (int s = 0; s < 8; ++s) {
                 const int w = gdir == 0 ? s : 7 - s;
-                const float4 tt = wt[w][gcol][gm];
-                float *dst = gdir == 0 ? &wcar[w][gcol][gm].x : &wcar[w][gcol][gm].z;
-                dst[0] = totr;
-                dst[1] = toti;
+                if ((gdir == 0 && w >= warp) || (gdir == 1 && w <= warp)) continue;
+                const float4 tt = wt[par][w][gcol][gm];
                 float nr, ni;
-                cmul(nr, ni, p4r, p4i, totr, toti);
-                totr = nr + (gdir == 0 ? tt.x : tt.z);
-                toti = ni + (gdir == 0 ? tt.y : tt.w);
+                cmul(nr, ni, p4r, p4i, Wr, Wi);
+                Wr = nr + (gdir == 0 ? tt.x : tt.z);
+                Wi = ni + (gdir == 0 ? tt.y : tt.w);
             }
-            float *dst = gdir == 0 ? &ct[k & 1][gcol][gm].x : &ct[k & 1][gcol][gm].z;
-            dst[0] = totr;
-            dst[1] = toti;
+            // CTA total: the last warp in scan order extends its incoming carry by its own total
+            if ((gdir == 0 && warp == 7) || (gdir == 1 && warp == 0)) {
+                const float4 tt = wt[par][warp][gcol][gm];
+                float tr = gdir == 0 ? tt.x : tt.z, ti = gdir == 0 ? tt.y : tt.w;
+                cmadd(tr, ti, p4r, p4i, Wr, Wi);
+                float *dst = gdir == 0 ? &ct[par][gcol][gm].x : &ct[par][gcol][gm].z;
+                dst[0] = tr;
+                dst[1] = ti;
+            }
         }
-        cl.sync();  // CTA totals of the whole cluster written
-        if (warp == 0) {
-            // level 3: carry entering this CTA from the other CTAs of the column
+        // CTA totals of the cluster written.  ct and wt are double-buffered by channel
+        // parity: peers may read this channel's values until the next cluster barrier.
+        cl.sync();
+        if (CL > 1) {
             const float p32r = cf.Pr[gm][5], p32i = cf.Pi[gm][5];
-            float Cr = 0.f, Ci = 0.f;
+            float Xr = 0.f, Xi = 0.f;
             const int nsteps = gdir == 0 ? rank : CL - 1 - rank;
             for (int s = 0; s < nsteps; ++s) {
                 const int r = gdir == 0 ? s : CL - 1 - s;
-                const float4 tt = *cl.map_shared_rank(&ct[k & 1][gcol][gm], r);
+                const float4 tt = *cl.map_shared_rank(&ct[par][gcol][gm], r);
                 float nr, ni;
-                cmul(nr, ni, p32r, p32i, Cr, Ci);
-                Cr = nr + (gdir == 0 ? tt.x : tt.z);
-                Ci = ni + (gdir == 0 ? tt.y : tt.w);
+                cmul(nr, ni, p32r, p32i, Xr, Xi);
+                Xr = nr + (gdir == 0 ? tt.x : tt.z);
+                Xi = ni + (gdir == 0 ? tt.y : tt.w);
             }
-            // propagate it through the warps before (causal) / after (anticausal) each warp
-            const float p4r = cf.Pr[gm][2], p4i = cf.Pi[gm][2];
-#pragma unroll
-            for (int s = 0; s < 8; ++s) {
-                const int w = gdir == 0 ? s : 7 - s;
-                float *dst = gdir == 0 ? &wcar[w][gcol][gm].x : &wcar[w][gcol][gm].z;
-                dst[0] += Cr;
-                dst[1] += Ci;
-                float nr, ni;
-                cmul(nr, ni, p4r, p4i, Cr, Ci);
-                Cr = nr;
-                Ci = ni;
-            }
+            cmadd(Wr, Wi, Phr, Phi, Xr, Xi);
         }
-        __syncthreads();
+        // hand each thread the warp carries of its column: lane (combo, col) -> threads (col, any l4)
 #pragma unroll
         for (int m = 0; m < NP; ++m) {
-            const float4 cw = wcar[warp][col][m];
-            cmadd(cr[m], ci[m], qcr[m], qci[m], cw.x, cw.y);
-            cmadd(ar[m], ai[m], qar[m], qai[m], cw.z, cw.w);
+            const float wcr = __shfl_sync(0xffffffffu, Wr, (0 * 2 + m) * 8 + col);
+            const float wci = __shfl_sync(0xffffffffu, Wi, (0 * 2 + m) * 8 + col);
+            const float war = __shfl_sync(0xffffffffu, Wr, (1 * 2 + m) * 8 + col);
+            const float wai = __shfl_sync(0xffffffffu, Wi, (1 * 2 + m) * 8 + col);
+            cmadd(cr[m], ci[m], qcr[m], qci[m], wcr, wci);
+            cmadd(ar[m], ai[m], qar[m], qai[m], war, wai);
         }
         chunk_correct<C>(y, cr, ci, ar, ai, cf);
         cb.step(k, a.N, P.s2, y);
@@ -1666,9 +1663,12 @@ struct BatchArgs {
     const IIRCoef *coef;  // per plane (chunk length 16 for rows and columns)
     PlaneParams *pp;
     StatPartial *part;
-    const int *pre_stats, *pre_rows, *pre_cols;  // n + 1 entries each
+    const int *pre_stats, *pre_rows, *pre_cols;  // n + 1 entries each (pre_cols over the planes in col_order)
+    const int *col_order;                        // planes sorted by column cluster size
     uint32_t *status;
     int n, centre_given;
+    int cid0;                                    // first (plane, strip) item of this column launch
+    int pad;
     double tc_given;
 };
 
@@ -1720,12 +1720,14 @@ __global__ void __launch_bounds__(256) batched_row_iir(BatchArgs b)
     row_iir_body<CMAX, MODE_FWD>(a, b.coef[p], blockIdx.x - b.pre_rows[p], 0);
 }
 
-// cluster (CLmax, 1, 1): one cluster per (plane, 8-column strip); CTAs below
-// a shorter plane's last row take part in the carries with empty tiles.
+// One launch per column cluster size: cluster (CL, 1, 1), one cluster per
+// (plane, 8-column strip) of the planes of that size (planes sorted by size in
+// col_order, items numbered from cid0).
 __global__ void __launch_bounds__(256, 2) batched_col_iir(BatchArgs b)
 {
-    const int cid = blockIdx.x / (int)cg::this_cluster().num_blocks();
-    const int p = find_plane(b.pre_cols, b.n, cid);
+    const int cid = b.cid0 + (int)(blockIdx.x / cg::this_cluster().num_blocks());
+    const int idx = find_plane(b.pre_cols, b.n, cid);
+    const int p = b.col_order[idx];
     const BatchPlane &d = b.bp[p];
     ColArgs a;
     a.ws = d.ws;
@@ -1742,7 +1744,7 @@ __global__ void __launch_bounds__(256, 2) batched_col_iir(BatchArgs b)
     a.Wp = d.Wp;
     a.K = d.K;
     a.N = d.N;
-    col_iir_body<CMAX, MODE_FWD>(a, b.coef[p], cid - b.pre_cols[p], 0);
+    col_iir_body<CMAX, MODE_FWD>(a, b.coef[p], cid - b.pre_cols[idx], 0);
 }
 
 }  // namespace bfgp
