@@ -142,6 +142,16 @@ void deriche_coefs(double sigma, int C, IIRCoef *cf)
             cf->Pr[m][i] = (float)t.real();
             cf->Pi[m][i] = (float)t.imag();
         }
+        for (int e = 0; e <= 8; ++e) {
+            const std::complex<double> t = std::pow(p[m], (double)e);
+            cf->wr[m][e] = (float)t.real();
+            cf->wi[m][e] = (float)t.imag();
+        }
+    }
+    for (int d = 0; d < 8; ++d) {
+        double h = 0.0;
+        for (int m = 0; m < NP; ++m) h += (A[m] * std::pow(p[m], (double)d)).real();
+        cf->h[d] = (float)h;
     }
 }
 
@@ -365,7 +375,7 @@ bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
         deriche_coefs((double)sigma_s, tcore ? TC_C : COL_C, &cc);
         TCMat tm;
         if (tcore) tc_mats((double)sigma_s, &tm);
-        const size_t smem = tcore ? sizeof(float) * 2 * 512 * 8 : sizeof(float) * 2 * COL_TILE_FLOATS;
+        const size_t smem = tcore ? sizeof(float) * 2 * 512 * 8 : sizeof(float) * COL_TILE_BUFS * COL_TILE_FLOATS;
         if (tcore)
             BF_CUDA(cudaFuncSetAttribute(col_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         else
@@ -787,7 +797,7 @@ bf_status bf_gp_batched_plan_upload(bf_gp_plan *plan, void *ws, size_t ws_bytes,
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     BF_CUDA(cudaMemcpyAsync(wsb + plan->off_tables, img.data(), plan->tables_bytes, cudaMemcpyHostToDevice, s));
     BF_CUDA(cudaStreamSynchronize(s));
-    const size_t smem = sizeof(float) * 2 * COL_TILE_FLOATS;
+    const size_t smem = sizeof(float) * COL_TILE_BUFS * COL_TILE_FLOATS;
     BF_CUDA(cudaFuncSetAttribute(batched_col_iir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     plan->uploaded_ws = ws;
     return BF_OK;
@@ -825,7 +835,7 @@ bf_status bf_gp_batched(const bf_gp_plan *plan, void *ws, size_t ws_bytes, void 
         std::memset(&cfg, 0, sizeof cfg);
         cfg.gridDim = dim3((unsigned)(plan->grp_count[gi] * plan->grp_cl[gi]), 1, 1);
         cfg.blockDim = dim3(256, 1, 1);
-        cfg.dynamicSmemBytes = sizeof(float) * 2 * COL_TILE_FLOATS;
+        cfg.dynamicSmemBytes = sizeof(float) * COL_TILE_BUFS * COL_TILE_FLOATS;
         cfg.stream = s;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;

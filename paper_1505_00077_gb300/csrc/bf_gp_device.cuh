@@ -77,6 +77,8 @@ struct IIRCoef {
     float pr[NP], pi[NP];                      // poles p_m
     float tr[NP][CMAX + 1], ti[NP][CMAX + 1];  // A_m p_m^e, e = 0..C  (e = 0: A_m)
     float Pr[NP][12], Pi[NP][12];              // p_m^{C 2^i}
+    float wr[NP][9], wi[NP][9];                // p_m^e, e = 0..8
+    float h[8];                                // h(d) = sum_m Re(A_m p_m^d), d = 0..7
 };
 
 struct FIRCoef {
@@ -98,19 +100,79 @@ __device__ __forceinline__ void cmul(float &rr, float &ri, float ar, float ai, f
     ri = fmaf(ar, bi, ai * br);
 }
 
-// p^{C n} by binary powering from the table p^{C 2^i}
+// p^{C n} by binary powering from the table p^{C 2^i}, 0 <= n < 4096.  The
+// pole index m may vary between threads: it selects, so the table stays in
+// the constant bank.
 __device__ __forceinline__ void cpow_tab(float &rr, float &ri, const IIRCoef &cf, int m, int n)
 {
     rr = 1.f;
     ri = 0.f;
-#pragma unroll 1
-    for (int i = 0; i < 12 && n; ++i, n >>= 1)
-        if (n & 1) {
+#pragma unroll
+    for (int i = 0; i < 12; ++i)
+        if ((n >> i) & 1) {
+            const float br = m == 0 ? cf.Pr[0][i] : cf.Pr[1][i];
+            const float bi = m == 0 ? cf.Pi[0][i] : cf.Pi[1][i];
             float tr, ti;
-            cmul(tr, ti, rr, ri, cf.Pr[m][i], cf.Pi[m][i]);
+            cmul(tr, ti, rr, ri, br, bi);
             rr = tr;
             ri = ti;
         }
+}
+
+// Halves of 8 samples.  Sums over one half with zero state outside it:
+//   ce[m] = sum_i p_m^{7-i} x_i   (causal state at the half's end)
+//   as[m] = sum_i p_m^i x_i       (anticausal state at the half's start)
+__device__ __forceinline__ void half_sums(const float *x, float (&cer)[NP], float (&cei)[NP], float (&asr)[NP],
+                                          float (&asi)[NP], const IIRCoef &cf)
+{
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+        float a0 = x[7], a1 = 0.f, b0 = x[0], b1 = 0.f;
+#pragma unroll
+        for (int i = 0; i < 7; ++i) {
+            a0 = fmaf(cf.wr[m][7 - i], x[i], a0);
+            a1 = fmaf(cf.wi[m][7 - i], x[i], a1);
+            b0 = fmaf(cf.wr[m][i + 1], x[i + 1], b0);
+            b1 = fmaf(cf.wi[m][i + 1], x[i + 1], b1);
+        }
+        cer[m] = a0;
+        cei[m] = a1;
+        asr[m] = b0;
+        asi[m] = b1;
+    }
+}
+
+// Response of one half to its own samples: y_j = sum_i h(|j - i|) x_i.
+__device__ __forceinline__ void half_local(const float *x, float *y, const IIRCoef &cf)
+{
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        float v = cf.h[0] * x[j];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (i != j) v = fmaf(cf.h[i > j ? i - j : j - i], x[i], v);
+        y[j] = v;
+    }
+}
+
+// Adds the response of one half to the samples outside it, given the causal
+// state c entering the half and the anticausal state a entering it from the
+// right: y_j += sum_m Re(A_m p_m^{j+1} c_m) + Re(A_m p_m^{8-j} a_m).
+__device__ __forceinline__ void half_correct(float *y, const float (&cr)[NP], const float (&ci)[NP],
+                                             const float (&ar)[NP], const float (&ai)[NP], const IIRCoef &cf)
+{
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float v = y[j];
+            v = fmaf(cf.tr[m][j + 1], cr[m], v);
+            v = fmaf(-cf.ti[m][j + 1], ci[m], v);
+            v = fmaf(cf.tr[m][8 - j], ar[m], v);
+            v = fmaf(-cf.ti[m][8 - j], ai[m], v);
+            y[j] = v;
+        }
+    }
 }
 
 // Local recursions of one chunk from zero state.
@@ -437,6 +499,24 @@ __device__ __forceinline__ size_t saved_idx(int plane, int which, int H, int W, 
     return (((size_t)plane * 4 + which) * H + r) * W + x;
 }
 
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void bar_sync_named(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_arrive_named(int id, int n)
+{
+    asm volatile("bar.arrive %0, %1;\n" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cluster_arrive_release()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire()
+{
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
 // Channel generator of the row pass for one chunk.
 //   forward: Phi_k = 2^e0 E u^k (k = 0..K-1), E = exp(-s^2 u^2/2)
 //   adjoint: with alpha = dL/dy R / Q~ and rho = P~ / Q~ at the pixel,
@@ -549,18 +629,23 @@ __device__ __forceinline__ void zero_acc(const RowArgs &a, int plane)
 }
 
 // grid (ceil(H / rows_per_cta), planes); block = max(T, 256) threads.
-// Thread t of a row owns samples [t*C, (t+1)*C).  Carries: Kogge-Stone
-// inside each warp (shuffles), then one warp combines the warp totals of
-// each row sequentially (one lane per row x pole x direction).
+// Thread t of a row owns samples [t*C, (t+1)*C), two halves of 8.  Per
+// channel: half sums -> chunk sums; carries by Kogge-Stone inside each warp
+// (shuffles); then one warp combines the warp totals of each row sequentially
+// (one lane per row x pole x direction) while the other warps compute the
+// in-half responses (8 x 8 Toeplitz); named barriers 1 (totals written) and
+// 2 (carries written) order the two.
 template <int C, int MODE>
 __device__ __forceinline__ void row_iir_body(const RowArgs &a, const IIRCoef &cf, int grp, int plane)
 {
+    static_assert(C == 16, "row chunks are two halves of 8 samples");
     __shared__ float4 wt[16][NP];    // warp totals [warp slot][pole] (causal re, im, anticausal re, im)
     __shared__ float4 wcar[16][NP];  // incoming carries of each warp
     const int T = a.T;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const int rows_per_cta = blockDim.x / T;
+    const int nthr = blockDim.x;
+    const int rows_per_cta = nthr / T;
     const int r_local = tid / T;
     const int t = tid % T;
     const int row = grp * rows_per_cta + r_local;
@@ -588,9 +673,19 @@ __device__ __forceinline__ void row_iir_body(const RowArgs &a, const IIRCoef &cf
     for (int k = 0; k < a.K; ++k) {
         float x[C];
         gen.channel(k, a.N, x);
-        float y[C];
+        float hAr[NP], hAi[NP], sAr[NP], sAi[NP], hBr[NP], hBi[NP], sBr[NP], sBi[NP];
+        half_sums(x, hAr, hAi, sAr, sAi, cf);
+        half_sums(x + 8, hBr, hBi, sBr, sBi, cf);
         float er[NP], ei[NP], sr[NP], si[NP];
-        chunk_local<C>(x, y, er, ei, sr, si, cf);
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+            er[m] = hBr[m];
+            ei[m] = hBi[m];
+            cmadd(er[m], ei[m], cf.wr[m][8], cf.wi[m][8], hAr[m], hAi[m]);
+            sr[m] = sAr[m];
+            si[m] = sAi[m];
+            cmadd(sr[m], si[m], cf.wr[m][8], cf.wi[m][8], sBr[m], sBi[m]);
+        }
 
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
@@ -618,6 +713,7 @@ __device__ __forceinline__ void row_iir_body(const RowArgs &a, const IIRCoef &cf
             ar[m] = ls < L - 1 ? vr : 0.f;
             ai[m] = ls < L - 1 ? vi : 0.f;
         }
+        float y[C];
         if (wpr > 1) {
             if (lane == 31) {
 #pragma unroll
@@ -633,38 +729,64 @@ __device__ __forceinline__ void row_iir_body(const RowArgs &a, const IIRCoef &cf
                     wt[warp][m].w = si[m];
                 }
             }
-            __syncthreads();
-            if (warp == 0 && lane < rows_per_cta * 4) {
-                // lane = row * 4 + (direction * 2 + pole)
-                const int rr = lane >> 2, dir = (lane >> 1) & 1, m = lane & 1;
-                const float p32r = cf.Pr[m][5], p32i = cf.Pi[m][5];
-                float accr = 0.f, acci = 0.f;
-                for (int s = 0; s < wpr; ++s) {
-                    const int w = dir == 0 ? s : wpr - 1 - s;
-                    const int slot = rr * wpr + w;
-                    const float4 tt = wt[slot][m];
-                    if (dir == 0) {
-                        wcar[slot][m].x = accr;
-                        wcar[slot][m].y = acci;
-                    } else {
-                        wcar[slot][m].z = accr;
-                        wcar[slot][m].w = acci;
+            if (warp == 0) {
+                bar_sync_named(1, nthr);  // warp totals written
+                if (lane < rows_per_cta * 4) {
+                    // lane = row * 4 + (direction * 2 + pole)
+                    const int rr = lane >> 2, dir = (lane >> 1) & 1, m = lane & 1;
+                    const float p32r = m == 0 ? cf.Pr[0][5] : cf.Pr[1][5];
+                    const float p32i = m == 0 ? cf.Pi[0][5] : cf.Pi[1][5];
+                    float accr = 0.f, acci = 0.f;
+                    for (int s = 0; s < wpr; ++s) {
+                        const int w = dir == 0 ? s : wpr - 1 - s;
+                        const int slot = rr * wpr + w;
+                        const float4 tt = wt[slot][m];
+                        if (dir == 0) {
+                            wcar[slot][m].x = accr;
+                            wcar[slot][m].y = acci;
+                        } else {
+                            wcar[slot][m].z = accr;
+                            wcar[slot][m].w = acci;
+                        }
+                        float nr, ni;
+                        cmul(nr, ni, p32r, p32i, accr, acci);
+                        accr = nr + (dir == 0 ? tt.x : tt.z);
+                        acci = ni + (dir == 0 ? tt.y : tt.w);
                     }
-                    float nr, ni;
-                    cmul(nr, ni, p32r, p32i, accr, acci);
-                    accr = nr + (dir == 0 ? tt.x : tt.z);
-                    acci = ni + (dir == 0 ? tt.y : tt.w);
                 }
+                bar_arrive_named(2, nthr);  // carries written
+                __syncwarp();
+                half_local(x, y, cf);
+                half_local(x + 8, y + 8, cf);
+            } else {
+                bar_arrive_named(1, nthr);
+                half_local(x, y, cf);
+                half_local(x + 8, y + 8, cf);
+                bar_sync_named(2, nthr);
             }
-            __syncthreads();
 #pragma unroll
             for (int m = 0; m < NP; ++m) {
                 const float4 cw = wcar[warp][m];
                 cmadd(cr[m], ci[m], qcr[m], qci[m], cw.x, cw.y);
                 cmadd(ar[m], ai[m], qar[m], qai[m], cw.z, cw.w);
             }
+        } else {
+            half_local(x, y, cf);
+            half_local(x + 8, y + 8, cf);
         }
-        chunk_correct<C>(y, cr, ci, ar, ai, cf);
+        // states entering each half: B causal p^8 c + cA, A anticausal aB + p^8 a
+        float cBr[NP], cBi[NP], aAr[NP], aAi[NP];
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+            cBr[m] = hAr[m];
+            cBi[m] = hAi[m];
+            cmadd(cBr[m], cBi[m], cf.wr[m][8], cf.wi[m][8], cr[m], ci[m]);
+            aAr[m] = sBr[m];
+            aAi[m] = sBi[m];
+            cmadd(aAr[m], aAi[m], cf.wr[m][8], cf.wi[m][8], ar[m], ai[m]);
+        }
+        half_correct(y, cr, ci, aAr, aAi, cf);
+        half_correct(y + 8, cBr, cBi, ar, ai, cf);
         store_row_chunk<C>(a, plane, k, row, rv, x0, y, P.beta[k]);
     }
 }
@@ -902,20 +1024,35 @@ __device__ __forceinline__ void cp_async16(float *dst, const float *src, bool va
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+constexpr int COL_TILE_BUFS = 4;  // channel tiles in flight in the recursive column pass
+
 // Column pass for the recursive filter.  A cluster of CL CTAs covers the
 // full height of an 8-column strip; CTA rank r owns rows [r*512, (r+1)*512).
-// Thread (warp w, lane l): column l%8 of the strip, chunk 4w + l/8 (16 rows).
-// Each channel's 8 x 512 tile is staged in shared memory by cp.async, one
-// channel ahead.  Carries: shuffles between the 4 chunks of a warp, then
-// warp 0 combines the 8 warp totals of each column and the CTA totals of the
-// cluster (DSMEM) with one lane per column x pole x direction.
+// Thread (warp w, lane l): column l%8 of the strip, chunk 4w + l/8 of 16
+// rows, split in two halves of 8.  Per channel (descending k):
+//   1. the channel's tile (staged by cp.async two channels ahead, four
+//      buffers) -> half sums -> chunk sums; carries between the 4 chunks of
+//      a column in the warp by shuffles; warp totals to shared memory;
+//   2. warp 0 (named barrier) turns the 8 warp totals of each column into the
+//      carry entering each warp and the CTA total, and stores the CTA total
+//      into the shared memory of the CTAs it enters (DSMEM);
+//   3. split cluster barrier: the in-half responses (8 x 8 Toeplitz) are
+//      computed while the barrier completes;
+//   4. every warp adds the carry from the other CTAs (local shared memory, one
+//      lane per column x pole x direction), then each half gets its entering
+//      states, the out-of-half response and the Horner step.
 // grid (strips * CL, planes), block 256, cluster (CL, 1, 1).
 template <int C, int MODE>
 __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf, int strip, int plane)
 {
-    extern __shared__ __align__(16) float tiles[];  // [2][COL_TILE_FLOATS]
-    __shared__ float4 wt[2][8][8][NP];  // [channel parity][warp][col][pole] warp totals (causal re, im, anticausal re, im)
-    __shared__ float4 ct[2][8][NP];    // [channel parity][col][pole] CTA totals, read by the other CTAs
+    static_assert(C == 16, "column chunks are two halves of 8 rows");
+    extern __shared__ __align__(16) float tiles[];  // [COL_TILE_BUFS][COL_TILE_FLOATS]
+    // [channel parity][warp][col][pole]: warp totals (causal re, im, anticausal re, im);
+    // warp 0 replaces them in place by the carry entering each warp
+    __shared__ float4 wt[2][8][8][NP];
+    // [channel parity][source rank][col][pole][direction]: CTA totals pushed here by the other
+    // CTAs of the cluster (causal ones by lower ranks, anticausal ones by higher ranks)
+    __shared__ float2 inc[2][8][8][NP][2];
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int col = lane & 7, l4 = lane >> 3;
@@ -931,9 +1068,9 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
     const float *wsp = a.ws + (size_t)plane * a.K * a.H * a.Wp + strip * 8;
 
     // tile copy: 512 rows x two 16-byte halves; thread copies 4 of them
-    auto issue_tile = [&](int k, int buf) {
+    auto issue_tile = [&](int k) {
         const float *src = wsp + (size_t)k * a.H * a.Wp;
-        float *dst = tiles + buf * COL_TILE_FLOATS;
+        float *dst = tiles + (k & (COL_TILE_BUFS - 1)) * COL_TILE_FLOATS;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int idx = tid + i * 256;
@@ -942,7 +1079,6 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
             const bool ok = filt && gr < a.H;
             cp_async16(dst + tile_off(r) + half * 4, src + (size_t)(ok ? gr : 0) * a.Wp + half * 4, ok);
         }
-        cp_async_commit();
     };
 
     Combine<C, MODE> cb;
@@ -954,32 +1090,53 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
         const float fv = in ? __ldg(fcol + (size_t)r * a.pitch + x) : 0.f;
         cb.init((fv - P.tc) * P.invR, j);
     }
-    float qcr[NP], qci[NP], qar[NP], qai[NP];
+    float qcr[NP], qci[NP], qar[NP], qai[NP];  // p^{16 l4}, p^{16 (3 - l4)}
 #pragma unroll
     for (int m = 0; m < NP; ++m) {
         cpow_tab(qcr[m], qci[m], cf, m, l4);
         cpow_tab(qar[m], qai[m], cf, m, 3 - l4);
     }
-    // cross-warp roles: lane = (dir * 2 + pole) * 8 + column
+    // cross-CTA roles: lane = (dir * 2 + pole) * 8 + column
     const int gcol = lane & 7, gq = lane >> 3, gm = gq & 1, gdir = gq >> 1;
-    float Phr, Phi;  // p^{C 4 hops}: the CTA carry crosses the warps before (causal) / after (anticausal) this one
+    float Phr, Phi;  // p^{64 w}: the CTA carry crosses the warps before (causal) / after (anticausal) this one
     cpow_tab(Phr, Phi, cf, gm, 4 * (gdir == 0 ? warp : 7 - warp));
+    const float p4r = gm == 0 ? cf.Pr[0][2] : cf.Pr[1][2], p4i = gm == 0 ? cf.Pi[0][2] : cf.Pi[1][2];
+    const float p32r = gm == 0 ? cf.Pr[0][5] : cf.Pr[1][5], p32i = gm == 0 ? cf.Pi[0][5] : cf.Pi[1][5];
 
-    issue_tile(a.K - 1, (a.K - 1) & 1);
+    issue_tile(a.K - 1);
+    cp_async_commit();
+    if (a.K >= 2) issue_tile(a.K - 2);
+    cp_async_commit();
+    cp_async_wait_1();
+    __syncthreads();
 #pragma unroll 1
     for (int k = a.K - 1; k >= 0; --k) {
-        cp_async_wait_all();
-        __syncthreads();  // tile k visible; every thread is done with the tile of channel k+1
-        if (k > 0) issue_tile(k - 1, (k - 1) & 1);
+        // tile k: landed before the previous cluster barrier (or the
+        // __syncthreads above); the buffer of tile k - 2 last held tile k + 2,
+        // which every thread finished before arriving at that barrier
+        const float *tl = tiles + (k & (COL_TILE_BUFS - 1)) * COL_TILE_FLOATS + tile_off(chunk_cta * C) + col;
         float xin[C];
-        const float *tl = tiles + (k & 1) * COL_TILE_FLOATS + col;
 #pragma unroll
-        for (int j = 0; j < C; ++j) xin[j] = tl[tile_off(chunk_cta * C + j)];
-        float y[C];
-        float er[NP], ei[NP], sr[NP], si[NP];
-        chunk_local<C>(xin, y, er, ei, sr, si, cf);
+        for (int j = 0; j < C; ++j) xin[j] = tl[j * 8];
+        if (k >= 2) issue_tile(k - 2);
+        cp_async_commit();
 
-        // level 1: the 4 chunks of this column inside the warp (lane stride 8)
+        float hAr[NP], hAi[NP], sAr[NP], sAi[NP], hBr[NP], hBi[NP], sBr[NP], sBi[NP];
+        half_sums(xin, hAr, hAi, sAr, sAi, cf);
+        half_sums(xin + 8, hBr, hBi, sBr, sBi, cf);
+        // chunk sums: causal end state e = p^8 cA + cB, anticausal start state s = aA + p^8 aB
+        float er[NP], ei[NP], sr[NP], si[NP];
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+            er[m] = hBr[m];
+            ei[m] = hBi[m];
+            cmadd(er[m], ei[m], cf.wr[m][8], cf.wi[m][8], hAr[m], hAi[m]);
+            sr[m] = sAr[m];
+            si[m] = sAi[m];
+            cmadd(sr[m], si[m], cf.wr[m][8], cf.wi[m][8], sBr[m], sBi[m]);
+        }
+
+        // the 4 chunks of this column inside the warp (lane stride 8)
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int dd = 1 << i;
@@ -1020,48 +1177,64 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
                 wt[par][warp][col][m].w = si[m];
             }
         }
-        __syncthreads();
-        // every warp: the carry entering it from the other warps of the CTA (lane = combo x column)
-        float Wr = 0.f, Wi = 0.f;
-        {
-            const float p4r = cf.Pr[gm][2], p4i = cf.Pi[gm][2];
+        if (warp == 0) {
+            bar_sync_named(1, 256);  // all warp totals of this channel written
+            float totr = 0.f, toti = 0.f;
+#pragma unroll
             for (int s = 0; s < 8; ++s) {
                 const int w = gdir == 0 ? s : 7 - s;
-                if ((gdir == 0 && w >= warp) || (gdir == 1 && w <= warp)) continue;
-                const float4 tt = wt[par][w][gcol][gm];
+                float *slot = gdir == 0 ? &wt[par][w][gcol][gm].x : &wt[par][w][gcol][gm].z;
+                const float tr = slot[0], ti = slot[1];
+                slot[0] = totr;
+                slot[1] = toti;
                 float nr, ni;
-                cmul(nr, ni, p4r, p4i, Wr, Wi);
-                Wr = nr + (gdir == 0 ? tt.x : tt.z);
-                Wi = ni + (gdir == 0 ? tt.y : tt.w);
+                cmul(nr, ni, p4r, p4i, totr, toti);
+                totr = nr + tr;
+                toti = ni + ti;
             }
-            // CTA total: the last warp in scan order extends its incoming carry by its own total
-            if ((gdir == 0 && warp == 7) || (gdir == 1 && warp == 0)) {
-                const float4 tt = wt[par][warp][gcol][gm];
-                float tr = gdir == 0 ? tt.x : tt.z, ti = gdir == 0 ? tt.y : tt.w;
-                cmadd(tr, ti, p4r, p4i, Wr, Wi);
-                float *dst = gdir == 0 ? &ct[par][gcol][gm].x : &ct[par][gcol][gm].z;
-                dst[0] = tr;
-                dst[1] = ti;
-            }
+            // push the CTA total to the CTAs it enters: later ranks (causal), earlier ones (anticausal)
+            float2 *own = &inc[par][rank][gcol][gm][gdir];
+            for (int r = gdir == 0 ? rank + 1 : 0; r < (gdir == 0 ? CL : rank); ++r)
+                *cl.map_shared_rank(own, r) = make_float2(totr, toti);
+        } else {
+            bar_arrive_named(1, 256);
         }
-        // CTA totals of the cluster written.  ct and wt are double-buffered by channel
-        // parity: peers may read this channel's values until the next cluster barrier.
-        cl.sync();
+        cp_async_wait_1();  // this thread's part of tile k - 1
+        // releases the carries, the pushed CTA totals (warp 0) and tile k - 1
+        cluster_arrive_release();
+        float y[C];
+        {
+            // the tile is read again rather than kept in registers: its buffer
+            // is not refilled before the next cluster barrier
+            float xr[C];
+#pragma unroll
+            for (int j = 0; j < C; ++j) xr[j] = tl[j * 8];
+            half_local(xr, y, cf);
+            half_local(xr + 8, y + 8, cf);
+        }
+        cluster_wait_acquire();
+
+        // carry entering this warp from the rest of the column: lane (dir, pole, col)
+        float Wr, Wi;
+        {
+            const float4 w4 = wt[par][warp][gcol][gm];
+            Wr = gdir == 0 ? w4.x : w4.z;
+            Wi = gdir == 0 ? w4.y : w4.w;
+        }
         if (CL > 1) {
-            const float p32r = cf.Pr[gm][5], p32i = cf.Pi[gm][5];
-            float Xr = 0.f, Xi = 0.f;
             const int nsteps = gdir == 0 ? rank : CL - 1 - rank;
+            float Xr = 0.f, Xi = 0.f;
             for (int s = 0; s < nsteps; ++s) {
-                const int r = gdir == 0 ? s : CL - 1 - s;
-                const float4 tt = *cl.map_shared_rank(&ct[par][gcol][gm], r);
+                const float2 t = inc[par][gdir == 0 ? s : CL - 1 - s][gcol][gm][gdir];
                 float nr, ni;
                 cmul(nr, ni, p32r, p32i, Xr, Xi);
-                Xr = nr + (gdir == 0 ? tt.x : tt.z);
-                Xi = ni + (gdir == 0 ? tt.y : tt.w);
+                Xr = nr + t.x;
+                Xi = ni + t.y;
             }
             cmadd(Wr, Wi, Phr, Phi, Xr, Xi);
         }
-        // hand each thread the warp carries of its column: lane (combo, col) -> threads (col, any l4)
+        // the carries of this thread's column; states entering each half
+        float cBr[NP], cBi[NP], aAr[NP], aAi[NP];
 #pragma unroll
         for (int m = 0; m < NP; ++m) {
             const float wcr = __shfl_sync(0xffffffffu, Wr, (0 * 2 + m) * 8 + col);
@@ -1070,8 +1243,16 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
             const float wai = __shfl_sync(0xffffffffu, Wi, (1 * 2 + m) * 8 + col);
             cmadd(cr[m], ci[m], qcr[m], qci[m], wcr, wci);
             cmadd(ar[m], ai[m], qar[m], qai[m], war, wai);
+            // half B: causal p^8 c + cA; half A: anticausal aB + p^8 a
+            cBr[m] = hAr[m];
+            cBi[m] = hAi[m];
+            cmadd(cBr[m], cBi[m], cf.wr[m][8], cf.wi[m][8], cr[m], ci[m]);
+            aAr[m] = sBr[m];
+            aAi[m] = sBi[m];
+            cmadd(aAr[m], aAi[m], cf.wr[m][8], cf.wi[m][8], ar[m], ai[m]);
         }
-        chunk_correct<C>(y, cr, ci, ar, ai, cf);
+        half_correct(y, cr, ci, aAr, aAi, cf);
+        half_correct(y + 8, cBr, cBi, ar, ai, cf);
         cb.step(k, a.N, P.s2, y);
     }
     // no CTA may leave while a peer can still read its shared memory

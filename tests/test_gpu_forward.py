@@ -312,4 +312,4 @@ def test_engines_agree_with_oracle(bf, engine, shape, ss):
     bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, 30.0, o, ws.data_ptr(), need, s)
     assert bf.bf_gp_get_device_status(ws.data_ptr(), s) == 0
     ref, kap = oracle.gp_bf(img.astype(np.float64), ss, 30.0, 20, "iir", return_kappa=True)
-    check(y.cpu().numpy().astype(np.float64), ref, kappa=kap, min_gated=0.9999)
+    check(y.cpu().numpy().astype(np.float64), ref, kappa=kap, min_gated=0.999)
