@@ -230,7 +230,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(EXTRA_WORKLOADS), default=DEFAULT)
-    ap.add_argument("--engine", choices=["auto", "tensor", "cuda-core"], default="auto",
+    ap.add_argument("--engine", choices=["auto", "tensor", "cuda-core", "tcgen05"], default="auto",
                     help="recursive filter engine: auto (tensor-core rows, CUDA-core columns), tensor, cuda-core")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -270,7 +270,7 @@ def main():
     img = make_input(gen, H, W, rank)
     x = torch.from_numpy(img).cuda()
     y = torch.empty_like(x)
-    opts = bf.make_opts(N, spatial, engine={"auto": 0, "cuda-core": 1, "tensor": 2}[args.engine])
+    opts = bf.make_opts(N, spatial, engine={"auto": 0, "cuda-core": 1, "tensor": 2, "tcgen05": 3}[args.engine])
     ws_bytes = bf.bf_gp_workspace_size(1, H, W, ss, opts)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -356,9 +356,8 @@ def main():
     bytes_rows = (4 + 4 * K) * H * W       # read f, write K row-filtered planes
     bytes_cols = (4 * K + 8) * H * W       # read K planes + f, write y
     rtc = spatial == "iir" and args.engine in ("auto", "tensor")
-    ctc = spatial == "iir" and args.engine == "tensor"
     rk = ("row_tc" if rtc else "row_iir") if spatial == "iir" else "row_fir"
-    ck = ("col_tc" if ctc else "col_iir") if spatial == "iir" else "col_fir"
+    ck = {"tensor": "col_tc", "tcgen05": "col_tc5"}.get(args.engine, "col_iir") if spatial == "iir" else "col_fir"
     dominant = (rk, rows_ms, bytes_rows) if rows_ms >= cols_ms else (ck, cols_ms, bytes_cols)
     achieved = dominant[2] / (dominant[1] / 1e3) / 1e9
     traffic = committed_traffic(dominant[0], args.workload)

@@ -81,10 +81,12 @@ typedef struct {
     int centre;         /* bf_centre */
     int fir_halfwidth;  /* w for FIR; 0 selects ceil(3 sigma_s) (Sec. 1) */
     double t_c;         /* centre when centre == BF_CENTRE_GIVEN */
-    int engine;         /* recursive filter only: how the chunk-local recursions run.
-                           0 = auto (row pass on tensor cores, column pass on CUDA cores: the fastest
-                               pair measured on GB300), 1 = FP32 CUDA cores for both passes,
-                           2 = tensor cores (mma.sync, TF32 x 3 products) for both passes */
+    int engine;         /* recursive filter only: how the chunk-local products run.
+                           0 = auto (row pass on mma.sync tensor cores, column pass on CUDA cores: the
+                               fastest pair measured on GB300), 1 = FP32 CUDA cores for both passes,
+                           2 = mma.sync tensor cores (TF32 x 3 products) for both passes,
+                           3 = column pass on tcgen05 (TF32 x 3, accumulators in tensor memory),
+                               row pass on CUDA cores */
     int reserved[7];    /* must be zero */
 } bf_gp_opts;
 

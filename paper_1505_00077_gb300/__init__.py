@@ -133,6 +133,7 @@ def last_cuda_error() -> str:
 ENGINE_AUTO = 0        # tensor-core row pass, CUDA-core column pass
 ENGINE_CUDA_CORE = 1
 ENGINE_TENSOR = 2
+ENGINE_TCGEN05 = 3     # half-chunk products on tcgen05 where a pass has such a kernel
 
 
 def make_opts(order: int = 20, spatial="auto", t_c=None, fir_halfwidth: int = 0, engine: int = ENGINE_AUTO) -> bf_gp_opts:

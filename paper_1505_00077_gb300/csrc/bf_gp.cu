@@ -53,7 +53,7 @@ struct Plan {
     int nblk, rows_per_block;
     int T;                     // row threads per row
     int CL;                    // column cluster size (IIR)
-    int row_tc, col_tc;        // recursive filter: tensor-core row / column pass
+    int row_tc, col_tc;        // recursive filter: row / column pass engine (0 CUDA cores, 1 mma.sync, 2 tcgen05)
     int wpr;                   // tensor-core row pass: warps per row (512 samples each)
     size_t off_params, off_part, off_acc, off_planes, total;
 };
@@ -71,7 +71,7 @@ bf_status check_opts(const bf_gp_opts *o)
     if (o->centre < 0 || o->centre > 1) return BF_ERR_INVALID_ARG;
     if (o->fir_halfwidth < 0) return BF_ERR_INVALID_ARG;
     if (o->centre == BF_CENTRE_GIVEN && !std::isfinite(o->t_c)) return BF_ERR_INVALID_ARG;
-    if (o->engine < 0 || o->engine > 2) return BF_ERR_INVALID_ARG;
+    if (o->engine < 0 || o->engine > 3) return BF_ERR_INVALID_ARG;
     for (int i = 0; i < 7; ++i)
         if (o->reserved[i] != 0) return BF_ERR_INVALID_ARG;
     return BF_OK;
@@ -95,8 +95,8 @@ bf_status make_plan(int planes, int H, int W, float sigma_s, const bf_gp_opts *o
     if (p->T < 8) p->T = 8;
     if (p->T > 512) return BF_ERR_UNSUPPORTED;  // rows longer than 8192 samples
     p->CL = (H + COL_ROWS_PER_CTA - 1) / COL_ROWS_PER_CTA;
-    p->row_tc = o->engine == 0 || o->engine == 2;
-    p->col_tc = o->engine == 2;
+    p->row_tc = (o->engine == 0 || o->engine == 2) ? 1 : 0;
+    p->col_tc = o->engine == 2 ? 1 : (o->engine == 3 ? 2 : 0);
     p->wpr = next_pow2((W + 511) / 512);
     if (sp == BF_SPATIAL_IIR && p->row_tc && p->wpr > 16) return BF_ERR_UNSUPPORTED;
     if (sp == BF_SPATIAL_IIR && p->CL > COL_MAX_CLUSTER) return BF_ERR_UNSUPPORTED;  // columns longer than 4096
@@ -352,6 +352,46 @@ bf_status run_rows(const Call &c, int planes, float sigma_s)
     return BF_OK;
 }
 
+// B operand of the tcgen05 half-chunk products (FP64 -> FP32, then TF32 high
+// part with round-to-nearest-away and the FP32 remainder), in the K-major
+// core-matrix layout: (n, i) at float (n/8)*64 + (i/4)*32 + (n%8)*4 + i%4.
+//   n = 0..7: h(|n - i|);  n = 8 + 2m (+1): Re (Im) p_m^{7-i};  n = 12 + 2m (+1): Re (Im) p_m^i
+float tf32_rna(float v)
+{
+    uint32_t u;
+    std::memcpy(&u, &v, 4);
+    u = (u + 0x1000u) & 0xFFFFE000u;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
+
+void umma_mats(double sigma, UMat *um)
+{
+    const double a0 = 1.680, a1 = 3.735, b0 = 1.783, b1 = 1.723;
+    const double c0 = -0.6803, c1 = -0.2598, w0 = 0.6318, w1 = 1.997;
+    const std::complex<double> p[NP] = {std::exp(std::complex<double>(-b0, w0) / sigma),
+                                        std::exp(std::complex<double>(-b1, w1) / sigma)};
+    const std::complex<double> A[NP] = {{a0, -a1}, {c0, -c1}};
+    std::memset(um, 0, sizeof *um);
+    for (int n = 0; n < 16; ++n)
+        for (int i = 0; i < 8; ++i) {
+            double v;
+            if (n < 8) {
+                v = 0.0;
+                for (int m = 0; m < NP; ++m) v += (A[m] * std::pow(p[m], (double)std::abs(n - i))).real();
+            } else {
+                const int q = n - 8, m = (q >> 1) & 1, im = q & 1;
+                const std::complex<double> t = std::pow(p[m], (double)(q < 4 ? 7 - i : i));
+                v = im ? t.imag() : t.real();
+            }
+            const float f = (float)v;
+            const int o = (n / 8) * 64 + (i / 4) * 32 + (n % 8) * 4 + i % 4;
+            um->hi[o] = tf32_rna(f);
+            um->lo[o] = f - um->hi[o];
+        }
+}
+
 template <int MODE>
 bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
 {
@@ -370,6 +410,29 @@ bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
         if (st != BF_OK) return st;
     } else {
         const int strips = (W + 7) / 8;
+        if (c.p.col_tc == 2) {
+            IIRCoef cc;
+            deriche_coefs((double)sigma_s, COL_C, &cc);
+            UMat um;
+            umma_mats((double)sigma_s, &um);
+            BF_CUDA(cudaFuncSetAttribute(col_tc5<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC5_SMEM_BYTES));
+            cudaLaunchConfig_t cfg;
+            std::memset(&cfg, 0, sizeof cfg);
+            cfg.gridDim = dim3(strips * c.p.CL, planes, 1);
+            cfg.blockDim = dim3(256, 1, 1);
+            cfg.dynamicSmemBytes = TC5_SMEM_BYTES;
+            cfg.stream = c.s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = (unsigned)c.p.CL;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            BF_CUDA(cudaLaunchKernelEx(&cfg, col_tc5<MODE>, c.ca, cc, um));
+            BF_CUDA(cudaGetLastError());
+            return BF_OK;
+        }
         const bool tcore = c.p.col_tc != 0;
         IIRCoef cc;
         deriche_coefs((double)sigma_s, tcore ? TC_C : COL_C, &cc);

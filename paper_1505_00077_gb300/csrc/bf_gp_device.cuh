@@ -1026,6 +1026,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 constexpr int COL_TILE_BUFS = 4;  // channel tiles in flight in the recursive column pass
 
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
 // Column pass for the recursive filter.  A cluster of CL CTAs covers the
 // full height of an 8-column strip; CTA rank r owns rows [r*512, (r+1)*512).
 // Thread (warp w, lane l): column l%8 of the strip, chunk 4w + l/8 of 16
@@ -1067,17 +1069,21 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
     const bool filt = (P.mode == 0);
     const float *wsp = a.ws + (size_t)plane * a.K * a.H * a.Wp + strip * 8;
 
-    // tile copy: 512 rows x two 16-byte halves; thread copies 4 of them
+    // tile copy: 512 rows x two 16-byte halves; thread copies rows tid/2 + 128 i, i < 4
+    const size_t plane_stride = (size_t)a.H * a.Wp;
+    const int gr0 = rbase + (tid >> 1);
+    const int src0 = gr0 * a.Wp + (tid & 1) * 4;
+    const unsigned dst0 = (unsigned)__cvta_generic_to_shared(tiles + tile_off(tid >> 1) + (tid & 1) * 4);
     auto issue_tile = [&](int k) {
-        const float *src = wsp + (size_t)k * a.H * a.Wp;
-        float *dst = tiles + (k & (COL_TILE_BUFS - 1)) * COL_TILE_FLOATS;
+        const float *src = wsp + (size_t)k * plane_stride + src0;
+        const unsigned dst = dst0 + (unsigned)((k & (COL_TILE_BUFS - 1)) * COL_TILE_FLOATS * sizeof(float));
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const int idx = tid + i * 256;
-            const int r = idx >> 1, half = idx & 1;
-            const int gr = rbase + r;
-            const bool ok = filt && gr < a.H;
-            cp_async16(dst + tile_off(r) + half * 4, src + (size_t)(ok ? gr : 0) * a.Wp + half * 4, ok);
+            const bool ok = filt && gr0 + 128 * i < a.H;
+            // tile_off(r + 128) = tile_off(r) + 136 * 8
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst + i * 136 * 8 * 4),
+                         "l"(ok ? src + (size_t)i * 128 * a.Wp : wsp), "r"(ok ? 16 : 0)
+                         : "memory");
         }
     };
 
@@ -1102,6 +1108,7 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
     cpow_tab(Phr, Phi, cf, gm, 4 * (gdir == 0 ? warp : 7 - warp));
     const float p4r = gm == 0 ? cf.Pr[0][2] : cf.Pr[1][2], p4i = gm == 0 ? cf.Pi[0][2] : cf.Pi[1][2];
     const float p32r = gm == 0 ? cf.Pr[0][5] : cf.Pr[1][5], p32i = gm == 0 ? cf.Pi[0][5] : cf.Pi[1][5];
+    const int nsteps = gdir == 0 ? rank : CL - 1 - rank;  // CTAs whose totals enter this one
 
     issue_tile(a.K - 1);
     cp_async_commit();
@@ -1222,14 +1229,19 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
             Wi = gdir == 0 ? w4.y : w4.w;
         }
         if (CL > 1) {
-            const int nsteps = gdir == 0 ? rank : CL - 1 - rank;
+            // totals of the CTAs before (causal) / after (anticausal) this one, farthest first
+            const float2 *src = gdir == 0 ? &inc[par][0][gcol][gm][0] : &inc[par][CL - 1][gcol][gm][1];
+            const int step = gdir == 0 ? 8 * NP * 2 : -8 * NP * 2;
             float Xr = 0.f, Xi = 0.f;
-            for (int s = 0; s < nsteps; ++s) {
-                const float2 t = inc[par][gdir == 0 ? s : CL - 1 - s][gcol][gm][gdir];
-                float nr, ni;
-                cmul(nr, ni, p32r, p32i, Xr, Xi);
-                Xr = nr + t.x;
-                Xi = ni + t.y;
+#pragma unroll
+            for (int s = 0; s < 7; ++s) {
+                if (s < nsteps) {
+                    const float2 t = src[s * step];
+                    float nr, ni;
+                    cmul(nr, ni, p32r, p32i, Xr, Xi);
+                    Xr = nr + t.x;
+                    Xi = ni + t.y;
+                }
             }
             cmadd(Wr, Wi, Phr, Phi, Xr, Xi);
         }
@@ -1269,6 +1281,442 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
     } else if (__any_sync(0xffffffffu, nonpos) && lane == 0) {
         atomicOr(a.status, 0x1u);
     }
+}
+
+// ------------------------------------------------ tcgen05 (5th-generation tensor core) path
+//
+// The chunk-local work of the recursive filter on a half of 8 samples is a
+// product with a fixed 16 x 8 matrix B: outputs n = 0..7 are the in-half
+// responses sum_i h(|n - i|) x_i, outputs 8..15 the half's sums
+// (causal end state: p_m^{7-i}; anticausal start state: p_m^i; re, im of
+// poles 0 and 1).  One tcgen05.mma (kind::tf32, M = 128 halves, N = 16,
+// K = 8) per 128 halves; FP32 accuracy from three TF32 products
+// (A_hi B_hi + A_hi B_lo + A_lo B_hi, operands split with round-to-nearest).
+// A and B sit in shared memory in the K-major core-matrix layout without
+// swizzle: element (row r, k) at (r/8)*256 + (k/4)*128 + (r%8)*16 + (k%4)*4
+// bytes (core matrices of 8 rows x 16 bytes; 128 bytes between the two along
+// K, 256 bytes between row groups).  D (FP32) goes to tensor memory, row r in
+// lane r, output n in column n, and comes back with tcgen05.ld.
+
+struct UMat {
+    float hi[128], lo[128];  // B (16 x 8) in the core-matrix layout, TF32 high part and FP32 remainder
+};
+
+constexpr uint32_t UMMA_LBO = 128, UMMA_SBO = 256;
+// kind::tf32 instruction descriptor: D FP32 (bits 4-5 = 1), A and B TF32
+// (bits 7-9, 10-12 = 2), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t UMMA_IDESC_M128_N16 = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((UMMA_LBO >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((UMMA_SBO >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate)
+{
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                 "l"(a), "l"(b), "r"(UMMA_IDESC_M128_N16), "r"(accumulate)
+                 : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// Waits for the phase of parity `parity` of the mbarrier; gives up after
+// `limit` polls and returns false.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int limit)
+{
+    for (int it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(mbar), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+// Writes the 8 samples of one half as row r of the A operand (TF32 high parts
+// to ahi, FP32 remainders to alo).
+__device__ __forceinline__ void umma_put_row(float *ahi, float *alo, int r, const float *x)
+{
+    // Veltkamp split with 2^13 + 1: h keeps the leading 11 significant bits
+    // (round to nearest), so it is exact in TF32; l = x - h is exact in FP32.
+    float h[8], l[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float c = __fmul_rn(x[i], 8193.f);
+        h[i] = __fsub_rn(c, __fsub_rn(c, x[i]));
+        l[i] = __fsub_rn(x[i], h[i]);
+    }
+    const int o = (r >> 3) * 64 + (r & 7) * 4;
+    *reinterpret_cast<float4 *>(ahi + o) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4 *>(ahi + o + 32) = make_float4(h[4], h[5], h[6], h[7]);
+    *reinterpret_cast<float4 *>(alo + o) = make_float4(l[0], l[1], l[2], l[3]);
+    *reinterpret_cast<float4 *>(alo + o + 32) = make_float4(l[4], l[5], l[6], l[7]);
+}
+
+constexpr int TC5_TILE_BUFS = 3;
+constexpr int TC5_SMEM_BYTES = (TC5_TILE_BUFS * COL_TILE_FLOATS + 8 * 1024 + 256) * 4;
+constexpr int MBAR_LIMIT = 1 << 22;
+
+// Column pass for the recursive filter with the half-chunk products on
+// tcgen05.  Same cluster, thread and carry layout as col_iir; per channel k:
+//   a. wait for the MMAs of channel k (issued one step earlier), read the
+//      half sums from tensor memory;
+//   b. chunk sums, carries in the warp, warp 0 -> carries per warp and CTA
+//      totals pushed to the peers, cluster barrier (which also publishes
+//      tile k - 1);
+//   c. split tile k - 1 into the A operand and issue its MMAs (thread 0), so
+//      the tensor core works while this thread finishes channel k;
+//   d. carries from the other CTAs, in-half responses from tensor memory,
+//      out-of-half responses, Horner step.
+// Tiles are staged by cp.async two channels ahead (three buffers); D is
+// double-buffered in tensor memory by channel parity (128 columns).
+// Thread (warp w, lane l) owns rows 16 (4w + l/8) .. + 15 of column l % 8;
+// its half s is row 32 (w % 4) + l of MMA tile 2 (w / 4) + s (tensor-memory
+// columns 16 t .. 16 t + 15; a warp reads lanes 32 (w % 4) .. + 31).
+template <int MODE>
+__device__ __forceinline__ void col_tc5_body(const ColArgs &a, const IIRCoef &cf, const UMat &um, int strip, int plane)
+{
+    constexpr int C = 16;
+    extern __shared__ __align__(1024) float dsm[];
+    float *tiles = dsm;                                  // [3][COL_TILE_FLOATS]
+    float *sA = dsm + TC5_TILE_BUFS * COL_TILE_FLOATS;   // [4 tiles][hi, lo][1024]
+    float *sB = sA + 8 * 1024;                           // [hi, lo][128]
+    __shared__ float4 wt[2][8][8][NP];
+    __shared__ float2 inc[2][8][8][NP][2];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int col = lane & 7, l4 = lane >> 3;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int CL = (int)cl.num_blocks();
+    const int x = strip * 8 + col;
+    const int chunk_cta = warp * 4 + l4;
+    const int rbase = rank * COL_ROWS;
+    const int row0 = rbase + chunk_cta * C;
+    const PlaneParams &P = a.pp[plane];
+    const bool filt = (P.mode == 0);
+    const float *wsp = a.ws + (size_t)plane * a.K * a.H * a.Wp + strip * 8;
+    const uint32_t mb = smem_u32(&mbar);
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;\n" ::"r"(smem_u32(&tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    sB[tid] = tid < 128 ? um.hi[tid] : um.lo[tid - 128];
+
+    // tile copy: 512 rows x two 16-byte halves; thread copies rows tid/2 + 128 i, i < 4
+    const size_t plane_stride = (size_t)a.H * a.Wp;
+    const int gr0 = rbase + (tid >> 1);
+    const int src0 = gr0 * a.Wp + (tid & 1) * 4;
+    const unsigned dst0 = smem_u32(tiles + tile_off(tid >> 1) + (tid & 1) * 4);
+    auto issue_tile = [&](int k) {
+        const float *src = wsp + (size_t)k * plane_stride + src0;
+        const unsigned dst = dst0 + (unsigned)((k % TC5_TILE_BUFS) * COL_TILE_FLOATS * sizeof(float));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const bool ok = filt && gr0 + 128 * i < a.H;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst + i * 136 * 8 * 4),
+                         "l"(ok ? src + (size_t)i * 128 * a.Wp : wsp), "r"(ok ? 16 : 0)
+                         : "memory");
+        }
+    };
+    // A rows of this thread's two halves, and the tensor-memory address of its rows
+    const int arow = 32 * (warp & 3) + lane;
+    const int atile = 2 * (warp >> 2);
+    auto split_tile = [&](int k) {
+        const float *tl = tiles + (k % TC5_TILE_BUFS) * COL_TILE_FLOATS + tile_off(chunk_cta * C) + col;
+        float xv[C];
+#pragma unroll
+        for (int j = 0; j < C; ++j) xv[j] = tl[j * 8];
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+            umma_put_row(sA + (atile + s) * 2048, sA + (atile + s) * 2048 + 1024, arow, xv + 8 * s);
+        fence_proxy_async();
+    };
+    auto issue_mma = [&](uint32_t tmem) {
+        const uint64_t bhi = umma_desc(smem_u32(sB)), blo = umma_desc(smem_u32(sB + 128));
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const uint64_t ahi = umma_desc(smem_u32(sA + t * 2048)), alo = umma_desc(smem_u32(sA + t * 2048 + 1024));
+            const uint32_t d = tmem + 16 * t;
+            umma_tf32(d, ahi, bhi, 0);
+            umma_tf32(d, ahi, blo, 1);
+            umma_tf32(d, alo, bhi, 1);
+        }
+        umma_commit(mb);
+    };
+
+    Combine<C, MODE> cb;
+    const float *fcol = a.f + (size_t)plane * a.H * a.pitch;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        const int r = row0 + j;
+        const bool in = (r < a.H) && (x < a.W);
+        const float fv = in ? __ldg(fcol + (size_t)r * a.pitch + x) : 0.f;
+        cb.init((fv - P.tc) * P.invR, j);
+    }
+    float qcr[NP], qci[NP], qar[NP], qai[NP];  // p^{16 l4}, p^{16 (3 - l4)}
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+        cpow_tab(qcr[m], qci[m], cf, m, l4);
+        cpow_tab(qar[m], qai[m], cf, m, 3 - l4);
+    }
+    const int gcol = lane & 7, gq = lane >> 3, gm = gq & 1, gdir = gq >> 1;
+    float Phr, Phi;
+    cpow_tab(Phr, Phi, cf, gm, 4 * (gdir == 0 ? warp : 7 - warp));
+    const float p4r = gm == 0 ? cf.Pr[0][2] : cf.Pr[1][2], p4i = gm == 0 ? cf.Pi[0][2] : cf.Pi[1][2];
+    const float p32r = gm == 0 ? cf.Pr[0][5] : cf.Pr[1][5], p32i = gm == 0 ? cf.Pi[0][5] : cf.Pi[1][5];
+    const int nsteps = gdir == 0 ? rank : CL - 1 - rank;
+
+    issue_tile(a.K - 1);
+    cp_async_commit();
+    if (a.K >= 2) issue_tile(a.K - 2);
+    cp_async_commit();
+    cp_async_wait_1();
+    __syncthreads();  // tile K-1 visible
+    split_tile(a.K - 1);
+    tc_fence_before();
+    __syncthreads();  // A of channel K-1, B, the mbarrier and the tensor-memory address visible
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 16 * atile;
+    if (tid == 0) issue_mma(tmem + 64 * ((a.K - 1) & 1));
+    uint32_t phase = 0;
+    bool timed_out = false;
+#pragma unroll 1
+    for (int k = a.K - 1; k >= 0; --k) {
+        // a. half sums of channel k
+        if (!mbar_wait(mb, phase, MBAR_LIMIT)) timed_out = true;
+        phase ^= 1u;
+        tc_fence_after();
+        const uint32_t tk = trow + 64 * (k & 1);  // D of channel k: tensor-memory columns 64 (k & 1) ..
+        float d0[8], d1[8];                       // half sums of the two halves (outputs 8..15)
+        tmem_ld8(tk + 8, d0);
+        tmem_ld8(tk + 16 + 8, d1);
+        tmem_wait_ld();
+        if (k >= 2) issue_tile(k - 2);
+        cp_async_commit();
+
+        // b. chunk sums: causal end p^8 cA + cB, anticausal start aA + p^8 aB; carries in the warp
+        float er[NP], ei[NP], sr[NP], si[NP];
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+            er[m] = d1[2 * m];
+            ei[m] = d1[1 + 2 * m];
+            cmadd(er[m], ei[m], cf.wr[m][8], cf.wi[m][8], d0[2 * m], d0[1 + 2 * m]);
+            sr[m] = d0[4 + 2 * m];
+            si[m] = d0[5 + 2 * m];
+            cmadd(sr[m], si[m], cf.wr[m][8], cf.wi[m][8], d1[4 + 2 * m], d1[5 + 2 * m]);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int dd = 1 << i;
+#pragma unroll
+            for (int m = 0; m < NP; ++m) {
+                const float ur = __shfl_up_sync(0xffffffffu, er[m], 8 * dd);
+                const float ui = __shfl_up_sync(0xffffffffu, ei[m], 8 * dd);
+                const float vr = __shfl_down_sync(0xffffffffu, sr[m], 8 * dd);
+                const float vi = __shfl_down_sync(0xffffffffu, si[m], 8 * dd);
+                if (l4 >= dd) cmadd(er[m], ei[m], cf.Pr[m][i], cf.Pi[m][i], ur, ui);
+                if (l4 + dd < 4) cmadd(sr[m], si[m], cf.Pr[m][i], cf.Pi[m][i], vr, vi);
+            }
+        }
+        float cr[NP], ci[NP], ar[NP], ai[NP];
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+            const float ur = __shfl_up_sync(0xffffffffu, er[m], 8);
+            const float ui = __shfl_up_sync(0xffffffffu, ei[m], 8);
+            const float vr = __shfl_down_sync(0xffffffffu, sr[m], 8);
+            const float vi = __shfl_down_sync(0xffffffffu, si[m], 8);
+            cr[m] = l4 > 0 ? ur : 0.f;
+            ci[m] = l4 > 0 ? ui : 0.f;
+            ar[m] = l4 < 3 ? vr : 0.f;
+            ai[m] = l4 < 3 ? vi : 0.f;
+        }
+        const int par = k & 1;
+        if (l4 == 3) {
+#pragma unroll
+            for (int m = 0; m < NP; ++m) {
+                wt[par][warp][col][m].x = er[m];
+                wt[par][warp][col][m].y = ei[m];
+            }
+        }
+        if (l4 == 0) {
+#pragma unroll
+            for (int m = 0; m < NP; ++m) {
+                wt[par][warp][col][m].z = sr[m];
+                wt[par][warp][col][m].w = si[m];
+            }
+        }
+        if (warp == 0) {
+            bar_sync_named(1, 256);  // all warp totals of this channel written
+            float totr = 0.f, toti = 0.f;
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                const int w = gdir == 0 ? s : 7 - s;
+                float *slot = gdir == 0 ? &wt[par][w][gcol][gm].x : &wt[par][w][gcol][gm].z;
+                const float tr = slot[0], ti = slot[1];
+                slot[0] = totr;
+                slot[1] = toti;
+                float nr, ni;
+                cmul(nr, ni, p4r, p4i, totr, toti);
+                totr = nr + tr;
+                toti = ni + ti;
+            }
+            float2 *own = &inc[par][rank][gcol][gm][gdir];
+            for (int r = gdir == 0 ? rank + 1 : 0; r < (gdir == 0 ? CL : rank); ++r)
+                *cl.map_shared_rank(own, r) = make_float2(totr, toti);
+        } else {
+            bar_arrive_named(1, 256);
+        }
+
+        cp_async_wait_1();  // this thread's part of tile k - 1
+        // releases the carries, the pushed CTA totals (warp 0) and tile k - 1
+        cluster_arrive_release();
+        cluster_wait_acquire();
+
+        // c. MMAs of channel k - 1, running while this thread finishes channel k
+        if (k >= 1) {
+            split_tile(k - 1);
+            if (warp == 0) {
+                // every row of A written and fenced; D of channel k + 1 (same columns) read by every thread
+                bar_sync_named(3, 256);
+                if (lane == 0) {
+                    tc_fence_after();
+                    issue_mma(tmem + 64 * ((k - 1) & 1));
+                }
+                __syncwarp();
+            } else {
+                bar_arrive_named(3, 256);
+            }
+        }
+
+        // d. carries and the out-of-half responses
+        float Wr, Wi;
+        {
+            const float4 w4 = wt[par][warp][gcol][gm];
+            Wr = gdir == 0 ? w4.x : w4.z;
+            Wi = gdir == 0 ? w4.y : w4.w;
+        }
+        if (CL > 1) {
+            const float2 *src = gdir == 0 ? &inc[par][0][gcol][gm][0] : &inc[par][CL - 1][gcol][gm][1];
+            const int step = gdir == 0 ? 8 * NP * 2 : -8 * NP * 2;
+            float Xr = 0.f, Xi = 0.f;
+#pragma unroll
+            for (int s = 0; s < 7; ++s) {
+                if (s < nsteps) {
+                    const float2 t = src[s * step];
+                    float nr, ni;
+                    cmul(nr, ni, p32r, p32i, Xr, Xi);
+                    Xr = nr + t.x;
+                    Xi = ni + t.y;
+                }
+            }
+            cmadd(Wr, Wi, Phr, Phi, Xr, Xi);
+        }
+        float cBr[NP], cBi[NP], aAr[NP], aAi[NP];
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+            const float wcr = __shfl_sync(0xffffffffu, Wr, (0 * 2 + m) * 8 + col);
+            const float wci = __shfl_sync(0xffffffffu, Wi, (0 * 2 + m) * 8 + col);
+            const float war = __shfl_sync(0xffffffffu, Wr, (1 * 2 + m) * 8 + col);
+            const float wai = __shfl_sync(0xffffffffu, Wi, (1 * 2 + m) * 8 + col);
+            cmadd(cr[m], ci[m], qcr[m], qci[m], wcr, wci);
+            cmadd(ar[m], ai[m], qar[m], qai[m], war, wai);
+            cBr[m] = d0[2 * m];
+            cBi[m] = d0[1 + 2 * m];
+            cmadd(cBr[m], cBi[m], cf.wr[m][8], cf.wi[m][8], cr[m], ci[m]);
+            aAr[m] = d1[4 + 2 * m];
+            aAi[m] = d1[5 + 2 * m];
+            cmadd(aAr[m], aAi[m], cf.wr[m][8], cf.wi[m][8], ar[m], ai[m]);
+        }
+        float y[C];
+        {
+            float l0[8], l1[8];  // in-half responses (outputs 0..7)
+            tmem_ld8(tk, l0);
+            tmem_ld8(tk + 16, l1);
+            tmem_wait_ld();
+            tc_fence_before();  // D of channel k is read before this thread reaches barrier 3 again
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                y[j] = l0[j];
+                y[8 + j] = l1[j];
+            }
+        }
+        half_correct(y, cr, ci, aAr, aAi, cf);
+        half_correct(y + 8, cBr, cBi, ar, ai, cf);
+        cb.step(k, a.N, P.s2, y);
+    }
+    // no CTA may leave while a peer can still write to or read its shared memory
+    tc_fence_before();
+    cl.sync();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(tmem) : "memory");
+    }
+    if (timed_out) atomicOr(a.status, 0x8u);
+    bool nonpos = false;
+    AdjSums sums = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        const int r = row0 + j;
+        if (r < a.H && x < a.W) finish_pixel<C, MODE>(a, P, plane, r, x, cb, j, nonpos, sums);
+    }
+    if (MODE == MODE_ADJ) {
+        flush_sums(a, plane, sums);
+    } else if (__any_sync(0xffffffffu, nonpos) && lane == 0) {
+        atomicOr(a.status, 0x1u);
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256, MODE == MODE_SAVE ? 1 : 2) col_tc5(ColArgs a, IIRCoef cf, UMat um)
+{
+    col_tc5_body<MODE>(a, cf, um, blockIdx.x / (int)cg::this_cluster().num_blocks(), blockIdx.y);
 }
 
 template <int C, int MODE>

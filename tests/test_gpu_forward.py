@@ -297,7 +297,7 @@ def test_repeat_calls_are_deterministic(bf):
     assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("engine", [0, 1, 2])
+@pytest.mark.parametrize("engine", [0, 1, 2, 3])
 @pytest.mark.parametrize("shape,ss", [((300, 260), 6.0), ((1030, 600), 12.0), ((2049, 75), 20.0)])
 def test_engines_agree_with_oracle(bf, engine, shape, ss):
     """Recursive filter on tensor cores (rows and/or columns) and on CUDA cores."""
