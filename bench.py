@@ -35,6 +35,8 @@ EXTRA_WORKLOADS = {
     "gpf-batched-64img-3ch-N20-iir": "config4",
     # differentiation: 16 x 512^2, sigma_s 5, sigma_r 25, N 20, forward + hand-written backward
     "gpf-16x512x512-ss5-sr25-N20-fwdbwd": "config5",
+    # runtime against sigma_s with the recursive filter: 1024^2, sigma_s in {2, 5, 10, 20}, sigma_r 30, N 20
+    "gpf-1024x1024-sr30-N20-iir-sigma-sweep": "config2-sweep",
 }
 
 WORKLOADS = {
@@ -408,7 +410,7 @@ def _clock_wrap(local, fn):
 
 
 def run_extra(args, rank, world, local):
-    """Batched (config 4) and forward + backward (config 5) workloads, one GPU."""
+    """Batched (config 4), forward + backward (config 5) and sigma_s-sweep (config 2) workloads, one GPU."""
     import numpy as np
     import torch
 
@@ -433,6 +435,41 @@ def run_extra(args, rank, world, local):
         e1.record(stream)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / steps
+
+    if kind == "config2-sweep":
+        img = synthetic.config2_image()
+        x = torch.from_numpy(img).cuda()
+        y = torch.empty_like(x)
+        H, W = x.shape
+        opts = bf.make_opts(20, "iir")
+        per = {}
+        steps = max(1, args.steps)
+        clocks = None
+        for ss in (2.0, 5.0, 10.0, 20.0):
+            need = bf.bf_gp_workspace_size(1, H, W, ss, opts)
+            ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+
+            def fwd():
+                bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, 30.0, opts, ws.data_ptr(), need, sp)
+            for _ in range(args.warmup):
+                fwd()
+            if ss == 10.0:
+                ms, clocks = _clock_wrap(local, lambda: timed(fwd, steps))
+            else:
+                ms = timed(fwd, steps)
+            per[f"{ss:g}"] = ms
+        mean_ms = sum(per.values()) / len(per)
+        line = {"metric": "Mpixel/s", "value": H * W / (mean_ms / 1e3) / 1e6, "unit": "Mpixel/s", "n_gpus": 1,
+                "steps": steps, "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": args.workload, "H": H, "W": W, "sigma_s": list(per), "sigma_r": 30.0,
+                           "order": 20, "spatial": "iir", "how": "bf_gp_forward per sigma_s, mean time"},
+                "ms_per_sigma_s": per, "max_over_min": max(per.values()) / min(per.values()),
+                "gpu_launches": 4 * steps * len(per)}
+        if clocks:
+            line["clocks"] = clocks
+        print(json.dumps(line), flush=True)
+        return 0
 
     if kind == "config4":
         specs = synthetic.config4_specs()
