@@ -1842,17 +1842,16 @@ struct TCMat {
     float cor[8][8];  // [e][n]
 };
 
-__device__ __forceinline__ unsigned tf32_rna(float x)
-{
-    unsigned r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
+// x = hi + lo with hi holding the leading 11 significant bits of x (exact in
+// TF32; Veltkamp split with 2^13 + 1, four FP32 operations on the FMA pipe)
+// and lo the exact FP32 remainder, of which the tensor core uses the leading
+// 11 bits: |x - hi - lo_tf32| <= 2^-22 |x|.
 __device__ __forceinline__ void tf32_split(float x, unsigned &hi, unsigned &lo)
 {
-    hi = tf32_rna(x);
-    lo = tf32_rna(x - __uint_as_float(hi));
+    const float c = __fmul_rn(x, 8193.f);
+    const float h = __fsub_rn(c, __fsub_rn(c, x));
+    hi = __float_as_uint(h);
+    lo = __float_as_uint(__fsub_rn(x, h));
 }
 
 __device__ __forceinline__ void mma_tf32(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
