@@ -243,6 +243,20 @@ bf_status bf_gp_forward_noalloc(const float *f, float *y, int planes, int H, int
  *     (no copies, no host synchronisation), so it can be captured into a
  *     CUDA graph and replayed.  ws must be the uploaded workspace.
  *   bf_gp_batched_plan_destroy: frees the plan.
+ *
+ * Per-plane centre and scale, for choosing each plane's order before the
+ * plan that filters (the error of Eq. (5) on [-R, R] depends on R / sigma_r,
+ * and R is known only from the data):
+ *   bf_gp_batched_plan_stats_workspace: device bytes bf_gp_batched_plane_stats
+ *     needs (tables and statistics only, no channel planes).
+ *   bf_gp_batched_plane_stats: runs the plan's statistics pass (Algorithm 1
+ *     step 1 and the scale R = max |f - t_c|) in ws, waits for it and writes
+ *     t_c[i] and R[i] for each of the plan's n planes (host arrays, n
+ *     entries, either may be NULL).  It uploads its own copy of the tables
+ *     into ws; ws needs no other preparation and is not usable by
+ *     bf_gp_batched afterwards unless uploaded again.  Pair it with
+ *     bf_gp_order_for_tol(sigma_r, R[i], eps) and a second plan created with
+ *     those orders.
  */
 typedef struct {
     const float *f;  /* device input plane */
@@ -259,6 +273,9 @@ bf_status bf_gp_batched_plan_workspace(const bf_gp_plan *plan, size_t *bytes);
 bf_status bf_gp_batched_plan_upload(bf_gp_plan *plan, void *ws, size_t ws_bytes, void *stream);
 bf_status bf_gp_batched(const bf_gp_plan *plan, void *ws, size_t ws_bytes, void *stream);
 void bf_gp_batched_plan_destroy(bf_gp_plan *plan);
+bf_status bf_gp_batched_plan_stats_workspace(const bf_gp_plan *plan, size_t *bytes);
+bf_status bf_gp_batched_plane_stats(const bf_gp_plan *plan, void *ws, size_t ws_bytes, void *stream, double *t_c,
+                                    double *R);
 
 /*
  * Read the device status word written by the last call that used `ws`
@@ -282,6 +299,14 @@ bf_status bf_gp_get_plane_stats(const void *ws, int plane, void *stream, double 
  * the interval.  Returns -1 if no N <= 62 reaches eps.  Host only.
  */
 int bf_gp_order_for_tol(double sigma_r, double R, double eps);
+
+/* Largest even order N <= 62 for which a plane with scale R = max |f - t_c|
+ * keeps every term beta_k Phi_k of the scaled channels inside FP32 (the
+ * statistics pass raises BF_DEV_RANGE beyond it; this host copy of that test
+ * keeps one bit of margin), or -1 if none does.  The Taylor terms of Eq. (4)
+ * grow like (s^2)^n / n! with s^2 = (R / sigma_r)^2, so large R / sigma_r
+ * bounds the order FP32 can carry. */
+int bf_gp_order_fp32_limit(double sigma_s, double sigma_r, double R);
 
 #ifdef __cplusplus
 }

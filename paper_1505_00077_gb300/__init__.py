@@ -96,6 +96,8 @@ def _load():
         "bf_gp_batched_plan_upload": (c_int, [c_void_p, c_void_p, c_size_t, c_void_p]),
         "bf_gp_batched": (c_int, [c_void_p, c_void_p, c_size_t, c_void_p]),
         "bf_gp_batched_plan_destroy": (None, [c_void_p]),
+        "bf_gp_batched_plan_stats_workspace": (c_int, [c_void_p, P(c_size_t)]),
+        "bf_gp_batched_plane_stats": (c_int, [c_void_p, c_void_p, c_size_t, c_void_p, P(c_double), P(c_double)]),
         "bf_gp_forward_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_float, c_float,
                                           P(bf_gp_opts), c_void_p]),
         "bf_gp_host_workspace_size": (c_int, [c_int, c_int, c_int, c_float, P(bf_gp_opts), P(c_size_t)]),
@@ -104,6 +106,7 @@ def _load():
         "bf_gp_get_device_status": (c_int, [c_void_p, c_void_p, P(ctypes.c_uint32)]),
         "bf_gp_get_plane_stats": (c_int, [c_void_p, c_int, c_void_p, P(c_double), P(c_double)]),
         "bf_gp_order_for_tol": (c_int, [c_double, c_double, c_double]),
+        "bf_gp_order_fp32_limit": (c_int, [c_double, c_double, c_double]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -118,8 +121,10 @@ def exported_symbols():
     return ["bf_gp_default_opts", "bf_status_string", "bf_gp_last_cuda_error", "bf_gp_version",
             "bf_gp_workspace_size", "bf_gp_forward", "bf_gp_phase_stats", "bf_gp_phase_rows", "bf_gp_phase_cols",
             "bf_gp_forward_train", "bf_gp_backward", "bf_gp_batched_plan_create", "bf_gp_batched_plan_workspace",
-            "bf_gp_batched_plan_upload", "bf_gp_batched", "bf_gp_batched_plan_destroy", "bf_gp_forward_noalloc", "bf_gp_host_workspace_size", "bf_gp_forward_host",
-            "bf_gp_get_device_status", "bf_gp_get_plane_stats", "bf_gp_order_for_tol"]
+            "bf_gp_batched_plan_upload", "bf_gp_batched", "bf_gp_batched_plan_destroy",
+            "bf_gp_batched_plan_stats_workspace", "bf_gp_batched_plane_stats", "bf_gp_forward_noalloc",
+            "bf_gp_host_workspace_size", "bf_gp_forward_host",
+            "bf_gp_get_device_status", "bf_gp_get_plane_stats", "bf_gp_order_for_tol", "bf_gp_order_fp32_limit"]
 
 
 def status_string(status: int) -> str:
@@ -238,17 +243,42 @@ def bf_gp_batched(plan, ws_ptr, ws_bytes, stream=0) -> None:
     _check(_load().bf_gp_batched(_vp(plan), _vp(ws_ptr), int(ws_bytes), _vp(stream)), "bf_gp_batched")
 
 
+def bf_gp_batched_plan_stats_workspace(plan) -> int:
+    n = ctypes.c_size_t(0)
+    _check(_load().bf_gp_batched_plan_stats_workspace(_vp(plan), ctypes.byref(n)), "bf_gp_batched_plan_stats_workspace")
+    return int(n.value)
+
+
+def bf_gp_batched_plane_stats(plan, n, ws_ptr, ws_bytes, stream=0):
+    """(t_c, R) per plane of the plan, from its statistics pass (synchronises)."""
+    tc = (ctypes.c_double * n)()
+    R = (ctypes.c_double * n)()
+    _check(_load().bf_gp_batched_plane_stats(_vp(plan), _vp(ws_ptr), int(ws_bytes), _vp(stream), tc, R),
+           "bf_gp_batched_plane_stats")
+    return list(tc), list(R)
+
+
 def bf_gp_batched_plan_destroy(plan) -> None:
     _load().bf_gp_batched_plan_destroy(_vp(plan))
+
+
+MAX_ORDER = 62  # K = N + 2 <= 64 channels
 
 
 class BatchedFilter:
     """Owns a batched plan and its workspace for a fixed list of (input, output,
     sigma_s, sigma_r, order) planes (float32 CUDA tensors [H, W]).  run()
-    enqueues the four batched launches on the current stream; it is safe to
-    capture in a CUDA graph."""
+    enqueues the batched launches on the current stream; it is safe to
+    capture in a CUDA graph.
 
-    def __init__(self, planes, order_default=20, t_c=None):
+    With tol, each plane gets its own order: the smallest even N whose
+    Gauss-polynomial kernel error on [-R, R] is at most tol
+    (bf_gp_order_for_tol), with R = max |f - t_c| measured on the device by
+    the plan's statistics pass, capped at max_order and at the largest order
+    whose terms FP32 can hold (bf_gp_order_fp32_limit).  The chosen orders are
+    in self.orders."""
+
+    def __init__(self, planes, order_default=20, t_c=None, tol=None, max_order=MAX_ORDER):
         import torch
         self._keep = []
         spec = []
@@ -259,11 +289,34 @@ class BatchedFilter:
             assert y.shape == x.shape and y.is_contiguous()
             self._keep.append((x, y))
             spec.append((x.data_ptr(), y.data_ptr(), x.shape[0], x.shape[1], x.shape[1], float(ss), float(sr), int(order)))
-        self.plan = bf_gp_batched_plan_create(spec, make_opts(order_default, "iir", t_c))
+        opts = make_opts(order_default, "iir", t_c)
+        if tol is not None:
+            spec = self._adaptive_orders(spec, opts, float(tol), int(max_order))
+        self.orders = [p[7] for p in spec]
+        self.plan = bf_gp_batched_plan_create(spec, opts)
         self.ws_bytes = bf_gp_batched_plan_workspace(self.plan)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
         bf_gp_batched_plan_upload(self.plan, self.ws.data_ptr(), self.ws_bytes,
                                   torch.cuda.current_stream().cuda_stream)
+
+    @staticmethod
+    def _adaptive_orders(spec, opts, tol, max_order):
+        import torch
+        probe = bf_gp_batched_plan_create([p[:7] + (0,) for p in spec], opts)
+        try:
+            need = bf_gp_batched_plan_stats_workspace(probe)
+            ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+            _, R = bf_gp_batched_plane_stats(probe, len(spec), ws.data_ptr(), need,
+                                             torch.cuda.current_stream().cuda_stream)
+        finally:
+            bf_gp_batched_plan_destroy(probe)
+        out = []
+        for p, r in zip(spec, R):
+            n = bf_gp_order_for_tol(p[6], r, tol)
+            n = max_order if n < 0 else min(n, max_order)
+            lim = bf_gp_order_fp32_limit(p[5], p[6], r)
+            out.append(p[:7] + (max(0, min(n, lim)),))
+        return out
 
     def run(self, stream=None):
         import torch
@@ -327,6 +380,10 @@ def bf_gp_get_plane_stats(ws_ptr, plane, stream=0):
 
 def bf_gp_order_for_tol(sigma_r, R, eps) -> int:
     return int(_load().bf_gp_order_for_tol(float(sigma_r), float(R), float(eps)))
+
+
+def bf_gp_order_fp32_limit(sigma_s, sigma_r, R) -> int:
+    return int(_load().bf_gp_order_fp32_limit(float(sigma_s), float(sigma_r), float(R)))
 
 
 def bf_gp_version() -> int:

@@ -717,6 +717,30 @@ int bf_gp_order_for_tol(double sigma_r, double R, double eps)
     return -1;
 }
 
+int bf_gp_order_fp32_limit(double sigma_s, double sigma_r, double R)
+{
+    if (!(sigma_s > 0.0) || !(sigma_r > 0.0) || !(R >= 0.0)) return -1;
+    // the statistics pass's range test (flag BF_DEV_RANGE), one bit tighter
+    const double s2 = std::isinf(sigma_r) ? 0.0 : (R / sigma_r) * (R / sigma_r);
+    const float s2f = (float)s2;
+    if (0.3606738f * s2f > 119.f) return -1;
+    const float e0 = std::fmax(0.f, std::ceil(0.7213475f * s2f - 120.f));
+    const float gain = 2.f * std::log2(2.6f * (float)sigma_s + 2.f);
+    int best = -1;
+    float top = 0.f;  // max over the channels so far of log2(beta_k max_u E u^k); channel 0 gives 0
+    double beta = 1.0;
+    for (int k = 1; k <= KMAX - 1; ++k) {
+        if (k >= 2) beta *= s2 * (1.0 / (double)k);
+        if (beta > 0.0) {
+            const float u2 = std::fmin(1.f, (float)k / s2f);
+            top = std::fmax(top, std::log2((float)beta) - 0.7213475f * s2f * u2 + 0.5f * (float)k * std::log2(u2));
+        }
+        const int N = k - 1, K = k + 1;  // channels 0..k
+        if (N % 2 == 0 && e0 + top + gain + 2.f * std::log2((float)K) <= 123.f) best = N;
+    }
+    return best;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------- batched
@@ -836,12 +860,13 @@ bf_status bf_gp_batched_plan_workspace(const bf_gp_plan *plan, size_t *bytes)
     return BF_OK;
 }
 
-bf_status bf_gp_batched_plan_upload(bf_gp_plan *plan, void *ws, size_t ws_bytes, void *stream)
+namespace {
+
+// Copies the plan's tables (descriptors with this workspace's plane pointers,
+// filter coefficients, prefix sums) into ws and waits for the copy.
+bf_status upload_tables(const bf_gp_plan *plan, char *wsb, cudaStream_t s)
 {
-    if (!plan || !ws) return BF_ERR_INVALID_ARG;
-    if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < plan->total) return BF_ERR_WORKSPACE;
     const int n = plan->n;
-    char *wsb = static_cast<char *>(ws);
     std::vector<char> img(plan->tables_bytes);
     std::vector<BatchPlane> bp = plan->bp;
     for (int i = 0; i < n; ++i) bp[i].ws = reinterpret_cast<float *>(wsb + plan->off_planes + plan->plane_off[i]);
@@ -857,21 +882,14 @@ bf_status bf_gp_batched_plan_upload(bf_gp_plan *plan, void *ws, size_t ws_bytes,
     std::memcpy(img.data() + o, plan->pre_cols.data(), sizeof(int) * (n + 1));
     o += sizeof(int) * (n + 1);
     std::memcpy(img.data() + o, plan->col_order.data(), sizeof(int) * n);
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     BF_CUDA(cudaMemcpyAsync(wsb + plan->off_tables, img.data(), plan->tables_bytes, cudaMemcpyHostToDevice, s));
     BF_CUDA(cudaStreamSynchronize(s));
-    const size_t smem = sizeof(float) * COL_TILE_BUFS * COL_TILE_FLOATS;
-    BF_CUDA(cudaFuncSetAttribute(batched_col_iir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    plan->uploaded_ws = ws;
     return BF_OK;
 }
 
-bf_status bf_gp_batched(const bf_gp_plan *plan, void *ws, size_t ws_bytes, void *stream)
+BatchArgs batch_args(const bf_gp_plan *plan, char *wsb)
 {
-    if (!plan || !ws) return BF_ERR_INVALID_ARG;
-    if (ws != plan->uploaded_ws || ws_bytes < plan->total) return BF_ERR_WORKSPACE;
     const int n = plan->n;
-    char *wsb = static_cast<char *>(ws);
     const char *tb = wsb + plan->off_tables;
     BatchArgs b;
     b.bp = reinterpret_cast<const BatchPlane *>(tb);
@@ -889,6 +907,61 @@ bf_status bf_gp_batched(const bf_gp_plan *plan, void *ws, size_t ws_bytes, void 
     b.n = n;
     b.centre_given = plan->centre_given;
     b.tc_given = plan->tc_given;
+    return b;
+}
+
+}  // namespace
+
+bf_status bf_gp_batched_plan_upload(bf_gp_plan *plan, void *ws, size_t ws_bytes, void *stream)
+{
+    if (!plan || !ws) return BF_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < plan->total) return BF_ERR_WORKSPACE;
+    bf_status st = upload_tables(plan, static_cast<char *>(ws), reinterpret_cast<cudaStream_t>(stream));
+    if (st != BF_OK) return st;
+    const size_t smem = sizeof(float) * COL_TILE_BUFS * COL_TILE_FLOATS;
+    BF_CUDA(cudaFuncSetAttribute(batched_col_iir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    plan->uploaded_ws = ws;
+    return BF_OK;
+}
+
+bf_status bf_gp_batched_plan_stats_workspace(const bf_gp_plan *plan, size_t *bytes)
+{
+    if (!plan || !bytes) return BF_ERR_INVALID_ARG;
+    *bytes = plan->off_planes;
+    return BF_OK;
+}
+
+bf_status bf_gp_batched_plane_stats(const bf_gp_plan *plan, void *ws, size_t ws_bytes, void *stream, double *t_c,
+                                    double *R)
+{
+    if (!plan || !ws) return BF_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < plan->off_planes) return BF_ERR_WORKSPACE;
+    char *wsb = static_cast<char *>(ws);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    bf_status st = upload_tables(plan, wsb, s);
+    if (st != BF_OK) return st;
+    BF_CUDA(cudaMemsetAsync(wsb, 0, sizeof(uint32_t), s));
+    BatchArgs b = batch_args(plan, wsb);
+    batched_stats_partial<<<plan->total_stats, 256, 0, s>>>(b);
+    batched_stats_finalize<<<plan->n, 256, 0, s>>>(b);
+    BF_CUDA(cudaGetLastError());
+    std::vector<PlaneParams> q(plan->n);
+    BF_CUDA(cudaMemcpyAsync(q.data(), wsb + plan->off_params, sizeof(PlaneParams) * (size_t)plan->n,
+                            cudaMemcpyDeviceToHost, s));
+    BF_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < plan->n; ++i) {
+        if (t_c) t_c[i] = q[i].tc_d;
+        if (R) R[i] = q[i].R_d;
+    }
+    return BF_OK;
+}
+
+bf_status bf_gp_batched(const bf_gp_plan *plan, void *ws, size_t ws_bytes, void *stream)
+{
+    if (!plan || !ws) return BF_ERR_INVALID_ARG;
+    if (ws != plan->uploaded_ws || ws_bytes < plan->total) return BF_ERR_WORKSPACE;
+    const int n = plan->n;
+    BatchArgs b = batch_args(plan, static_cast<char *>(ws));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     batched_stats_partial<<<plan->total_stats, 256, 0, s>>>(b);
     batched_stats_finalize<<<n, 256, 0, s>>>(b);

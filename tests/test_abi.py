@@ -116,3 +116,16 @@ def test_order_rule():
     assert bfgp.bf_gp_order_for_tol(50.0, 127.5, 1e-3) == 16
     assert bfgp.bf_gp_order_for_tol(1e9, 127.5, 1e-3) == 0
     assert bfgp.bf_gp_order_for_tol(5.0, 127.5, 1e-3) == -1
+
+
+def test_fp32_order_limit():
+    """The host copy of the range test: wide range kernels carry any order,
+    the limit falls as (R / sigma_r)^2 grows, and none is possible where
+    exp(-s^2 / 2) leaves FP32 altogether."""
+    import paper_1505_00077_gb300 as bf
+    assert bf.bf_gp_order_fp32_limit(3.0, 100.0, 127.5) == 62
+    lims = [bf.bf_gp_order_fp32_limit(3.0, sr, 127.5) for sr in (60.0, 30.0, 20.0, 15.0, 12.0, 10.0)]
+    assert all(a >= b for a, b in zip(lims, lims[1:]))
+    assert lims[0] == 62 and lims[-1] < 62
+    assert bf.bf_gp_order_fp32_limit(3.0, 0.1, 127.5) == -1
+    assert bf.bf_gp_order_fp32_limit(3.0, -1.0, 127.5) == -1

@@ -89,3 +89,45 @@ def test_batched_rejects_bad_plans(bf):
         bf.bf_gp_batched_plan_create([(x.data_ptr(), x.data_ptr(), 16, 16, 8, 2.0, 30.0, 20)])  # pitch < W
     with pytest.raises(bf.BFError):
         bf.bf_gp_batched_plan_create([(x.data_ptr(), x.data_ptr(), 16, 5000, 5000, 2.0, 30.0, 20)])  # W > 4096
+
+
+def test_adaptive_order_per_plane(bf):
+    """tol given: each plane's order is the smallest even N whose kernel error on
+    [-R, R] is <= tol, with R = max |f - mean f| measured on the device, capped
+    at 62 and at the FP32 range limit; no plane raises BF_DEV_RANGE, every
+    plane matches the FP64 oracle run with its own order, and a plane that
+    gets more than N = 20 is closer to Eq. (1) than N = 20."""
+    specs = [(300, 280, 3.0, 70.0), (256, 512, 2.0, 45.0), (640, 200, 8.0, 30.0), (200, 200, 4.0, 20.0),
+             (129, 333, 1.5, 100.0), (512, 96, 6.0, 15.0)]
+    planes, imgs = [], []
+    for i, (H, W, ss, sr) in enumerate(specs):
+        img = synthetic.make_image(H, W, 8, 10.0, 0.0, synthetic.seed_for(4, 500 + i))
+        imgs.append(img)
+        x = torch.from_numpy(img).cuda()
+        planes.append((x, torch.empty_like(x), ss, sr))
+    tol = 1e-3
+    bfilt = bf.BatchedFilter(planes, tol=tol)
+    f64 = [im.astype(np.float64) for im in imgs]
+    expect = []
+    for im, (H, W, ss, sr) in zip(f64, specs):
+        R = float(np.max(np.abs(im - oracle.mean(im))))
+        n = bf.bf_gp_order_for_tol(sr, R, tol)
+        n = 62 if n < 0 else min(n, 62)
+        expect.append(max(0, min(n, bf.bf_gp_order_fp32_limit(ss, sr, R))))
+    assert bfilt.orders == expect
+    assert len(set(expect)) >= 4 and max(expect) > 20  # uneven channel counts in one batch
+    bfilt.run()
+    torch.cuda.synchronize()
+    assert (bfilt.status() & ~bf.BF_DEV_NONPOS_Q) == 0
+    for i, ((x, y, ss, sr), im, N) in enumerate(zip(planes, f64, bfilt.orders)):
+        ref, kap = oracle.gp_bf(im, ss, sr, N, "iir", return_kappa=True)
+        gated = np.isfinite(ref) & (kap <= 8e-4 * 2 ** 24 / 16)
+        assert gated.mean() >= 0.999, i
+        assert np.abs(y.cpu().numpy()[gated] - ref[gated]).max() <= 1e-3, i
+    i = int(np.argmax(expect))
+    ref20 = oracle.gp_bf(f64[i], specs[i][2], specs[i][3], 20, "iir")
+    exact = oracle.direct_bf(f64[i], specs[i][2], specs[i][3])
+    out = planes[i][1].cpu().numpy().astype(np.float64)
+    good = np.isfinite(ref20) & np.isfinite(out)
+    assert good.mean() > 0.99
+    assert np.mean((out[good] - exact[good]) ** 2) < np.mean((ref20[good] - exact[good]) ** 2)
