@@ -44,6 +44,7 @@ WORKLOADS = {
     "gpf-4096x4096-ss10-sr20-N20-iir": (4096, 4096, 10.0, 20.0, 20, "iir", "config3"),
     "gpf-256x256-ss3-sr30-N20-fir": (256, 256, 3.0, 30.0, 20, "fir", "config1"),
     "gpf-2048x2048-ss10-sr20-N20-iir": (2048, 2048, 10.0, 20.0, 20, "iir", "config3-crop"),
+    "gpf-1024x1024-ss2-sr30-N20-fir": (1024, 1024, 2.0, 30.0, 20, "fir", "config2"),
 }
 DEFAULT = "gpf-4096x4096-ss10-sr20-N20-iir"
 FALLBACK_HBM_GBS = 6800.0
@@ -57,6 +58,10 @@ def make_input(gen, H, W, rank):
         return synthetic.make_image(H, W, 512, 15.0, 0.0, synthetic.seed_for(3, rank))
     if gen == "config3-crop":
         return synthetic.make_image(H, W, 128, 15.0, 0.0, synthetic.seed_for(3, 100 + rank))
+    if gen == "config2":
+        if rank == 0:
+            return synthetic.config2_image()
+        return synthetic.make_image(H, W, 64, 10.0, 60.0, synthetic.seed_for(2, rank))
     if gen == "config1":
         if rank == 0:
             return synthetic.config1_image()
@@ -294,40 +299,72 @@ def main():
     sp = stream.cuda_stream
     K = N + 2
 
-    def step(ev=None):
-        if ev is not None:
-            ev[0].record(stream)
-        bf.bf_gp_phase_stats(x.data_ptr(), 1, H, W, W, ss, sr, opts, ws.data_ptr(), ws_bytes, sp)
-        if ev is not None:
-            ev[1].record(stream)
-        bf.bf_gp_phase_rows(x.data_ptr(), 1, H, W, W, ss, sr, opts, ws.data_ptr(), ws_bytes, sp)
-        if ev is not None:
-            ev[2].record(stream)
-        bf.bf_gp_phase_cols(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, sr, opts, ws.data_ptr(), ws_bytes, sp)
-        if ev is not None:
-            ev[3].record(stream)
+    fused = spatial == "fir" and not opts.fir_two_pass
+    working_set = (12 * H * W) if fused else (ws_bytes + 8 * H * W)
+    small = working_set < 2 * 129e6
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda") if small else None
+
+    def step():
+        # one forward pass through the public entry point: stats, then rows + columns
+        # (recursive filter or two-pass FIR) or the fused FIR tile kernel
+        bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, sr, opts, ws.data_ptr(), ws_bytes, sp)
 
     for _ in range(args.warmup):
         step()
     status = bf.bf_gp_get_device_status(ws.data_ptr(), sp)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     sampler = ClockSampler(local)
     sampler.start()
     barrier()
     sampler.mark("t0")
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    for i in range(args.steps):
-        step(evs[i])
-    t_end.record(stream)
-    barrier()
-    sampler.mark("t1")
-    clocks = sampler.stop()
-    total_ms = t_start.elapsed_time(t_end)
-    stats_ms = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
-    rows_ms = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps
-    cols_ms = sum(e[2].elapsed_time(e[3]) for e in evs) / args.steps
+    if small:
+        # working set below the 129 MB L2: each step is timed alone, with the L2
+        # flushed (a 512 MB buffer overwritten) between steps, outside the events
+        pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                 for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            pairs[i][0].record(stream)
+            step()
+            pairs[i][1].record(stream)
+        barrier()
+        sampler.mark("t1")
+        clocks = sampler.stop()
+        total_ms = sum(a.elapsed_time(b) for a, b in pairs)
+    else:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            step()
+        t_end.record(stream)
+        barrier()
+        sampler.mark("t1")
+        clocks = sampler.stop()
+        total_ms = t_start.elapsed_time(t_end)
+
+    # per-kernel times (CUDA events on the launching stream), after the timed region
+    n_ph = max(1, min(args.steps, 50))
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(n_ph)]
+    for i in range(n_ph):
+        e = evs[i]
+        e[0].record(stream)
+        bf.bf_gp_phase_stats(x.data_ptr(), 1, H, W, W, ss, sr, opts, ws.data_ptr(), ws_bytes, sp)
+        e[1].record(stream)
+        if fused:
+            step()
+            e[2].record(stream)
+        else:
+            bf.bf_gp_phase_rows(x.data_ptr(), 1, H, W, W, ss, sr, opts, ws.data_ptr(), ws_bytes, sp)
+            e[2].record(stream)
+            bf.bf_gp_phase_cols(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, sr, opts, ws.data_ptr(), ws_bytes, sp)
+        e[3].record(stream)
+    torch.cuda.synchronize()
+    stats_ms = sum(e[0].elapsed_time(e[1]) for e in evs) / n_ph
+    rows_ms = sum(e[1].elapsed_time(e[2]) for e in evs) / n_ph
+    cols_ms = sum(e[2].elapsed_time(e[3]) for e in evs) / n_ph
+    if fused:  # e[1] -> e[2] is a whole forward (stats + fused kernel)
+        fused_ms = max(rows_ms - stats_ms, 1e-6)
+        rows_ms = cols_ms = 0.0
     total_ms = reduce_max(total_ms, dist, "cuda")
     ms_per_step = total_ms / args.steps
     value = job_throughput(H * W, world, args.steps, total_ms)
@@ -368,9 +405,26 @@ def main():
     rtc = spatial == "iir" and args.engine in ("auto", "tensor")
     rk = ("row_tc" if rtc else "row_iir") if spatial == "iir" else "row_fir"
     ck = {"tensor": "col_tc", "tcgen05": "col_tc5"}.get(args.engine, "col_iir") if spatial == "iir" else "col_fir"
-    dominant = (rk, rows_ms, bytes_rows) if rows_ms >= cols_ms else (ck, cols_ms, bytes_cols)
-    achieved = dominant[2] / (dominant[1] / 1e3) / 1e9
-    traffic = committed_traffic(dominant[0], args.workload)
+    if fused:
+        # FP32 FMA per pixel of the separable filter (row + column, 2w + 1 taps each) and the combine,
+        # against the FP32 FMA rate of the SMs (152 SMs x 128 lanes x the measured maximum SM clock)
+        w_half = int(math.ceil(3 * ss - 1e-12))  # W = ceil(3 sigma_s), the default window
+        fma_px = K * (2 * (2 * w_half + 1) + 3)
+        alu_peak = 152 * 128 * float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]) * 1e6 \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 152 * 128 * 2.07e9
+        achieved = fma_px * H * W / (fused_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "kernel": "fir_fused", "achieved": achieved, "peak": alu_peak / 1e12,
+                    "unit": "T FMA/s", "frac": achieved / (alu_peak / 1e12),
+                    "peak_kind": "derived (152 SMs x 128 FP32 lanes x sm_max_mhz of MEASURED_PEAKS.json)",
+                    "algorithmic_fma_per_launch": fma_px * H * W, "kernel_ms": fused_ms,
+                    "traffic": committed_traffic("fir_fused", args.workload)}
+    else:
+        dominant = (rk, rows_ms, bytes_rows) if rows_ms >= cols_ms else (ck, cols_ms, bytes_cols)
+        achieved = dominant[2] / (dominant[1] / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": dominant[0], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_kind": f"{peak_kind} (hbm_gbs)",
+                    "algorithmic_bytes_per_launch": dominant[2], "kernel_ms": dominant[1],
+                    "traffic": committed_traffic(dominant[0], args.workload)}
     line = {
         "metric": "Mpixel/s", "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -378,16 +432,18 @@ def main():
         "config": {"workload": args.workload, "H": H, "W": W, "planes_per_gpu": 1, "sigma_s": ss, "sigma_r": sr,
                    "order": N, "channels": K, "spatial": spatial, "engine": args.engine,
                    "parallelism": f"replicas x{world}",
-                   "l2": f"working set {(ws_bytes + 8 * H * W) / 1e9:.2f} GB per step > 129 MB L2 (no flush needed)"},
-        "phases_ms": {"stats": stats_ms, "rows": rows_ms, "cols": cols_ms},
-        "roofline": {"bound": "hbm", "kernel": dominant[0], "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": f"{peak_kind} (hbm_gbs)",
-                     "algorithmic_bytes_per_launch": dominant[2], "traffic": traffic},
-        "gpu_launches": 4 * args.steps,
+                   "l2": (f"working set {working_set / 1e6:.1f} MB < 2 x 129 MB L2: each step timed alone, "
+                          "L2 flushed (512 MB written) between steps" if small else
+                          f"working set {working_set / 1e9:.2f} GB per step > 129 MB L2 (no flush needed)")},
+        "phases_ms": ({"stats": stats_ms, "fir_fused": fused_ms} if fused else
+                      {"stats": stats_ms, "rows": rows_ms, "cols": cols_ms}),
+        "roofline": roofline,
+        "gpu_launches": (3 if fused else 4) * args.steps,
         "device_status": status,
     }
-    line["step_roofline"] = {"algorithmic_bytes_per_step": (8 * K + 16) * H * W,
-                             "frac": (8 * K + 16) * H * W / (ms_per_step / 1e3) / 1e9 / peak}
+    step_bytes = (12 if fused else 8 * K + 16) * H * W
+    line["step_roofline"] = {"bound": "hbm", "algorithmic_bytes_per_step": step_bytes,
+                             "frac": step_bytes / (ms_per_step / 1e3) / 1e9 / peak}
     if clocks is not None:
         line["clocks"] = clocks
     if e2e is not None:

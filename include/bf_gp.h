@@ -87,7 +87,11 @@ typedef struct {
                            2 = mma.sync tensor cores (TF32 x 3 products) for both passes,
                            3 = column pass on tcgen05 (TF32 x 3, accumulators in tensor memory),
                                row pass on CUDA cores */
-    int reserved[7];    /* must be zero */
+    int fir_two_pass;   /* FIR forward only: 0 = one fused kernel per 32 x 32 tile (channels, row and
+                           column filters and combine in shared memory, no row-filtered planes in
+                           HBM), 1 = the separate row and column passes (what bf_gp_phase_rows /
+                           bf_gp_phase_cols always run) */
+    int reserved[6];    /* must be zero */
 } bf_gp_opts;
 
 /* Fill *opts with the defaults: N = 20, AUTO spatial operator, mean centre. */

@@ -51,7 +51,7 @@ class BFError(RuntimeError):
 class bf_gp_opts(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("spatial", ctypes.c_int), ("centre", ctypes.c_int),
                 ("fir_halfwidth", ctypes.c_int), ("t_c", ctypes.c_double), ("engine", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("fir_two_pass", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 class bf_gp_plane(ctypes.Structure):
@@ -141,11 +141,13 @@ ENGINE_TENSOR = 2
 ENGINE_TCGEN05 = 3     # half-chunk products on tcgen05 where a pass has such a kernel
 
 
-def make_opts(order: int = 20, spatial="auto", t_c=None, fir_halfwidth: int = 0, engine: int = ENGINE_AUTO) -> bf_gp_opts:
+def make_opts(order: int = 20, spatial="auto", t_c=None, fir_halfwidth: int = 0, engine: int = ENGINE_AUTO,
+              fir_two_pass: bool = False) -> bf_gp_opts:
     o = bf_gp_opts()
     _load().bf_gp_default_opts(ctypes.byref(o))
     o.order = int(order)
     o.engine = int(engine)
+    o.fir_two_pass = int(bool(fir_two_pass))
     o.spatial = _SPATIAL[spatial] if isinstance(spatial, str) else int(spatial)
     o.fir_halfwidth = int(fir_halfwidth)
     if t_c is not None:

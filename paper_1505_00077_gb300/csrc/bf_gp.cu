@@ -72,7 +72,8 @@ bf_status check_opts(const bf_gp_opts *o)
     if (o->fir_halfwidth < 0) return BF_ERR_INVALID_ARG;
     if (o->centre == BF_CENTRE_GIVEN && !std::isfinite(o->t_c)) return BF_ERR_INVALID_ARG;
     if (o->engine < 0 || o->engine > 3) return BF_ERR_INVALID_ARG;
-    for (int i = 0; i < 7; ++i)
+    if (o->fir_two_pass < 0 || o->fir_two_pass > 1) return BF_ERR_INVALID_ARG;
+    for (int i = 0; i < 6; ++i)
         if (o->reserved[i] != 0) return BF_ERR_INVALID_ARG;
     return BF_OK;
 }
@@ -392,6 +393,23 @@ void umma_mats(double sigma, UMat *um)
         }
 }
 
+bf_status run_fir_fused(const Call &c, int planes, float sigma_s)
+{
+    FIRCoef g;
+    fir_coefs((double)sigma_s, c.p.w, &g);
+    dim3 grid((c.ca.W + 31) / 32, (c.ca.H + 31) / 32, planes);
+    switch (c.p.w) {
+#define BF_CASE(WW) \
+    case WW: fir_fused<WW><<<grid, 256, 0, c.s>>>(c.ca, g); break;
+        BF_CASE(1) BF_CASE(2) BF_CASE(3) BF_CASE(4) BF_CASE(5) BF_CASE(6)
+        BF_CASE(7) BF_CASE(8) BF_CASE(9) BF_CASE(10) BF_CASE(11) BF_CASE(12)
+#undef BF_CASE
+    default: return BF_ERR_UNSUPPORTED;
+    }
+    BF_CUDA(cudaGetLastError());
+    return BF_OK;
+}
+
 template <int MODE>
 bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
 {
@@ -517,7 +535,9 @@ bf_status bf_gp_forward(const float *f, float *y, int planes, int H, int W, int 
     bf_status st = prepare(f, y, planes, H, W, pitch, sigma_s, sigma_r, opts, ws, ws_bytes, stream, true, &c);
     if (st != BF_OK) return st;
     st = run_stats(c, planes, H, W, pitch, sigma_s, sigma_r, opts, 0);
-    if (st == BF_OK) st = run_rows<MODE_FWD>(c, planes, sigma_s);
+    if (st != BF_OK) return st;
+    if (c.p.spatial == BF_SPATIAL_FIR && opts->fir_two_pass == 0) return run_fir_fused(c, planes, sigma_s);
+    st = run_rows<MODE_FWD>(c, planes, sigma_s);
     if (st == BF_OK) st = run_cols<MODE_FWD>(c, planes, W, sigma_s);
     return st;
 }

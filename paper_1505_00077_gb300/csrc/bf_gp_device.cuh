@@ -1787,6 +1787,130 @@ __global__ void __launch_bounds__(256) col_fir(ColArgs a, FIRCoef g)
     }
 }
 
+// Fused forward for the FIR operator (Eq. (8) with the window of Eq. (1)):
+// one CTA computes a 32 x 32 output tile for all K
+// channels without writing the row-filtered planes.  Per channel k (ascending):
+//   1. Phi_k = 2^e0 E u^k on the tile plus a WH halo (zero outside the image),
+//      by one multiply per sample from the previous channel, into shared memory;
+//   2. row filter of the (32 + 2 WH) rows x 32 columns (threads: row x strip of 8);
+//   3. column filter of the 32 x 32 outputs (threads: column x 4 rows), times beta_k,
+//      accumulated with running powers of u:
+//        p += k u^{k-1} Psi_k,  q += u^{k-1} Psi_k (1 <= k <= N),  Psi_0 kept;
+//   y = t_c + R p / (Psi_0 + s^2 u q).
+// The row-filtered tile is double-buffered by channel parity, so each channel
+// costs two barriers.  grid (ceil(W/32), ceil(H/32), planes), block 256.
+template <int WH>
+__global__ void __launch_bounds__(256) fir_fused(ColArgs a, FIRCoef g)
+{
+    constexpr int T = 32;
+    constexpr int RS = T + 2 * WH;              // side of the tile plus halo
+    constexpr int NR = (RS * RS + 255) / 256;   // halo samples per thread
+    __shared__ float phi[RS][RS + 1];
+    __shared__ float rf[2][RS][T + 1];
+    const int tid = threadIdx.x;
+    const int plane = blockIdx.z;
+    const int x0 = blockIdx.x * T, y0 = blockIdx.y * T;
+    const PlaneParams &P = a.pp[plane];
+    const float *fp = a.f + (size_t)plane * a.H * a.pitch;
+    // output pixels of this thread: column c, rows r0 .. r0 + 3
+    const int c = tid & 31, r0 = (tid >> 5) * 4;
+    const int xo = x0 + c;
+    if (P.mode != 0) {  // constant plane or non-finite input: the result is the input
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int yo = y0 + r0 + j;
+            if (yo < a.H && xo < a.W) {
+                const size_t pix = ((size_t)plane * a.H + yo) * a.pitch + xo;
+                a.y[pix] = __ldg(a.f + pix);
+            }
+        }
+        return;
+    }
+    float hu[NR], hv[NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        const int idx = tid + 256 * i;
+        const int rr = idx / RS, cc = idx % RS;
+        const int gy = y0 - WH + rr, gx = x0 - WH + cc;
+        const bool in = idx < RS * RS && gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
+        const float uu = in ? (__ldg(fp + (size_t)gy * a.pitch + gx) - P.tc) * P.invR : 0.f;
+        hu[i] = uu;
+        hv[i] = in ? envelope(P, uu) : 0.f;
+    }
+    float ou[4], pacc[4], qacc[4], psi0[4], w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int yo = y0 + r0 + j;
+        const bool in = yo < a.H && xo < a.W;
+        ou[j] = in ? (__ldg(fp + (size_t)yo * a.pitch + xo) - P.tc) * P.invR : 0.f;
+        pacc[j] = qacc[j] = psi0[j] = 0.f;
+        w[j] = 1.f;
+    }
+    // row-filter work item: row rr, columns 8 s .. 8 s + 7 (RS x 4 items)
+    const bool row_item = tid < 4 * RS;
+    const int rr_row = tid >> 2, cs = (tid & 3) * 8;
+#pragma unroll 1
+    for (int k = 0; k < a.K; ++k) {
+        const int buf = k & 1;
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            const int idx = tid + 256 * i;
+            if (k > 0) hv[i] *= hu[i];
+            if (idx < RS * RS) phi[idx / RS][idx % RS] = hv[i];
+        }
+        __syncthreads();  // Phi_k on the halo tile; every thread is past the row filter of channel k - 1
+        if (row_item) {
+            float win[8 + 2 * WH];
+#pragma unroll
+            for (int j = 0; j < 8 + 2 * WH; ++j) win[j] = phi[rr_row][cs + j];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                float acc = g.g[0] * win[j + WH];
+#pragma unroll
+                for (int dd = 1; dd <= WH; ++dd) acc = fmaf(g.g[dd], win[j + WH - dd] + win[j + WH + dd], acc);
+                rf[buf][rr_row][cs + j] = acc;
+            }
+        }
+        __syncthreads();  // row-filtered tile of channel k
+        float win[4 + 2 * WH];
+#pragma unroll
+        for (int j = 0; j < 4 + 2 * WH; ++j) win[j] = rf[buf][r0 + j][c];
+        const float beta = P.beta[k];
+        const float mk = (float)k;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float acc = g.g[0] * win[j + WH];
+#pragma unroll
+            for (int dd = 1; dd <= WH; ++dd) acc = fmaf(g.g[dd], win[j + WH - dd] + win[j + WH + dd], acc);
+            const float psi = acc * beta;
+            if (k == 0) {
+                psi0[j] = psi;
+            } else {
+                pacc[j] = fmaf(mk * w[j], psi, pacc[j]);
+                if (k <= a.N) qacc[j] = fmaf(w[j], psi, qacc[j]);
+                w[j] *= ou[j];
+            }
+        }
+    }
+    bool nonpos = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int yo = y0 + r0 + j;
+        if (yo < a.H && xo < a.W) {
+            const float Q = fmaf(P.s2 * ou[j], qacc[j], psi0[j]);
+            float out;
+            if (!(Q > 0.f)) {
+                nonpos = true;
+                out = __int_as_float(0x7fc00000);
+            } else {
+                out = fmaf(P.R, __fdiv_rn(pacc[j], Q), P.tc);
+            }
+            a.y[((size_t)plane * a.H + yo) * a.pitch + xo] = out;
+        }
+    }
+    if (__any_sync(0xffffffffu, nonpos) && (tid & 31) == 0) atomicOr(a.status, 0x1u);
+}
+
 // Backward finish: dL/df = dL/dh + (sum dL/dy - sum dL/dh) / |I| when the
 // centre is the plane mean (Algorithm 1 step 1), and dL/dsigma_r per plane
 // = dL/d(s^2) * d(s^2)/dsigma_r = dL/d(s^2) * (-2 s^2 / sigma_r).

@@ -313,3 +313,45 @@ def test_engines_agree_with_oracle(bf, engine, shape, ss):
     assert bf.bf_gp_get_device_status(ws.data_ptr(), s) == 0
     ref, kap = oracle.gp_bf(img.astype(np.float64), ss, 30.0, 20, "iir", return_kappa=True)
     check(y.cpu().numpy().astype(np.float64), ref, kappa=kap, min_gated=0.999)
+
+
+# ---------------------------------------------------------------- fused FIR forward
+
+def _forward(bf, img, ss, sr, N, two_pass):
+    x = torch.from_numpy(np.ascontiguousarray(img, dtype=np.float32)).cuda()
+    H, W = x.shape
+    o = bf.make_opts(N, "fir", fir_two_pass=two_pass)
+    need = bf.bf_gp_workspace_size(1, H, W, ss, o)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    y = torch.full_like(x, float("nan"))
+    s = torch.cuda.current_stream().cuda_stream
+    bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, sr, o, ws.data_ptr(), need, s)
+    return y.cpu().numpy().astype(np.float64), bf.bf_gp_get_device_status(ws.data_ptr(), s)
+
+
+@pytest.mark.parametrize("shape,ss", [((1, 1), 1.0), ((7, 300), 0.4), ((33, 65), 2.0), ((256, 256), 3.0),
+                                      ((100, 1030), 3.7), ((300, 47), 4.0)])
+def test_fir_fused_matches_two_pass_and_oracle(bf, shape, ss):
+    """One fused kernel per 32 x 32 tile (channels, both filters and the combine in
+    shared memory) against the two-pass form and the oracle: tiles straddling
+    every image edge, windows from W = 2 to 12."""
+    H, W = shape
+    img = synthetic.make_image(H, W, 6, 10.0, 20.0, synthetic.seed_for(9, 7000 + H + W))
+    fused, b1 = _forward(bf, img, ss, 30.0, 20, False)
+    two, b2 = _forward(bf, img, ss, 30.0, 20, True)
+    assert b1 == 0 and b2 == 0
+    assert np.abs(fused - two).max() <= 2e-4
+    ref, kap = oracle.gp_bf(img.astype(np.float64), ss, 30.0, 20, "fir", return_kappa=True)
+    check(fused, ref, kappa=kap, min_gated=0.999)
+
+
+def test_fir_fused_copy_planes(bf):
+    """Constant plane -> itself; non-finite input -> passed through and flagged."""
+    img = np.full((40, 50), 77.25, np.float32)
+    out, bits = _forward(bf, img, 2.0, 30.0, 20, False)
+    assert bits == 0 and np.array_equal(out, img.astype(np.float64))
+    img2 = synthetic.make_image(40, 50, 4, 10.0, 0.0, synthetic.seed_for(9, 7100))
+    img2[3, 4] = np.nan
+    out2, bits2 = _forward(bf, img2, 2.0, 30.0, 20, False)
+    assert bits2 & bf.BF_DEV_NONFINITE_IN
+    assert np.array_equal(np.isnan(out2), np.isnan(img2)) and np.array_equal(out2[~np.isnan(out2)], img2[~np.isnan(img2)].astype(np.float64))
