@@ -101,9 +101,11 @@ bf_status make_plan(int planes, int H, int W, float sigma_s, const bf_gp_opts *o
     p->wpr = next_pow2((W + 511) / 512);
     if (sp == BF_SPATIAL_IIR && p->row_tc && p->wpr > 16) return BF_ERR_UNSUPPORTED;
     if (sp == BF_SPATIAL_IIR && p->CL > COL_MAX_CLUSTER) return BF_ERR_UNSUPPORTED;  // columns longer than 4096
-    // stats partials: ~16K pixels per block
     const long long px = (long long)H * W;
-    int nblk = (int)std::min<long long>((long long)H, std::max<long long>(1, (px + 16383) / 16384));
+    // stats partials: at most 1024 blocks, at least 2048 pixels each (small images still spread
+    // over many SMs; every block's loads are independent)
+    const long long per_blk = std::max<long long>(2048, (px + 1023) / 1024);
+    int nblk = (int)std::min<long long>((long long)H, std::max<long long>(1, (px + per_blk - 1) / per_blk));
     p->rows_per_block = (H + nblk - 1) / nblk;
     p->nblk = (H + p->rows_per_block - 1) / p->rows_per_block;
     size_t off = HDR_BYTES;

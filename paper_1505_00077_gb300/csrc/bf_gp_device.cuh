@@ -254,48 +254,56 @@ __device__ __forceinline__ void stats_partial_body(const float *__restrict__ f, 
     double sum = 0.0;
     int bad = 0;
     const bool vec = ((pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(f) & 15) == 0);
-    for (int r = r0; r < r1; ++r) {
-        const float *row = f + ((size_t)plane * H + r) * pitch;
-        float s = 0.f;  // FP32 partial over this thread's share of one row
-        if (vec) {
-            const int W4 = W >> 2;
-            for (int i = threadIdx.x; i < W4; i += blockDim.x) {
-                const float4 v = __ldg(reinterpret_cast<const float4 *>(row) + i);
-                const float a[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    if (!isfinite(a[t])) {
-                        ++bad;
-                        continue;
-                    }
-                    s += a[t];
-                    mn = fminf(mn, a[t]);
-                    mx = fmaxf(mx, a[t]);
-                }
-            }
-            for (int x = (W4 << 2) + threadIdx.x; x < W; x += blockDim.x) {
-                const float a = __ldg(row + x);
-                if (!isfinite(a)) {
-                    ++bad;
-                    continue;
-                }
-                s += a;
-                mn = fminf(mn, a);
-                mx = fmaxf(mx, a);
-            }
-        } else {
-            for (int x = threadIdx.x; x < W; x += blockDim.x) {
-                const float a = __ldg(row + x);
-                if (!isfinite(a)) {
-                    ++bad;
-                    continue;
-                }
-                s += a;
-                mn = fminf(mn, a);
-                mx = fmaxf(mx, a);
-            }
+    const float *base = f + (size_t)plane * H * pitch;
+    const int nrow = r1 > r0 ? r1 - r0 : 0;
+    // the band as independent (row, 4-column group) items: no load waits on another
+    const int W4 = vec ? (W >> 2) : 0;
+    const int items = nrow * W4;
+    float acc = 0.f;
+    int nacc = 0;
+    // item i = (row r0 + r, group c4), stepped without a division per item
+    int r = r0 + (W4 > 0 ? (int)threadIdx.x / W4 : 0), c4 = W4 > 0 ? (int)threadIdx.x % W4 : 0;
+    const int dr = W4 > 0 ? (int)blockDim.x / W4 : 0, dc = W4 > 0 ? (int)blockDim.x % W4 : 0;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < items; i += blockDim.x) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(base + (size_t)r * pitch) + c4);
+        r += dr;
+        c4 += dc;
+        if (c4 >= W4) {
+            c4 -= W4;
+            ++r;
         }
-        sum += (double)s;
+        const float a[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (!isfinite(a[t])) {
+                ++bad;
+                continue;
+            }
+            acc += a[t];
+            mn = fminf(mn, a[t]);
+            mx = fmaxf(mx, a[t]);
+        }
+        if (++nacc == 4) {  // FP32 over at most 16 values, then FP64
+            sum += (double)acc;
+            acc = 0.f;
+            nacc = 0;
+        }
+    }
+    sum += (double)acc;
+    // the columns the 4-groups leave (all of them without vector loads)
+    const int tail0 = W4 << 2, tw = W - tail0;
+    const int titems = nrow * tw;
+    for (int i = threadIdx.x; i < titems; i += blockDim.x) {
+        const int r = r0 + i / tw, x = tail0 + (i - (i / tw) * tw);
+        const float a = __ldg(base + (size_t)r * pitch + x);
+        if (!isfinite(a)) {
+            ++bad;
+            continue;
+        }
+        sum += (double)a;
+        mn = fminf(mn, a);
+        mx = fmaxf(mx, a);
     }
     __shared__ double ssum[8];
     __shared__ float smn[8], smx[8];
