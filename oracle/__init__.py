@@ -78,6 +78,10 @@ def _load():
     lib.bfo_gp_adjoint.restype = i
     lib.bfo_gp_kernel.argtypes = [d, d, d, i]
     lib.bfo_gp_kernel.restype = d
+    lib.bfo_direct_joint.argtypes = [dp, dp, i, i, d, d, i, i, i, i, i, dp]
+    lib.bfo_direct_joint.restype = None
+    lib.bfo_gp_joint.argtypes = [dp, dp, i, i, d, d, i, d, i, i, i, i, i, i, i, dp, dp]
+    lib.bfo_gp_joint.restype = i
     _lib = lib
     return lib
 
@@ -147,6 +151,44 @@ def gp_bf(f, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop=None, ro
     rc = _load().bfo_gp(_ptr(f), H, W, float(sigma_s), float(sigma_r), int(N), tc, sp, w,
                         1 if round_coef_f32 else 0, r0, r1, c0, c1, _ptr(out),
                         _ptr(kap) if kap is not None else None)
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    return (out, kap) if return_kappa else out
+
+
+def direct_bf_joint(f, g, sigma_s, sigma_r, w=None, crop=None):
+    """Joint (cross) bilateral filter by direct summation: Eq. (1) with the range
+    kernel on the guide g and the data f."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    assert f.shape == g.shape
+    H, W = f.shape
+    w = window(sigma_s) if w is None else int(w)
+    r0, r1, c0, c1 = _crop(crop, H, W)
+    out = np.empty((r1 - r0, c1 - c0), np.float64)
+    _load().bfo_direct_joint(_ptr(f), _ptr(g), H, W, float(sigma_s), float(sigma_r), w, r0, r1, c0, c1, _ptr(out))
+    return out
+
+
+def gp_bf_joint(f, g, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop=None, round_coef_f32=False,
+                return_kappa=False):
+    """Joint (cross) bilateral filter by the Gauss-polynomial decomposition in
+    FP64: Algorithm 1 with the range kernel on the centred guide g (t_c = None:
+    the guide's mean), 2 (N + 1) filterings (F_n and F_n (f - t_c)).  Arguments
+    as gp_bf; kappa without the sigma_r factor."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    assert f.shape == g.shape
+    H, W = f.shape
+    sp = FIR if spatial == "fir" else IIR
+    w = window(sigma_s) if w is None else int(w)
+    r0, r1, c0, c1 = _crop(crop, H, W)
+    out = np.empty((r1 - r0, c1 - c0), np.float64)
+    kap = np.empty_like(out) if return_kappa else None
+    tc = float("nan") if t_c is None else float(t_c)
+    rc = _load().bfo_gp_joint(_ptr(f), _ptr(g), H, W, float(sigma_s), float(sigma_r), int(N), tc, sp, w,
+                              1 if round_coef_f32 else 0, r0, r1, c0, c1, _ptr(out),
+                              _ptr(kap) if kap is not None else None)
     if rc != 0:
         raise MemoryError("oracle allocation failed")
     return (out, kap) if return_kappa else out

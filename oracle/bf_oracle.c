@@ -444,6 +444,172 @@ done:
 }
 
 /*
+ * Joint (cross) bilateral filter, direct: Eq. (1) with the range kernel
+ * evaluated on a guide image g instead of f (the extension the paper names in
+ * its conclusion): weights g_s(j) g_r(g(i - j) - g(i)), data f(i - j).
+ */
+void bfo_direct_joint(const double *f, const double *g, int H, int W, double sigma_s, double sigma_r, int w,
+                      int r0, int r1, int c0, int c1, double *out)
+{
+    const int cw = c1 - c0;
+    const double inv2s2 = 1.0 / (2.0 * sigma_s * sigma_s);
+    const double inv2r2 = isinf(sigma_r) ? 0.0 : 1.0 / (2.0 * sigma_r * sigma_r);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int y = r0; y < r1; ++y) {
+        for (int x = c0; x < c1; ++x) {
+            const double tau = g[(long)y * W + x];
+            double num = 0.0, den = 0.0;
+            for (int dy = -w; dy <= w; ++dy) {
+                const int yy = y - dy;
+                if (yy < 0 || yy >= H) continue;
+                for (int dx = -w; dx <= w; ++dx) {
+                    const int xx = x - dx;
+                    if (xx < 0 || xx >= W) continue;
+                    const double t = g[(long)yy * W + xx];
+                    const double gs = exp(-(double)(dx * dx + dy * dy) * inv2s2);
+                    const double gr = exp(-(t - tau) * (t - tau) * inv2r2);
+                    num += gs * gr * f[(long)yy * W + xx];
+                    den += gs * gr;
+                }
+            }
+            out[(long)(y - r0) * cw + (x - c0)] = num / den;
+        }
+    }
+}
+
+/*
+ * Joint (cross) bilateral filter by the Gauss-polynomial decomposition:
+ * Algorithm 1 with the range kernel's translate decomposition (Eq. (3)) taken
+ * on the centred guide h = g - t_c, so the auxiliary images of Eq. (7) are
+ * F_n = H^n exp(-h^2 / 2 sigma_r^2) for the denominator and F_n (f - t_c) for
+ * the numerator, n = 0..N (2 (N + 1) filterings):
+ *     Q = sum_n G_n S(F_n) / n!,  P = sum_n G_n S(F_n (f - t_c)) / n!,
+ *     result = t_c + P / Q,
+ * with G_n = H^n at the output pixel (Eqs. (9)-(10) with the data f in place
+ * of h in the numerator).  With g = f this is Algorithm 1 (P here is sigma_r
+ * times the P of Eq. (9)).  t_c: NaN selects the guide's mean.  Other
+ * arguments and kappa as bfo_gp (kappa without the sigma_r factor).
+ */
+int bfo_gp_joint(const double *f, const double *g, int H, int W, double sigma_s, double sigma_r, int N,
+                 double t_c, int spatial, int w, int round_f32,
+                 int r0, int r1, int c0, int c1, double *out, double *kappa)
+{
+    const int cw = c1 - c0, ch = r1 - r0;
+    const long ncrop = (long)cw * ch;
+    int ylo = 0, yhi = H;
+    if (spatial == BFO_FIR) {
+        ylo = r0 - w < 0 ? 0 : r0 - w;
+        yhi = r1 + w > H ? H : r1 + w;
+    }
+    const long nreg = (long)(yhi - ylo) * W;
+
+    double *taps = NULL;
+    deriche_t D;
+    spatial_op S = {spatial, w, NULL, NULL, NULL, 0};
+    if (spatial == BFO_FIR) {
+        taps = malloc(sizeof(double) * (size_t)(w + 1));
+        if (!taps) return -1;
+        make_taps(sigma_s, w, taps);
+        S.taps = taps;
+    } else {
+        deriche_design(sigma_s, round_f32, &D);
+        S.D = &D;
+    }
+    double *abs_h = NULL;
+    if (kappa) {
+        int Dn = spatial == BFO_FIR ? w : (int)ceil(40.0 * sigma_s);
+        const int nmax = (H > W ? H : W) - 1;
+        if (spatial != BFO_FIR && Dn > nmax) Dn = nmax;
+        if (Dn < 0) Dn = 0;
+        abs_h = malloc(sizeof(double) * (size_t)(Dn + 1));
+        if (!abs_h) { free(taps); return -1; }
+        for (int d = 0; d <= Dn; ++d) {
+            if (spatial == BFO_FIR) abs_h[d] = taps[d];
+            else {
+                double acc = 0.0;
+                for (int m = 0; m < 2; ++m) acc += creal(D.A[m] * cpow(D.p[m], (double)d));
+                abs_h[d] = fabs(acc);
+            }
+        }
+        S.abs_h = abs_h;
+        S.abs_D = Dn;
+    }
+
+    double *F = malloc(sizeof(double) * (size_t)nreg);   /* F_n on the rows the operator reads */
+    double *FD = malloc(sizeof(double) * (size_t)nreg);  /* F_n (f - t_c) */
+    double *Hs = malloc(sizeof(double) * (size_t)nreg);
+    double *Dc = malloc(sizeof(double) * (size_t)nreg);  /* f - t_c */
+    double *rowtmp = malloc(sizeof(double) * (size_t)((long)(yhi - ylo) * cw));
+    double *Fbar = malloc(sizeof(double) * (size_t)ncrop);
+    double *G = malloc(sizeof(double) * (size_t)ncrop);
+    double *Hc = malloc(sizeof(double) * (size_t)ncrop);
+    double *P = calloc((size_t)ncrop, sizeof(double));
+    double *Q = calloc((size_t)ncrop, sizeof(double));
+    double *Pa = calloc((size_t)ncrop, sizeof(double));
+    double *Qa = calloc((size_t)ncrop, sizeof(double));
+    double *Fa = kappa ? malloc(sizeof(double) * (size_t)nreg) : NULL;
+    double *FbarA = kappa ? malloc(sizeof(double) * (size_t)ncrop) : NULL;
+    if (!F || !FD || !Hs || !Dc || !rowtmp || !Fbar || !G || !Hc || !P || !Q || !Pa || !Qa ||
+        (kappa && (!Fa || !FbarA))) {
+        free(F); free(FD); free(Hs); free(Dc); free(rowtmp); free(Fbar); free(G); free(Hc); free(P); free(Q);
+        free(Pa); free(Qa); free(Fa); free(FbarA); free(taps); free(abs_h);
+        return -1;
+    }
+
+    /* step 1 on the guide */
+    if (isnan(t_c)) t_c = bfo_mean(g, (long)H * W);
+    const int inf_r = isinf(sigma_r);
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < nreg; ++i) {
+        const double h = g[(long)ylo * W + i] - t_c;
+        F[i] = inf_r ? 1.0 : exp(-h * h / (2.0 * sigma_r * sigma_r));
+        Hs[i] = inf_r ? 0.0 : h / sigma_r;
+        Dc[i] = f[(long)ylo * W + i] - t_c;
+    }
+    for (int y = r0; y < r1; ++y)
+        for (int x = c0; x < c1; ++x) {
+            const long k = (long)(y - r0) * cw + (x - c0);
+            Hc[k] = inf_r ? 0.0 : (g[(long)y * W + x] - t_c) / sigma_r;
+            G[k] = 1.0;
+        }
+    double c = 1.0; /* 1/n! */
+    const int nmax = inf_r ? 0 : N;
+    for (int n = 0; n <= nmax; ++n) {
+        if (n > 0) {
+#pragma omp parallel for schedule(static)
+            for (long i = 0; i < nreg; ++i) F[i] *= Hs[i];
+        }
+        /* denominator: Q += G_n S(F_n) / n! */
+        apply_S(&S, F, W, ylo, yhi, r0, r1, c0, c1, rowtmp, Fbar);
+        for (long i = 0; i < ncrop; ++i) Q[i] += c * G[i] * Fbar[i];
+        if (kappa) {
+            for (long i = 0; i < nreg; ++i) Fa[i] = fabs(F[i]);
+            apply_S_impl(&S, 1, Fa, W, ylo, yhi, r0, r1, c0, c1, rowtmp, FbarA);
+            for (long i = 0; i < ncrop; ++i) Qa[i] += fabs(c * G[i]) * FbarA[i];
+        }
+        /* numerator: P += G_n S(F_n (f - t_c)) / n! */
+#pragma omp parallel for schedule(static)
+        for (long i = 0; i < nreg; ++i) FD[i] = F[i] * Dc[i];
+        apply_S(&S, FD, W, ylo, yhi, r0, r1, c0, c1, rowtmp, Fbar);
+        for (long i = 0; i < ncrop; ++i) P[i] += c * G[i] * Fbar[i];
+        if (kappa) {
+            for (long i = 0; i < nreg; ++i) Fa[i] = fabs(FD[i]);
+            apply_S_impl(&S, 1, Fa, W, ylo, yhi, r0, r1, c0, c1, rowtmp, FbarA);
+            for (long i = 0; i < ncrop; ++i) Pa[i] += fabs(c * G[i]) * FbarA[i];
+        }
+        for (long i = 0; i < ncrop; ++i) G[i] *= Hc[i];
+        c /= (double)(n + 1);
+    }
+    for (long i = 0; i < ncrop; ++i) {
+        out[i] = Q[i] > 0.0 ? P[i] / Q[i] + t_c : NAN;
+        if (kappa) kappa[i] = Q[i] > 0.0 ? (Pa[i] + fabs(P[i] / Q[i]) * Qa[i]) / Q[i] : INFINITY;
+    }
+    free(F); free(FD); free(Hs); free(Dc); free(rowtmp); free(Fbar); free(G); free(Hc); free(P); free(Q);
+    free(Pa); free(Qa); free(Fa); free(FbarA); free(taps); free(abs_h);
+    return 0;
+}
+
+/*
  * Eq. (5): the Gauss-polynomial of degree N that replaces the translated range
  * kernel g_{sigma_r}(t - tau) of Eq. (3): the two Gaussian factors times the
  * first N + 1 Taylor terms of exp(tau t / sigma_r^2) (Eq. (4)).

@@ -392,3 +392,87 @@ def test_adjoint_directional_derivatives(sp, ss):
         v = rng.normal(size=f.shape)
         fd = (L(f + 1e-4 * v) - L(f - 1e-4 * v)) / 2e-4
         assert abs((g * v).sum() - fd) <= 1e-6 * max(1.0, abs(fd))
+
+
+# ------------------------------------------------ joint (cross) bilateral
+
+
+def brute_joint(f, g, gs, sr, w):
+    """Eq. (1) with the range kernel on the guide g, written out (4 loops)."""
+    H, W = f.shape
+    out = np.empty_like(f)
+    for y in range(H):
+        for x in range(W):
+            num = den = 0.0
+            for dy in range(-w, w + 1):
+                for dx in range(-w, w + 1):
+                    yy, xx = y - dy, x - dx
+                    if 0 <= yy < H and 0 <= xx < W:
+                        wgt = gs(dx, dy) * math.exp(-(g[yy, xx] - g[y, x]) ** 2 / (2 * sr * sr))
+                        num += wgt * f[yy, xx]
+                        den += wgt
+            out[y, x] = num / den
+    return out
+
+
+def test_joint_direct_matches_brute_force():
+    f = small_image(11, 9, 21, n_rect=4)
+    g = small_image(11, 9, 22, n_rect=3)
+    w = oracle.window(1.5)
+    ref = brute_joint(f, g, lambda dx, dy: math.exp(-(dx * dx + dy * dy) / (2 * 1.5 * 1.5)), 30.0, w)
+    np.testing.assert_allclose(oracle.direct_bf_joint(f, g, 1.5, 30.0), ref, rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("sp", ["fir", "iir"])
+def test_joint_with_guide_equal_to_data_is_the_bilateral_filter(sp):
+    """g = f: the joint filter is the bilateral filter, directly and by Algorithm 1
+    (the pinned single-image oracles)."""
+    f = small_image(40, 36, 23)
+    np.testing.assert_allclose(oracle.direct_bf_joint(f, f, 2.0, 30.0), oracle.direct_bf(f, 2.0, 30.0),
+                               rtol=0, atol=1e-11)
+    np.testing.assert_allclose(oracle.gp_bf_joint(f, f, 2.0, 30.0, 16, sp), oracle.gp_bf(f, 2.0, 30.0, 16, sp),
+                               rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("sr,N", [(30.0, 80), (50.0, 50)])
+def test_joint_gp_converges_to_direct(sr, N):
+    """Eq. (4)'s remainder at x = s^2 = (R / sigma_r)^2 (30 and 11 for this guide)
+    is negligible at these orders: the decomposition reproduces Eq. (1)."""
+    f = small_image(36, 30, 24, ramp=40.0)
+    g = small_image(36, 30, 25)
+    np.testing.assert_allclose(oracle.gp_bf_joint(f, g, 2.0, sr, N, "fir"), oracle.direct_bf_joint(f, g, 2.0, sr),
+                               rtol=0, atol=1e-8)
+
+
+@pytest.mark.parametrize("sp", ["fir", "iir"])
+def test_joint_constant_guide_is_normalised_gaussian(sp):
+    """A constant guide makes every range weight 1: the result is S(f) / S(1)
+    (scipy's separable filter for the window sum)."""
+    f = small_image(30, 34, 26)
+    g = np.full_like(f, 91.0)
+    out = oracle.gp_bf_joint(f, g, 2.0, 25.0, 10, sp)
+    if sp == "fir":
+        ref = gauss_filter_scipy(f, 2.0, 6) / gauss_filter_scipy(np.ones_like(f), 2.0, 6)
+        np.testing.assert_allclose(out, ref, rtol=0, atol=1e-10)
+    np.testing.assert_allclose(out, oracle.gp_bf_joint(f, g, 2.0, float("inf"), 10, sp), rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("sp", ["fir", "iir"])
+def test_joint_is_linear_in_the_data(sp):
+    """For a fixed guide the filter is linear in f (weights depend on g only)."""
+    g = small_image(32, 28, 27)
+    f1, f2 = small_image(32, 28, 28), small_image(32, 28, 29, ramp=30.0)
+    a, b = 0.75, -1.5
+    lhs = oracle.gp_bf_joint(a * f1 + b * f2, g, 2.5, 35.0, 14, sp)
+    rhs = a * oracle.gp_bf_joint(f1, g, 2.5, 35.0, 14, sp) + b * oracle.gp_bf_joint(f2, g, 2.5, 35.0, 14, sp)
+    np.testing.assert_allclose(lhs, rhs, rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("sp", ["fir", "iir"])
+def test_joint_guide_affine_equivariance(sp):
+    """Scaling the guide by a and sigma_r by a, and shifting the guide, leaves the
+    weights and hence the result unchanged (Eq. (3) depends on (t - tau) / sigma_r)."""
+    f = small_image(30, 30, 30)
+    g = small_image(30, 30, 31)
+    np.testing.assert_allclose(oracle.gp_bf_joint(f, 2.0 * g + 17.0, 2.0, 60.0, 16, sp),
+                               oracle.gp_bf_joint(f, g, 2.0, 30.0, 16, sp), rtol=0, atol=1e-9)
