@@ -37,6 +37,8 @@ EXTRA_WORKLOADS = {
     "gpf-16x512x512-ss5-sr25-N20-fwdbwd": "config5",
     # runtime against sigma_s with the recursive filter: 1024^2, sigma_s in {2, 5, 10, 20}, sigma_r 30, N 20
     "gpf-1024x1024-sr30-N20-iir-sigma-sweep": "config2-sweep",
+    # joint (cross) filter: data = the 4096^2 image, guide = a second seeded 4096^2 image, K = 42 channels
+    "gpf-joint-4096x4096-ss10-sr20-N20-iir": "joint",
 }
 
 WORKLOADS = {
@@ -466,7 +468,8 @@ def _clock_wrap(local, fn):
 
 
 def run_extra(args, rank, world, local):
-    """Batched (config 4), forward + backward (config 5) and sigma_s-sweep (config 2) workloads, one GPU."""
+    """Batched (config 4), forward + backward (config 5), sigma_s-sweep (config 2) and joint-filter
+    workloads, one GPU."""
     import numpy as np
     import torch
 
@@ -491,6 +494,39 @@ def run_extra(args, rank, world, local):
         e1.record(stream)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / steps
+
+    if kind == "joint":
+        H = W = 4096
+        fd = torch.from_numpy(synthetic.config3_image()).cuda()
+        gd = torch.from_numpy(synthetic.make_image(H, W, 512, 15.0, 0.0, synthetic.seed_for(3, 900))).cuda()
+        y = torch.empty_like(fd)
+        opts = bf.make_opts(20, "iir")
+        need = bf.bf_gp_joint_workspace_size(1, H, W, 10.0, opts)
+        ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+        K = 42
+
+        def fwd():
+            bf.bf_gp_forward_joint(fd.data_ptr(), gd.data_ptr(), y.data_ptr(), 1, H, W, W, 10.0, 20.0, opts,
+                                   ws.data_ptr(), need, sp)
+        for _ in range(args.warmup):
+            fwd()
+        steps = max(1, args.steps)
+        ms, clocks = _clock_wrap(local, lambda: timed(fwd, steps))
+        bytes_step = (8 * K + 20) * H * W  # stats (guide), rows read guide + data and write K planes, columns
+        line = {"metric": "Mpixel/s", "value": H * W / (ms / 1e3) / 1e6, "unit": "Mpixel/s", "n_gpus": 1,
+                "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": args.workload, "H": H, "W": W, "sigma_s": 10.0, "sigma_r": 20.0, "order": 20,
+                           "channels": K, "spatial": "iir", "how": "bf_gp_forward_joint, CUDA-core passes"},
+                "step_roofline": {"bound": "hbm", "algorithmic_bytes_per_step": bytes_step,
+                                  "achieved": bytes_step / (ms / 1e3) / 1e9, "peak": peak,
+                                  "frac": bytes_step / (ms / 1e3) / 1e9 / peak, "peak_kind": peak_kind},
+                "gpu_launches": 4 * steps,
+                "device_status": bf.bf_gp_get_device_status(ws.data_ptr(), sp)}
+        if clocks:
+            line["clocks"] = clocks
+        print(json.dumps(line), flush=True)
+        return 0
 
     if kind == "config2-sweep":
         img = synthetic.config2_image()

@@ -149,6 +149,27 @@ bf_status bf_gp_phase_cols(const float *f, float *y, int planes, int H, int W, i
                            float sigma_r, const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * Joint (cross) bilateral filter: Eq. (1) with the range kernel evaluated on a
+ * guide image g and the weights applied to the data image f (the extension
+ * the paper's conclusion names).  By the same decomposition (Eqs. (3)-(5)) on
+ * the centred guide, with u = (g - t_c) / R, E = exp(-s^2 u^2 / 2) and
+ * d = (f - t_c) / R:
+ *   y = t_c + R (sum_n a_n S(E u^n d)) / (sum_n a_n S(E u^n)),  a_n = (s^2 u)^n / n!,
+ * i.e. K = 2 (N + 1) filterings (so N <= 31).  t_c and R are the guide's
+ * (mean or the given centre; R = max |g - t_c|); a constant guide gives the
+ * normalised Gaussian filter of f; a guide with NaN/Inf passes f through and
+ * raises BF_DEV_NONFINITE_IN.  f, g, y: device, layout and pitch of
+ * bf_gp_forward, y may alias neither input.  Recursive filter or FIR (two
+ * passes) with the CUDA-core kernels (opts.engine and opts.fir_two_pass are
+ * not used).  ws: bf_gp_joint_workspace_size bytes.  Async on `stream`.
+ */
+bf_status bf_gp_joint_workspace_size(int planes, int H, int W, float sigma_s, const bf_gp_opts *opts,
+                                     size_t *bytes);
+bf_status bf_gp_forward_joint(const float *f, const float *g, float *y, int planes, int H, int W, int pitch,
+                              float sigma_s, float sigma_r, const bf_gp_opts *opts, void *ws, size_t ws_bytes,
+                              void *stream);
+
+/*
  * Training support (no counterpart in the paper, which has no derivative):
  * reverse-mode derivative of bf_gp_forward with respect to the image and
  * sigma_r.

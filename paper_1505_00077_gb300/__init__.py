@@ -107,6 +107,9 @@ def _load():
         "bf_gp_get_plane_stats": (c_int, [c_void_p, c_int, c_void_p, P(c_double), P(c_double)]),
         "bf_gp_order_for_tol": (c_int, [c_double, c_double, c_double]),
         "bf_gp_order_fp32_limit": (c_int, [c_double, c_double, c_double]),
+        "bf_gp_joint_workspace_size": (c_int, [c_int, c_int, c_int, c_float, P(bf_gp_opts), P(c_size_t)]),
+        "bf_gp_forward_joint": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_float, c_float,
+                                        P(bf_gp_opts), c_void_p, c_size_t, c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -124,7 +127,8 @@ def exported_symbols():
             "bf_gp_batched_plan_upload", "bf_gp_batched", "bf_gp_batched_plan_destroy",
             "bf_gp_batched_plan_stats_workspace", "bf_gp_batched_plane_stats", "bf_gp_forward_noalloc",
             "bf_gp_host_workspace_size", "bf_gp_forward_host",
-            "bf_gp_get_device_status", "bf_gp_get_plane_stats", "bf_gp_order_for_tol", "bf_gp_order_fp32_limit"]
+            "bf_gp_get_device_status", "bf_gp_get_plane_stats", "bf_gp_order_for_tol", "bf_gp_order_fp32_limit",
+            "bf_gp_joint_workspace_size", "bf_gp_forward_joint"]
 
 
 def status_string(status: int) -> str:
@@ -433,6 +437,44 @@ def bilateral_gp(x, sigma_s: float, sigma_r: float, order: int = 20, spatial="au
     stream = torch.cuda.current_stream(xc.device).cuda_stream
     bf_gp_forward(xc.data_ptr(), y.data_ptr(), planes, H, W, W, sigma_s, sigma_r, opts, buf.data_ptr(),
                   buf.numel(), stream)
+    return y
+
+
+def bf_gp_joint_workspace_size(planes, H, W, sigma_s, opts=None) -> int:
+    n = ctypes.c_size_t(0)
+    _check(_load().bf_gp_joint_workspace_size(int(planes), int(H), int(W), float(sigma_s), _op(opts),
+                                              ctypes.byref(n)), "bf_gp_joint_workspace_size")
+    return int(n.value)
+
+
+def bf_gp_forward_joint(f_ptr, g_ptr, y_ptr, planes, H, W, pitch, sigma_s, sigma_r, opts, ws_ptr, ws_bytes,
+                        stream=0) -> None:
+    _check(_load().bf_gp_forward_joint(_vp(f_ptr), _vp(g_ptr), _vp(y_ptr), int(planes), int(H), int(W), int(pitch),
+                                       float(sigma_s), float(sigma_r), _op(opts), _vp(ws_ptr), int(ws_bytes),
+                                       _vp(stream)), "bf_gp_forward_joint")
+
+
+def bilateral_gp_joint(f, g, sigma_s: float, sigma_r: float, order: int = 20, spatial="auto", t_c=None,
+                       out=None, ws=None):
+    """Joint (cross) bilateral filter of the float32 CUDA tensor f with range
+    weights from the guide g (same shape [..., H, W]); see bf_gp_forward_joint."""
+    import torch
+    if not (f.is_cuda and g.is_cuda and f.dtype == torch.float32 and g.dtype == torch.float32):
+        raise TypeError("bilateral_gp_joint needs float32 CUDA tensors")
+    if f.shape != g.shape or f.dim() < 2:
+        raise ValueError("f and g need the same shape [..., H, W]")
+    fc, gc = f.contiguous(), g.contiguous()
+    H, W = fc.shape[-2], fc.shape[-1]
+    planes = max(1, fc.numel() // (H * W))
+    opts = make_opts(order, spatial, t_c)
+    need = bf_gp_joint_workspace_size(planes, H, W, sigma_s, opts)
+    buf = ws if ws is not None else workspace(need, fc.device)
+    if buf.numel() < need:
+        raise ValueError(f"workspace too small: {buf.numel()} < {need}")
+    y = torch.empty_like(fc) if out is None else out
+    stream = torch.cuda.current_stream(fc.device).cuda_stream
+    bf_gp_forward_joint(fc.data_ptr(), gc.data_ptr(), y.data_ptr(), planes, H, W, W, sigma_s, sigma_r, opts,
+                        buf.data_ptr(), buf.numel(), stream)
     return y
 
 

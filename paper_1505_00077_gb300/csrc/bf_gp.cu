@@ -54,6 +54,7 @@ struct Plan {
     int T;                     // row threads per row
     int CL;                    // column cluster size (IIR)
     int row_tc, col_tc;        // recursive filter: row / column pass engine (0 CUDA cores, 1 mma.sync, 2 tcgen05)
+    int joint;                 // joint filter: K = 2 (N + 1), CUDA-core passes
     int wpr;                   // tensor-core row pass: warps per row (512 samples each)
     size_t off_params, off_part, off_acc, off_planes, total;
 };
@@ -78,14 +79,16 @@ bf_status check_opts(const bf_gp_opts *o)
     return BF_OK;
 }
 
-bf_status make_plan(int planes, int H, int W, float sigma_s, const bf_gp_opts *o, Plan *p)
+bf_status make_plan(int planes, int H, int W, float sigma_s, const bf_gp_opts *o, Plan *p, int joint = 0)
 {
     if (planes < 1 || H < 1 || W < 1) return BF_ERR_INVALID_ARG;
     if (!(sigma_s > 0.f) || !std::isfinite(sigma_s)) return BF_ERR_INVALID_ARG;
     bf_status st = check_opts(o);
     if (st != BF_OK) return st;
+    if (joint && 2 * (o->order + 1) > KMAX) return BF_ERR_INVALID_ARG;
+    p->joint = joint;
     p->N = o->order;
-    p->K = o->order + 2;
+    p->K = joint ? 2 * (o->order + 1) : o->order + 2;
     p->w = fir_halfwidth(sigma_s, o);
     int sp = o->spatial;
     if (sp == BF_SPATIAL_AUTO) sp = (p->w <= FIR_WMAX) ? BF_SPATIAL_FIR : BF_SPATIAL_IIR;
@@ -96,8 +99,8 @@ bf_status make_plan(int planes, int H, int W, float sigma_s, const bf_gp_opts *o
     if (p->T < 8) p->T = 8;
     if (p->T > 512) return BF_ERR_UNSUPPORTED;  // rows longer than 8192 samples
     p->CL = (H + COL_ROWS_PER_CTA - 1) / COL_ROWS_PER_CTA;
-    p->row_tc = (o->engine == 0 || o->engine == 2) ? 1 : 0;
-    p->col_tc = o->engine == 2 ? 1 : (o->engine == 3 ? 2 : 0);
+    p->row_tc = (!joint && (o->engine == 0 || o->engine == 2)) ? 1 : 0;
+    p->col_tc = joint ? 0 : (o->engine == 2 ? 1 : (o->engine == 3 ? 2 : 0));
     p->wpr = next_pow2((W + 511) / 512);
     if (sp == BF_SPATIAL_IIR && p->row_tc && p->wpr > 16) return BF_ERR_UNSUPPORTED;
     if (sp == BF_SPATIAL_IIR && p->CL > COL_MAX_CLUSTER) return BF_ERR_UNSUPPORTED;  // columns longer than 4096
@@ -241,7 +244,8 @@ struct Call {
 // Validates the common arguments and lays out the workspace.  out: y for the
 // forward, grad_f for the backward (may be null for the stats/rows phases).
 bf_status prepare(const float *f, float *out, int planes, int H, int W, int pitch, float sigma_s, float sigma_r,
-                  const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream, bool need_out, Call *c)
+                  const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream, bool need_out, Call *c,
+                  const float *data = nullptr)
 {
     if (!f || !ws || (need_out && !out)) return BF_ERR_INVALID_ARG;
     if (pitch < W) return BF_ERR_INVALID_ARG;
@@ -251,15 +255,18 @@ bf_status prepare(const float *f, float *out, int planes, int H, int W, int pitc
         bf_gp_default_opts(&d);
         opts = &d;
     }
-    bf_status st = make_plan(planes, H, W, sigma_s, opts, &c->p);
+    bf_status st = make_plan(planes, H, W, sigma_s, opts, &c->p, data ? 1 : 0);
     if (st != BF_OK) return st;
     if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < c->p.total) return BF_ERR_WORKSPACE;
     if (need_out) {
-        // input and output must not overlap
-        const char *fb = reinterpret_cast<const char *>(f);
+        // inputs and output must not overlap
         const char *yb = reinterpret_cast<const char *>(out);
         const size_t span = sizeof(float) * ((size_t)planes * H * pitch);
-        if (fb < yb + span && yb < fb + span) return BF_ERR_INVALID_ARG;
+        for (const float *in : {f, data}) {
+            if (!in) continue;
+            const char *fb = reinterpret_cast<const char *>(in);
+            if (fb < yb + span && yb < fb + span) return BF_ERR_INVALID_ARG;
+        }
     }
     c->s = reinterpret_cast<cudaStream_t>(stream);
     char *wsb = static_cast<char *>(ws);
@@ -271,6 +278,7 @@ bf_status prepare(const float *f, float *out, int planes, int H, int W, int pitc
     RowArgs &ra = c->ra;
     std::memset(&ra, 0, sizeof ra);
     ra.f = f;
+    ra.fd = data;
     ra.ws = c->planesbuf;
     ra.pp = c->pp;
     ra.acc = c->acc;
@@ -285,6 +293,7 @@ bf_status prepare(const float *f, float *out, int planes, int H, int W, int pitc
     std::memset(&ca, 0, sizeof ca);
     ca.ws = c->planesbuf;
     ca.f = f;
+    ca.gy = data;  // joint filter: the data image (copied for planes the filter does not run on)
     ca.y = out;
     ca.pp = c->pp;
     ca.status = c->status;
@@ -344,7 +353,7 @@ bf_status run_rows(const Call &c, int planes, float sigma_s)
         const int tblock = 32 * c.p.wpr > 256 ? 32 * c.p.wpr : 256;
         const int trows = (tblock / 32) / c.p.wpr;
         dim3 grid((c.ra.H + trows - 1) / trows, planes);
-        row_tc<MODE><<<grid, tblock, 0, c.s>>>(ra, cr, tm);
+        if constexpr (MODE != MODE_JOINT) row_tc<MODE><<<grid, tblock, 0, c.s>>>(ra, cr, tm);
     } else {
         IIRCoef cr;
         deriche_coefs((double)sigma_s, ROW_C, &cr);
@@ -435,7 +444,9 @@ bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
             deriche_coefs((double)sigma_s, COL_C, &cc);
             UMat um;
             umma_mats((double)sigma_s, &um);
-            BF_CUDA(cudaFuncSetAttribute(col_tc5<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC5_SMEM_BYTES));
+            if constexpr (MODE != MODE_JOINT)
+                BF_CUDA(cudaFuncSetAttribute(col_tc5<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             TC5_SMEM_BYTES));
             cudaLaunchConfig_t cfg;
             std::memset(&cfg, 0, sizeof cfg);
             cfg.gridDim = dim3(strips * c.p.CL, planes, 1);
@@ -449,7 +460,7 @@ bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
             attr[0].val.clusterDim.z = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            BF_CUDA(cudaLaunchKernelEx(&cfg, col_tc5<MODE>, c.ca, cc, um));
+            if constexpr (MODE != MODE_JOINT) BF_CUDA(cudaLaunchKernelEx(&cfg, col_tc5<MODE>, c.ca, cc, um));
             BF_CUDA(cudaGetLastError());
             return BF_OK;
         }
@@ -459,9 +470,11 @@ bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
         TCMat tm;
         if (tcore) tc_mats((double)sigma_s, &tm);
         const size_t smem = tcore ? sizeof(float) * 2 * 512 * 8 : sizeof(float) * COL_TILE_BUFS * COL_TILE_FLOATS;
-        if (tcore)
-            BF_CUDA(cudaFuncSetAttribute(col_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        else
+        if constexpr (MODE != MODE_JOINT) {
+            if (tcore)
+                BF_CUDA(cudaFuncSetAttribute(col_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        }
+        if (!tcore)
             BF_CUDA(cudaFuncSetAttribute(col_iir<COL_C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         cudaLaunchConfig_t cfg;
         std::memset(&cfg, 0, sizeof cfg);
@@ -476,8 +489,10 @@ bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        if (tcore) BF_CUDA(cudaLaunchKernelEx(&cfg, col_tc<MODE>, c.ca, cc, tm));
-        else BF_CUDA(cudaLaunchKernelEx(&cfg, col_iir<COL_C, MODE>, c.ca, cc));
+        if constexpr (MODE != MODE_JOINT) {
+            if (tcore) BF_CUDA(cudaLaunchKernelEx(&cfg, col_tc<MODE>, c.ca, cc, tm));
+        }
+        if (!tcore) BF_CUDA(cudaLaunchKernelEx(&cfg, col_iir<COL_C, MODE>, c.ca, cc));
     }
     BF_CUDA(cudaGetLastError());
     return BF_OK;
@@ -541,6 +556,37 @@ bf_status bf_gp_forward(const float *f, float *y, int planes, int H, int W, int 
     if (c.p.spatial == BF_SPATIAL_FIR && opts->fir_two_pass == 0) return run_fir_fused(c, planes, sigma_s);
     st = run_rows<MODE_FWD>(c, planes, sigma_s);
     if (st == BF_OK) st = run_cols<MODE_FWD>(c, planes, W, sigma_s);
+    return st;
+}
+
+bf_status bf_gp_joint_workspace_size(int planes, int H, int W, float sigma_s, const bf_gp_opts *opts,
+                                     size_t *bytes)
+{
+    if (!bytes) return BF_ERR_INVALID_ARG;
+    bf_gp_opts d;
+    if (!opts) {
+        bf_gp_default_opts(&d);
+        opts = &d;
+    }
+    Plan p;
+    bf_status st = make_plan(planes, H, W, sigma_s, opts, &p, 1);
+    if (st != BF_OK) return st;
+    *bytes = p.total;
+    return BF_OK;
+}
+
+bf_status bf_gp_forward_joint(const float *f, const float *g, float *y, int planes, int H, int W, int pitch,
+                              float sigma_s, float sigma_r, const bf_gp_opts *opts, void *ws, size_t ws_bytes,
+                              void *stream)
+{
+    if (!f || !g) return BF_ERR_INVALID_ARG;
+    Call c;
+    bf_status st = prepare(g, y, planes, H, W, pitch, sigma_s, sigma_r, opts, ws, ws_bytes, stream, true, &c, f);
+    if (st != BF_OK) return st;
+    // statistics of the guide; a constant guide is filtered (every range weight 1)
+    st = run_stats(c, planes, H, W, pitch, sigma_s, sigma_r, opts, 3);
+    if (st == BF_OK) st = run_rows<MODE_JOINT>(c, planes, sigma_s);
+    if (st == BF_OK) st = run_cols<MODE_JOINT>(c, planes, W, sigma_s);
     return st;
 }
 

@@ -362,7 +362,8 @@ __constant__ double c_inv[KMAX + 1] = {
 // its PlaneParams: t_c, R, s^2, beta_k = s^{2(k-1)}/k! (thread k, FP64
 // product of s^2 / j), the common scale 2^e0 and the range flag.  ORs its
 // flags into the status word (zeroed by stats_partial of the same call).
-// for_backward: a constant plane is filtered (R := 1) instead of copied.
+// for_backward bit 0: a constant plane is filtered (R := 1) instead of copied;
+// bit 1: the joint filter's channels (beta_{2n} = beta_{2n+1} = s^{2n} / n!).
 __device__ __forceinline__ void stats_finalize_body(const StatPartial *__restrict__ part, int nblk, long long npix,
                                                     int centre_given, double tc_given, double sigma_r,
                                                     double sigma_s, int K, int for_backward, int c,
@@ -416,7 +417,7 @@ __device__ __forceinline__ void stats_finalize_body(const StatPartial *__restric
             // constant plane: the forward copies it; for training the filter runs
             // with R = 1 (the result is independent of R), which gives y = t_c = f
             // exactly and a defined derivative
-            if (!for_backward) mode = mode ? mode : 1;
+            if (!(for_backward & 1)) mode = mode ? mode : 1;
             R = 1.0;
         }
         sh_tc = tc;
@@ -430,13 +431,20 @@ __device__ __forceinline__ void stats_finalize_body(const StatPartial *__restric
     const int k = threadIdx.x;
     double beta = 0.0;
     float lmax = -INFINITY;
+    // joint filter: channels 2n and 2n + 1 carry u^n with beta = s^{2n} / n!
+    const bool joint = (for_backward & 2) != 0;
     if (k < K) {
         beta = 1.0;
-        for (int j = 2; j <= k; ++j) beta *= s2 * c_inv[j];
-        if (k >= 1 && beta > 0.0) {
+        const int n = joint ? (k >> 1) : k;  // power of u in the channel
+        if (joint) {
+            for (int j = 1; j <= n; ++j) beta *= s2 * c_inv[j];
+        } else {
+            for (int j = 2; j <= k; ++j) beta *= s2 * c_inv[j];
+        }
+        if (n >= 1 && beta > 0.0) {
             const float s2f = (float)s2;
-            const float u2 = fminf(1.f, (float)k / s2f);
-            lmax = log2f((float)beta) - 0.7213475f * s2f * u2 + 0.5f * (float)k * log2f(u2);
+            const float u2 = fminf(1.f, (float)n / s2f);
+            lmax = log2f((float)beta) - 0.7213475f * s2f * u2 + 0.5f * (float)n * log2f(u2);
         } else {
             lmax = 0.f;
         }
@@ -483,7 +491,10 @@ __global__ void __launch_bounds__(256) stats_finalize(const StatPartial *__restr
 
 // MODE_FWD: forward.  MODE_SAVE: forward that also writes, per pixel, the
 // four sums the backward pass needs.  MODE_ADJ: backward (adjoint) pass.
-enum { MODE_FWD = 0, MODE_SAVE = 1, MODE_ADJ = 2 };
+// MODE_JOINT: joint (cross) filter, range weights from a guide, data from a
+// second image (channels D_n = 2^e0 E u^n and U_n = D_n d, n = 0..N, with u
+// and E from the guide and d = (data - t_c) / R; K = 2 (N + 1)).
+enum { MODE_FWD = 0, MODE_SAVE = 1, MODE_ADJ = 2, MODE_JOINT = 3 };
 
 // Saved per pixel by MODE_SAVE, layout [planes][4][H][W]:
 //   0: P~   1: Q~   2: dp = sum_{m>=2} m (m-1) u^{m-2} Psi_m  (= dP~/du)
@@ -495,6 +506,7 @@ constexpr int NACC = 4;
 struct RowArgs {
     const float *f;
     const float *gy;     // MODE_ADJ: dL/dy, same layout as f
+    const float *fd;     // MODE_JOINT: the data image, same layout as f (f is the guide)
     const float *saved;  // MODE_ADJ: the MODE_SAVE sums
     float *ws;           // [planes][K][H][Wp]
     const PlaneParams *pp;
@@ -561,7 +573,10 @@ struct RowGen {
             const bool in = rv && (x0 + j < a.W);
             const float uu = (fv[j] - P.tc) * P.invR;
             u[j] = in ? uu : 0.f;
-            if (MODE != MODE_ADJ) {
+            if (MODE == MODE_JOINT) {
+                v[j] = in ? envelope(P, uu) : 0.f;
+                t[j] = in ? (__ldg(a.fd + ((size_t)plane * a.H + row) * a.pitch + x0 + j) - P.tc) * P.invR : 0.f;
+            } else if (MODE != MODE_ADJ) {
                 v[j] = in ? envelope(P, uu) : 0.f;
                 t[j] = 0.f;
             } else {
@@ -583,6 +598,20 @@ struct RowGen {
     // channel k into x (k increasing from 0)
     __device__ __forceinline__ void channel(int k, int N, float (&x)[C])
     {
+        if (MODE == MODE_JOINT) {  // k = 2n: D_n, k = 2n + 1: U_n
+            if (k & 1) {
+#pragma unroll
+                for (int j = 0; j < C; ++j) x[j] = v[j] * t[j];
+            } else {
+                if (k > 0) {
+#pragma unroll
+                    for (int j = 0; j < C; ++j) v[j] *= u[j];
+                }
+#pragma unroll
+                for (int j = 0; j < C; ++j) x[j] = v[j];
+            }
+            return;
+        }
         if (MODE != MODE_ADJ) {
             if (k > 0) {
 #pragma unroll
@@ -865,7 +894,7 @@ struct ColArgs {
     const float *ws;  // [planes][K][H][Wp]
     const float *f;
     float *y;         // forward: output image; adjoint: dL/dh (dL/df after the finish kernel)
-    const float *gy;  // MODE_ADJ: dL/dy
+    const float *gy;  // MODE_ADJ: dL/dy; MODE_JOINT: the data image (f is the guide)
     float *saved;     // MODE_SAVE: written; MODE_ADJ: read
     const PlaneParams *pp;
     uint32_t *status;
@@ -889,6 +918,16 @@ struct Combine {
     }
     __device__ __forceinline__ void step(int m, int N, float s2, const float (&y)[RPT])
     {
+        if (MODE == MODE_JOINT) {  // descending m: U_n (odd m) into p, D_n (even m) into q, Horner in u
+            if (m & 1) {
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) p[j] = fmaf(u[j], p[j], y[j]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) q[j] = fmaf(u[j], q[j], y[j]);
+            }
+            return;
+        }
         const float mk = (float)m;
         if (MODE == MODE_ADJ) {
             // A's lowest term is m = 1 (power u^0): channel 0 does not enter it
@@ -964,8 +1003,8 @@ __device__ __forceinline__ void finish_pixel(const ColArgs &a, const PlaneParams
         if (P.s2 > 0.f) sums.s2g += __fdiv_rn(u, P.s2) * gdir - 0.5f * u * u * E * cb.q[j];
         return;
     }
-    if (P.mode != 0) {
-        a.y[pix] = __ldg(a.f + pix);
+    if (P.mode != 0) {  // copied plane: the input (for the joint filter, its data image)
+        a.y[pix] = __ldg((MODE == MODE_JOINT ? a.gy : a.f) + pix);
         return;
     }
     const float Q = cb.q[j];
