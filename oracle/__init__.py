@@ -95,6 +95,19 @@ def window(sigma_s: float) -> int:
     return int(math.ceil(3.0 * sigma_s - 1e-12))
 
 
+BOX = 10  # BOX + P: P passes of a box of half-width r (window half-width P r)
+
+
+def _spatial(spatial, sigma_s, w, box):
+    """(operator code, window half-width) for 'fir', 'iir' or 'box' (box = (r, passes))."""
+    if spatial == "box":
+        r, passes = (int(v) for v in box)
+        if not (r >= 1 and 1 <= passes <= 3):
+            raise ValueError(f"bad box {box}")
+        return BOX + passes, passes * r
+    return (FIR if spatial == "fir" else IIR), (window(sigma_s) if w is None else int(w))
+
+
 def max_threads() -> int:
     return int(_load().bfo_max_threads())
 
@@ -129,11 +142,13 @@ def mean(f) -> float:
 
 
 def gp_bf(f, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop=None, round_coef_f32=False,
-          return_kappa=False):
+          return_kappa=False, box=None):
     """O2: Algorithm 1 (GPF) in FP64.
 
-    spatial: 'fir' (window sum of Eq. (8), zero extension) or 'iir' (Deriche's
-    recursive Gaussian, causal + anticausal).  t_c: centre (None = image mean,
+    spatial: 'fir' (window sum of Eq. (8), zero extension), 'iir' (Deriche's
+    recursive Gaussian, causal + anticausal) or 'box' with box = (r, passes):
+    the window sum with the passes-fold iterated box of half-width r in place
+    of the Gaussian (the paper's constant-time alternative).  t_c: centre (None = image mean,
     the algorithm's first step).  crop: (r0, r1, c0, c1) output region; the
     operator still reads every sample it needs from the full image.
     return_kappa: also return kappa = sigma_r (sum|p_n| + |P/Q| sum|q_n|) / |Q|,
@@ -142,8 +157,7 @@ def gp_bf(f, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop=None, ro
     """
     f = np.ascontiguousarray(f, dtype=np.float64)
     H, W = f.shape
-    sp = FIR if spatial == "fir" else IIR
-    w = window(sigma_s) if w is None else int(w)
+    sp, w = _spatial(spatial, sigma_s, w, box)
     r0, r1, c0, c1 = _crop(crop, H, W)
     out = np.empty((r1 - r0, c1 - c0), np.float64)
     kap = np.empty_like(out) if return_kappa else None
@@ -171,7 +185,7 @@ def direct_bf_joint(f, g, sigma_s, sigma_r, w=None, crop=None):
 
 
 def gp_bf_joint(f, g, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop=None, round_coef_f32=False,
-                return_kappa=False):
+                return_kappa=False, box=None):
     """Joint (cross) bilateral filter by the Gauss-polynomial decomposition in
     FP64: Algorithm 1 with the range kernel on the centred guide g (t_c = None:
     the guide's mean), 2 (N + 1) filterings (F_n and F_n (f - t_c)).  Arguments
@@ -180,8 +194,7 @@ def gp_bf_joint(f, g, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop
     g = np.ascontiguousarray(g, dtype=np.float64)
     assert f.shape == g.shape
     H, W = f.shape
-    sp = FIR if spatial == "fir" else IIR
-    w = window(sigma_s) if w is None else int(w)
+    sp, w = _spatial(spatial, sigma_s, w, box)
     r0, r1, c0, c1 = _crop(crop, H, W)
     out = np.empty((r1 - r0, c1 - c0), np.float64)
     kap = np.empty_like(out) if return_kappa else None
@@ -194,7 +207,7 @@ def gp_bf_joint(f, g, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop
     return (out, kap) if return_kappa else out
 
 
-def gp_adjoint(f, sigma_s, sigma_r, N, ybar, spatial="fir", t_c=None, w=None):
+def gp_adjoint(f, sigma_s, sigma_r, N, ybar, spatial="fir", t_c=None, w=None, box=None):
     """O3: reverse-mode derivative of gp_bf (Algorithm 1) on the full image.
 
     Returns (dL/df, dL/dsigma_r) for L = sum(ybar * gp_bf(f, ...)).  t_c=None is
@@ -205,25 +218,24 @@ def gp_adjoint(f, sigma_s, sigma_r, N, ybar, spatial="fir", t_c=None, w=None):
     H, W = f.shape
     yb = np.ascontiguousarray(ybar, dtype=np.float64)
     assert yb.shape == f.shape
-    w = window(sigma_s) if w is None else int(w)
+    sp, w = _spatial(spatial, sigma_s, w, box)
     fb = np.empty_like(f)
     srb = np.zeros(1)
     tc = float("nan") if t_c is None else float(t_c)
     rc = _load().bfo_gp_adjoint(_ptr(f), H, W, float(sigma_s), float(sigma_r), int(N), tc,
-                                FIR if spatial == "fir" else IIR, w, _ptr(yb), _ptr(fb), _ptr(srb))
+                                sp, w, _ptr(yb), _ptr(fb), _ptr(srb))
     if rc != 0:
         raise MemoryError("oracle allocation failed")
     return fb, float(srb[0])
 
 
-def line_filter(x, sigma_s, spatial="fir", w=None, round_coef_f32=False):
+def line_filter(x, sigma_s, spatial="fir", w=None, round_coef_f32=False, box=None):
     """The 1-D spatial operator applied to each row of x (zero extension)."""
     x = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
     count, n = x.shape
-    w = window(sigma_s) if w is None else int(w)
+    sp, w = _spatial(spatial, sigma_s, w, box)
     y = np.empty_like(x)
-    _load().bfo_line_filter(_ptr(x), count, n, float(sigma_s), FIR if spatial == "fir" else IIR, w,
-                            1 if round_coef_f32 else 0, _ptr(y))
+    _load().bfo_line_filter(_ptr(x), count, n, float(sigma_s), sp, w, 1 if round_coef_f32 else 0, _ptr(y))
     return y
 
 

@@ -48,6 +48,7 @@
 
 #define BFO_FIR 1
 #define BFO_IIR 2
+#define BFO_BOX 10 /* BFO_BOX + P: P passes of a box of half-width w / P (window of half-width w) */
 
 typedef struct {
     double complex p[2]; /* poles */
@@ -123,6 +124,32 @@ static void make_taps(double sigma_s, int w, double *taps)
     for (int d = 0; d <= w; ++d) taps[d] = exp(-(double)d * d / (2.0 * sigma_s * sigma_s));
 }
 
+/*
+ * The box-filter variant of the spatial operator (the paper allows any
+ * constant-time filter in place of the Gaussian, e.g. a box): P passes of the
+ * flat kernel of half-width r, i.e. the P-fold convolution of 2r + 1 ones,
+ * half-width w = P r, taps[d] for d = 0..w (symmetric).  Used with the same
+ * zero extension of the input as the window sum of Eq. (8).
+ */
+static void make_box_taps(int passes, int r, double *taps)
+{
+    const int w = passes * r, n = 2 * w + 1;
+    double *k = calloc((size_t)n, sizeof(double)), *t = calloc((size_t)n, sizeof(double));
+    for (int i = -r; i <= r; ++i) k[w + i] = 1.0;
+    for (int p = 1; p < passes; ++p) {
+        for (int i = 0; i < n; ++i) {
+            double acc = 0.0;
+            for (int j = -r; j <= r; ++j)
+                if (i - j >= 0 && i - j < n) acc += k[i - j];
+            t[i] = acc;
+        }
+        memcpy(k, t, sizeof(double) * (size_t)n);
+    }
+    for (int d = 0; d <= w; ++d) taps[d] = k[w + d];
+    free(k);
+    free(t);
+}
+
 int bfo_max_threads(void)
 {
 #ifdef _OPENMP
@@ -170,9 +197,13 @@ void bfo_deriche_coefs(double sigma, int round_f32, double *out)
 void bfo_line_filter(const double *x, int count, int n, double sigma_s, int spatial,
                      int w, int round_f32, double *y)
 {
+    /* box variant: P passes of a flat kernel, evaluated as its window sum */
+    const int box = spatial > BFO_BOX ? spatial - BFO_BOX : 0;
+    if (box) spatial = BFO_FIR;
     if (spatial == BFO_FIR) {
         double *taps = malloc(sizeof(double) * (size_t)(w + 1));
-        make_taps(sigma_s, w, taps);
+        if (box) make_box_taps(box, w / box, taps);
+        else make_taps(sigma_s, w, taps);
 #pragma omp parallel for schedule(static)
         for (int l = 0; l < count; ++l) fir_line(x + (long)l * n, 1, n, taps, w, y + (long)l * n, 1);
         free(taps);
@@ -308,6 +339,9 @@ int bfo_gp(const double *f, int H, int W, double sigma_s, double sigma_r, int N,
            double t_c, int spatial, int w, int round_f32,
            int r0, int r1, int c0, int c1, double *out, double *kappa)
 {
+    /* box variant: P passes of a flat kernel, evaluated as its window sum */
+    const int box = spatial > BFO_BOX ? spatial - BFO_BOX : 0;
+    if (box) spatial = BFO_FIR;
     const int cw = c1 - c0, ch = r1 - r0;
     const long ncrop = (long)cw * ch;
     int ylo = 0, yhi = H;
@@ -323,7 +357,8 @@ int bfo_gp(const double *f, int H, int W, double sigma_s, double sigma_r, int N,
     if (spatial == BFO_FIR) {
         taps = malloc(sizeof(double) * (size_t)(w + 1));
         if (!taps) return -1;
-        make_taps(sigma_s, w, taps);
+        if (box) make_box_taps(box, w / box, taps);
+        else make_taps(sigma_s, w, taps);
         S.taps = taps;
     } else {
         deriche_design(sigma_s, round_f32, &D);
@@ -494,6 +529,9 @@ int bfo_gp_joint(const double *f, const double *g, int H, int W, double sigma_s,
                  double t_c, int spatial, int w, int round_f32,
                  int r0, int r1, int c0, int c1, double *out, double *kappa)
 {
+    /* box variant: P passes of a flat kernel, evaluated as its window sum */
+    const int box = spatial > BFO_BOX ? spatial - BFO_BOX : 0;
+    if (box) spatial = BFO_FIR;
     const int cw = c1 - c0, ch = r1 - r0;
     const long ncrop = (long)cw * ch;
     int ylo = 0, yhi = H;
@@ -509,7 +547,8 @@ int bfo_gp_joint(const double *f, const double *g, int H, int W, double sigma_s,
     if (spatial == BFO_FIR) {
         taps = malloc(sizeof(double) * (size_t)(w + 1));
         if (!taps) return -1;
-        make_taps(sigma_s, w, taps);
+        if (box) make_box_taps(box, w / box, taps);
+        else make_taps(sigma_s, w, taps);
         S.taps = taps;
     } else {
         deriche_design(sigma_s, round_f32, &D);
@@ -646,6 +685,9 @@ double bfo_gp_kernel(double t, double tau, double sigma_r, int N)
 int bfo_gp_adjoint(const double *f, int H_, int W, double sigma_s, double sigma_r, int N, double t_c_given,
                    int spatial, int w, const double *ybar, double *fbar, double *sigma_r_bar)
 {
+    /* box variant: P passes of a flat kernel, evaluated as its window sum */
+    const int box = spatial > BFO_BOX ? spatial - BFO_BOX : 0;
+    if (box) spatial = BFO_FIR;
     const long n = (long)H_ * W;
     const int K = N + 2;
     double *taps = NULL;
@@ -654,7 +696,8 @@ int bfo_gp_adjoint(const double *f, int H_, int W, double sigma_s, double sigma_
     if (spatial == BFO_FIR) {
         taps = malloc(sizeof(double) * (size_t)(w + 1));
         if (!taps) return -1;
-        make_taps(sigma_s, w, taps);
+        if (box) make_box_taps(box, w / box, taps);
+        else make_taps(sigma_s, w, taps);
         S.taps = taps;
     } else {
         deriche_design(sigma_s, 0, &D);

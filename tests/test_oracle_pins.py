@@ -476,3 +476,40 @@ def test_joint_guide_affine_equivariance(sp):
     g = small_image(30, 30, 31)
     np.testing.assert_allclose(oracle.gp_bf_joint(f, 2.0 * g + 17.0, 2.0, 60.0, 16, sp),
                                oracle.gp_bf_joint(f, g, 2.0, 30.0, 16, sp), rtol=0, atol=1e-9)
+
+
+# ------------------------------------------------------------ box variant
+
+
+@pytest.mark.parametrize("r,passes", [(1, 1), (4, 1), (2, 2), (3, 3), (4, 3)])
+def test_box_line_operator_is_iterated_flat_kernel(r, passes):
+    """The box variant's line operator: the passes-fold convolution of 2r + 1
+    ones (numpy), applied with zero extension (scipy correlate1d)."""
+    k = np.ones(2 * r + 1)
+    for _ in range(passes - 1):
+        k = np.convolve(k, np.ones(2 * r + 1))
+    x = np.random.default_rng(5).normal(size=(3, 57))
+    ref = correlate1d(x, k, axis=1, mode="constant")
+    np.testing.assert_allclose(oracle.line_filter(x, 1.0, "box", box=(r, passes)), ref, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("r,passes", [(2, 1), (1, 3)])
+def test_box_gp_converges_to_brute_force_with_box_weights(r, passes):
+    """Algorithm 1 with S = the iterated box reproduces Eq. (1) with those spatial
+    weights (brute force) once N is large."""
+    f = small_image(12, 11, 32, n_rect=4)
+    k = np.ones(2 * r + 1)
+    for _ in range(passes - 1):
+        k = np.convolve(k, np.ones(2 * r + 1))
+    w = passes * r
+    ref = brute_bf(f, lambda dx, dy: float(k[w + dx] * k[w + dy]), 40.0, w)
+    np.testing.assert_allclose(oracle.gp_bf(f, 1.0, 40.0, 60, "box", box=(r, passes)), ref, rtol=0, atol=1e-9)
+
+
+def test_box_sigma_r_infinite_is_normalised_box():
+    f = small_image(30, 28, 33)
+    k = np.convolve(np.ones(5), np.ones(5))
+    ref = correlate1d(correlate1d(f - oracle.mean(f), k, axis=1, mode="constant"), k, axis=0, mode="constant")
+    one = correlate1d(correlate1d(np.ones_like(f), k, axis=1, mode="constant"), k, axis=0, mode="constant")
+    np.testing.assert_allclose(oracle.gp_bf(f, 1.0, float("inf"), 8, "box", box=(2, 2)), ref / one + oracle.mean(f),
+                               rtol=0, atol=1e-10)
