@@ -47,6 +47,8 @@ WORKLOADS = {
     "gpf-256x256-ss3-sr30-N20-fir": (256, 256, 3.0, 30.0, 20, "fir", "config1"),
     "gpf-2048x2048-ss10-sr20-N20-iir": (2048, 2048, 10.0, 20.0, 20, "iir", "config3-crop"),
     "gpf-1024x1024-ss2-sr30-N20-fir": (1024, 1024, 2.0, 30.0, 20, "fir", "config2"),
+    # box variant of S: 3 passes of a flat kernel matched to sigma_s = 3 (r = 3), fused kernel
+    "gpf-1024x1024-ss3-sr30-N20-box3": (1024, 1024, 3.0, 30.0, 20, "box", "config2"),
 }
 DEFAULT = "gpf-4096x4096-ss10-sr20-N20-iir"
 FALLBACK_HBM_GBS = 6800.0
@@ -301,7 +303,7 @@ def main():
     sp = stream.cuda_stream
     K = N + 2
 
-    fused = spatial == "fir" and not opts.fir_two_pass
+    fused = spatial == "box" or (spatial == "fir" and not opts.fir_two_pass)
     working_set = (12 * H * W) if fused else (ws_bytes + 8 * H * W)
     small = working_set < 2 * 129e6
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda") if small else None
@@ -411,7 +413,9 @@ def main():
         # FP32 FMA per pixel of the separable filter (row + column, 2w + 1 taps each) and the combine,
         # against the FP32 FMA rate of the SMs (152 SMs x 128 lanes x the measured maximum SM clock)
         w_half = int(math.ceil(3 * ss - 1e-12))  # W = ceil(3 sigma_s), the default window
-        fma_px = K * (2 * (2 * w_half + 1) + 3)
+        # window sum: 2 w + 1 multiply-adds per sample and direction; box variant (3 passes): two
+        # running-sum additions per pass and direction
+        fma_px = K * ((4 * 3 if spatial == "box" else 2 * (2 * w_half + 1)) + 3)
         alu_peak = 152 * 128 * float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]) * 1e6 \
             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 152 * 128 * 2.07e9
         achieved = fma_px * H * W / (fused_ms / 1e3) / 1e12

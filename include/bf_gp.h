@@ -67,7 +67,12 @@ typedef enum {
 typedef enum {
     BF_SPATIAL_AUTO = 0, /* FIR for w <= 12, recursive otherwise */
     BF_SPATIAL_FIR = 1,  /* window sum of Eq. (8), taps exp(-d^2 / 2 sigma_s^2), |d| <= w */
-    BF_SPATIAL_IIR = 2   /* Deriche's 4th-order recursive Gaussian, causal + anticausal */
+    BF_SPATIAL_IIR = 2,  /* Deriche's 4th-order recursive Gaussian, causal + anticausal */
+    BF_SPATIAL_BOX = 3   /* the paper's constant-time alternative (Sec. 3: any constant-time filter,
+                            e.g. a box): box_passes passes of a flat kernel of half-width r
+                            (fir_halfwidth, or chosen so that box_passes ((2r + 1)^2 - 1) / 12 is
+                            closest to sigma_s^2), zero extension; box_passes * r <= 12; forward
+                            (bf_gp_forward, fused kernel) only */
 } bf_spatial;
 
 typedef enum {
@@ -91,7 +96,8 @@ typedef struct {
                            column filters and combine in shared memory, no row-filtered planes in
                            HBM), 1 = the separate row and column passes (what bf_gp_phase_rows /
                            bf_gp_phase_cols always run) */
-    int reserved[6];    /* must be zero */
+    int box_passes;     /* BF_SPATIAL_BOX: passes of the flat kernel, 1..3 (0 selects 3) */
+    int reserved[5];    /* must be zero */
 } bf_gp_opts;
 
 /* Fill *opts with the defaults: N = 20, AUTO spatial operator, mean centre. */

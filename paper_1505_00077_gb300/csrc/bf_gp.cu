@@ -55,6 +55,7 @@ struct Plan {
     int CL;                    // column cluster size (IIR)
     int row_tc, col_tc;        // recursive filter: row / column pass engine (0 CUDA cores, 1 mma.sync, 2 tcgen05)
     int joint;                 // joint filter: K = 2 (N + 1), CUDA-core passes
+    int box_passes, box_r;     // box variant: passes of a flat kernel of half-width box_r (w = passes * box_r)
     int wpr;                   // tensor-core row pass: warps per row (512 samples each)
     size_t off_params, off_part, off_acc, off_planes, total;
 };
@@ -68,13 +69,14 @@ int fir_halfwidth(float sigma_s, const bf_gp_opts *o)
 bf_status check_opts(const bf_gp_opts *o)
 {
     if (o->order < 0 || o->order > KMAX - 2) return BF_ERR_INVALID_ARG;
-    if (o->spatial < 0 || o->spatial > 2) return BF_ERR_INVALID_ARG;
+    if (o->spatial < 0 || o->spatial > 3) return BF_ERR_INVALID_ARG;
     if (o->centre < 0 || o->centre > 1) return BF_ERR_INVALID_ARG;
     if (o->fir_halfwidth < 0) return BF_ERR_INVALID_ARG;
     if (o->centre == BF_CENTRE_GIVEN && !std::isfinite(o->t_c)) return BF_ERR_INVALID_ARG;
     if (o->engine < 0 || o->engine > 3) return BF_ERR_INVALID_ARG;
     if (o->fir_two_pass < 0 || o->fir_two_pass > 1) return BF_ERR_INVALID_ARG;
-    for (int i = 0; i < 6; ++i)
+    if (o->box_passes < 0 || o->box_passes > 3) return BF_ERR_INVALID_ARG;
+    for (int i = 0; i < 5; ++i)
         if (o->reserved[i] != 0) return BF_ERR_INVALID_ARG;
     return BF_OK;
 }
@@ -91,6 +93,22 @@ bf_status make_plan(int planes, int H, int W, float sigma_s, const bf_gp_opts *o
     p->K = joint ? 2 * (o->order + 1) : o->order + 2;
     p->w = fir_halfwidth(sigma_s, o);
     int sp = o->spatial;
+    p->box_passes = 0;
+    p->box_r = 0;
+    if (sp == BF_SPATIAL_BOX) {
+        // box variant: passes x half-width r; the window the fused kernel stages is passes * r
+        const int P = o->box_passes ? o->box_passes : 3;
+        int r = o->fir_halfwidth;
+        if (r <= 0) {
+            const double s2 = (double)sigma_s * (double)sigma_s;
+            r = (int)std::lround((std::sqrt(12.0 * s2 / P + 1.0) - 1.0) / 2.0);
+            if (r < 1) r = 1;
+        }
+        if (P * r > FIR_WMAX || joint) return BF_ERR_UNSUPPORTED;
+        p->box_passes = P;
+        p->box_r = r;
+        p->w = P * r;
+    }
     if (sp == BF_SPATIAL_AUTO) sp = (p->w <= FIR_WMAX) ? BF_SPATIAL_FIR : BF_SPATIAL_IIR;
     if (sp == BF_SPATIAL_FIR && p->w > FIR_WMAX) return BF_ERR_UNSUPPORTED;
     p->spatial = sp;
@@ -327,6 +345,7 @@ bf_status run_stats(const Call &c, int planes, int H, int W, int pitch, float si
 template <int MODE>
 bf_status run_rows(const Call &c, int planes, float sigma_s)
 {
+    if (c.p.spatial == BF_SPATIAL_BOX) return BF_ERR_UNSUPPORTED;  // the box variant runs fused only
     const int T = c.ra.T;
     const int block = T > 256 ? T : 256;
     const int rows_per_cta = block / T;
@@ -409,6 +428,21 @@ bf_status run_fir_fused(const Call &c, int planes, float sigma_s)
     FIRCoef g;
     fir_coefs((double)sigma_s, c.p.w, &g);
     dim3 grid((c.ca.W + 31) / 32, (c.ca.H + 31) / 32, planes);
+    if (c.p.box_passes) {
+        const int key = c.p.box_passes * 16 + c.p.box_r;
+        switch (key) {
+#define BF_BOX(P, R) \
+    case P * 16 + R: fir_fused<P * R, P><<<grid, 256, 0, c.s>>>(c.ca, g); break;
+            BF_BOX(1, 1) BF_BOX(1, 2) BF_BOX(1, 3) BF_BOX(1, 4) BF_BOX(1, 5) BF_BOX(1, 6)
+            BF_BOX(1, 7) BF_BOX(1, 8) BF_BOX(1, 9) BF_BOX(1, 10) BF_BOX(1, 11) BF_BOX(1, 12)
+            BF_BOX(2, 1) BF_BOX(2, 2) BF_BOX(2, 3) BF_BOX(2, 4) BF_BOX(2, 5) BF_BOX(2, 6)
+            BF_BOX(3, 1) BF_BOX(3, 2) BF_BOX(3, 3) BF_BOX(3, 4)
+#undef BF_BOX
+        default: return BF_ERR_UNSUPPORTED;
+        }
+        BF_CUDA(cudaGetLastError());
+        return BF_OK;
+    }
     switch (c.p.w) {
 #define BF_CASE(WW) \
     case WW: fir_fused<WW><<<grid, 256, 0, c.s>>>(c.ca, g); break;
@@ -424,6 +458,7 @@ bf_status run_fir_fused(const Call &c, int planes, float sigma_s)
 template <int MODE>
 bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
 {
+    if (c.p.spatial == BF_SPATIAL_BOX) return BF_ERR_UNSUPPORTED;
     if (c.p.spatial == BF_SPATIAL_FIR) {
         FIRCoef g;
         fir_coefs((double)sigma_s, c.p.w, &g);
@@ -553,6 +588,10 @@ bf_status bf_gp_forward(const float *f, float *y, int planes, int H, int W, int 
     if (st != BF_OK) return st;
     st = run_stats(c, planes, H, W, pitch, sigma_s, sigma_r, opts, 0);
     if (st != BF_OK) return st;
+    if (c.p.spatial == BF_SPATIAL_BOX) {
+        if (opts->fir_two_pass) return BF_ERR_UNSUPPORTED;
+        return run_fir_fused(c, planes, sigma_s);
+    }
     if (c.p.spatial == BF_SPATIAL_FIR && opts->fir_two_pass == 0) return run_fir_fused(c, planes, sigma_s);
     st = run_rows<MODE_FWD>(c, planes, sigma_s);
     if (st == BF_OK) st = run_cols<MODE_FWD>(c, planes, W, sigma_s);
@@ -840,7 +879,8 @@ bf_status bf_gp_batched_plan_create(const bf_gp_plane *planes, int n, const bf_g
     }
     bf_status st = check_opts(opts);
     if (st != BF_OK) return st;
-    if (opts->spatial == BF_SPATIAL_FIR) return BF_ERR_UNSUPPORTED;  // batched planes use the recursive filter
+    if (opts->spatial == BF_SPATIAL_FIR || opts->spatial == BF_SPATIAL_BOX)
+        return BF_ERR_UNSUPPORTED;  // batched planes use the recursive filter
     bf_gp_plan *pl = new (std::nothrow) bf_gp_plan;
     if (!pl) return BF_ERR_INVALID_ARG;
     pl->n = n;

@@ -1834,7 +1834,11 @@ __global__ void __launch_bounds__(256) col_fir(ColArgs a, FIRCoef g)
     }
 }
 
-// Fused forward for the FIR operator (Eq. (8) with the window of Eq. (1)):
+// Fused forward for the FIR operator (Eq. (8) with the window of Eq. (1)), or
+// with BOXP > 0 for the box variant (BOXP passes of a flat kernel of
+// half-width WH / BOXP, by running sums: about 2 BOXP additions per sample
+// plus one window sum per 8 (rows) or 4 (columns) samples, instead of
+// 2 WH + 1 multiply-adds):
 // one CTA computes a 32 x 32 output tile for all K
 // channels without writing the row-filtered planes.  Per channel k (ascending):
 //   1. Phi_k = 2^e0 E u^k on the tile plus a WH halo (zero outside the image),
@@ -1846,7 +1850,39 @@ __global__ void __launch_bounds__(256) col_fir(ColArgs a, FIRCoef g)
 //   y = t_c + R p / (Psi_0 + s^2 u q).
 // The row-filtered tile is double-buffered by channel parity, so each channel
 // costs two barriers.  grid (ceil(W/32), ceil(H/32), planes), block 256.
-template <int WH>
+// Sum over j of win[j .. j + 2 R] for the LOUT outputs after BOXP passes of a
+// box of half-width R (running sums; each pass shortens the window by 2 R).
+template <int BOXP, int R, int LOUT>
+__device__ __forceinline__ void box_passes(const float *win, float *out)
+{
+    constexpr int L0 = LOUT + 2 * BOXP * R;
+    float cur[L0];
+#pragma unroll
+    for (int j = 0; j < L0; ++j) cur[j] = win[j];
+#pragma unroll
+    for (int p = 0; p < BOXP; ++p) {
+        const int lin = L0 - 2 * R * p, lout = lin - 2 * R;
+        float acc = 0.f;
+#pragma unroll
+        for (int i = 0; i <= 2 * R; ++i) acc += cur[i];
+        float nxt[L0];
+        nxt[0] = acc;
+#pragma unroll
+        for (int j = 1; j < L0; ++j) {
+            if (j < lout) {
+                acc += cur[j + 2 * R] - cur[j - 1];
+                nxt[j] = acc;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < L0; ++j)
+            if (j < lout) cur[j] = nxt[j];
+    }
+#pragma unroll
+    for (int j = 0; j < LOUT; ++j) out[j] = cur[j];
+}
+
+template <int WH, int BOXP = 0>
 __global__ void __launch_bounds__(256) fir_fused(ColArgs a, FIRCoef g)
 {
     constexpr int T = 32;
@@ -1910,12 +1946,19 @@ __global__ void __launch_bounds__(256) fir_fused(ColArgs a, FIRCoef g)
             float win[8 + 2 * WH];
 #pragma unroll
             for (int j = 0; j < 8 + 2 * WH; ++j) win[j] = phi[rr_row][cs + j];
+            if constexpr (BOXP > 0) {
+                float o8[8];
+                box_passes<BOXP, WH / (BOXP > 0 ? BOXP : 1), 8>(win, o8);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                float acc = g.g[0] * win[j + WH];
+                for (int j = 0; j < 8; ++j) rf[buf][rr_row][cs + j] = o8[j];
+            } else {
 #pragma unroll
-                for (int dd = 1; dd <= WH; ++dd) acc = fmaf(g.g[dd], win[j + WH - dd] + win[j + WH + dd], acc);
-                rf[buf][rr_row][cs + j] = acc;
+                for (int j = 0; j < 8; ++j) {
+                    float acc = g.g[0] * win[j + WH];
+#pragma unroll
+                    for (int dd = 1; dd <= WH; ++dd) acc = fmaf(g.g[dd], win[j + WH - dd] + win[j + WH + dd], acc);
+                    rf[buf][rr_row][cs + j] = acc;
+                }
             }
         }
         __syncthreads();  // row-filtered tile of channel k
@@ -1924,12 +1967,21 @@ __global__ void __launch_bounds__(256) fir_fused(ColArgs a, FIRCoef g)
         for (int j = 0; j < 4 + 2 * WH; ++j) win[j] = rf[buf][r0 + j][c];
         const float beta = P.beta[k];
         const float mk = (float)k;
+        float o4[4];
+        if constexpr (BOXP > 0) {
+            box_passes<BOXP, WH / (BOXP > 0 ? BOXP : 1), 4>(win, o4);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float acc = g.g[0] * win[j + WH];
+#pragma unroll
+                for (int dd = 1; dd <= WH; ++dd) acc = fmaf(g.g[dd], win[j + WH - dd] + win[j + WH + dd], acc);
+                o4[j] = acc;
+            }
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            float acc = g.g[0] * win[j + WH];
-#pragma unroll
-            for (int dd = 1; dd <= WH; ++dd) acc = fmaf(g.g[dd], win[j + WH - dd] + win[j + WH + dd], acc);
-            const float psi = acc * beta;
+            const float psi = o4[j] * beta;
             if (k == 0) {
                 psi0[j] = psi;
             } else {

@@ -355,3 +355,43 @@ def test_fir_fused_copy_planes(bf):
     out2, bits2 = _forward(bf, img2, 2.0, 30.0, 20, False)
     assert bits2 & bf.BF_DEV_NONFINITE_IN
     assert np.array_equal(np.isnan(out2), np.isnan(img2)) and np.array_equal(out2[~np.isnan(out2)], img2[~np.isnan(img2)].astype(np.float64))
+
+
+# ---------------------------------------------------------------- box variant
+
+@pytest.mark.parametrize("shape,r,passes", [((96, 100), 1, 1), ((130, 70), 12, 1), ((64, 256), 3, 2), ((257, 33), 6, 2),
+                                            ((200, 190), 2, 3), ((45, 300), 4, 3)])
+def test_box_variant_matches_oracle(bf, shape, r, passes):
+    """S = passes-fold iterated box of half-width r by running sums in the fused
+    tile kernel, against Algorithm 1 with that operator (oracle, explicit taps)."""
+    H, W = shape
+    img = synthetic.make_image(H, W, 6, 10.0, 15.0, synthetic.seed_for(9, 8000 + 7 * r + passes))
+    x = torch.from_numpy(img).cuda()
+    o = bf.make_opts(20, "box", fir_halfwidth=r, box_passes=passes)
+    need = bf.bf_gp_workspace_size(1, H, W, 1.0, o)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    y = torch.full_like(x, float("nan"))
+    s = torch.cuda.current_stream().cuda_stream
+    bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, H, W, W, 1.0, 30.0, o, ws.data_ptr(), need, s)
+    assert bf.bf_gp_get_device_status(ws.data_ptr(), s) == 0
+    ref, kap = oracle.gp_bf(img.astype(np.float64), 1.0, 30.0, 20, "box", box=(r, passes), return_kappa=True)
+    check(y.cpu().numpy().astype(np.float64), ref, kappa=kap, min_gated=0.999)
+
+
+def test_box_variant_radius_from_sigma_and_limits(bf):
+    """Without a radius the box is matched to sigma_s (passes ((2r+1)^2 - 1) / 12
+    closest to sigma_s^2); wider windows than 12 and the two-pass form are refused."""
+    img = synthetic.make_image(120, 140, 6, 10.0, 0.0, synthetic.seed_for(9, 8100))
+    x = torch.from_numpy(img).cuda()
+    y = bf.bilateral_gp(x, 3.0, 30.0, 20, "box").cpu().numpy().astype(np.float64)
+    r = int(round((np.sqrt(12 * 9.0 / 3 + 1) - 1) / 2))
+    ref, kap = oracle.gp_bf(img.astype(np.float64), 3.0, 30.0, 20, "box", box=(r, 3), return_kappa=True)
+    check(y, ref, kappa=kap, min_gated=0.999)
+    with pytest.raises(bf.BFError):
+        bf.bf_gp_workspace_size(1, 64, 64, 1.0, bf.make_opts(20, "box", fir_halfwidth=5, box_passes=3))
+    o = bf.make_opts(20, "box", fir_halfwidth=2, box_passes=2, fir_two_pass=True)
+    need = bf.bf_gp_workspace_size(1, 120, 140, 1.0, o)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    with pytest.raises(bf.BFError):
+        bf.bf_gp_forward(x.data_ptr(), torch.empty_like(x).data_ptr(), 1, 120, 140, 140, 1.0, 30.0, o, ws.data_ptr(),
+                         need, torch.cuda.current_stream().cuda_stream)
