@@ -177,6 +177,20 @@ void deriche_coefs(double sigma, int C, IIRCoef *cf)
         for (int m = 0; m < NP; ++m) h += (A[m] * std::pow(p[m], (double)d)).real();
         cf->h[d] = (float)h;
     }
+    // pairs for the two-lane FMA: the same FP32 values
+    for (int m = 0; m < NP; ++m) {
+        for (int i = 0; i < 8; ++i) {
+            cf->wc[m][i] = make_float2(cf->wr[m][7 - i], cf->wi[m][7 - i]);
+            cf->wa[m][i] = make_float2(cf->wr[m][i], cf->wi[m][i]);
+        }
+        for (int j = 0; j < 8; j += 2) {
+            cf->kc[m][j >> 1] = make_float2(cf->tr[m][j + 1], cf->tr[m][j + 2]);
+            cf->kcn[m][j >> 1] = make_float2(-cf->ti[m][j + 1], -cf->ti[m][j + 2]);
+            cf->ka[m][j >> 1] = make_float2(cf->tr[m][8 - j], cf->tr[m][7 - j]);
+            cf->kan[m][j >> 1] = make_float2(-cf->ti[m][8 - j], -cf->ti[m][7 - j]);
+        }
+    }
+    for (int d = -7; d <= 7; ++d) cf->hp[d + 7] = make_float2(cf->h[std::abs(d)], cf->h[std::abs(d + 1) < 8 ? std::abs(d + 1) : 7]);
 }
 
 // The three 8 x 8 matrices of the tensor-core passes (chunk length 8), FP64 -> FP32:

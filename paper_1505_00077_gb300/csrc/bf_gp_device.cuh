@@ -79,6 +79,12 @@ struct IIRCoef {
     float Pr[NP][12], Pi[NP][12];              // p_m^{C 2^i}
     float wr[NP][9], wi[NP][9];                // p_m^e, e = 0..8
     float h[8];                                // h(d) = sum_m Re(A_m p_m^d), d = 0..7
+    // the same numbers paired for the two-lane FMA (fma.rn.f32x2)
+    float2 wc[NP][8];                          // {Re, Im} p_m^{7-i}: causal half sums
+    float2 wa[NP][8];                          // {Re, Im} p_m^i: anticausal half sums
+    float2 hp[15];                             // {h(|d|), h(|d+1|)}, d = -7..7 at d + 7
+    float2 kc[NP][4], kcn[NP][4];              // {Re, -Im} of A_m p_m^{j+1}, A_m p_m^{j+2}, j = 0, 2, 4, 6
+    float2 ka[NP][4], kan[NP][4];              // {Re, -Im} of A_m p_m^{8-j}, A_m p_m^{7-j}
 };
 
 struct FIRCoef {
@@ -98,6 +104,36 @@ __device__ __forceinline__ void cmul(float &rr, float &ri, float ar, float ai, f
 {
     rr = fmaf(ar, br, -ai * bi);
     ri = fmaf(ar, bi, ai * br);
+}
+
+// Two FP32 FMAs in one instruction (fma.rn.f32x2, round to nearest each):
+// (d.x, d.y) = (a.x b.x + c.x, a.y b.y + c.y).
+__device__ __forceinline__ uint64_t pack2(float x, float y)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+__device__ __forceinline__ void fma2(float &dx, float &dy, float ax, float ay, float bx, float by)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pack2(ax, ay)), "l"(pack2(bx, by)), "l"(pack2(dx, dy)));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(dx), "=f"(dy) : "l"(d));
+}
+
+// (rx, ry) = (ax bx, ay by), rounded to nearest
+__device__ __forceinline__ void mul2(float &rx, float &ry, float ax, float ay, float bx, float by)
+{
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pack2(ax, ay)), "l"(pack2(bx, by)));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(rx), "=f"(ry) : "l"(d));
+}
+// (rx, ry) = (ax bx + cx, ay by + cy)
+__device__ __forceinline__ void fma2r(float &rx, float &ry, float ax, float ay, float bx, float by, float cx, float cy)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pack2(ax, ay)), "l"(pack2(bx, by)), "l"(pack2(cx, cy)));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(rx), "=f"(ry) : "l"(d));
 }
 
 // p^{C n} by binary powering from the table p^{C 2^i}, 0 <= n < 4096.  The
@@ -171,6 +207,66 @@ __device__ __forceinline__ void half_correct(float *y, const float (&cr)[NP], co
             v = fmaf(cf.tr[m][8 - j], ar[m], v);
             v = fmaf(-cf.ti[m][8 - j], ai[m], v);
             y[j] = v;
+        }
+    }
+}
+
+// half_sums, half_local and half_correct with the pairs of the coefficient
+// tables in two-lane FMAs (same results: every product and sum is still one
+// FP32 fused multiply-add in the same order).
+__device__ __forceinline__ void half_sums2(const float *x, float (&cer)[NP], float (&cei)[NP], float (&asr)[NP],
+                                           float (&asi)[NP], const IIRCoef &cf)
+{
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+        float a0 = x[7], a1 = 0.f, b0 = x[0], b1 = 0.f;
+#pragma unroll
+        for (int i = 0; i < 7; ++i) {
+            fma2(a0, a1, cf.wc[m][i].x, cf.wc[m][i].y, x[i], x[i]);
+            fma2(b0, b1, cf.wa[m][i + 1].x, cf.wa[m][i + 1].y, x[i + 1], x[i + 1]);
+        }
+        cer[m] = a0;
+        cei[m] = a1;
+        asr[m] = b0;
+        asi[m] = b1;
+    }
+}
+
+__device__ __forceinline__ void half_local2(const float *x, float *y, const IIRCoef &cf)
+{
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+        float v0 = cf.h[0] * x[j], v1 = cf.h[0] * x[j + 1];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (i == j) {
+                v1 = fmaf(cf.h[1], x[i], v1);
+            } else if (i == j + 1) {
+                v0 = fmaf(cf.h[1], x[i], v0);
+            } else {
+                // pair (h(|j - i|), h(|j + 1 - i|)) = hp[j - i + 7]
+                fma2(v0, v1, cf.hp[j - i + 7].x, cf.hp[j - i + 7].y, x[i], x[i]);
+            }
+        }
+        y[j] = v0;
+        y[j + 1] = v1;
+    }
+}
+
+__device__ __forceinline__ void half_correct2(float *y, const float (&cr)[NP], const float (&ci)[NP],
+                                              const float (&ar)[NP], const float (&ai)[NP], const IIRCoef &cf)
+{
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+            float v0 = y[j], v1 = y[j + 1];
+            fma2(v0, v1, cf.kc[m][j >> 1].x, cf.kc[m][j >> 1].y, cr[m], cr[m]);
+            fma2(v0, v1, cf.kcn[m][j >> 1].x, cf.kcn[m][j >> 1].y, ci[m], ci[m]);
+            fma2(v0, v1, cf.ka[m][j >> 1].x, cf.ka[m][j >> 1].y, ar[m], ar[m]);
+            fma2(v0, v1, cf.kan[m][j >> 1].x, cf.kan[m][j >> 1].y, ai[m], ai[m]);
+            y[j] = v0;
+            y[j + 1] = v1;
         }
     }
 }
@@ -615,7 +711,7 @@ struct RowGen {
         if (MODE != MODE_ADJ) {
             if (k > 0) {
 #pragma unroll
-                for (int j = 0; j < C; ++j) v[j] *= u[j];
+                for (int j = 0; j < C; j += 2) mul2(v[j], v[j + 1], v[j], v[j + 1], u[j], u[j + 1]);
             }
 #pragma unroll
             for (int j = 0; j < C; ++j) x[j] = v[j];
@@ -650,9 +746,12 @@ __device__ __forceinline__ void store_row_chunk(const RowArgs &a, int plane, int
     float *out = a.ws + (((size_t)plane * a.K + k) * a.H + row) * a.Wp;
     if (x0 + C <= a.Wp) {
 #pragma unroll
-        for (int j = 0; j < C; j += 4)
-            *reinterpret_cast<float4 *>(out + x0 + j) =
-                make_float4(y[j] * beta, y[j + 1] * beta, y[j + 2] * beta, y[j + 3] * beta);
+        for (int j = 0; j < C; j += 4) {
+            float4 o;
+            mul2(o.x, o.y, y[j], y[j + 1], beta, beta);
+            mul2(o.z, o.w, y[j + 2], y[j + 3], beta, beta);
+            *reinterpret_cast<float4 *>(out + x0 + j) = o;
+        }
     } else {
 #pragma unroll
         for (int j = 0; j < C; ++j)
@@ -711,8 +810,8 @@ __device__ __forceinline__ void row_iir_body(const RowArgs &a, const IIRCoef &cf
         float x[C];
         gen.channel(k, a.N, x);
         float hAr[NP], hAi[NP], sAr[NP], sAi[NP], hBr[NP], hBi[NP], sBr[NP], sBi[NP];
-        half_sums(x, hAr, hAi, sAr, sAi, cf);
-        half_sums(x + 8, hBr, hBi, sBr, sBi, cf);
+        half_sums2(x, hAr, hAi, sAr, sAi, cf);
+        half_sums2(x + 8, hBr, hBi, sBr, sBi, cf);
         float er[NP], ei[NP], sr[NP], si[NP];
 #pragma unroll
         for (int m = 0; m < NP; ++m) {
@@ -793,12 +892,12 @@ __device__ __forceinline__ void row_iir_body(const RowArgs &a, const IIRCoef &cf
                 }
                 bar_arrive_named(2, nthr);  // carries written
                 __syncwarp();
-                half_local(x, y, cf);
-                half_local(x + 8, y + 8, cf);
+                half_local2(x, y, cf);
+                half_local2(x + 8, y + 8, cf);
             } else {
                 bar_arrive_named(1, nthr);
-                half_local(x, y, cf);
-                half_local(x + 8, y + 8, cf);
+                half_local2(x, y, cf);
+                half_local2(x + 8, y + 8, cf);
                 bar_sync_named(2, nthr);
             }
 #pragma unroll
@@ -808,8 +907,8 @@ __device__ __forceinline__ void row_iir_body(const RowArgs &a, const IIRCoef &cf
                 cmadd(ar[m], ai[m], qar[m], qai[m], cw.z, cw.w);
             }
         } else {
-            half_local(x, y, cf);
-            half_local(x + 8, y + 8, cf);
+            half_local2(x, y, cf);
+            half_local2(x + 8, y + 8, cf);
         }
         // states entering each half: B causal p^8 c + cA, A anticausal aB + p^8 a
         float cBr[NP], cBi[NP], aAr[NP], aAi[NP];
@@ -822,8 +921,8 @@ __device__ __forceinline__ void row_iir_body(const RowArgs &a, const IIRCoef &cf
             aAi[m] = sBi[m];
             cmadd(aAr[m], aAi[m], cf.wr[m][8], cf.wi[m][8], ar[m], ai[m]);
         }
-        half_correct(y, cr, ci, aAr, aAi, cf);
-        half_correct(y + 8, cBr, cBi, ar, ai, cf);
+        half_correct2(y, cr, ci, aAr, aAi, cf);
+        half_correct2(y + 8, cBr, cBi, ar, ai, cf);
         store_row_chunk<C>(a, plane, k, row, rv, x0, y, P.beta[k]);
     }
 }
@@ -942,6 +1041,14 @@ struct Combine {
         if (m == 0) {
 #pragma unroll
             for (int j = 0; j < RPT; ++j) q[j] = fmaf(s2 * u[j], q[j], y[j]);  // Q~
+            return;
+        }
+        if (MODE == MODE_FWD && (RPT & 1) == 0) {  // the same FMAs, two per instruction
+#pragma unroll
+            for (int j = 0; j < RPT; j += 2) {
+                if (m <= N) fma2r(q[j], q[j + 1], u[j], u[j + 1], q[j], q[j + 1], y[j], y[j + 1]);
+                fma2r(p[j], p[j + 1], u[j], u[j + 1], p[j], p[j + 1], mk * y[j], mk * y[j + 1]);
+            }
             return;
         }
         if (MODE == MODE_SAVE) {
@@ -1176,8 +1283,8 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
         cp_async_commit();
 
         float hAr[NP], hAi[NP], sAr[NP], sAi[NP], hBr[NP], hBi[NP], sBr[NP], sBi[NP];
-        half_sums(xin, hAr, hAi, sAr, sAi, cf);
-        half_sums(xin + 8, hBr, hBi, sBr, sBi, cf);
+        half_sums2(xin, hAr, hAi, sAr, sAi, cf);
+        half_sums2(xin + 8, hBr, hBi, sBr, sBi, cf);
         // chunk sums: causal end state e = p^8 cA + cB, anticausal start state s = aA + p^8 aB
         float er[NP], ei[NP], sr[NP], si[NP];
 #pragma unroll
@@ -1263,8 +1370,8 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
             float xr[C];
 #pragma unroll
             for (int j = 0; j < C; ++j) xr[j] = tl[j * 8];
-            half_local(xr, y, cf);
-            half_local(xr + 8, y + 8, cf);
+            half_local2(xr, y, cf);
+            half_local2(xr + 8, y + 8, cf);
         }
         cluster_wait_acquire();
 
@@ -1310,8 +1417,8 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
             aAi[m] = sBi[m];
             cmadd(aAr[m], aAi[m], cf.wr[m][8], cf.wi[m][8], ar[m], ai[m]);
         }
-        half_correct(y, cr, ci, aAr, aAi, cf);
-        half_correct(y + 8, cBr, cBi, ar, ai, cf);
+        half_correct2(y, cr, ci, aAr, aAi, cf);
+        half_correct2(y + 8, cBr, cBi, ar, ai, cf);
         cb.step(k, a.N, P.s2, y);
     }
     // no CTA may leave while a peer can still read its shared memory
@@ -2115,6 +2222,8 @@ struct AFrag {
     unsigned h0, h1, h2, h3, l0, l1, l2, l3;
     __device__ __forceinline__ void set(float a0, float a1, float a2, float a3)
     {
+        // scalar __fmul_rn / __fsub_rn: the split needs the product rounded before the
+        // subtraction, which a contracted (fused) multiply-subtract would skip
         tf32_split(a0, h0, l0);
         tf32_split(a1, h1, l1);
         tf32_split(a2, h2, l2);
