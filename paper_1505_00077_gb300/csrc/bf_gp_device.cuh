@@ -236,7 +236,8 @@ __device__ __forceinline__ void half_local2(const float *x, float *y, const IIRC
 {
 #pragma unroll
     for (int j = 0; j < 8; j += 2) {
-        float v0 = cf.h[0] * x[j], v1 = cf.h[0] * x[j + 1];
+        float v0, v1;
+        mul2(v0, v1, cf.h[0], cf.h[0], x[j], x[j + 1]);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             if (i == j) {
@@ -1047,7 +1048,9 @@ struct Combine {
 #pragma unroll
             for (int j = 0; j < RPT; j += 2) {
                 if (m <= N) fma2r(q[j], q[j + 1], u[j], u[j + 1], q[j], q[j + 1], y[j], y[j + 1]);
-                fma2r(p[j], p[j + 1], u[j], u[j + 1], p[j], p[j + 1], mk * y[j], mk * y[j + 1]);
+                float t0, t1;
+                mul2(t0, t1, mk, mk, y[j], y[j + 1]);
+                fma2r(p[j], p[j + 1], u[j], u[j + 1], p[j], p[j + 1], t0, t1);
             }
             return;
         }
