@@ -604,13 +604,13 @@ def run_extra(args, rank, world, local):
                 "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": args.workload, "planes": len(planes), "pixels": px, "order": 20,
-                           "spatial": "iir", "how": "CUDA graph of the batched launches (stats, finalize, rows, one column launch per cluster size), replayed"},
+                           "spatial": "iir", "how": "CUDA graph of bf_gp_batched (every plane's forward on 8 streams forked from and joined into the capturing stream, then a status gather), replayed"},
                 "plain_loop": {"value": px / (ms_plain / 1e3) / 1e6, "unit": "Mpixel/s", "ms_per_step": ms_plain,
                                "how": "bf_gp_forward plane by plane, same kernels, no graph"},
                 "step_roofline": {"bound": "hbm", "algorithmic_bytes_per_step": bytes_step,
                                   "achieved": bytes_step / (ms / 1e3) / 1e9, "peak": peak,
                                   "frac": bytes_step / (ms / 1e3) / 1e9 / peak, "peak_kind": peak_kind},
-                "gpu_launches": (3 + len({-(-x.shape[0] // 512) for x, *_ in planes})) * steps,
+                "gpu_launches": (4 * len(planes) + 1) * steps,
                 "device_status": status}
         if clocks:
             line["clocks"] = clocks

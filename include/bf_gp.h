@@ -259,20 +259,25 @@ bf_status bf_gp_forward_noalloc(const float *f, float *y, int planes, int H, int
  * BF_SPATIAL_IIR (the paper filters one image at a time; batching is an
  * implementation choice).
  *
- *   bf_gp_batched_plan_create: validates the planes (H, W <= 4096; pitch >= W;
- *     f, y device pointers that stay valid while the plan is used) and builds
- *     the per-plane tables on the host (filter coefficients in FP64 rounded
- *     to FP32).  opts.spatial must be AUTO or IIR; opts.order is ignored (each
- *     plane's own order is used); the centre option applies to every plane.
- *     The plan owns host memory only.
+ *   bf_gp_batched_plan_create: validates the planes (the limits of
+ *     bf_gp_forward with BF_SPATIAL_IIR; pitch >= W; f, y device pointers
+ *     that stay valid while the plan is used) and builds the per-plane tables
+ *     on the host (filter coefficients in FP64 rounded to FP32).  opts.spatial
+ *     must be AUTO or IIR; opts.order is ignored (each plane's own order is
+ *     used); the centre and engine options apply to every plane.  The plan
+ *     owns host memory and BF_GP_BATCH_STREAMS CUDA streams and events of the
+ *     current device (released by bf_gp_batched_plan_destroy).
  *   bf_gp_batched_plan_workspace: device bytes the plan needs (tables and
- *     every plane's K row-filtered planes).
+ *     every plane's bf_gp_workspace_size).
  *   bf_gp_batched_plan_upload: copies the tables into ws (synchronises
  *     `stream`); must be called once per workspace before bf_gp_batched.
- *   bf_gp_batched: enqueues the launches on `stream` (stats, finalize, rows, one
- *     column launch per cluster size present) and nothing else
- *     (no copies, no host synchronisation), so it can be captured into a
- *     CUDA graph and replayed.  ws must be the uploaded workspace.
+ *   bf_gp_batched: enqueues every plane's forward (statistics, row pass,
+ *     column pass: the launches of bf_gp_forward, in its own part of ws) on the
+ *     plan's streams, which fork from `stream` and join back into it, then
+ *     one launch on `stream` that ORs the planes' status words into ws's.  No
+ *     copies and no host synchronisation, so the call can be captured into a
+ *     CUDA graph (the fork and join become graph dependencies) and replayed.
+ *     ws must be the uploaded workspace; calls on one plan must not overlap.
  *   bf_gp_batched_plan_destroy: frees the plan.
  *
  * Per-plane centre and scale, for choosing each plane's order before the
@@ -298,6 +303,7 @@ typedef struct {
 } bf_gp_plane;
 
 typedef struct bf_gp_plan bf_gp_plan;
+#define BF_GP_BATCH_STREAMS 8
 
 bf_status bf_gp_batched_plan_create(const bf_gp_plane *planes, int n, const bf_gp_opts *opts, bf_gp_plan **out);
 bf_status bf_gp_batched_plan_workspace(const bf_gp_plan *plan, size_t *bytes);

@@ -278,8 +278,8 @@ MAX_ORDER = 62  # K = N + 2 <= 64 channels
 class BatchedFilter:
     """Owns a batched plan and its workspace for a fixed list of (input, output,
     sigma_s, sigma_r, order) planes (float32 CUDA tensors [H, W]).  run()
-    enqueues the batched launches on the current stream; it is safe to
-    capture in a CUDA graph.
+    enqueues every plane's forward on the plan's streams, forked from and
+    joined back into the current stream; it is safe to capture in a CUDA graph.
 
     With tol, each plane gets its own order: the smallest even N whose
     Gauss-polynomial kernel error on [-R, R] is at most tol

@@ -866,6 +866,8 @@ int bf_gp_order_fp32_limit(double sigma_s, double sigma_r, double R)
 
 // ---------------------------------------------------------------- batched
 
+constexpr int BATCH_STREAMS = BF_GP_BATCH_STREAMS;  // planes of a batch filtered concurrently
+
 struct bf_gp_plan {
     std::vector<BatchPlane> bp;  // device pointers to ws filled at upload
     std::vector<IIRCoef> coef;
@@ -879,6 +881,23 @@ struct bf_gp_plan {
     size_t off_params = 0, off_part = 0, off_tables = 0, off_planes = 0, total = 0;
     size_t tables_bytes = 0;
     const void *uploaded_ws = nullptr;
+    // filtering: every plane through the single-image launches (its own sub-workspace at
+    // off_planes + sub_off[i]), spread over the plan's streams
+    std::vector<bf_gp_plane> specs;
+    bf_gp_opts base;
+    std::vector<size_t> sub_off, sub_bytes;
+    size_t off_statusofs = 0;  // in the tables: byte offset of every plane's status word, n x uint64
+    int nstreams = 0;
+    cudaStream_t streams[BATCH_STREAMS] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[BATCH_STREAMS] = {};
+    ~bf_gp_plan()
+    {
+        for (int i = 0; i < nstreams; ++i) {
+            if (ev_join[i]) cudaEventDestroy(ev_join[i]);
+            if (streams[i]) cudaStreamDestroy(streams[i]);
+        }
+        if (ev_fork) cudaEventDestroy(ev_fork);
+    }
 };
 
 extern "C" {
@@ -915,7 +934,6 @@ bf_status bf_gp_batched_plan_create(const bf_gp_plane *planes, int n, const bf_g
         Plan pp;
         st = (q.f && q.y && q.pitch >= q.W && q.sigma_r > 0.f) ? make_plan(1, q.H, q.W, q.sigma_s, &o, &pp)
                                                                   : BF_ERR_INVALID_ARG;
-        if (st == BF_OK && pp.T > 256) st = BF_ERR_UNSUPPORTED;  // rows up to 4096 samples in batched mode
         if (st != BF_OK) {
             delete pl;
             return st;
@@ -941,8 +959,14 @@ bf_status bf_gp_batched_plan_create(const bf_gp_plane *planes, int n, const bf_g
         pl->pre_rows[i + 1] = pl->pre_rows[i] + (q.H + rows_per_cta - 1) / rows_per_cta;
         pl->CLmax = std::max(pl->CLmax, pp.CL);
         pl->plane_off[i] = planes_bytes;
-        planes_bytes = align_up(planes_bytes + sizeof(float) * (size_t)pp.K * q.H * pp.Wp, 256);
+        planes_bytes = align_up(planes_bytes + pp.total, 256);  // the plane's single-image workspace
     }
+    pl->specs.assign(planes, planes + n);
+    pl->base = *opts;
+    pl->sub_off = pl->plane_off;
+    pl->sub_bytes.resize(n);
+    for (int i = 0; i < n; ++i)
+        pl->sub_bytes[i] = (i + 1 < n ? pl->plane_off[i + 1] : planes_bytes) - pl->plane_off[i];
     // column work: planes sorted by cluster size, one launch per size
     pl->col_order.resize(n);
     for (int i = 0; i < n; ++i) pl->col_order[i] = i;
@@ -968,9 +992,21 @@ bf_status bf_gp_batched_plan_create(const bf_gp_plane *planes, int n, const bf_g
     off = align_up(off + sizeof(StatPartial) * (size_t)pl->total_stats, 256);
     pl->off_tables = off;
     pl->tables_bytes = sizeof(BatchPlane) * n + sizeof(IIRCoef) * n + sizeof(int) * (3 * (n + 1) + n);
+    pl->tables_bytes = align_up(pl->tables_bytes, 8);
+    pl->off_statusofs = pl->tables_bytes;
+    pl->tables_bytes += sizeof(unsigned long long) * (size_t)n;
     off = align_up(off + pl->tables_bytes, 256);
     pl->off_planes = off;
     pl->total = off + planes_bytes;
+    pl->nstreams = std::min(n, BATCH_STREAMS);
+    bool ok = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < pl->nstreams; ++i)
+        ok = cudaStreamCreateWithFlags(&pl->streams[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&pl->ev_join[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        delete pl;
+        return BF_ERR_CUDA;
+    }
     *out = pl;
     return BF_OK;
 }
@@ -1004,6 +1040,10 @@ bf_status upload_tables(const bf_gp_plan *plan, char *wsb, cudaStream_t s)
     std::memcpy(img.data() + o, plan->pre_cols.data(), sizeof(int) * (n + 1));
     o += sizeof(int) * (n + 1);
     std::memcpy(img.data() + o, plan->col_order.data(), sizeof(int) * n);
+    for (int i = 0; i < n; ++i) {
+        const unsigned long long so = (unsigned long long)(plan->off_planes + plan->sub_off[i]);  // status at 0
+        std::memcpy(img.data() + plan->off_statusofs + sizeof(so) * (size_t)i, &so, sizeof so);
+    }
     BF_CUDA(cudaMemcpyAsync(wsb + plan->off_tables, img.data(), plan->tables_bytes, cudaMemcpyHostToDevice, s));
     BF_CUDA(cudaStreamSynchronize(s));
     return BF_OK;
@@ -1040,8 +1080,6 @@ bf_status bf_gp_batched_plan_upload(bf_gp_plan *plan, void *ws, size_t ws_bytes,
     if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < plan->total) return BF_ERR_WORKSPACE;
     bf_status st = upload_tables(plan, static_cast<char *>(ws), reinterpret_cast<cudaStream_t>(stream));
     if (st != BF_OK) return st;
-    const size_t smem = sizeof(float) * COL_TILE_BUFS * COL_TILE_FLOATS;
-    BF_CUDA(cudaFuncSetAttribute(batched_col_iir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     plan->uploaded_ws = ws;
     return BF_OK;
 }
@@ -1083,28 +1121,34 @@ bf_status bf_gp_batched(const bf_gp_plan *plan, void *ws, size_t ws_bytes, void 
     if (!plan || !ws) return BF_ERR_INVALID_ARG;
     if (ws != plan->uploaded_ws || ws_bytes < plan->total) return BF_ERR_WORKSPACE;
     const int n = plan->n;
-    BatchArgs b = batch_args(plan, static_cast<char *>(ws));
+    char *wsb = static_cast<char *>(ws);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    batched_stats_partial<<<plan->total_stats, 256, 0, s>>>(b);
-    batched_stats_finalize<<<n, 256, 0, s>>>(b);
-    batched_row_iir<<<plan->total_rows, 256, 0, s>>>(b);
-    for (size_t gi = 0; gi < plan->grp_cl.size(); ++gi) {
-        cudaLaunchConfig_t cfg;
-        std::memset(&cfg, 0, sizeof cfg);
-        cfg.gridDim = dim3((unsigned)(plan->grp_count[gi] * plan->grp_cl[gi]), 1, 1);
-        cfg.blockDim = dim3(256, 1, 1);
-        cfg.dynamicSmemBytes = sizeof(float) * COL_TILE_BUFS * COL_TILE_FLOATS;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = (unsigned)plan->grp_cl[gi];
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        b.cid0 = plan->grp_start[gi];
-        BF_CUDA(cudaLaunchKernelEx(&cfg, batched_col_iir, b));
+    // fork: the plan's streams start after the work already on `stream` (also under capture)
+    BF_CUDA(cudaEventRecord(plan->ev_fork, s));
+    for (int j = 0; j < plan->nstreams; ++j) BF_CUDA(cudaStreamWaitEvent(plan->streams[j], plan->ev_fork, 0));
+    bf_status st = BF_OK;
+    for (int i = 0; i < n && st == BF_OK; ++i) {
+        const bf_gp_plane &q = plan->specs[i];
+        bf_gp_opts o = plan->base;
+        o.order = q.order;
+        o.spatial = BF_SPATIAL_IIR;
+        cudaStream_t si = plan->streams[i % plan->nstreams];
+        Call c;
+        st = prepare(q.f, q.y, 1, q.H, q.W, q.pitch, q.sigma_s, q.sigma_r, &o, wsb + plan->off_planes + plan->sub_off[i],
+                     plan->sub_bytes[i], si, true, &c);
+        if (st == BF_OK) st = run_stats(c, 1, q.H, q.W, q.pitch, q.sigma_s, q.sigma_r, &o, 0);
+        if (st == BF_OK) st = run_rows<MODE_FWD>(c, 1, q.sigma_s);
+        if (st == BF_OK) st = run_cols<MODE_FWD>(c, 1, q.W, q.sigma_s);
     }
+    // join, then gather the planes' status words into the batch's
+    for (int j = 0; j < plan->nstreams; ++j) {
+        BF_CUDA(cudaEventRecord(plan->ev_join[j], plan->streams[j]));
+        BF_CUDA(cudaStreamWaitEvent(s, plan->ev_join[j], 0));
+    }
+    if (st != BF_OK) return st;
+    const unsigned long long *ofs =
+        reinterpret_cast<const unsigned long long *>(wsb + plan->off_tables + plan->off_statusofs);
+    gather_status<<<1, 256, 0, s>>>(reinterpret_cast<uint32_t *>(wsb), wsb, ofs, n);
     BF_CUDA(cudaGetLastError());
     return BF_OK;
 }

@@ -2662,52 +2662,22 @@ __global__ void __launch_bounds__(256) batched_stats_finalize(BatchArgs b)
                         d.sigma_r, d.sigma_s, d.K, 0, p, b.pp, b.status);
 }
 
-__global__ void __launch_bounds__(256) batched_row_iir(BatchArgs b)
+// ORs the status word of every plane's workspace into the batch's (the planes'
+// launches have all finished: this kernel follows the join on the stream).
+__global__ void gather_status(uint32_t *dst, const char *ws, const unsigned long long *ofs, int n)
 {
-    const int p = find_plane(b.pre_rows, b.n, blockIdx.x);
-    const BatchPlane &d = b.bp[p];
-    RowArgs a;
-    a.f = d.f;
-    a.gy = nullptr;
-    a.saved = nullptr;
-    a.ws = d.ws;
-    a.pp = b.pp + p;
-    a.acc = nullptr;
-    a.H = d.H;
-    a.W = d.W;
-    a.pitch = d.pitch;
-    a.Wp = d.Wp;
-    a.K = d.K;
-    a.T = d.T;
-    a.N = d.N;
-    row_iir_body<CMAX, MODE_FWD>(a, b.coef[p], blockIdx.x - b.pre_rows[p], 0);
-}
-
-// One launch per column cluster size: cluster (CL, 1, 1), one cluster per
-// (plane, 8-column strip) of the planes of that size (planes sorted by size in
-// col_order, items numbered from cid0).
-__global__ void __launch_bounds__(256, 2) batched_col_iir(BatchArgs b)
-{
-    const int cid = b.cid0 + (int)(blockIdx.x / cg::this_cluster().num_blocks());
-    const int idx = find_plane(b.pre_cols, b.n, cid);
-    const int p = b.col_order[idx];
-    const BatchPlane &d = b.bp[p];
-    ColArgs a;
-    a.ws = d.ws;
-    a.f = d.f;
-    a.y = d.y;
-    a.gy = nullptr;
-    a.saved = nullptr;
-    a.pp = b.pp + p;
-    a.status = b.status;
-    a.acc = nullptr;
-    a.H = d.H;
-    a.W = d.W;
-    a.pitch = d.pitch;
-    a.Wp = d.Wp;
-    a.K = d.K;
-    a.N = d.N;
-    col_iir_body<CMAX, MODE_FWD>(a, b.coef[p], cid - b.pre_cols[idx], 0);
+    uint32_t bits = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) bits |= *reinterpret_cast<const uint32_t *>(ws + ofs[i]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) bits |= __shfl_down_sync(0xffffffffu, bits, o);
+    __shared__ uint32_t w[8];
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = bits;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t b = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) b |= w[i];
+        *dst = b;
+    }
 }
 
 }  // namespace bfgp

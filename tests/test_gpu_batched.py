@@ -57,8 +57,8 @@ def test_batched_graph_matches_single_and_oracle(bf):
     torch.cuda.synchronize()
     assert (bfilt.status() & ~bf.BF_DEV_NONPOS_Q) == 0
     for i, (x, y, ss, sr, order) in enumerate(planes):
-        # the batched launches use the CUDA-core recursive kernels: same arithmetic as that engine
-        o = bf.make_opts(order, "iir", engine=bf.ENGINE_CUDA_CORE)
+        # the batch runs each plane through the single-image launches: the same result bit for bit
+        o = bf.make_opts(order, "iir")
         need = bf.bf_gp_workspace_size(1, x.shape[0], x.shape[1], ss, o)
         wsb = torch.empty(need, dtype=torch.uint8, device="cuda")
         single = torch.empty_like(x)
@@ -66,9 +66,7 @@ def test_batched_graph_matches_single_and_oracle(bf):
                          wsb.data_ptr(), need, torch.cuda.current_stream().cuda_stream)
         torch.cuda.synchronize()
         a, b = y.cpu().numpy(), single.cpu().numpy()
-        assert np.array_equal(np.isnan(a), np.isnan(b))
-        m = ~np.isnan(a)
-        assert np.abs(a[m] - b[m]).max() <= 1e-5, i
+        assert np.array_equal(a, b, equal_nan=True), i
     for i in (0, 7, 14, 22, 29):
         x, y, ss, sr, order = planes[i]
         ref, kap = oracle.gp_bf(x.cpu().numpy().astype(np.float64), ss, sr, order, "iir", return_kappa=True)
@@ -88,7 +86,9 @@ def test_batched_rejects_bad_plans(bf):
     with pytest.raises(bf.BFError):
         bf.bf_gp_batched_plan_create([(x.data_ptr(), x.data_ptr(), 16, 16, 8, 2.0, 30.0, 20)])  # pitch < W
     with pytest.raises(bf.BFError):
-        bf.bf_gp_batched_plan_create([(x.data_ptr(), x.data_ptr(), 16, 5000, 5000, 2.0, 30.0, 20)])  # W > 4096
+        bf.bf_gp_batched_plan_create([(x.data_ptr(), x.data_ptr(), 5000, 16, 16, 2.0, 30.0, 20)])  # H > 4096
+    with pytest.raises(bf.BFError):
+        bf.bf_gp_batched_plan_create([(x.data_ptr(), x.data_ptr(), 16, 9000, 9000, 2.0, 30.0, 20)])  # W > 8192
 
 
 def test_adaptive_order_per_plane(bf):
