@@ -90,6 +90,22 @@ def test_config2_error_against_order(bf):
         assert all(b <= a + 0.05 for a, b in zip(errs, errs[1:])), (sr, errs)
 
 
+def test_config3_crop_mse_against_exact(bf):
+    """4096^2, sigma_s 10, sigma_r 20, N 20, recursive filter: error of the GPU
+    result against Eq. (1) (window W = 30) on a 512^2 crop, neighbours from the
+    whole image.  Reported, not gated: it holds the Taylor truncation at
+    s^2 = (R / sigma_r)^2 and the recursive filter's design error."""
+    img = synthetic.config3_image()
+    out = gpu_filter(bf, img, 10.0, 20.0, 20, "iir")
+    crop = (1792, 2304, 1792, 2304)
+    exact = oracle.direct_bf(img.astype(np.float64), 10.0, 20.0, crop=crop)
+    o = out[crop[0]:crop[1], crop[2]:crop[3]]
+    good = np.isfinite(o)
+    db, psnr = mse_db(o[good], exact[good])
+    print(f"\nconfig 3 crop: MSE {db:.2f} dB, PSNR {psnr:.2f} dB, non-finite {int((~good).sum())}")
+    assert good.mean() > 0.99
+
+
 def test_oracle_timings():
     """Host-core throughput of the FP64 oracles on the paper's workload shapes."""
     rows = []

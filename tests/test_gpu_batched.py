@@ -67,11 +67,11 @@ def test_batched_graph_matches_single_and_oracle(bf):
         torch.cuda.synchronize()
         a, b = y.cpu().numpy(), single.cpu().numpy()
         assert np.array_equal(a, b, equal_nan=True), i
-    for i in (0, 7, 14, 22, 29):
+    for i in (0, 4, 7, 11, 14, 19, 22, 29):  # 8 sampled planes
         x, y, ss, sr, order = planes[i]
         ref, kap = oracle.gp_bf(x.cpu().numpy().astype(np.float64), ss, sr, order, "iir", return_kappa=True)
         gated = np.isfinite(ref) & (kap <= 8e-4 * 2 ** 24 / 16)
-        assert gated.mean() >= 0.999
+        assert gated.mean() >= 0.995  # sigma_r is drawn down to 10: a few pixels are ill-conditioned
         assert np.abs(y.cpu().numpy()[gated] - ref[gated]).max() <= 1e-3, i
     # replaying again gives the same result
     before = [y.clone() for _, y, *_ in planes]
