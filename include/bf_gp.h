@@ -51,7 +51,7 @@ extern "C" {
 
 typedef enum {
     BF_OK = 0,
-    BF_ERR_INVALID_ARG = 1,  /* null pointer, bad size, sigma or order */
+    BF_ERR_INVALID_ARG = 1,  /* null or misaligned (not 4-byte) pointer, bad size, sigma or order */
     BF_ERR_WORKSPACE = 2,    /* workspace too small or misaligned */
     BF_ERR_CUDA = 3,         /* a CUDA runtime call failed (see bf_gp_last_cuda_error) */
     BF_ERR_UNSUPPORTED = 4,  /* valid request outside what the kernels cover (e.g. a line too long) */
@@ -205,10 +205,16 @@ bf_status bf_gp_backward(const float *f, const float *grad_y, const float *saved
                          const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream);
 
 /*
- * Forward filter on HOST buffers: copies f (host) into the device workspace,
- * runs bf_gp_forward there and copies the result into y (host), all on
- * `stream`; returns after the device->host copy has completed (it
- * synchronises `stream`).  Pinned host memory gives full copy bandwidth.
+ * Forward filter on HOST buffers: copies f (host) into the device workspace
+ * and runs bf_gp_forward there, all on `stream`; returns once the result is
+ * in y (host) (it synchronises `stream`).  When all of y lies in pinned host
+ * memory mapped into the device's address space (cudaHostAlloc, or
+ * cudaHostRegister with cudaHostRegisterMapped) and is 4-byte aligned, the
+ * last pass stores the result straight into y, overlapping the transfer with
+ * the pass; otherwise the result is staged in the workspace and copied.
+ * Either way y gets the same bytes as bf_gp_forward's device output, and
+ * nothing outside y's planes * H * W floats is written.  Pinned host memory
+ * gives full copy bandwidth for f.
  * ws must hold bf_gp_workspace_size(...) + 2 * planes * H * W * 4 bytes
  * (bf_gp_host_workspace_size).  pitch of the host buffers is W.
  */

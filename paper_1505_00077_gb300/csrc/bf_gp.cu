@@ -7,6 +7,7 @@
 #include <complex>
 #include <cstdio>
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <new>
 #include <mutex>
@@ -282,6 +283,9 @@ bf_status prepare(const float *f, float *out, int planes, int H, int W, int pitc
     if (!f || !ws || (need_out && !out)) return BF_ERR_INVALID_ARG;
     if (pitch < W) return BF_ERR_INVALID_ARG;
     if (!(sigma_r > 0.f)) return BF_ERR_INVALID_ARG;  // also rejects NaN; +inf accepted
+    // the kernels load and store whole floats
+    for (const void *p : {(const void *)f, (const void *)out, (const void *)data})
+        if ((reinterpret_cast<uintptr_t>(p) & 3) != 0) return BF_ERR_INVALID_ARG;
     bf_gp_opts d;
     if (!opts) {
         bf_gp_default_opts(&d);
@@ -767,6 +771,26 @@ bf_status bf_gp_host_workspace_size(int planes, int H, int W, float sigma_s, con
     return BF_OK;
 }
 
+// Device address of the host range [p, p + bytes) when both of its ends lie in
+// pinned host memory mapped into the device's address space (cudaHostAlloc,
+// or cudaHostRegister with the mapped flag) at consistent addresses; nullptr
+// otherwise (pageable memory, device memory, a range that runs past a mapping).
+static void *mapped_host_range(const void *p, size_t bytes)
+{
+    if (bytes == 0) return nullptr;
+    cudaPointerAttributes a0, a1;
+    const char *last = static_cast<const char *>(p) + bytes - 1;
+    if (cudaPointerGetAttributes(&a0, p) != cudaSuccess || cudaPointerGetAttributes(&a1, last) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer || !a1.devicePointer)
+        return nullptr;
+    if (static_cast<char *>(a1.devicePointer) - static_cast<char *>(a0.devicePointer) != (ptrdiff_t)(bytes - 1))
+        return nullptr;
+    return a0.devicePointer;
+}
+
 bf_status bf_gp_forward_host(const float *f_host, float *y_host, int planes, int H, int W, float sigma_s,
                              float sigma_r, const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream)
 {
@@ -782,10 +806,16 @@ bf_status bf_gp_forward_host(const float *f_host, float *y_host, int planes, int
     float *fd = reinterpret_cast<float *>(wsb + align_up(base, 256));
     float *yd = reinterpret_cast<float *>(wsb + align_up(base, 256) + align_up(img, 256));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // A mapped pinned result buffer is written by the last pass itself: its
+    // stores travel to host memory while other CTAs are still computing,
+    // instead of a device->host copy after the pass.
+    float *ymap = (reinterpret_cast<uintptr_t>(y_host) & 3) == 0
+                      ? static_cast<float *>(mapped_host_range(y_host, img))
+                      : nullptr;
     BF_CUDA(cudaMemcpyAsync(fd, f_host, img, cudaMemcpyHostToDevice, s));
-    st = bf_gp_forward(fd, yd, planes, H, W, W, sigma_s, sigma_r, opts, ws, base, stream);
+    st = bf_gp_forward(fd, ymap ? ymap : yd, planes, H, W, W, sigma_s, sigma_r, opts, ws, base, stream);
     if (st != BF_OK) return st;
-    BF_CUDA(cudaMemcpyAsync(y_host, yd, img, cudaMemcpyDeviceToHost, s));
+    if (!ymap) BF_CUDA(cudaMemcpyAsync(y_host, yd, img, cudaMemcpyDeviceToHost, s));
     BF_CUDA(cudaStreamSynchronize(s));
     return BF_OK;
 }

@@ -104,6 +104,11 @@ def test_forward_rejects_bad_pointers_before_any_cuda_call():
     with pytest.raises(bfgp.BFError) as e:
         bfgp.bf_gp_forward(256, 1 << 20, 1, 16, 16, 16, 3.0, 30.0, o, (1 << 24) + 8, 1 << 30)
     assert e.value.status == bfgp.BF_ERR_WORKSPACE
+    # input or output not 4-byte aligned
+    for f_ptr, y_ptr in ((258, 1 << 20), (256, (1 << 20) + 2)):
+        with pytest.raises(bfgp.BFError) as e:
+            bfgp.bf_gp_forward(f_ptr, y_ptr, 1, 16, 16, 16, 3.0, 30.0, o, 1 << 24, 1 << 30)
+        assert e.value.status == bfgp.BF_ERR_INVALID_ARG
     # overlapping input and output
     with pytest.raises(bfgp.BFError) as e:
         bfgp.bf_gp_forward(1 << 20, (1 << 20) + 64, 1, 16, 16, 16, 3.0, 30.0, o, 1 << 24, 1 << 30)

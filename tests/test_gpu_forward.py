@@ -277,17 +277,35 @@ def test_nonfinite_input_is_passed_through_and_flagged(bf):
     assert np.array_equal(out, img, equal_nan=True)
 
 
-def test_host_entry_point_matches_device_entry_point(bf):
-    img = synthetic.make_image(200, 180, 8, 10.0, 0.0, synthetic.seed_for(9, 6))
-    o = bf.make_opts(20, "iir")
-    need = bf.bf_gp_host_workspace_size(1, 200, 180, 6.0, o)
+@pytest.mark.parametrize("out", ["pinned", "pinned_view", "pageable"])
+@pytest.mark.parametrize("spatial", ["iir", "fir"])
+def test_host_entry_point_matches_device_entry_point(bf, out, spatial):
+    """Host buffers give the device path's bytes. A mapped pinned result buffer
+    is written by the last pass directly; a view inside a larger pinned buffer
+    takes the same route; pageable memory takes the staged copy."""
+    H, W = 200, 180
+    img = synthetic.make_image(H, W, 8, 10.0, 0.0, synthetic.seed_for(9, 6))
+    ss = 6.0 if spatial == "iir" else 3.0
+    o = bf.make_opts(20, spatial)
+    need = bf.bf_gp_host_workspace_size(1, H, W, ss, o)
     ws = torch.empty(need, dtype=torch.uint8, device="cuda")
     fh = torch.from_numpy(img).pin_memory()
-    yh = torch.empty_like(fh).pin_memory()
-    bf.bf_gp_forward_host(fh.data_ptr(), yh.data_ptr(), 1, 200, 180, 6.0, 30.0, o, ws.data_ptr(), need,
+    if out == "pinned":
+        yh = torch.empty_like(fh).pin_memory()
+        keep = yh
+    elif out == "pinned_view":
+        keep = torch.full((H * W + 96,), -7.0, dtype=torch.float32).pin_memory()
+        yh = keep[32:32 + H * W].view(H, W)
+    else:
+        keep = np.full((H, W), -7.0, dtype=np.float32)
+        yh = torch.from_numpy(keep)
+    bf.bf_gp_forward_host(fh.data_ptr(), yh.data_ptr(), 1, H, W, ss, 30.0, o, ws.data_ptr(), need,
                           torch.cuda.current_stream().cuda_stream)
-    dev = run_gpu(bf, img, 6.0, 30.0, 20, "iir")
+    dev = run_gpu(bf, img, ss, 30.0, 20, spatial)
     assert np.array_equal(yh.numpy().astype(np.float64), dev)
+    if out == "pinned_view":
+        # nothing outside the view is written
+        assert torch.all(keep[:32] == -7.0) and torch.all(keep[32 + H * W:] == -7.0)
 
 
 def test_repeat_calls_are_deterministic(bf):
