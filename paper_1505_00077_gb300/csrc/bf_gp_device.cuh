@@ -136,6 +136,14 @@ __device__ __forceinline__ void fma2r(float &rx, float &ry, float ax, float ay, 
     asm("mov.b64 {%0, %1}, %2;" : "=f"(rx), "=f"(ry) : "l"(d));
 }
 
+// (rx, ry) = (ax - bx, ay - by), rounded to nearest
+__device__ __forceinline__ void sub2(float &rx, float &ry, float ax, float ay, float bx, float by)
+{
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pack2(ax, ay)), "l"(pack2(bx, by)));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(rx), "=f"(ry) : "l"(d));
+}
+
 // p^{C n} by binary powering from the table p^{C 2^i}, 0 <= n < 4096.  The
 // pole index m may vary between threads: it selects, so the table stays in
 // the constant bank.
@@ -2175,16 +2183,18 @@ struct TCMat {
     float cor[8][8];  // [e][n]
 };
 
-// x = hi + lo with hi holding the leading 11 significant bits of x (exact in
-// TF32; Veltkamp split with 2^13 + 1, four FP32 operations on the FMA pipe)
-// and lo the exact FP32 remainder, of which the tensor core uses the leading
-// 11 bits: |x - hi - lo_tf32| <= 2^-22 |x|.
+// x = hi + lo with hi = x rounded to its leading 11 significant bits (exact in
+// TF32) and lo = x - hi (exact in FP32), of which the tensor core uses the
+// leading 11 bits: |x - hi - lo_tf32| < 2^-22 |x|.  The rounding is done on
+// the bit pattern: adding half of the 13 dropped mantissa bits' range rounds
+// the magnitude half away from zero (carrying into the exponent when the kept
+// bits overflow), the mask drops them.  Two integer operations and one FP32
+// subtraction; x must be finite and below 2^127 in magnitude.
+__device__ __forceinline__ unsigned tf32_hi(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
 __device__ __forceinline__ void tf32_split(float x, unsigned &hi, unsigned &lo)
 {
-    const float c = __fmul_rn(x, 8193.f);
-    const float h = __fsub_rn(c, __fsub_rn(c, x));
-    hi = __float_as_uint(h);
-    lo = __float_as_uint(__fsub_rn(x, h));
+    hi = tf32_hi(x);
+    lo = __float_as_uint(__fsub_rn(x, __uint_as_float(hi)));
 }
 
 __device__ __forceinline__ void mma_tf32(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
@@ -2225,12 +2235,17 @@ struct AFrag {
     unsigned h0, h1, h2, h3, l0, l1, l2, l3;
     __device__ __forceinline__ void set(float a0, float a1, float a2, float a3)
     {
-        // scalar __fmul_rn / __fsub_rn: the split needs the product rounded before the
-        // subtraction, which a contracted (fused) multiply-subtract would skip
-        tf32_split(a0, h0, l0);
-        tf32_split(a1, h1, l1);
-        tf32_split(a2, h2, l2);
-        tf32_split(a3, h3, l3);
+        h0 = tf32_hi(a0);
+        h1 = tf32_hi(a1);
+        h2 = tf32_hi(a2);
+        h3 = tf32_hi(a3);
+        float r0, r1, r2, r3;  // the remainders, two exact subtractions per instruction
+        sub2(r0, r1, a0, a1, __uint_as_float(h0), __uint_as_float(h1));
+        sub2(r2, r3, a2, a3, __uint_as_float(h2), __uint_as_float(h3));
+        l0 = __float_as_uint(r0);
+        l1 = __float_as_uint(r1);
+        l2 = __float_as_uint(r2);
+        l3 = __float_as_uint(r3);
     }
 };
 
@@ -2353,10 +2368,10 @@ __device__ __forceinline__ void row_tc_body(const RowArgs &a, const IIRCoef &cf,
         float vr = 0.f, vi = 0.f;
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
-            float nr, ni;
-            cmul(nr, ni, P1r, P1i, vr, vi);
-            vr = nr + sq.r[s];
-            vi = ni + sq.i[s];
+            float nr = sq.r[s], ni = sq.i[s];
+            cmadd(nr, ni, P1r, P1i, vr, vi);
+            vr = nr;
+            vi = ni;
         }
         // across the 8 threads g of the warp, in scan order (p^{64 d} per d threads)
 #pragma unroll
@@ -2383,10 +2398,10 @@ __device__ __forceinline__ void row_tc_body(const RowArgs &a, const IIRCoef &cf,
                 const int w = rev ? wpr - 1 - s : s;
                 if ((!rev && w >= wr) || (rev && w <= wr)) continue;
                 const float2 tt = wtot[w0 + w][t];
-                float nr, ni;
-                cmul(nr, ni, pwr, pwi, Wr, Wi);
-                Wr = nr + tt.x;
-                Wi = ni + tt.y;
+                float nr = tt.x, ni = tt.y;
+                cmadd(nr, ni, pwr, pwi, Wr, Wi);
+                Wr = nr;
+                Wi = ni;
             }
             cmadd(er, ei, Pjr, Pji, Wr, Wi);
             __syncthreads();  // wtot reused by the next channel
@@ -2397,10 +2412,10 @@ __device__ __forceinline__ void row_tc_body(const RowArgs &a, const IIRCoef &cf,
         for (int s = 0; s < 8; ++s) {
             inr_s[s] = er;
             ini_s[s] = ei;
-            float nr, ni;
-            cmul(nr, ni, P1r, P1i, er, ei);
-            er = nr + sq.r[s];
-            ei = ni + sq.i[s];
+            float nr = sq.r[s], ni = sq.i[s];
+            cmadd(nr, ni, P1r, P1i, er, ei);
+            er = nr;
+            ei = ni;
         }
         const float beta = P.beta[k];
         float *o = orow + (size_t)k * a.H * a.Wp;
@@ -2414,8 +2429,11 @@ __device__ __forceinline__ void row_tc_body(const RowArgs &a, const IIRCoef &cf,
             mma3f(D[q], cfr, bc);
             if (rv) {
                 const int xa = xw + 16 * q + 2 * t, xb = xa + 8;
-                if (xa + 1 < a.Wp) *reinterpret_cast<float2 *>(o + xa) = make_float2(D[q][0] * beta, D[q][1] * beta);
-                if (xb + 1 < a.Wp) *reinterpret_cast<float2 *>(o + xb) = make_float2(D[q][2] * beta, D[q][3] * beta);
+                float2 oa, ob;
+                mul2(oa.x, oa.y, D[q][0], D[q][1], beta, beta);
+                mul2(ob.x, ob.y, D[q][2], D[q][3], beta, beta);
+                if (xa + 1 < a.Wp) *reinterpret_cast<float2 *>(o + xa) = oa;
+                if (xb + 1 < a.Wp) *reinterpret_cast<float2 *>(o + xb) = ob;
             }
         }
     }
