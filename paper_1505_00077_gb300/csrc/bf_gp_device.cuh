@@ -2287,7 +2287,9 @@ template <int MODE>
 __device__ __forceinline__ void row_tc_body(const RowArgs &a, const IIRCoef &cf, const TCMat &tm, int grp,
                                             int plane)
 {
-    __shared__ float2 wtot[16][4];  // [warp][combo] warp totals
+    // [channel parity][warp][combo] warp totals: a thread writes the slot of channel k + 2 only after
+    // every thread has passed the barrier of channel k + 1, so one barrier per channel suffices
+    __shared__ float2 wtot[2][16][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
     const int wpr = a.T;  // warps per row
@@ -2347,6 +2349,28 @@ __device__ __forceinline__ void row_tc_body(const RowArgs &a, const IIRCoef &cf,
     float Pjr, Pji;                                    // p^{64 jpos}: the warp carry reaches this thread
     cpow_tab(Pjr, Pji, cf, m, 8 * jpos);
     float *orow = a.ws + ((size_t)plane * a.K * a.H + (rv ? row : 0)) * a.Wp;
+    // The carry entering warp wr from the other warps of the row is
+    // sum_w p^{512 d_w} T_w over the warp totals T_w that precede it in scan
+    // order, d_w = wr - 1 - w (causal) or w - wr - 1 (anticausal).  Thread g
+    // takes the terms of warps g and g + 8 (weight 0 where w does not precede
+    // wr); the 8 threads of the combo add them up.
+    float Q0r = 0.f, Q0i = 0.f, Q1r = 0.f, Q1i = 0.f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int w = g + 8 * h;
+        const int d = rev ? w - wr - 1 : wr - 1 - w;
+        if (w < wpr && d >= 0) {
+            float qr, qi;
+            cpow_tab(qr, qi, cf, m, 64 * d);
+            if (h == 0) {
+                Q0r = qr;
+                Q0i = qi;
+            } else {
+                Q1r = qr;
+                Q1i = qi;
+            }
+        }
+    }
 
 #pragma unroll 1
     for (int k = 0; k < a.K; ++k) {
@@ -2389,22 +2413,26 @@ __device__ __forceinline__ void row_tc_body(const RowArgs &a, const IIRCoef &cf,
         if (wpr > 1) {
             const int last = 4 * (rev ? 0 : 7) + t;
             const float wtr = __shfl_sync(0xffffffffu, vr, last), wti = __shfl_sync(0xffffffffu, vi, last);
-            if (g == 0) wtot[warp][t] = make_float2(wtr, wti);
+            const int par = k & 1;
+            if (g == 0) wtot[par][warp][t] = make_float2(wtr, wti);
             __syncthreads();
-            const float pwr = cf.Pr[m][6], pwi = cf.Pi[m][6];  // p^512: one warp
-            float Wr = 0.f, Wi = 0.f;
             const int w0 = r_local * wpr;
-            for (int s = 0; s < wpr; ++s) {
-                const int w = rev ? wpr - 1 - s : s;
-                if ((!rev && w >= wr) || (rev && w <= wr)) continue;
-                const float2 tt = wtot[w0 + w][t];
-                float nr = tt.x, ni = tt.y;
-                cmadd(nr, ni, pwr, pwi, Wr, Wi);
-                Wr = nr;
-                Wi = ni;
+            float Wr, Wi;
+            {
+                // warps g >= wpr read the row's last total (written, finite) with weight 0
+                const float2 tt = wtot[par][w0 + min(g, wpr - 1)][t];
+                cmul(Wr, Wi, Q0r, Q0i, tt.x, tt.y);
+            }
+            if (wpr > 8) {
+                const float2 tt = wtot[par][w0 + g + 8][t];
+                cmadd(Wr, Wi, Q1r, Q1i, tt.x, tt.y);
+            }
+#pragma unroll
+            for (int o = 4; o < 32; o <<= 1) {
+                Wr += __shfl_xor_sync(0xffffffffu, Wr, o);
+                Wi += __shfl_xor_sync(0xffffffffu, Wi, o);
             }
             cmadd(er, ei, Pjr, Pji, Wr, Wi);
-            __syncthreads();  // wtot reused by the next channel
         }
         // incoming state of each chunk, in scan order, then back to chunk order
         float inr_s[8], ini_s[8];
