@@ -1218,7 +1218,9 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
     // warp 0 replaces them in place by the carry entering each warp
     __shared__ float4 wt[2][8][8][NP];
     // [channel parity][source rank][col][pole][direction]: CTA totals pushed here by the other
-    // CTAs of the cluster (causal ones by lower ranks, anticausal ones by higher ranks)
+    // CTAs of the cluster (causal ones by lower ranks, anticausal ones by higher ranks), each
+    // already carried across the CTAs between source and destination; the slots no CTA writes
+    // stay zero, so the carry entering this CTA is the plain sum over all slots
     __shared__ float2 inc[2][8][8][NP][2];
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -1273,7 +1275,11 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
     cpow_tab(Phr, Phi, cf, gm, 4 * (gdir == 0 ? warp : 7 - warp));
     const float p4r = gm == 0 ? cf.Pr[0][2] : cf.Pr[1][2], p4i = gm == 0 ? cf.Pi[0][2] : cf.Pi[1][2];
     const float p32r = gm == 0 ? cf.Pr[0][5] : cf.Pr[1][5], p32i = gm == 0 ? cf.Pi[0][5] : cf.Pi[1][5];
-    const int nsteps = gdir == 0 ? rank : CL - 1 - rank;  // CTAs whose totals enter this one
+    {
+        float2 *z = &inc[0][0][0][0][0];
+        for (int e = tid; e < 2 * 8 * 8 * NP * 2; e += blockDim.x) z[e] = make_float2(0.f, 0.f);
+    }
+    cl.sync();  // zeroed before any peer pushes
 
     issue_tile(a.K - 1);
     cp_async_commit();
@@ -1364,10 +1370,17 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
                 totr = nr + tr;
                 toti = ni + ti;
             }
-            // push the CTA total to the CTAs it enters: later ranks (causal), earlier ones (anticausal)
+            // push the CTA total to the CTAs it enters, later ranks (causal) or earlier ones
+            // (anticausal), times p^512 per CTA crossed on the way
             float2 *own = &inc[par][rank][gcol][gm][gdir];
-            for (int r = gdir == 0 ? rank + 1 : 0; r < (gdir == 0 ? CL : rank); ++r)
-                *cl.map_shared_rank(own, r) = make_float2(totr, toti);
+            const int nd = gdir == 0 ? CL - 1 - rank : rank;
+            for (int d = 1; d <= nd; ++d) {
+                *cl.map_shared_rank(own, gdir == 0 ? rank + d : rank - d) = make_float2(totr, toti);
+                float nr, ni;
+                cmul(nr, ni, p32r, p32i, totr, toti);
+                totr = nr;
+                toti = ni;
+            }
         } else {
             bar_arrive_named(1, 256);
         }
@@ -1394,19 +1407,14 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
             Wi = gdir == 0 ? w4.y : w4.w;
         }
         if (CL > 1) {
-            // totals of the CTAs before (causal) / after (anticausal) this one, farthest first
-            const float2 *src = gdir == 0 ? &inc[par][0][gcol][gm][0] : &inc[par][CL - 1][gcol][gm][1];
-            const int step = gdir == 0 ? 8 * NP * 2 : -8 * NP * 2;
+            // carry from the CTAs before (causal) / after (anticausal) this one, in rank order
+            const float2 *src = &inc[par][0][gcol][gm][gdir];
             float Xr = 0.f, Xi = 0.f;
 #pragma unroll
-            for (int s = 0; s < 7; ++s) {
-                if (s < nsteps) {
-                    const float2 t = src[s * step];
-                    float nr, ni;
-                    cmul(nr, ni, p32r, p32i, Xr, Xi);
-                    Xr = nr + t.x;
-                    Xi = ni + t.y;
-                }
+            for (int s = 0; s < 8; ++s) {
+                const float2 t = src[s * 8 * NP * 2];
+                Xr += t.x;
+                Xi += t.y;
             }
             cmadd(Wr, Wi, Phr, Phi, Xr, Xi);
         }
