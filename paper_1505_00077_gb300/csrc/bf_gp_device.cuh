@@ -776,16 +776,17 @@ __device__ __forceinline__ void zero_acc(const RowArgs &a, int plane)
 // grid (ceil(H / rows_per_cta), planes); block = max(T, 256) threads.
 // Thread t of a row owns samples [t*C, (t+1)*C), two halves of 8.  Per
 // channel: half sums -> chunk sums; carries by Kogge-Stone inside each warp
-// (shuffles); then one warp combines the warp totals of each row sequentially
-// (one lane per row x pole x direction) while the other warps compute the
-// in-half responses (8 x 8 Toeplitz); named barriers 1 (totals written) and
-// 2 (carries written) order the two.
+// (shuffles); warp totals to shared memory, in-half responses (8 x 8
+// Toeplitz), one barrier; then every warp forms the carries entering it as a
+// weighted sum of the other warps' totals (lane = direction x pole x source
+// warp, butterfly over the source warps).
 template <int C, int MODE>
 __device__ __forceinline__ void row_iir_body(const RowArgs &a, const IIRCoef &cf, int grp, int plane)
 {
     static_assert(C == 16, "row chunks are two halves of 8 samples");
-    __shared__ float4 wt[16][NP];    // warp totals [warp slot][pole] (causal re, im, anticausal re, im)
-    __shared__ float4 wcar[16][NP];  // incoming carries of each warp
+    // warp totals [channel parity][warp slot][pole] (causal re, im, anticausal re, im); a slot is
+    // rewritten two channels later, after every thread has passed the next channel's barrier
+    __shared__ float4 wt[2][16][NP];
     const int T = a.T;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -812,6 +813,31 @@ __device__ __forceinline__ void row_iir_body(const RowArgs &a, const IIRCoef &cf
     for (int m = 0; m < NP; ++m) {
         cpow_tab(qcr[m], qci[m], cf, m, ls);
         cpow_tab(qar[m], qai[m], cf, m, 31 - ls);
+    }
+
+    // The carry entering warp wr of a row in direction dir, pole m, is
+    // sum_w p^{512 d_w} T_w over the totals T_w of the warps before it in
+    // scan order, d_w = wr - 1 - w (causal) or w - wr - 1 (anticausal).  Lane
+    // (dir, m, gw) takes the terms of warps gw and gw + 8 (weight 0 where w
+    // does not precede wr).
+    const int wr = wpr > 0 ? warp % wpr : 0, w0 = warp - wr;
+    const int gw = lane & 7, gm = (lane >> 3) & 1, gdir = lane >> 4;
+    float Q0r = 0.f, Q0i = 0.f, Q1r = 0.f, Q1i = 0.f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int w = gw + 8 * h;
+        const int d = gdir == 0 ? wr - 1 - w : w - wr - 1;
+        if (w < wpr && d >= 0) {
+            float qr, qi;
+            cpow_tab(qr, qi, cf, gm, 32 * d);
+            if (h == 0) {
+                Q0r = qr;
+                Q0i = qi;
+            } else {
+                Q1r = qr;
+                Q1i = qi;
+            }
+        }
     }
 
 #pragma unroll 1
@@ -860,60 +886,47 @@ __device__ __forceinline__ void row_iir_body(const RowArgs &a, const IIRCoef &cf
         }
         float y[C];
         if (wpr > 1) {
+            const int par = k & 1;
             if (lane == 31) {
 #pragma unroll
                 for (int m = 0; m < NP; ++m) {
-                    wt[warp][m].x = er[m];
-                    wt[warp][m].y = ei[m];
+                    wt[par][warp][m].x = er[m];
+                    wt[par][warp][m].y = ei[m];
                 }
             }
             if (lane == 0) {
 #pragma unroll
                 for (int m = 0; m < NP; ++m) {
-                    wt[warp][m].z = sr[m];
-                    wt[warp][m].w = si[m];
+                    wt[par][warp][m].z = sr[m];
+                    wt[par][warp][m].w = si[m];
                 }
             }
-            if (warp == 0) {
-                bar_sync_named(1, nthr);  // warp totals written
-                if (lane < rows_per_cta * 4) {
-                    // lane = row * 4 + (direction * 2 + pole)
-                    const int rr = lane >> 2, dir = (lane >> 1) & 1, m = lane & 1;
-                    const float p32r = m == 0 ? cf.Pr[0][5] : cf.Pr[1][5];
-                    const float p32i = m == 0 ? cf.Pi[0][5] : cf.Pi[1][5];
-                    float accr = 0.f, acci = 0.f;
-                    for (int s = 0; s < wpr; ++s) {
-                        const int w = dir == 0 ? s : wpr - 1 - s;
-                        const int slot = rr * wpr + w;
-                        const float4 tt = wt[slot][m];
-                        if (dir == 0) {
-                            wcar[slot][m].x = accr;
-                            wcar[slot][m].y = acci;
-                        } else {
-                            wcar[slot][m].z = accr;
-                            wcar[slot][m].w = acci;
-                        }
-                        float nr, ni;
-                        cmul(nr, ni, p32r, p32i, accr, acci);
-                        accr = nr + (dir == 0 ? tt.x : tt.z);
-                        acci = ni + (dir == 0 ? tt.y : tt.w);
-                    }
-                }
-                bar_arrive_named(2, nthr);  // carries written
-                __syncwarp();
-                half_local2(x, y, cf);
-                half_local2(x + 8, y + 8, cf);
-            } else {
-                bar_arrive_named(1, nthr);
-                half_local2(x, y, cf);
-                half_local2(x + 8, y + 8, cf);
-                bar_sync_named(2, nthr);
+            half_local2(x, y, cf);
+            half_local2(x + 8, y + 8, cf);
+            __syncthreads();  // every warp total of this channel written
+            float Cr, Ci;
+            {
+                // source warps gw >= wpr read the row's last total (written, finite) with weight 0
+                const float4 t0 = wt[par][w0 + min(gw, wpr - 1)][gm];
+                cmul(Cr, Ci, Q0r, Q0i, gdir == 0 ? t0.x : t0.z, gdir == 0 ? t0.y : t0.w);
+            }
+            if (wpr > 8) {
+                const float4 t1 = wt[par][w0 + gw + 8][gm];
+                cmadd(Cr, Ci, Q1r, Q1i, gdir == 0 ? t1.x : t1.z, gdir == 0 ? t1.y : t1.w);
+            }
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                Cr += __shfl_xor_sync(0xffffffffu, Cr, o);
+                Ci += __shfl_xor_sync(0xffffffffu, Ci, o);
             }
 #pragma unroll
             for (int m = 0; m < NP; ++m) {
-                const float4 cw = wcar[warp][m];
-                cmadd(cr[m], ci[m], qcr[m], qci[m], cw.x, cw.y);
-                cmadd(ar[m], ai[m], qar[m], qai[m], cw.z, cw.w);
+                const float cwr = __shfl_sync(0xffffffffu, Cr, (0 * 2 + m) * 8);
+                const float cwi = __shfl_sync(0xffffffffu, Ci, (0 * 2 + m) * 8);
+                const float awr = __shfl_sync(0xffffffffu, Cr, (1 * 2 + m) * 8);
+                const float awi = __shfl_sync(0xffffffffu, Ci, (1 * 2 + m) * 8);
+                cmadd(cr[m], ci[m], qcr[m], qci[m], cwr, cwi);
+                cmadd(ar[m], ai[m], qar[m], qai[m], awr, awi);
             }
         } else {
             half_local2(x, y, cf);
