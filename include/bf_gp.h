@@ -59,7 +59,7 @@ typedef enum {
 } bf_status;
 
 /* Bits of the device status word, set by the kernels of the last call. */
-#define BF_DEV_NONPOS_Q 0x1u      /* some pixel had Q <= 0 (only possible for odd N); it was set to NaN */
+#define BF_DEV_NONPOS_Q 0x1u      /* some pixel had Q <= 0 (odd N, or FP32 cancellation when (R/sigma_r)^2 is large); it was set to NaN */
 #define BF_DEV_NONFINITE_IN 0x2u  /* the input held NaN/Inf; the plane was passed through unchanged */
 #define BF_DEV_RANGE 0x4u         /* (R/sigma_r)^2 / 2 > 80: exp(-s^2 u^2 / 2) underflows FP32 */
 #define BF_DEV_TIMEOUT 0x8u       /* a bounded inter-block wait gave up */
