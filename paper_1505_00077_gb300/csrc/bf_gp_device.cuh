@@ -365,35 +365,40 @@ __device__ __forceinline__ void stats_partial_body(const float *__restrict__ f, 
     const int W4 = vec ? (W >> 2) : 0;
     const int items = nrow * W4;
     float acc = 0.f;
-    int nacc = 0;
-    // item i = (row r0 + r, group c4), stepped without a division per item
+    // item i = (row r0 + r, group c4), stepped without a division per item.  Four
+    // items per round, all four loads issued before any value is used, and no
+    // branch on the data: the loads of a round are in flight together.
     int r = r0 + (W4 > 0 ? (int)threadIdx.x / W4 : 0), c4 = W4 > 0 ? (int)threadIdx.x % W4 : 0;
     const int dr = W4 > 0 ? (int)blockDim.x / W4 : 0, dc = W4 > 0 ? (int)blockDim.x % W4 : 0;
-#pragma unroll 4
-    for (int i = threadIdx.x; i < items; i += blockDim.x) {
-        const float4 v = __ldg(reinterpret_cast<const float4 *>(base + (size_t)r * pitch) + c4);
-        r += dr;
-        c4 += dc;
-        if (c4 >= W4) {
-            c4 -= W4;
-            ++r;
-        }
-        const float a[4] = {v.x, v.y, v.z, v.w};
+    for (int i = threadIdx.x; i < items; i += 4 * (int)blockDim.x) {
+        float4 v[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            if (!isfinite(a[t])) {
-                ++bad;
-                continue;
+        for (int q = 0; q < 4; ++q) {
+            const bool ok = i + q * (int)blockDim.x < items;
+            v[q] = ok ? __ldg(reinterpret_cast<const float4 *>(base + (size_t)r * pitch) + c4)
+                      : make_float4(NAN, NAN, NAN, NAN);
+            r += dr;
+            c4 += dc;
+            if (c4 >= W4) {
+                c4 -= W4;
+                ++r;
             }
-            acc += a[t];
-            mn = fminf(mn, a[t]);
-            mx = fmaxf(mx, a[t]);
         }
-        if (++nacc == 4) {  // FP32 over at most 16 values, then FP64
-            sum += (double)acc;
-            acc = 0.f;
-            nacc = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const bool ok = i + q * (int)blockDim.x < items;
+            const float a[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const bool fin = isfinite(a[t]);
+                bad += (ok && !fin) ? 1 : 0;
+                acc += fin ? a[t] : 0.f;
+                mn = fminf(mn, fin ? a[t] : INFINITY);
+                mx = fmaxf(mx, fin ? a[t] : -INFINITY);
+            }
         }
+        sum += (double)acc;  // FP32 over at most 16 values, then FP64
+        acc = 0.f;
     }
     sum += (double)acc;
     // the columns the 4-groups leave (all of them without vector loads)
