@@ -343,16 +343,22 @@ bf_status prepare(const float *f, float *out, int planes, int H, int W, int pitc
     return BF_OK;
 }
 
+// src / copy: when given, the statistics pass reads the input from src
+// (mapped host memory) and stores it into copy, the device input of the call.
 bf_status run_stats(const Call &c, int planes, int H, int W, int pitch, float sigma_s, float sigma_r,
-                    const bf_gp_opts *opts, int for_backward)
+                    const bf_gp_opts *opts, int for_backward, const float *src = nullptr, float *copy = nullptr)
 {
     bf_gp_opts d;
     if (!opts) {
         bf_gp_default_opts(&d);
         opts = &d;
     }
-    stats_partial<<<dim3(c.p.nblk, planes), 256, 0, c.s>>>(c.ra.f, H, W, pitch, c.p.rows_per_block, c.part,
-                                                           c.status);
+    if (src)
+        stats_partial<true><<<dim3(c.p.nblk, planes), 256, 0, c.s>>>(src, H, W, pitch, c.p.rows_per_block, c.part,
+                                                                     c.status, copy);
+    else
+        stats_partial<false><<<dim3(c.p.nblk, planes), 256, 0, c.s>>>(c.ra.f, H, W, pitch, c.p.rows_per_block,
+                                                                      c.part, c.status, nullptr);
     stats_finalize<<<planes, 256, 0, c.s>>>(c.part, c.p.nblk, (long long)H * W,
                                             opts->centre == BF_CENTRE_GIVEN ? 1 : 0, opts->t_c, (double)sigma_r,
                                             (double)sigma_s, c.p.K, for_backward, c.pp, c.status);
@@ -598,13 +604,16 @@ bf_status bf_gp_workspace_size(int planes, int H, int W, float sigma_s, const bf
     return BF_OK;
 }
 
-bf_status bf_gp_forward(const float *f, float *y, int planes, int H, int W, int pitch, float sigma_s, float sigma_r,
-                        const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream)
+// The forward filter.  With src given, f is device memory the statistics
+// pass fills from src (mapped host memory) before the other passes read it.
+static bf_status forward_impl(const float *f, float *y, int planes, int H, int W, int pitch, float sigma_s,
+                              float sigma_r, const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream,
+                              const float *src, float *f_fill)
 {
     Call c;
     bf_status st = prepare(f, y, planes, H, W, pitch, sigma_s, sigma_r, opts, ws, ws_bytes, stream, true, &c);
     if (st != BF_OK) return st;
-    st = run_stats(c, planes, H, W, pitch, sigma_s, sigma_r, opts, 0);
+    st = run_stats(c, planes, H, W, pitch, sigma_s, sigma_r, opts, 0, src, f_fill);
     if (st != BF_OK) return st;
     if (c.p.spatial == BF_SPATIAL_BOX) {
         if (opts->fir_two_pass) return BF_ERR_UNSUPPORTED;
@@ -614,6 +623,12 @@ bf_status bf_gp_forward(const float *f, float *y, int planes, int H, int W, int 
     st = run_rows<MODE_FWD>(c, planes, sigma_s);
     if (st == BF_OK) st = run_cols<MODE_FWD>(c, planes, W, sigma_s);
     return st;
+}
+
+bf_status bf_gp_forward(const float *f, float *y, int planes, int H, int W, int pitch, float sigma_s, float sigma_r,
+                        const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream)
+{
+    return forward_impl(f, y, planes, H, W, pitch, sigma_s, sigma_r, opts, ws, ws_bytes, stream, nullptr, nullptr);
 }
 
 bf_status bf_gp_joint_workspace_size(int planes, int H, int W, float sigma_s, const bf_gp_opts *opts,
@@ -812,8 +827,14 @@ bf_status bf_gp_forward_host(const float *f_host, float *y_host, int planes, int
     float *ymap = (reinterpret_cast<uintptr_t>(y_host) & 3) == 0
                       ? static_cast<float *>(mapped_host_range(y_host, img))
                       : nullptr;
-    BF_CUDA(cudaMemcpyAsync(fd, f_host, img, cudaMemcpyHostToDevice, s));
-    st = bf_gp_forward(fd, ymap ? ymap : yd, planes, H, W, W, sigma_s, sigma_r, opts, ws, base, stream);
+    // Likewise a mapped pinned input is read by the statistics pass itself,
+    // which stores the device copy the other passes use.
+    const float *fmap = (reinterpret_cast<uintptr_t>(f_host) & 3) == 0
+                            ? static_cast<const float *>(mapped_host_range(f_host, img))
+                            : nullptr;
+    if (!fmap) BF_CUDA(cudaMemcpyAsync(fd, f_host, img, cudaMemcpyHostToDevice, s));
+    st = forward_impl(fd, ymap ? ymap : yd, planes, H, W, W, sigma_s, sigma_r, opts, ws, base, stream, fmap,
+                      fmap ? fd : nullptr);
     if (st != BF_OK) return st;
     if (!ymap) BF_CUDA(cudaMemcpyAsync(y_host, yd, img, cudaMemcpyDeviceToHost, s));
     BF_CUDA(cudaStreamSynchronize(s));

@@ -349,8 +349,14 @@ __device__ __forceinline__ float envelope(const PlaneParams &P, float u)
 
 // grid (nblk, planes), block 256.  Each block reduces a band of rows.  Block
 // (0, 0) also zeroes the status word of this call.
+// COPY: f is host memory mapped into the device's address space (read with
+// plain loads), and every value read is also stored at the same place of
+// `copy` (device memory, same pitch): the input crosses the host link once,
+// inside this pass.
+template <bool COPY = false>
 __device__ __forceinline__ void stats_partial_body(const float *__restrict__ f, int H, int W, int pitch,
-                                                   int rows_per_block, int blk, StatPartial *__restrict__ out)
+                                                   int rows_per_block, int blk, StatPartial *__restrict__ out,
+                                                   float *__restrict__ copy = nullptr)
 {
     const int plane = 0;
     const int r0 = blk * rows_per_block;
@@ -375,8 +381,9 @@ __device__ __forceinline__ void stats_partial_body(const float *__restrict__ f, 
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const bool ok = i + q * (int)blockDim.x < items;
-            v[q] = ok ? __ldg(reinterpret_cast<const float4 *>(base + (size_t)r * pitch) + c4)
-                      : make_float4(NAN, NAN, NAN, NAN);
+            const float4 *src = reinterpret_cast<const float4 *>(base + (size_t)r * pitch) + c4;
+            v[q] = ok ? (COPY ? *src : __ldg(src)) : make_float4(NAN, NAN, NAN, NAN);
+            if (COPY && ok) reinterpret_cast<float4 *>(copy + (size_t)r * pitch)[c4] = v[q];
             r += dr;
             c4 += dc;
             if (c4 >= W4) {
@@ -406,7 +413,8 @@ __device__ __forceinline__ void stats_partial_body(const float *__restrict__ f, 
     const int titems = nrow * tw;
     for (int i = threadIdx.x; i < titems; i += blockDim.x) {
         const int r = r0 + i / tw, x = tail0 + (i - (i / tw) * tw);
-        const float a = __ldg(base + (size_t)r * pitch + x);
+        const float a = COPY ? base[(size_t)r * pitch + x] : __ldg(base + (size_t)r * pitch + x);
+        if (COPY) copy[(size_t)r * pitch + x] = a;
         if (!isfinite(a)) {
             ++bad;
             continue;
@@ -450,13 +458,15 @@ __device__ __forceinline__ void stats_partial_body(const float *__restrict__ f, 
     }
 }
 
+template <bool COPY>
 __global__ void __launch_bounds__(256) stats_partial(const float *__restrict__ f, int H, int W, int pitch,
                                                      int rows_per_block, StatPartial *__restrict__ part,
-                                                     uint32_t *__restrict__ status)
+                                                     uint32_t *__restrict__ status, float *__restrict__ copy)
 {
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *status = 0u;
-    stats_partial_body(f + (size_t)blockIdx.y * H * pitch, H, W, pitch, rows_per_block, blockIdx.x,
-                       part + (size_t)blockIdx.y * gridDim.x + blockIdx.x);
+    const size_t po = (size_t)blockIdx.y * H * pitch;
+    stats_partial_body<COPY>(f + po, H, W, pitch, rows_per_block, blockIdx.x,
+                             part + (size_t)blockIdx.y * gridDim.x + blockIdx.x, COPY ? copy + po : nullptr);
 }
 
 // 1/m, m = 0..KMAX (entry 0 unused): the beta recurrence multiplies instead of dividing.

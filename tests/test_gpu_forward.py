@@ -277,19 +277,23 @@ def test_nonfinite_input_is_passed_through_and_flagged(bf):
     assert np.array_equal(out, img, equal_nan=True)
 
 
+@pytest.mark.parametrize("inp", ["pinned", "pageable"])
 @pytest.mark.parametrize("out", ["pinned", "pinned_view", "pageable"])
 @pytest.mark.parametrize("spatial", ["iir", "fir"])
-def test_host_entry_point_matches_device_entry_point(bf, out, spatial):
-    """Host buffers give the device path's bytes. A mapped pinned result buffer
-    is written by the last pass directly; a view inside a larger pinned buffer
-    takes the same route; pageable memory takes the staged copy."""
+def test_host_entry_point_matches_device_entry_point(bf, inp, out, spatial):
+    """Host buffers give the device path's bytes. A mapped pinned input is
+    read by the statistics pass itself; a mapped pinned result buffer is
+    written by the last pass directly; a view inside a larger pinned buffer
+    takes the same route; pageable memory takes the staged copies."""
     H, W = 200, 180
     img = synthetic.make_image(H, W, 8, 10.0, 0.0, synthetic.seed_for(9, 6))
     ss = 6.0 if spatial == "iir" else 3.0
     o = bf.make_opts(20, spatial)
     need = bf.bf_gp_host_workspace_size(1, H, W, ss, o)
     ws = torch.empty(need, dtype=torch.uint8, device="cuda")
-    fh = torch.from_numpy(img).pin_memory()
+    fh = torch.from_numpy(np.ascontiguousarray(img, dtype=np.float32))
+    if inp == "pinned":
+        fh = fh.pin_memory()
     if out == "pinned":
         yh = torch.empty_like(fh).pin_memory()
         keep = yh
@@ -306,6 +310,23 @@ def test_host_entry_point_matches_device_entry_point(bf, out, spatial):
     if out == "pinned_view":
         # nothing outside the view is written
         assert torch.all(keep[:32] == -7.0) and torch.all(keep[32 + H * W:] == -7.0)
+
+
+def test_host_entry_point_nonfinite_input(bf):
+    """A NaN in a mapped pinned input reaches the device copy the statistics
+    pass writes: the plane is flagged and passed through unchanged."""
+    H, W = 64, 72
+    img = synthetic.make_image(H, W, 8, 10.0, 0.0, synthetic.seed_for(9, 8)).astype(np.float32)
+    img[5, 7] = np.nan
+    o = bf.make_opts(20, "iir")
+    need = bf.bf_gp_host_workspace_size(1, H, W, 4.0, o)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    fh = torch.from_numpy(img).pin_memory()
+    yh = torch.empty_like(fh).pin_memory()
+    s = torch.cuda.current_stream().cuda_stream
+    bf.bf_gp_forward_host(fh.data_ptr(), yh.data_ptr(), 1, H, W, 4.0, 30.0, o, ws.data_ptr(), need, s)
+    assert bf.bf_gp_get_device_status(ws.data_ptr(), s) & bf.BF_DEV_NONFINITE_IN
+    assert np.array_equal(yh.numpy(), img, equal_nan=True)
 
 
 def test_repeat_calls_are_deterministic(bf):
