@@ -205,16 +205,17 @@ bf_status bf_gp_backward(const float *f, const float *grad_y, const float *saved
                          const bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream);
 
 /*
- * Forward filter on HOST buffers: copies f (host) into the device workspace
+ * Forward filter on HOST buffers: brings f (host) into the device workspace
  * and runs bf_gp_forward there, all on `stream`; returns once the result is
- * in y (host) (it synchronises `stream`).  When all of y lies in pinned host
- * memory mapped into the device's address space (cudaHostAlloc, or
- * cudaHostRegister with cudaHostRegisterMapped) and is 4-byte aligned, the
- * last pass stores the result straight into y, overlapping the transfer with
- * the pass; otherwise the result is staged in the workspace and copied.
- * Either way y gets the same bytes as bf_gp_forward's device output, and
- * nothing outside y's planes * H * W floats is written.  Pinned host memory
- * gives full copy bandwidth for f.
+ * in y (host) (it synchronises `stream`).  A buffer "mapped" here is 4-byte
+ * aligned and lies wholly in pinned host memory mapped into the device's
+ * address space (cudaHostAlloc, or cudaHostRegister with
+ * cudaHostRegisterMapped).  A mapped f is read by the statistics pass itself,
+ * which stores the device copy; any other f is copied first.  A mapped y
+ * receives the result straight from the last pass, overlapping the transfer
+ * with the pass; any other y gets it from a copy of a staged result.  Either
+ * way y gets the same bytes as bf_gp_forward's device output, and nothing
+ * outside y's planes * H * W floats is written.
  * ws must hold bf_gp_workspace_size(...) + 2 * planes * H * W * 4 bytes
  * (bf_gp_host_workspace_size).  pitch of the host buffers is W.
  */
