@@ -391,8 +391,8 @@ def main():
         dt = reduce_max(dt, dist, "cuda")
         e2e = {"value": job_throughput(H * W, world, args.e2e_steps, dt * 1e3), "unit": "Mpixel/s",
                "h2d_bytes_per_step": 4 * H * W, "d2h_bytes_per_step": 4 * H * W,
-               "how": "bf_gp_forward_host, wall clock: pinned host f copied to the device, forward, the last pass "
-                      "storing y straight into mapped pinned host memory"}
+               "how": "bf_gp_forward_host, wall clock: the statistics pass reads the pinned host f and stores the "
+                      "device copy, forward, the last pass stores y straight into mapped pinned host memory"}
         # the host path must agree with the device path bit for bit
         step()
         torch.cuda.synchronize()
