@@ -260,10 +260,10 @@ bf_status bf_gp_forward_noalloc(const float *f, float *y, int planes, int H, int
 
 /*
  * Batched filtering: many planes of different sizes, each with its own
- * sigma_s, sigma_r and order, filtered by four launches over all planes
- * (stats, finalize, rows, columns), with the recursive Gaussian for every
- * plane.  Same method and per-plane result as bf_gp_forward with
- * BF_SPATIAL_IIR (the paper filters one image at a time; batching is an
+ * sigma_s, sigma_r and order, filtered with the recursive Gaussian: every
+ * plane's forward (the launches of bf_gp_forward) on a few streams, one
+ * graph-capturable call.  Same method and per-plane result as bf_gp_forward
+ * with BF_SPATIAL_IIR (the paper filters one image at a time; batching is an
  * implementation choice).
  *
  *   bf_gp_batched_plan_create: validates the planes (the limits of
@@ -271,7 +271,8 @@ bf_status bf_gp_forward_noalloc(const float *f, float *y, int planes, int H, int
  *     that stay valid while the plan is used) and builds the per-plane tables
  *     on the host (filter coefficients in FP64 rounded to FP32).  opts.spatial
  *     must be AUTO or IIR; opts.order is ignored (each plane's own order is
- *     used); the centre and engine options apply to every plane.  The plan
+ *     used); the centre and engine options apply to every plane (until
+ *     bf_gp_batched_plan_tune picks an engine per plane).  The plan
  *     owns host memory and BF_GP_BATCH_STREAMS CUDA streams and events of the
  *     current device (released by bf_gp_batched_plan_destroy).
  *   bf_gp_batched_plan_workspace: device bytes the plan needs (tables and
@@ -320,6 +321,37 @@ void bf_gp_batched_plan_destroy(bf_gp_plan *plan);
 bf_status bf_gp_batched_plan_stats_workspace(const bf_gp_plan *plan, size_t *bytes);
 bf_status bf_gp_batched_plane_stats(const bf_gp_plan *plan, void *ws, size_t ws_bytes, void *stream, double *t_c,
                                     double *R);
+
+/*
+ * Autotuner.  The engines of the recursive filter (opts.engine 0..3) and the
+ * fused or two-pass form of the FIR filter (opts.fir_two_pass) compute the
+ * same filter with different kernels; which is fastest depends on the shape.
+ *
+ *   bf_gp_autotune: for the shape class of the call (device, planes, H, W,
+ *     pitch, the spatial operator opts resolves to, K and the FIR half-width)
+ *     returns the fastest candidate in opts->engine / opts->fir_two_pass (the
+ *     other fields are left as given).  On the first call for a class it
+ *     times every candidate the workspace can hold: one untimed forward, then
+ *     `reps` forwards (<= 0 selects 5) between two CUDA events on `stream`,
+ *     on the caller's f, y and ws (y is overwritten), and waits for them;
+ *     later calls return the stored choice without launching anything.  ms
+ *     (NULL, or BF_GP_TUNE_CANDIDATES floats) gets each candidate's mean time
+ *     in milliseconds in candidate order (recursive: engines 0..3; FIR: fused,
+ *     two-pass), -1 where nothing was timed.  Not capturable into a graph.
+ *     BF_ERR_UNSUPPORTED if no candidate runs.
+ *   bf_gp_autotune_clear: forgets every stored choice.
+ *   bf_gp_batched_plan_tune: runs bf_gp_autotune for every plane of an
+ *     uploaded plan (on the plane's own buffers and part of ws, so the planes'
+ *     outputs are overwritten) and makes bf_gp_batched use each plane's choice.
+ *   bf_gp_batched_plan_engines: the engine each plane runs with (n entries).
+ */
+#define BF_GP_TUNE_CANDIDATES 4
+bf_status bf_gp_autotune(const float *f, float *y, int planes, int H, int W, int pitch, float sigma_s,
+                         float sigma_r, bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream, int reps,
+                         float *ms);
+void bf_gp_autotune_clear(void);
+bf_status bf_gp_batched_plan_tune(bf_gp_plan *plan, void *ws, size_t ws_bytes, void *stream, int reps);
+bf_status bf_gp_batched_plan_engines(const bf_gp_plan *plan, int *engines);
 
 /*
  * Read the device status word written by the last call that used `ws`

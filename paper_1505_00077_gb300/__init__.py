@@ -111,6 +111,11 @@ def _load():
         "bf_gp_joint_workspace_size": (c_int, [c_int, c_int, c_int, c_float, P(bf_gp_opts), P(c_size_t)]),
         "bf_gp_forward_joint": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_float, c_float,
                                         P(bf_gp_opts), c_void_p, c_size_t, c_void_p]),
+        "bf_gp_autotune": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_float, c_float, P(bf_gp_opts),
+                                   c_void_p, c_size_t, c_void_p, c_int, P(c_float)]),
+        "bf_gp_autotune_clear": (None, []),
+        "bf_gp_batched_plan_tune": (c_int, [c_void_p, c_void_p, c_size_t, c_void_p, c_int]),
+        "bf_gp_batched_plan_engines": (c_int, [c_void_p, P(c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -129,7 +134,8 @@ def exported_symbols():
             "bf_gp_batched_plan_stats_workspace", "bf_gp_batched_plane_stats", "bf_gp_forward_noalloc",
             "bf_gp_host_workspace_size", "bf_gp_forward_host",
             "bf_gp_get_device_status", "bf_gp_get_plane_stats", "bf_gp_order_for_tol", "bf_gp_order_fp32_limit",
-            "bf_gp_joint_workspace_size", "bf_gp_forward_joint"]
+            "bf_gp_joint_workspace_size", "bf_gp_forward_joint", "bf_gp_autotune", "bf_gp_autotune_clear",
+            "bf_gp_batched_plan_tune", "bf_gp_batched_plan_engines"]
 
 
 def status_string(status: int) -> str:
@@ -253,6 +259,37 @@ def bf_gp_batched(plan, ws_ptr, ws_bytes, stream=0) -> None:
     _check(_load().bf_gp_batched(_vp(plan), _vp(ws_ptr), int(ws_bytes), _vp(stream)), "bf_gp_batched")
 
 
+BF_GP_TUNE_CANDIDATES = 4
+
+
+def bf_gp_autotune(f_ptr, y_ptr, planes, H, W, pitch, sigma_s, sigma_r, opts, ws_ptr, ws_bytes, stream=0, reps=0):
+    """Fastest engine (recursive filter) or FIR form for this shape class,
+    written into opts (a bf_gp_opts, modified in place and returned) with each
+    candidate's mean time in ms (-1: not timed, e.g. a stored choice).  Times
+    on the given buffers (y is overwritten) and synchronises; see include/bf_gp.h."""
+    ms = (ctypes.c_float * BF_GP_TUNE_CANDIDATES)()
+    _check(_load().bf_gp_autotune(_vp(f_ptr), _vp(y_ptr), int(planes), int(H), int(W), int(pitch), float(sigma_s),
+                                  float(sigma_r), ctypes.byref(opts), _vp(ws_ptr), int(ws_bytes), _vp(stream),
+                                  int(reps), ms),
+           "bf_gp_autotune")
+    return opts, [float(v) for v in ms]
+
+
+def bf_gp_autotune_clear() -> None:
+    _load().bf_gp_autotune_clear()
+
+
+def bf_gp_batched_plan_tune(plan, ws_ptr, ws_bytes, stream=0, reps=0) -> None:
+    _check(_load().bf_gp_batched_plan_tune(_vp(plan), _vp(ws_ptr), int(ws_bytes), _vp(stream), int(reps)),
+           "bf_gp_batched_plan_tune")
+
+
+def bf_gp_batched_plan_engines(plan, n):
+    e = (ctypes.c_int * n)()
+    _check(_load().bf_gp_batched_plan_engines(_vp(plan), e), "bf_gp_batched_plan_engines")
+    return [int(v) for v in e]
+
+
 def bf_gp_batched_plan_stats_workspace(plan) -> int:
     n = ctypes.c_size_t(0)
     _check(_load().bf_gp_batched_plan_stats_workspace(_vp(plan), ctypes.byref(n)), "bf_gp_batched_plan_stats_workspace")
@@ -286,9 +323,13 @@ class BatchedFilter:
     (bf_gp_order_for_tol), with R = max |f - t_c| measured on the device by
     the plan's statistics pass, capped at max_order and at the largest order
     whose terms FP32 can hold (bf_gp_order_fp32_limit).  The chosen orders are
-    in self.orders."""
+    in self.orders.
 
-    def __init__(self, planes, order_default=20, t_c=None, tol=None, max_order=MAX_ORDER):
+    With autotune, each plane runs with the engine the autotuner measures
+    fastest for its shape (bf_gp_batched_plan_tune; the outputs are written
+    while it times).  The engines are in self.engines."""
+
+    def __init__(self, planes, order_default=20, t_c=None, tol=None, max_order=MAX_ORDER, autotune=False):
         import torch
         self._keep = []
         spec = []
@@ -308,6 +349,10 @@ class BatchedFilter:
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
         bf_gp_batched_plan_upload(self.plan, self.ws.data_ptr(), self.ws_bytes,
                                   torch.cuda.current_stream().cuda_stream)
+        if autotune:
+            bf_gp_batched_plan_tune(self.plan, self.ws.data_ptr(), self.ws_bytes,
+                                    torch.cuda.current_stream().cuda_stream)
+        self.engines = bf_gp_batched_plan_engines(self.plan, len(spec))
 
     @staticmethod
     def _adaptive_orders(spec, opts, tol, max_order):
@@ -418,11 +463,14 @@ def workspace(nbytes: int, device=None):
 
 
 def bilateral_gp(x, sigma_s: float, sigma_r: float, order: int = 20, spatial="auto", t_c=None,
-                 fir_halfwidth: int = 0, out=None, ws=None):
+                 fir_halfwidth: int = 0, out=None, ws=None, autotune=False):
     """Filter a float32 CUDA tensor [..., H, W] (leading dims are independent planes).
 
     Every plane gets its own centre (the plane mean unless t_c is given) and
-    scale.  Runs asynchronously on torch's current stream.
+    scale.  Runs asynchronously on torch's current stream.  With autotune, the
+    engine (or FIR form) is the autotuner's choice for this shape class: the
+    first call for a class times the candidates (and waits for them), later
+    calls reuse the choice.
     """
     import torch
     if not (x.is_cuda and x.dtype == torch.float32):
@@ -439,6 +487,9 @@ def bilateral_gp(x, sigma_s: float, sigma_r: float, order: int = 20, spatial="au
         raise ValueError(f"workspace too small: {buf.numel()} < {need}")
     y = torch.empty_like(xc) if out is None else out
     stream = torch.cuda.current_stream(xc.device).cuda_stream
+    if autotune:
+        bf_gp_autotune(xc.data_ptr(), y.data_ptr(), planes, H, W, W, sigma_s, sigma_r, opts, buf.data_ptr(),
+                       buf.numel(), stream)
     bf_gp_forward(xc.data_ptr(), y.data_ptr(), planes, H, W, W, sigma_s, sigma_r, opts, buf.data_ptr(),
                   buf.numel(), stream)
     return y

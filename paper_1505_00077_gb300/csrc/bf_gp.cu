@@ -10,7 +10,9 @@
 #include <cstddef>
 #include <cstring>
 #include <new>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "../../include/bf_gp.h"
@@ -936,6 +938,7 @@ struct bf_gp_plan {
     // off_planes + sub_off[i]), spread over the plan's streams
     std::vector<bf_gp_plane> specs;
     bf_gp_opts base;
+    std::vector<int> engine;  // per plane: base.engine, or the autotuner's choice (bf_gp_batched_plan_tune)
     std::vector<size_t> sub_off, sub_bytes;
     size_t off_statusofs = 0;  // in the tables: byte offset of every plane's status word, n x uint64
     int nstreams = 0;
@@ -1014,6 +1017,7 @@ bf_status bf_gp_batched_plan_create(const bf_gp_plane *planes, int n, const bf_g
     }
     pl->specs.assign(planes, planes + n);
     pl->base = *opts;
+    pl->engine.assign(n, opts->engine);
     pl->sub_off = pl->plane_off;
     pl->sub_bytes.resize(n);
     for (int i = 0; i < n; ++i)
@@ -1183,6 +1187,7 @@ bf_status bf_gp_batched(const bf_gp_plan *plan, void *ws, size_t ws_bytes, void 
         bf_gp_opts o = plan->base;
         o.order = q.order;
         o.spatial = BF_SPATIAL_IIR;
+        o.engine = plan->engine[i];
         cudaStream_t si = plan->streams[i % plan->nstreams];
         Call c;
         st = prepare(q.f, q.y, 1, q.H, q.W, q.pitch, q.sigma_s, q.sigma_r, &o, wsb + plan->off_planes + plan->sub_off[i],
@@ -1205,5 +1210,143 @@ bf_status bf_gp_batched(const bf_gp_plan *plan, void *ws, size_t ws_bytes, void 
 }
 
 void bf_gp_batched_plan_destroy(bf_gp_plan *plan) { delete plan; }
+
+// ------------------------------------------------------------------ autotuner
+//
+// The engines of the recursive filter (and the fused or two-pass form of the
+// FIR filter) compute the same filter with different kernels; which is
+// fastest depends on the shape (measured on GB300: the tensor-core row pass
+// wins from 2048^2 up, the CUDA-core row pass on small and thin images).
+// The tuner times every candidate on the caller's own buffers and keeps the
+// winner per shape class for the life of the process.
+
+}  // extern "C"
+
+namespace {
+
+// shape class: device, planes, H, W, pitch, resolved spatial operator, K, FIR half-width
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int>;
+std::mutex g_tune_mutex;
+std::map<TuneKey, bf_gp_opts> g_tune;
+
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~EventPair()
+    {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+bf_status bf_gp_autotune(const float *f, float *y, int planes, int H, int W, int pitch, float sigma_s,
+                         float sigma_r, bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream, int reps,
+                         float *ms)
+{
+    if (!f || !y || !opts || !ws) return BF_ERR_INVALID_ARG;
+    if (ms)
+        for (int i = 0; i < BF_GP_TUNE_CANDIDATES; ++i) ms[i] = -1.f;
+    Plan p;
+    bf_status st = make_plan(planes, H, W, sigma_s, opts, &p);
+    if (st != BF_OK) return st;
+    int dev = 0;
+    BF_CUDA(cudaGetDevice(&dev));
+    const TuneKey key{dev, planes, H, W, pitch, p.spatial, p.K, p.spatial == BF_SPATIAL_FIR ? p.w : 0};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            opts->engine = it->second.engine;
+            opts->fir_two_pass = it->second.fir_two_pass;
+            return BF_OK;
+        }
+    }
+    // candidates, in the order their times are reported
+    bf_gp_opts cand[BF_GP_TUNE_CANDIDATES];
+    int nc = 0;
+    if (p.spatial == BF_SPATIAL_IIR) {
+        for (int e = 0; e < 4; ++e) {
+            cand[nc] = *opts;
+            cand[nc++].engine = e;
+        }
+    } else if (p.spatial == BF_SPATIAL_FIR) {
+        for (int t = 0; t < 2; ++t) {
+            cand[nc] = *opts;
+            cand[nc++].fir_two_pass = t;
+        }
+    } else {
+        cand[nc++] = *opts;
+    }
+    if (reps <= 0) reps = 5;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    EventPair ev;
+    BF_CUDA(cudaEventCreate(&ev.a));
+    BF_CUDA(cudaEventCreate(&ev.b));
+    int best = -1;
+    float best_ms = 0.f;
+    for (int i = 0; i < nc; ++i) {
+        size_t need = 0;
+        if (bf_gp_workspace_size(planes, H, W, sigma_s, &cand[i], &need) != BF_OK || need > ws_bytes) continue;
+        // one untimed run; a candidate the kernels do not cover is skipped
+        if (bf_gp_forward(f, y, planes, H, W, pitch, sigma_s, sigma_r, &cand[i], ws, ws_bytes, stream) != BF_OK)
+            continue;
+        BF_CUDA(cudaEventRecord(ev.a, s));
+        for (int r = 0; r < reps; ++r) {
+            st = bf_gp_forward(f, y, planes, H, W, pitch, sigma_s, sigma_r, &cand[i], ws, ws_bytes, stream);
+            if (st != BF_OK) return st;
+        }
+        BF_CUDA(cudaEventRecord(ev.b, s));
+        BF_CUDA(cudaEventSynchronize(ev.b));
+        float t = 0.f;
+        BF_CUDA(cudaEventElapsedTime(&t, ev.a, ev.b));
+        t /= (float)reps;
+        if (ms) ms[i] = t;
+        if (best < 0 || t < best_ms) {
+            best = i;
+            best_ms = t;
+        }
+    }
+    if (best < 0) return BF_ERR_UNSUPPORTED;
+    opts->engine = cand[best].engine;
+    opts->fir_two_pass = cand[best].fir_two_pass;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune[key] = *opts;
+    return BF_OK;
+}
+
+void bf_gp_autotune_clear(void)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune.clear();
+}
+
+bf_status bf_gp_batched_plan_tune(bf_gp_plan *plan, void *ws, size_t ws_bytes, void *stream, int reps)
+{
+    if (!plan || !ws) return BF_ERR_INVALID_ARG;
+    if (ws != plan->uploaded_ws || ws_bytes < plan->total) return BF_ERR_WORKSPACE;
+    char *wsb = static_cast<char *>(ws);
+    for (int i = 0; i < plan->n; ++i) {
+        const bf_gp_plane &q = plan->specs[i];
+        bf_gp_opts o = plan->base;
+        o.order = q.order;
+        o.spatial = BF_SPATIAL_IIR;
+        bf_status st = bf_gp_autotune(q.f, q.y, 1, q.H, q.W, q.pitch, q.sigma_s, q.sigma_r, &o,
+                                      wsb + plan->off_planes + plan->sub_off[i], plan->sub_bytes[i], stream, reps,
+                                      nullptr);
+        if (st != BF_OK) return st;
+        plan->engine[i] = o.engine;
+    }
+    return BF_OK;
+}
+
+bf_status bf_gp_batched_plan_engines(const bf_gp_plan *plan, int *engines)
+{
+    if (!plan || !engines) return BF_ERR_INVALID_ARG;
+    for (int i = 0; i < plan->n; ++i) engines[i] = plan->engine[i];
+    return BF_OK;
+}
 
 }  // extern "C"

@@ -115,6 +115,18 @@ def test_forward_rejects_bad_pointers_before_any_cuda_call():
     assert e.value.status == bfgp.BF_ERR_INVALID_ARG
 
 
+def test_autotuner_rejects_bad_pointers_before_any_cuda_call():
+    o = bfgp.make_opts()
+    for args in ((0, 256), (256, 0)):
+        with pytest.raises(bfgp.BFError) as e:
+            bfgp.bf_gp_autotune(args[0], args[1], 1, 16, 16, 16, 3.0, 30.0, o, 1 << 20, 1 << 20)
+        assert e.value.status == bfgp.BF_ERR_INVALID_ARG
+    with pytest.raises(bfgp.BFError) as e:
+        bfgp.bf_gp_batched_plan_tune(0, 1 << 20, 1 << 20)
+    assert e.value.status == bfgp.BF_ERR_INVALID_ARG
+    bfgp.bf_gp_autotune_clear()  # no device needed
+
+
 def test_order_rule():
     """Smallest even N whose Gauss-polynomial kernel error is <= eps on [-R, R]."""
     assert bfgp.bf_gp_order_for_tol(30.0, 127.5, 1e-3) == 34
