@@ -115,7 +115,11 @@ int bf_gp_version(void);
 /*
  * Workspace bytes a forward call on `planes` planes of H x W needs with these
  * options (sigma_s matters only for the spatial-operator choice; pass the
- * value you will use).  Returns BF_ERR_INVALID_ARG for bad sizes.
+ * value you will use).  Returns BF_ERR_INVALID_ARG for bad sizes and
+ * BF_ERR_UNSUPPORTED outside the sizes the kernels cover: W <= 8192 (a row is
+ * at most 512 threads of 16 samples); with the recursive filter H <= 4096 (a
+ * column is one thread-block cluster of at most 8 CTAs of 512 rows); FIR
+ * half-width <= 12; box passes x half-width <= 12.
  */
 bf_status bf_gp_workspace_size(int planes, int H, int W, float sigma_s, const bf_gp_opts *opts,
                                size_t *bytes);
