@@ -117,9 +117,12 @@ int bf_gp_version(void);
  * options (sigma_s matters only for the spatial-operator choice; pass the
  * value you will use).  Returns BF_ERR_INVALID_ARG for bad sizes and
  * BF_ERR_UNSUPPORTED outside the sizes the kernels cover: W <= 8192 (a row is
- * at most 512 threads of 16 samples); with the recursive filter H <= 4096 (a
- * column is one thread-block cluster of at most 8 CTAs of 512 rows); FIR
- * half-width <= 12; box passes x half-width <= 12.
+ * at most 512 threads of 16 samples); with the recursive filter a column is
+ * one thread-block cluster of 512-row CTAs, so H <= 8192 with engines 0 and 1
+ * (clusters of more than 8 CTAs use the non-portable cluster size; a device
+ * that cannot hold such a cluster makes the call return BF_ERR_UNSUPPORTED)
+ * and H <= 4096 with engines 2 and 3; FIR half-width <= 12; box passes x
+ * half-width <= 12.
  */
 bf_status bf_gp_workspace_size(int planes, int H, int W, float sigma_s, const bf_gp_opts *opts,
                                size_t *bytes);

@@ -39,7 +39,7 @@ bf_status cuda_fail(cudaError_t e, const char *where)
 constexpr int ROW_C = 16;           // samples per thread along a row
 constexpr int COL_C = 16;           // rows per thread along a column
 constexpr int COL_ROWS_PER_CTA = COL_ROWS;  // 32 chunks of COL_C rows
-constexpr int COL_MAX_CLUSTER = 8;
+constexpr int COL_MAX_CLUSTER_TC = 8;  // column cluster limit of the tensor-core column passes
 constexpr size_t HDR_BYTES = 4096;  // status word + spare
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -124,7 +124,8 @@ bf_status make_plan(int planes, int H, int W, float sigma_s, const bf_gp_opts *o
     p->col_tc = joint ? 0 : (o->engine == 2 ? 1 : (o->engine == 3 ? 2 : 0));
     p->wpr = next_pow2((W + 511) / 512);
     if (sp == BF_SPATIAL_IIR && p->row_tc && p->wpr > 16) return BF_ERR_UNSUPPORTED;
-    if (sp == BF_SPATIAL_IIR && p->CL > COL_MAX_CLUSTER) return BF_ERR_UNSUPPORTED;  // columns longer than 4096
+    // columns longer than 8192 (CUDA-core column pass) or 4096 (tensor-core column passes)
+    if (sp == BF_SPATIAL_IIR && p->CL > (p->col_tc ? COL_MAX_CLUSTER_TC : COL_MAX_CTAS)) return BF_ERR_UNSUPPORTED;
     const long long px = (long long)H * W;
     // stats partials: at most 1024 blocks, at least 2048 pixels each (small images still spread
     // over many SMs; every block's loads are independent)
@@ -535,8 +536,9 @@ bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
             if (tcore)
                 BF_CUDA(cudaFuncSetAttribute(col_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         }
-        if (!tcore)
-            BF_CUDA(cudaFuncSetAttribute(col_iir<COL_C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        // the column pass for up to 4096 rows, or its instantiation for 16-CTA clusters
+        auto col_kernel = c.p.CL > 8 ? col_iir<COL_C, MODE, COL_MAX_CTAS> : col_iir<COL_C, MODE, 8>;
+        if (!tcore) BF_CUDA(cudaFuncSetAttribute(col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         cudaLaunchConfig_t cfg;
         std::memset(&cfg, 0, sizeof cfg);
         cfg.gridDim = dim3(strips * c.p.CL, planes, 1);
@@ -553,7 +555,19 @@ bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
         if constexpr (MODE != MODE_JOINT) {
             if (tcore) BF_CUDA(cudaLaunchKernelEx(&cfg, col_tc<MODE>, c.ca, cc, tm));
         }
-        if (!tcore) BF_CUDA(cudaLaunchKernelEx(&cfg, col_iir<COL_C, MODE>, c.ca, cc));
+        if (!tcore) {
+            if (c.p.CL > 8) {
+                // a column of more than 4096 rows: a cluster beyond the portable 8 CTAs, if the
+                // device can hold one with this kernel's resources
+                BF_CUDA(cudaFuncSetAttribute(col_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+                int nclusters = 0;
+                if (cudaOccupancyMaxActiveClusters(&nclusters, col_kernel, &cfg) != cudaSuccess || nclusters < 1) {
+                    cudaGetLastError();
+                    return BF_ERR_UNSUPPORTED;
+                }
+            }
+            BF_CUDA(cudaLaunchKernelEx(&cfg, col_kernel, c.ca, cc));
+        }
     }
     BF_CUDA(cudaGetLastError());
     return BF_OK;

@@ -1218,6 +1218,9 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 constexpr int COL_TILE_BUFS = 4;  // channel tiles in flight in the recursive column pass
+// CTAs of 512 rows in one column cluster of the recursive column pass (more
+// than 8 is a non-portable cluster size the launch has to opt into)
+constexpr int COL_MAX_CTAS = 16;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -1236,8 +1239,9 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)_
 //   4. every warp adds the carry from the other CTAs (local shared memory, one
 //      lane per column x pole x direction), then each half gets its entering
 //      states, the out-of-half response and the Horner step.
-// grid (strips * CL, planes), block 256, cluster (CL, 1, 1).
-template <int C, int MODE>
+// grid (strips * CL, planes), block 256, cluster (CL, 1, 1), CL <= MAXCTA
+// (8: the portable cluster size; COL_MAX_CTAS: columns of up to 8192 rows).
+template <int C, int MODE, int MAXCTA = 8>
 __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf, int strip, int plane)
 {
     static_assert(C == 16, "column chunks are two halves of 8 rows");
@@ -1249,7 +1253,7 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
     // CTAs of the cluster (causal ones by lower ranks, anticausal ones by higher ranks), each
     // already carried across the CTAs between source and destination; the slots no CTA writes
     // stay zero, so the carry entering this CTA is the plain sum over all slots
-    __shared__ float2 inc[2][8][8][NP][2];
+    __shared__ float2 inc[2][MAXCTA][8][NP][2];
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int col = lane & 7, l4 = lane >> 3;
@@ -1305,7 +1309,7 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
     const float p32r = gm == 0 ? cf.Pr[0][5] : cf.Pr[1][5], p32i = gm == 0 ? cf.Pi[0][5] : cf.Pi[1][5];
     {
         float2 *z = &inc[0][0][0][0][0];
-        for (int e = tid; e < 2 * 8 * 8 * NP * 2; e += blockDim.x) z[e] = make_float2(0.f, 0.f);
+        for (int e = tid; e < 2 * MAXCTA * 8 * NP * 2; e += blockDim.x) z[e] = make_float2(0.f, 0.f);
     }
     cl.sync();  // zeroed before any peer pushes
 
@@ -1439,7 +1443,7 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
             const float2 *src = &inc[par][0][gcol][gm][gdir];
             float Xr = 0.f, Xi = 0.f;
 #pragma unroll
-            for (int s = 0; s < 8; ++s) {
+            for (int s = 0; s < MAXCTA; ++s) {
                 const float2 t = src[s * 8 * NP * 2];
                 Xr += t.x;
                 Xi += t.y;
@@ -1920,10 +1924,10 @@ __global__ void __launch_bounds__(256, MODE == MODE_SAVE ? 1 : 2) col_tc5(ColArg
     col_tc5_body<MODE>(a, cf, um, blockIdx.x / (int)cg::this_cluster().num_blocks(), blockIdx.y);
 }
 
-template <int C, int MODE>
+template <int C, int MODE, int MAXCTA = 8>
 __global__ void __launch_bounds__(256, MODE == MODE_SAVE ? 1 : 2) col_iir(ColArgs a, IIRCoef cf)
 {
-    col_iir_body<C, MODE>(a, cf, blockIdx.x / (int)cg::this_cluster().num_blocks(), blockIdx.y);
+    col_iir_body<C, MODE, MAXCTA>(a, cf, blockIdx.x / (int)cg::this_cluster().num_blocks(), blockIdx.y);
 }
 
 // Column pass for the FIR filter: 2-D tiles of 32 columns x 64 rows; the

@@ -73,14 +73,19 @@ def test_bad_options_rejected():
 
 
 def test_unsupported_sizes_reported():
-    # FIR window wider than the kernels' 12 taps, rows longer than 8192, IIR columns longer than 4096
+    # FIR window wider than the kernels' 12 taps, rows longer than 8192, IIR columns longer than 8192
+    # (CUDA-core column pass) or 4096 (tensor-core column passes)
     with pytest.raises(bfgp.BFError) as e:
         bfgp.bf_gp_workspace_size(1, 64, 64, 5.0, bfgp.make_opts(20, "fir"))
     assert e.value.status == bfgp.BF_ERR_UNSUPPORTED
     with pytest.raises(bfgp.BFError):
         bfgp.bf_gp_workspace_size(1, 16, 8193, 5.0, bfgp.make_opts(20, "iir"))
-    with pytest.raises(bfgp.BFError):
-        bfgp.bf_gp_workspace_size(1, 4097, 16, 5.0, bfgp.make_opts(20, "iir"))
+    for engine, hmax in ((0, 8192), (1, 8192), (2, 4096), (3, 4096)):
+        o = bfgp.make_opts(20, "iir", engine=engine)
+        with pytest.raises(bfgp.BFError) as e:
+            bfgp.bf_gp_workspace_size(1, hmax + 1, 16, 5.0, o)
+        assert e.value.status == bfgp.BF_ERR_UNSUPPORTED
+        assert bfgp.bf_gp_workspace_size(1, hmax, 16, 5.0, o) > 0
     assert bfgp.bf_gp_workspace_size(1, 4096, 8192, 5.0, bfgp.make_opts(20, "iir")) > 0
 
 

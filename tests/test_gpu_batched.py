@@ -86,7 +86,7 @@ def test_batched_rejects_bad_plans(bf):
     with pytest.raises(bf.BFError):
         bf.bf_gp_batched_plan_create([(x.data_ptr(), x.data_ptr(), 16, 16, 8, 2.0, 30.0, 20)])  # pitch < W
     with pytest.raises(bf.BFError):
-        bf.bf_gp_batched_plan_create([(x.data_ptr(), x.data_ptr(), 5000, 16, 16, 2.0, 30.0, 20)])  # H > 4096
+        bf.bf_gp_batched_plan_create([(x.data_ptr(), x.data_ptr(), 9000, 16, 16, 2.0, 30.0, 20)])  # H > 8192
     with pytest.raises(bf.BFError):
         bf.bf_gp_batched_plan_create([(x.data_ptr(), x.data_ptr(), 16, 9000, 9000, 2.0, 30.0, 20)])  # W > 8192
 

@@ -95,12 +95,38 @@ def test_ragged_shapes(bf, shape, spatial, ss):
     check(run_gpu(bf, img, ss, 30.0, 12, spatial), ref)
 
 
-@pytest.mark.parametrize("H", [511, 512, 513, 1024, 2047, 2049, 3000, 4096])
+@pytest.mark.parametrize("H", [511, 512, 513, 1024, 2047, 2049, 3000, 4096, 4097, 6000, 8192])
 def test_iir_column_cluster_sizes(bf, H):
-    """Columns spanning 1..8 CTAs of the clustered column pass."""
+    """Columns spanning 1..16 CTAs of the clustered column pass (more than 8:
+    the non-portable cluster size)."""
     img = synthetic.make_image(H, 24, 8, 10.0, 30.0, synthetic.seed_for(9, H))
     ref = oracle.gp_bf(img.astype(np.float64), 7.0, 40.0, 10, "iir")
     check(run_gpu(bf, img, 7.0, 40.0, 10, "iir"), ref)
+
+
+@pytest.mark.parametrize("engine", [0, 1])
+@pytest.mark.parametrize("H", [4600, 8192])
+def test_iir_tall_columns_engines_and_training(bf, H, engine):
+    """Columns of more than 4096 rows on both CUDA-core column engines, and the
+    forward that saves the sums for the backward pass (one CTA per SM, so its
+    16-CTA cluster needs 16 SMs of one GPC)."""
+    W = 40
+    img = synthetic.make_image(H, W, 8, 10.0, 30.0, synthetic.seed_for(9, H + engine))
+    ref = oracle.gp_bf(img.astype(np.float64), 9.0, 40.0, 10, "iir")
+    o = bf.make_opts(10, "iir", engine=engine)
+    x = torch.from_numpy(img).cuda()
+    need = bf.bf_gp_workspace_size(1, H, W, 9.0, o)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    y = torch.full_like(x, float("nan"))
+    bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, H, W, W, 9.0, 40.0, o, ws.data_ptr(), need, s)
+    assert bf.bf_gp_get_device_status(ws.data_ptr(), s) == 0
+    check(y.cpu().numpy().astype(np.float64), ref)
+    saved = torch.empty((1, 4, H, W), dtype=torch.float32, device="cuda")
+    y2 = torch.full_like(x, float("nan"))
+    bf.bf_gp_forward_train(x.data_ptr(), y2.data_ptr(), saved.data_ptr(), 1, H, W, W, 9.0, 40.0, o, ws.data_ptr(),
+                           need, s)
+    check(y2.cpu().numpy().astype(np.float64), ref)
 
 
 @pytest.mark.parametrize("W", [511, 512, 513, 1024, 4095, 4096, 4097, 8192])
