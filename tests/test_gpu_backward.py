@@ -67,6 +67,20 @@ def test_backward_matches_oracle_adjoint(bf, spatial, ss, shape, t_c):
     assert abs(gsr[0] - ref_s) <= RTOL * max(abs(ref_s), 1e-6 * np.abs(ref_g).max() * H * W), (gsr[0], ref_s)
 
 
+@pytest.mark.parametrize("H", [3000, 6000])
+def test_backward_tall_columns(bf, H):
+    """Columns of more than 4096 rows: the adjoint column pass in 16-CTA
+    clusters (and one of up to 8 CTAs for comparison)."""
+    W = 24
+    img = synthetic.make_image(H, W, 8, 10.0, 0.0, synthetic.seed_for(5, 7000 + H))
+    gy = np.random.default_rng(H).normal(size=(H, W)).astype(np.float32)
+    y, gx, gsr, bits = gpu_fwd_bwd(bf, img[None], gy[None], 9.0, 40.0, 12, "iir")
+    assert bits == 0
+    ref_g, ref_s = oracle.gp_adjoint(img.astype(np.float64), 9.0, 40.0, 12, gy.astype(np.float64), "iir")
+    check_grad(gx[0], ref_g, "dL/df")
+    assert abs(gsr[0] - ref_s) <= RTOL * max(abs(ref_s), 1e-6 * np.abs(ref_g).max() * H * W), (gsr[0], ref_s)
+
+
 def test_config5_batch(bf):
     """16 x 1 x 512^2, sigma_s 5, sigma_r 25, N 20 (recursive filter): every plane's
     forward against O2, and the adjoint of four of them against O3."""
