@@ -531,7 +531,10 @@ bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
         deriche_coefs((double)sigma_s, tcore ? TC_C : COL_C, &cc);
         TCMat tm;
         if (tcore) tc_mats((double)sigma_s, &tm);
-        const size_t smem = tcore ? sizeof(float) * 2 * 512 * 8 : sizeof(float) * COL_TILE_BUFS * COL_TILE_FLOATS;
+        // the CUDA-core pass: the channel tiles, and for the saving forward its dp, dq ([2 C][256])
+        const size_t smem = tcore ? sizeof(float) * 2 * 512 * 8
+                                  : sizeof(float) * (COL_TILE_BUFS * COL_TILE_FLOATS +
+                                                     (MODE == MODE_SAVE ? 2 * COL_C * 256 : 0));
         if constexpr (MODE != MODE_JOINT) {
             if (tcore)
                 BF_CUDA(cudaFuncSetAttribute(col_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -1043,15 +1043,29 @@ struct ColArgs {
 //            the last channel (m = 0) turns into Q~ = Psi_0 + s^2 u q
 //   save:    also dp = sum_{m>=2} m(m-1) u^{m-2} Psi_m, dq = sum_{1..N} m u^{m-1} Psi_m
 //   adjoint: with c_m the filtered adjoint channel, p = A = sum m c_m u^{m-1}, q = B = sum c_m u^m
-template <int RPT, int MODE>
+// DSMEM: dp and dq live in shared memory (sd[j * 256] and sd[(RPT + j) * 256],
+// sd pointing at this thread's column of a [2 RPT][256] block), which frees
+// 2 RPT registers per thread.
+template <int RPT, int MODE, bool DSMEM = false>
 struct Combine {
-    float u[RPT], p[RPT], q[RPT], dp[MODE == MODE_SAVE ? RPT : 1], dq[MODE == MODE_SAVE ? RPT : 1];
+    static constexpr bool SAVE_REG = MODE == MODE_SAVE && !DSMEM;
+    float u[RPT], p[RPT], q[RPT], dp[SAVE_REG ? RPT : 1], dq[SAVE_REG ? RPT : 1];
+    float *sd;
     __device__ __forceinline__ void init(float uu, int j)
     {
         u[j] = uu;
         p[j] = q[j] = 0.f;
-        if (MODE == MODE_SAVE) dp[j] = dq[j] = 0.f;
+        if (MODE == MODE_SAVE) {
+            if (DSMEM) {
+                sd[j * 256] = 0.f;
+                sd[(RPT + j) * 256] = 0.f;
+            } else {
+                dp[j] = dq[j] = 0.f;
+            }
+        }
     }
+    __device__ __forceinline__ float get_dp(int j) const { return DSMEM ? sd[j * 256] : dp[j]; }
+    __device__ __forceinline__ float get_dq(int j) const { return DSMEM ? sd[(RPT + j) * 256] : dq[j]; }
     __device__ __forceinline__ void step(int m, int N, float s2, const float (&y)[RPT])
     {
         if (MODE == MODE_JOINT) {  // descending m: U_n (odd m) into p, D_n (even m) into q, Horner in u
@@ -1094,11 +1108,21 @@ struct Combine {
             const float mm1 = mk * (float)(m - 1);
             if (m >= 2) {  // dp's lowest term is m = 2 (power u^0)
 #pragma unroll
-                for (int j = 0; j < RPT; ++j) dp[j] = fmaf(u[j], dp[j], mm1 * y[j]);
+                for (int j = 0; j < RPT; ++j) {
+                    if (DSMEM)
+                        sd[j * 256] = fmaf(u[j], sd[j * 256], mm1 * y[j]);
+                    else
+                        dp[j] = fmaf(u[j], dp[j], mm1 * y[j]);
+                }
             }
             if (m <= N) {
 #pragma unroll
-                for (int j = 0; j < RPT; ++j) dq[j] = fmaf(u[j], dq[j], mk * y[j]);
+                for (int j = 0; j < RPT; ++j) {
+                    if (DSMEM)
+                        sd[(RPT + j) * 256] = fmaf(u[j], sd[(RPT + j) * 256], mk * y[j]);
+                    else
+                        dq[j] = fmaf(u[j], dq[j], mk * y[j]);
+                }
             }
         }
         if (m <= N) {
@@ -1115,9 +1139,10 @@ struct AdjSums {
 };
 
 // Writes the result for one pixel (r, x) of the plane.
-template <int RPT, int MODE>
+template <int RPT, int MODE, bool DSMEM>
 __device__ __forceinline__ void finish_pixel(const ColArgs &a, const PlaneParams &P, int plane, int r, int x,
-                                             const Combine<RPT, MODE> &cb, int j, bool &nonpos, AdjSums &sums)
+                                             const Combine<RPT, MODE, DSMEM> &cb, int j, bool &nonpos,
+                                             AdjSums &sums)
 {
     const size_t pix = ((size_t)plane * a.H + r) * a.pitch + x;
     if (MODE == MODE_ADJ) {
@@ -1165,8 +1190,8 @@ __device__ __forceinline__ void finish_pixel(const ColArgs &a, const PlaneParams
     if (MODE == MODE_SAVE) {
         a.saved[saved_idx(plane, 0, a.H, a.W, r, x)] = cb.p[j];
         a.saved[saved_idx(plane, 1, a.H, a.W, r, x)] = Q;
-        a.saved[saved_idx(plane, 2, a.H, a.W, r, x)] = cb.dp[j];
-        a.saved[saved_idx(plane, 3, a.H, a.W, r, x)] = cb.dq[j];
+        a.saved[saved_idx(plane, 2, a.H, a.W, r, x)] = cb.get_dp(j);
+        a.saved[saved_idx(plane, 3, a.H, a.W, r, x)] = cb.get_dq(j);
     }
 }
 
@@ -1286,7 +1311,9 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
         }
     };
 
-    Combine<C, MODE> cb;
+    // the saving forward keeps dp, dq in the dynamic shared memory after the tiles
+    Combine<C, MODE, MODE == MODE_SAVE> cb;
+    cb.sd = tiles + COL_TILE_BUFS * COL_TILE_FLOATS + tid;
     const float *fcol = a.f + (size_t)plane * a.H * a.pitch;
 #pragma unroll
     for (int j = 0; j < C; ++j) {
@@ -1479,7 +1506,7 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
 #pragma unroll
     for (int j = 0; j < C; ++j) {
         const int r = row0 + j;
-        if (r < a.H && x < a.W) finish_pixel<C, MODE>(a, P, plane, r, x, cb, j, nonpos, sums);
+        if (r < a.H && x < a.W) finish_pixel(a, P, plane, r, x, cb, j, nonpos, sums);
     }
     if (MODE == MODE_ADJ) {
         flush_sums(a, plane, sums);
@@ -1925,7 +1952,7 @@ __global__ void __launch_bounds__(256, MODE == MODE_SAVE ? 1 : 2) col_tc5(ColArg
 }
 
 template <int C, int MODE, int MAXCTA = 8>
-__global__ void __launch_bounds__(256, MODE == MODE_SAVE ? 1 : 2) col_iir(ColArgs a, IIRCoef cf)
+__global__ void __launch_bounds__(256, 2) col_iir(ColArgs a, IIRCoef cf)
 {
     col_iir_body<C, MODE, MAXCTA>(a, cf, blockIdx.x / (int)cg::this_cluster().num_blocks(), blockIdx.y);
 }
