@@ -744,8 +744,9 @@ bf_status bf_gp_backward(const float *f, const float *grad_y, const float *saved
     if (st == BF_OK) st = run_rows<MODE_ADJ>(c, planes, sigma_s);
     if (st == BF_OK) st = run_cols<MODE_ADJ>(c, planes, W, sigma_s);
     if (st != BF_OK) return st;
-    const long long n = (long long)H * W;
-    dim3 grid((unsigned)((n + 255) / 256), planes);
+    // bands of about 2048 pixels, at least one row each
+    const int rows_per_band = std::max(1, 2048 / std::max(1, W));
+    dim3 grid((unsigned)((H + rows_per_band - 1) / rows_per_band), planes);
     grad_finish<<<grid, 256, 0, c.s>>>(grad_f, c.acc, c.pp, H, W, pitch, opts->centre == BF_CENTRE_MEAN ? 1 : 0,
                                        (double)sigma_r, grad_sigma_r);
     BF_CUDA(cudaGetLastError());

@@ -2199,25 +2199,32 @@ __global__ void __launch_bounds__(256) fir_fused(ColArgs a, FIRCoef g)
 // centre is the plane mean (Algorithm 1 step 1), and dL/dsigma_r per plane
 // = dL/d(s^2) * d(s^2)/dsigma_r = dL/d(s^2) * (-2 s^2 / sigma_r).
 // grid (ceil(H*W / 256), planes), block 256.
+// grid (row bands, planes), block 256: the centring term of the gradient and
+// dL/dsigma_r.  The per-plane shift is formed once per block (one FP64
+// division) and added along the band's rows.
 __global__ void __launch_bounds__(256) grad_finish(float *__restrict__ grad, const double *__restrict__ acc,
                                                    const PlaneParams *__restrict__ pp, int H, int W, int pitch,
                                                    int centre_mean, double sigma_r, float *__restrict__ grad_sigma_r)
 {
     const int plane = blockIdx.y;
     const double *ac = acc + plane * NACC;
-    const long long n = (long long)H * W;
-    const float shift = centre_mean ? (float)((ac[0] - ac[1]) / (double)n) : 0.f;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) {
-        const int r = (int)(i / W), c = (int)(i % W);
-        grad[((size_t)plane * H + r) * pitch + c] += shift;
+    __shared__ float sh_shift;
+    if (threadIdx.x == 0) {
+        sh_shift = centre_mean ? (float)((ac[0] - ac[1]) / ((double)H * (double)W)) : 0.f;
+        if (blockIdx.x == 0 && grad_sigma_r) {
+            const double s2 = (double)pp[plane].s2;
+            grad_sigma_r[plane] = (s2 > 0.0 && pp[plane].mode == 0 && !isinf(sigma_r))
+                                      ? (float)(ac[2] * (-2.0 * s2 / sigma_r))
+                                      : 0.f;
+        }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && grad_sigma_r) {
-        const double s2 = (double)pp[plane].s2;
-        grad_sigma_r[plane] = (s2 > 0.0 && pp[plane].mode == 0 && !isinf(sigma_r))
-                                  ? (float)(ac[2] * (-2.0 * s2 / sigma_r))
-                                  : 0.f;
-    }
+    __syncthreads();
+    const float shift = sh_shift;
+    const int rows = (H + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int r0 = blockIdx.x * rows, r1 = min(H, r0 + rows);
+    float *g = grad + (size_t)plane * H * pitch;
+    for (int r = r0; r < r1; ++r)
+        for (int c = threadIdx.x; c < W; c += blockDim.x) g[(size_t)r * pitch + c] += shift;
 }
 
 // ------------------------------------------------------------------ tensor-core passes
