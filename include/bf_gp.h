@@ -88,7 +88,8 @@ typedef struct {
     double t_c;         /* centre when centre == BF_CENTRE_GIVEN */
     int engine;         /* recursive filter only: how the chunk-local products run.
                            0 = auto (row pass on mma.sync tensor cores, column pass on CUDA cores: the
-                               fastest pair measured on GB300), 1 = FP32 CUDA cores for both passes,
+                               fastest pair measured on GB300; the backward's row pass on CUDA cores,
+                               faster for it), 1 = FP32 CUDA cores for both passes,
                            2 = mma.sync tensor cores (TF32 x 3 products) for both passes,
                            3 = column pass on tcgen05 (TF32 x 3, accumulators in tensor memory),
                                row pass on CUDA cores */

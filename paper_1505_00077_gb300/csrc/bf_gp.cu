@@ -57,6 +57,7 @@ struct Plan {
     int T;                     // row threads per row
     int CL;                    // column cluster size (IIR)
     int row_tc, col_tc;        // recursive filter: row / column pass engine (0 CUDA cores, 1 mma.sync, 2 tcgen05)
+    int engine_auto;           // opts.engine == 0 (the adjoint row pass then runs on CUDA cores)
     int joint;                 // joint filter: K = 2 (N + 1), CUDA-core passes
     int box_passes, box_r;     // box variant: passes of a flat kernel of half-width box_r (w = passes * box_r)
     int wpr;                   // tensor-core row pass: warps per row (512 samples each)
@@ -121,6 +122,7 @@ bf_status make_plan(int planes, int H, int W, float sigma_s, const bf_gp_opts *o
     if (p->T > 512) return BF_ERR_UNSUPPORTED;  // rows longer than 8192 samples
     p->CL = (H + COL_ROWS_PER_CTA - 1) / COL_ROWS_PER_CTA;
     p->row_tc = (!joint && (o->engine == 0 || o->engine == 2)) ? 1 : 0;
+    p->engine_auto = o->engine == 0 ? 1 : 0;
     p->col_tc = joint ? 0 : (o->engine == 2 ? 1 : (o->engine == 3 ? 2 : 0));
     p->wpr = next_pow2((W + 511) / 512);
     if (sp == BF_SPATIAL_IIR && p->row_tc && p->wpr > 16) return BF_ERR_UNSUPPORTED;
@@ -389,7 +391,8 @@ bf_status run_rows(const Call &c, int planes, float sigma_s)
         default: break;
         }
         if (st != BF_OK) return st;
-    } else if (c.p.row_tc) {
+    } else if (c.p.row_tc && !(MODE == MODE_ADJ && c.p.engine_auto)) {
+        // (engine auto runs the adjoint row pass on CUDA cores: measured faster for it at every size)
         IIRCoef cr;
         deriche_coefs((double)sigma_s, TC_C, &cr);
         TCMat tm;
