@@ -108,8 +108,8 @@ def test_iir_column_cluster_sizes(bf, H):
 @pytest.mark.parametrize("H", [4600, 8192])
 def test_iir_tall_columns_engines_and_training(bf, H, engine):
     """Columns of more than 4096 rows on both CUDA-core column engines, and the
-    forward that saves the sums for the backward pass (one CTA per SM, so its
-    16-CTA cluster needs 16 SMs of one GPC)."""
+    forward that saves the sums for the backward pass (its column pass holds
+    the most shared memory per CTA)."""
     W = 40
     img = synthetic.make_image(H, W, 8, 10.0, 30.0, synthetic.seed_for(9, H + engine))
     ref = oracle.gp_bf(img.astype(np.float64), 9.0, 40.0, 10, "iir")
