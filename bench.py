@@ -32,23 +32,23 @@ sys.path.insert(0, ROOT)
 
 EXTRA_WORKLOADS = {
     # batched: 64 images, sides U{256..2048}, 3 planes each, per-image sigma_s in [1, 16], sigma_r in [10, 60]
-    "gpf-batched-64img-3ch-N20-iir": "config4",
+    "gpf-batched-64img-3ch-N20-iir": "uneven-batch",
     # differentiation: 16 x 512^2, sigma_s 5, sigma_r 25, N 20, forward + hand-written backward
-    "gpf-16x512x512-ss5-sr25-N20-fwdbwd": "config5",
+    "gpf-16x512x512-ss5-sr25-N20-fwdbwd": "batch512-fwdbwd",
     # runtime against sigma_s with the recursive filter: 1024^2, sigma_s in {2, 5, 10, 20}, sigma_r 30, N 20
-    "gpf-1024x1024-sr30-N20-iir-sigma-sweep": "config2-sweep",
+    "gpf-1024x1024-sr30-N20-iir-sigma-sweep": "rects-ramp1024-sweep",
     # joint (cross) filter: data = the 4096^2 image, guide = a second seeded 4096^2 image, K = 42 channels
     "gpf-joint-4096x4096-ss10-sr20-N20-iir": "joint",
 }
 
 WORKLOADS = {
     # name: (H, W, sigma_s, sigma_r, order, spatial, generator)
-    "gpf-4096x4096-ss10-sr20-N20-iir": (4096, 4096, 10.0, 20.0, 20, "iir", "config3"),
-    "gpf-256x256-ss3-sr30-N20-fir": (256, 256, 3.0, 30.0, 20, "fir", "config1"),
-    "gpf-2048x2048-ss10-sr20-N20-iir": (2048, 2048, 10.0, 20.0, 20, "iir", "config3-crop"),
-    "gpf-1024x1024-ss2-sr30-N20-fir": (1024, 1024, 2.0, 30.0, 20, "fir", "config2"),
+    "gpf-4096x4096-ss10-sr20-N20-iir": (4096, 4096, 10.0, 20.0, 20, "iir", "rects4096"),
+    "gpf-256x256-ss3-sr30-N20-fir": (256, 256, 3.0, 30.0, 20, "fir", "rects256"),
+    "gpf-2048x2048-ss10-sr20-N20-iir": (2048, 2048, 10.0, 20.0, 20, "iir", "rects4096-crop"),
+    "gpf-1024x1024-ss2-sr30-N20-fir": (1024, 1024, 2.0, 30.0, 20, "fir", "rects-ramp1024"),
     # box variant of S: 3 passes of a flat kernel matched to sigma_s = 3 (r = 3), fused kernel
-    "gpf-1024x1024-ss3-sr30-N20-box3": (1024, 1024, 3.0, 30.0, 20, "box", "config2"),
+    "gpf-1024x1024-ss3-sr30-N20-box3": (1024, 1024, 3.0, 30.0, 20, "box", "rects-ramp1024"),
 }
 DEFAULT = "gpf-4096x4096-ss10-sr20-N20-iir"
 FALLBACK_HBM_GBS = 6800.0
@@ -56,19 +56,19 @@ FALLBACK_HBM_GBS = 6800.0
 
 def make_input(gen, H, W, rank):
     import synthetic
-    if gen == "config3":
+    if gen == "rects4096":
         if rank == 0:
-            return synthetic.config3_image()
+            return synthetic.rects4096_image()
         return synthetic.make_image(H, W, 512, 15.0, 0.0, synthetic.seed_for(3, rank))
-    if gen == "config3-crop":
+    if gen == "rects4096-crop":
         return synthetic.make_image(H, W, 128, 15.0, 0.0, synthetic.seed_for(3, 100 + rank))
-    if gen == "config2":
+    if gen == "rects-ramp1024":
         if rank == 0:
-            return synthetic.config2_image()
+            return synthetic.rects_ramp1024_image()
         return synthetic.make_image(H, W, 64, 10.0, 60.0, synthetic.seed_for(2, rank))
-    if gen == "config1":
+    if gen == "rects256":
         if rank == 0:
-            return synthetic.config1_image()
+            return synthetic.rects256_image()
         return synthetic.make_image(H, W, 16, 10.0, 0.0, synthetic.seed_for(1, rank))
     raise ValueError(gen)
 
@@ -473,7 +473,7 @@ def _clock_wrap(local, fn):
 
 
 def run_extra(args, rank, world, local):
-    """Batched (config 4), forward + backward (config 5), sigma_s-sweep (config 2) and joint-filter
+    """Batched (uneven batch), forward + backward (16 x 512^2), sigma_s-sweep (1024^2) and joint-filter
     workloads, one GPU."""
     import numpy as np
     import torch
@@ -502,7 +502,7 @@ def run_extra(args, rank, world, local):
 
     if kind == "joint":
         H = W = 4096
-        fd = torch.from_numpy(synthetic.config3_image()).cuda()
+        fd = torch.from_numpy(synthetic.rects4096_image()).cuda()
         gd = torch.from_numpy(synthetic.make_image(H, W, 512, 15.0, 0.0, synthetic.seed_for(3, 900))).cuda()
         y = torch.empty_like(fd)
         opts = bf.make_opts(20, "iir")
@@ -533,8 +533,8 @@ def run_extra(args, rank, world, local):
         print(json.dumps(line), flush=True)
         return 0
 
-    if kind == "config2-sweep":
-        img = synthetic.config2_image()
+    if kind == "rects-ramp1024-sweep":
+        img = synthetic.rects_ramp1024_image()
         x = torch.from_numpy(img).cuda()
         y = torch.empty_like(x)
         H, W = x.shape
@@ -568,12 +568,12 @@ def run_extra(args, rank, world, local):
         print(json.dumps(line), flush=True)
         return 0
 
-    if kind == "config4":
-        specs = synthetic.config4_specs()
+    if kind == "uneven-batch":
+        specs = synthetic.uneven_batch_specs()
         planes = []
         K = 22
         for spec in specs:
-            img = synthetic.config4_image(spec)
+            img = synthetic.uneven_batch_image(spec)
             for c in range(3):
                 x = torch.from_numpy(np.ascontiguousarray(img[c])).cuda()
                 planes.append((x, torch.empty_like(x), spec[3], spec[4], 20))
@@ -623,8 +623,8 @@ def run_extra(args, rank, world, local):
         print(json.dumps(line), flush=True)
         return 0
 
-    # config 5: forward + backward on a 16 x 512^2 batch (planes in one call)
-    xb = synthetic.config5_batch(16)[:, 0]
+    # forward + backward on a 16 x 512^2 batch (planes in one call)
+    xb = synthetic.batch512(16)[:, 0]
     B, H, W = xb.shape
     K = 22
     x = torch.from_numpy(np.ascontiguousarray(xb)).cuda()

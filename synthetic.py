@@ -30,8 +30,9 @@ import numpy as np
 SEED_BASE = 150500077  # arXiv 1505.00077
 
 
-def seed_for(config: int, index: int = 0) -> int:
-    return SEED_BASE + 1000 * int(config) + int(index)
+def seed_for(family: int, index: int = 0) -> int:
+    """Seed of image `index` of a workload family (a small integer per workload)."""
+    return SEED_BASE + 1000 * int(family) + int(index)
 
 
 def make_image(H: int, W: int, n_rect: int, noise_std: float, ramp_amp: float = 0.0,
@@ -74,22 +75,22 @@ class PlaneSpec:
     ramp_amp: float = 0.0
 
 
-def config1_image() -> np.ndarray:
+def rects256_image() -> np.ndarray:
     """256x256, 16 rectangles, noise std 10 (sigma_s 3, sigma_r 30)."""
     return make_image(256, 256, 16, 10.0, 0.0, seed_for(1))
 
 
-def config2_image() -> np.ndarray:
+def rects_ramp1024_image() -> np.ndarray:
     """1024x1024, 64 rectangles + sinusoidal ramp of amplitude 60, noise std 10."""
     return make_image(1024, 1024, 64, 10.0, 60.0, seed_for(2))
 
 
-def config3_image() -> np.ndarray:
+def rects4096_image() -> np.ndarray:
     """4096x4096 (16.7 Mpx), 512 rectangles, noise std 15 (sigma_s 10, sigma_r 20)."""
     return make_image(4096, 4096, 512, 15.0, 0.0, seed_for(3))
 
 
-def config4_specs(n_images: int = 64, order: int = 20):
+def uneven_batch_specs(n_images: int = 64, order: int = 20):
     """Batched workload: n_images images, sides ~ U{256..2048} independently,
     3 planes each; per image sigma_s ~ logU[1, 16], sigma_r ~ logU[10, 60];
     16 rectangles per 256^2 of area, noise std 10.  Returns a list of
@@ -106,11 +107,11 @@ def config4_specs(n_images: int = 64, order: int = 20):
     return out
 
 
-def config4_image(spec) -> np.ndarray:
+def uneven_batch_image(spec) -> np.ndarray:
     _, H, W, _, _, n_rect, seed = spec
     return make_image(H, W, n_rect, 10.0, 0.0, seed, planes=3)
 
 
-def config5_batch(batch: int = 16) -> np.ndarray:
+def batch512(batch: int = 16) -> np.ndarray:
     """[batch, 1, 512, 512], 32 rectangles, noise std 10 (sigma_s 5, sigma_r 25)."""
     return np.stack([make_image(512, 512, 32, 10.0, 0.0, seed_for(5, i))[None] for i in range(batch)])

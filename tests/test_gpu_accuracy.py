@@ -37,10 +37,10 @@ def mse_db(a, b):
     return 10.0 * np.log10(mse), 10.0 * np.log10(255.0 ** 2 / mse)
 
 
-def test_config1_mse_against_exact(bf):
+def test_rects256_mse_against_exact(bf):
     """256^2, sigma_s 3 (W = 9), sigma_r 30: N = 20 (the paper's order) and the
     order of the kernel-error rule for 1e-3; MSE in dB (Sec. 4's measure) and PSNR."""
-    img = synthetic.config1_image().astype(np.float64)
+    img = synthetic.rects256_image().astype(np.float64)
     exact = oracle.direct_bf(img, 3.0, 30.0)
     R = float(np.max(np.abs(img - oracle.mean(img))))
     n_tol = bf.bf_gp_order_for_tol(30.0, R, 1e-3)
@@ -61,14 +61,14 @@ SIGMA_R = (10.0, 30.0, 50.0)
 ORDERS = tuple(range(4, 21, 2))
 
 
-def test_config2_error_against_order(bf):
+def test_rects_ramp1024_error_against_order(bf):
     """1024^2 (ramp + rectangles + noise), error of the GPU result against
     Eq. (1) on the centre 256^2 (neighbours from the whole image) for every
     sigma_s x sigma_r x even N.  sigma_s = 2 uses the truncated Gaussian of
     Eq. (1) (FIR), the others Deriche's recursive filter, whose own design
     error is part of the figure.  Where the order is the only error source
     (FIR) and s^2 is moderate (sigma_r >= 30), the error must fall with N."""
-    img = synthetic.config2_image().astype(np.float64)
+    img = synthetic.rects_ramp1024_image().astype(np.float64)
     crop = (384, 640, 384, 640)
     table = {}
     for ss in SIGMA_S:
@@ -90,26 +90,26 @@ def test_config2_error_against_order(bf):
         assert all(b <= a + 0.05 for a, b in zip(errs, errs[1:])), (sr, errs)
 
 
-def test_config3_crop_mse_against_exact(bf):
+def test_rects4096_crop_mse_against_exact(bf):
     """4096^2, sigma_s 10, sigma_r 20, N 20, recursive filter: error of the GPU
     result against Eq. (1) (window W = 30) on a 512^2 crop, neighbours from the
     whole image.  Reported, not gated: it holds the Taylor truncation at
     s^2 = (R / sigma_r)^2 and the recursive filter's design error."""
-    img = synthetic.config3_image()
+    img = synthetic.rects4096_image()
     out = gpu_filter(bf, img, 10.0, 20.0, 20, "iir")
     crop = (1792, 2304, 1792, 2304)
     exact = oracle.direct_bf(img.astype(np.float64), 10.0, 20.0, crop=crop)
     o = out[crop[0]:crop[1], crop[2]:crop[3]]
     good = np.isfinite(o)
     db, psnr = mse_db(o[good], exact[good])
-    print(f"\nconfig 3 crop: MSE {db:.2f} dB, PSNR {psnr:.2f} dB, non-finite {int((~good).sum())}")
+    print(f"\n4096^2 crop: MSE {db:.2f} dB, PSNR {psnr:.2f} dB, non-finite {int((~good).sum())}")
     assert good.mean() > 0.99
 
 
 def test_oracle_timings():
     """Host-core throughput of the FP64 oracles on the paper's workload shapes."""
     rows = []
-    img1 = synthetic.config1_image().astype(np.float64)
+    img1 = synthetic.rects256_image().astype(np.float64)
     for name, fn, px in (
         ("O1 direct, 256^2, sigma_s 3, sigma_r 30", lambda: oracle.direct_bf(img1, 3.0, 30.0), img1.size),
         ("O2 Algorithm 1 FIR, 256^2, sigma_s 3, N 20", lambda: oracle.gp_bf(img1, 3.0, 30.0, 20, "fir"), img1.size),
@@ -117,7 +117,7 @@ def test_oracle_timings():
         t = time.perf_counter()
         fn()
         rows.append((name, px / (time.perf_counter() - t) / 1e6))
-    img3 = synthetic.config3_image().astype(np.float64)
+    img3 = synthetic.rects4096_image().astype(np.float64)
     crop = (1792, 2304, 1792, 2304)
     t = time.perf_counter()
     oracle.direct_bf(img3, 10.0, 20.0, crop=crop)

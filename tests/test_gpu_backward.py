@@ -81,10 +81,10 @@ def test_backward_tall_columns(bf, H):
     assert abs(gsr[0] - ref_s) <= RTOL * max(abs(ref_s), 1e-6 * np.abs(ref_g).max() * H * W), (gsr[0], ref_s)
 
 
-def test_config5_batch(bf):
+def test_batch512_forward_backward(bf):
     """16 x 1 x 512^2, sigma_s 5, sigma_r 25, N 20 (recursive filter): every plane's
     forward against O2, and the adjoint of four of them against O3."""
-    x = synthetic.config5_batch(16)[:, 0]
+    x = synthetic.batch512(16)[:, 0]
     rng = np.random.default_rng(55)
     gy = rng.normal(size=x.shape).astype(np.float32)
     y, gx, gsr, bits = gpu_fwd_bwd(bf, x, gy, 5.0, 25.0, 20, "iir")

@@ -64,18 +64,18 @@ def check(gpu, ref, tol=TOL, kappa=None, min_gated=1.0):
     return err.max()
 
 
-# ---------------------------------------------------------------- config 1
+# ---------------------------------------------------------------- 256^2 rectangles, sigma_s 3, sigma_r 30
 
 @pytest.mark.parametrize("N", [20, 34])
-def test_config1_fir(bf, N):
-    img = synthetic.config1_image()
+def test_rects256_fir(bf, N):
+    img = synthetic.rects256_image()
     f64 = img.astype(np.float64)
     ref = oracle.gp_bf(f64, 3.0, 30.0, N, "fir")
     check(run_gpu(bf, img, 3.0, 30.0, N, "fir"), ref)
 
 
-def test_config1_iir(bf):
-    img = synthetic.config1_image()
+def test_rects256_iir(bf):
+    img = synthetic.rects256_image()
     ref = oracle.gp_bf(img.astype(np.float64), 3.0, 30.0, 20, "iir")
     check(run_gpu(bf, img, 3.0, 30.0, 20, "iir"), ref)
 
@@ -136,15 +136,15 @@ def test_iir_long_rows(bf, W):
     check(run_gpu(bf, img, 11.0, 40.0, 10, "iir"), ref)
 
 
-# ---------------------------------------------------------------- config 2 sweep
+# ---------------------------------------------------------------- 1024^2 rectangles + ramp, sweeps
 
 @pytest.mark.parametrize("ss,sr,N,spatial", [
     (2.0, 30.0, 20, "fir"), (2.0, 10.0, 20, "fir"), (2.0, 50.0, 8, "fir"), (3.0, 10.0, 12, "fir"),
     (5.0, 30.0, 20, "iir"), (5.0, 50.0, 4, "iir"), (10.0, 30.0, 20, "iir"), (10.0, 50.0, 12, "iir"),
     (20.0, 30.0, 20, "iir"), (20.0, 50.0, 16, "iir"), (20.0, 30.0, 6, "iir"),
 ])
-def test_config2_sweep(bf, ss, sr, N, spatial):
-    img = synthetic.config2_image()
+def test_rects_ramp1024_sweep(bf, ss, sr, N, spatial):
+    img = synthetic.rects_ramp1024_image()
     ref, kap = oracle.gp_bf(img.astype(np.float64), ss, sr, N, spatial, return_kappa=True)
     out, bits = run_gpu(bf, img, ss, sr, N, spatial, status=True)
     assert bits == 0
@@ -152,7 +152,7 @@ def test_config2_sweep(bf, ss, sr, N, spatial):
 
 
 @pytest.mark.parametrize("ss", [5.0, 10.0, 20.0])
-def test_config2_recursive_small_sigma_r(bf, ss):
+def test_rects_ramp1024_recursive_small_sigma_r(bf, ss):
     """sigma_r = 10 on the 1024^2 image gives s^2 = 234.  With the recursive
     Gaussian, whose kernel dips to -1.4e-4 of its peak far out, the N = 20
     approximation breaks down here: Q <= 0 on 0.2-1.4% of the pixels even in
@@ -161,7 +161,7 @@ def test_config2_recursive_small_sigma_r(bf, ss):
     does not model, so in this regime the gate is: NaN sets agree wherever
     the pixel is conditioned, 99.99% of the conditioned pixels are within
     1e-3 and all of them within 1e-2."""
-    img = synthetic.config2_image()
+    img = synthetic.rects_ramp1024_image()
     ref, kap = oracle.gp_bf(img.astype(np.float64), ss, 10.0, 20, "iir", return_kappa=True)
     out, bits = run_gpu(bf, img, ss, 10.0, 20, "iir", status=True)
     assert (bits & ~bf.BF_DEV_NONPOS_Q) == 0
@@ -179,7 +179,7 @@ def test_config2_recursive_small_sigma_r(bf, ss):
 def test_large_s2_stays_in_fp32_range(bf):
     """(R / sigma_r)^2 = 234 on the 1024^2 image (R = 153, sigma_r = 10): exp(-s^2 u^2 / 2)
     would underflow FP32 at |u| = 1 without the common power-of-two channel scale."""
-    img = synthetic.config2_image()
+    img = synthetic.rects_ramp1024_image()
     out, bits = run_gpu(bf, img, 2.0, 10.0, 20, "fir", status=True)
     assert bits == 0
     ref, kap = oracle.gp_bf(img.astype(np.float64), 2.0, 10.0, 20, "fir", return_kappa=True)
@@ -193,12 +193,12 @@ def test_range_flag_beyond_fp32(bf):
     assert bits & bf.BF_DEV_RANGE
 
 
-# ---------------------------------------------------------------- config 3
+# ---------------------------------------------------------------- 4096^2 rectangles, sigma_s 10, sigma_r 20
 
-def test_config3_crop(bf):
+def test_rects4096_crop(bf):
     """4096^2, sigma_s 10, sigma_r 20, N 20, recursive filter: a 512^2 crop of the
     GPU output against the oracle run on full lines of the full image."""
-    img = synthetic.config3_image()
+    img = synthetic.rects4096_image()
     f64 = img.astype(np.float64)
     gpu = run_gpu(bf, img, 10.0, 20.0, 20, "iir")
     r0, c0 = 1792, 2304

@@ -29,7 +29,7 @@ def _rank_main(rank, world, port, out):
     try:
         local_ms = 10.0 + 5.0 * rank  # rank 1 is the slow one
         total = bench.reduce_max(local_ms, dist, "cpu")
-        img = bench.make_input("config3-crop", 64, 64, rank)
+        img = bench.make_input("rects4096-crop", 64, 64, rank)
         digest = float(np.asarray(img, dtype=np.float64).sum())
         t = torch.tensor([digest], dtype=torch.float64)
         gathered = [torch.zeros(1, dtype=torch.float64) for _ in range(world)]
