@@ -368,6 +368,18 @@ bf_status bf_gp_batched_plan_engines(const bf_gp_plan *plan, int *engines);
 bf_status bf_gp_get_device_status(const void *ws, void *stream, uint32_t *bits);
 
 /*
+ * Counts behind the status bits of the last call that used `ws` (for a batch:
+ * summed over its planes), into counters[BF_GP_NCOUNTERS]:
+ *   [0] pixels whose Q <= 0 (set to NaN; BF_DEV_NONPOS_Q)
+ *   [1] non-finite input values (BF_DEV_NONFINITE_IN)
+ *   [2] planes whose exponentials leave the FP32 range (BF_DEV_RANGE)
+ *   [3] bounded waits that gave up (BF_DEV_TIMEOUT)
+ * Synchronises `stream` first.
+ */
+#define BF_GP_NCOUNTERS 4
+bf_status bf_gp_get_device_counters(const void *ws, void *stream, unsigned long long *counters);
+
+/*
  * Read back, for plane `plane` of the last forward call that used `ws`, the
  * centre t_c and the scale R the device computed (FP64).  Synchronises
  * `stream`.

@@ -106,6 +106,7 @@ def _load():
                                        c_void_p, c_size_t, c_void_p]),
         "bf_gp_get_device_status": (c_int, [c_void_p, c_void_p, P(ctypes.c_uint32)]),
         "bf_gp_get_plane_stats": (c_int, [c_void_p, c_int, c_void_p, P(c_double), P(c_double)]),
+        "bf_gp_get_device_counters": (c_int, [c_void_p, c_void_p, P(ctypes.c_ulonglong)]),
         "bf_gp_order_for_tol": (c_int, [c_double, c_double, c_double]),
         "bf_gp_order_fp32_limit": (c_int, [c_double, c_double, c_double]),
         "bf_gp_joint_workspace_size": (c_int, [c_int, c_int, c_int, c_float, P(bf_gp_opts), P(c_size_t)]),
@@ -133,7 +134,7 @@ def exported_symbols():
             "bf_gp_batched_plan_upload", "bf_gp_batched", "bf_gp_batched_plan_destroy",
             "bf_gp_batched_plan_stats_workspace", "bf_gp_batched_plane_stats", "bf_gp_forward_noalloc",
             "bf_gp_host_workspace_size", "bf_gp_forward_host",
-            "bf_gp_get_device_status", "bf_gp_get_plane_stats", "bf_gp_order_for_tol", "bf_gp_order_fp32_limit",
+            "bf_gp_get_device_status", "bf_gp_get_device_counters", "bf_gp_get_plane_stats", "bf_gp_order_for_tol", "bf_gp_order_fp32_limit",
             "bf_gp_joint_workspace_size", "bf_gp_forward_joint", "bf_gp_autotune", "bf_gp_autotune_clear",
             "bf_gp_batched_plan_tune", "bf_gp_batched_plan_engines"]
 
@@ -382,6 +383,11 @@ class BatchedFilter:
         import torch
         return bf_gp_get_device_status(self.ws.data_ptr(), torch.cuda.current_stream().cuda_stream)
 
+    def counters(self):
+        """The device counters of the last run, summed over the planes."""
+        import torch
+        return bf_gp_get_device_counters(self.ws.data_ptr(), torch.cuda.current_stream().cuda_stream)
+
     def __del__(self):
         try:
             if getattr(self, "plan", None):
@@ -417,6 +423,17 @@ def bf_gp_forward_host(f_host_ptr, y_host_ptr, planes, H, W, sigma_s, sigma_r, o
                                       ctypes.byref(opts) if opts is not None else None,
                                       ctypes.c_void_p(int(ws_ptr)), int(ws_bytes), ctypes.c_void_p(int(stream))),
            "bf_gp_forward_host")
+
+
+BF_GP_NCOUNTERS = 4
+
+
+def bf_gp_get_device_counters(ws_ptr, stream=0):
+    """[pixels with Q <= 0, non-finite input values, planes beyond the FP32
+    range, bounded waits that gave up] of the last call that used ws."""
+    c = (ctypes.c_ulonglong * BF_GP_NCOUNTERS)()
+    _check(_load().bf_gp_get_device_counters(_vp(ws_ptr), _vp(stream), c), "bf_gp_get_device_counters")
+    return [int(v) for v in c]
 
 
 def bf_gp_get_device_status(ws_ptr, stream=0) -> int:

@@ -873,6 +873,16 @@ bf_status bf_gp_get_device_status(const void *ws, void *stream, uint32_t *bits)
     return BF_OK;
 }
 
+bf_status bf_gp_get_device_counters(const void *ws, void *stream, unsigned long long *counters)
+{
+    if (!ws || !counters) return BF_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    BF_CUDA(cudaStreamSynchronize(s));
+    BF_CUDA(cudaMemcpy(counters, static_cast<const char *>(ws) + 8, sizeof(unsigned long long) * NCOUNTERS,
+                       cudaMemcpyDeviceToHost));
+    return BF_OK;
+}
+
 bf_status bf_gp_get_plane_stats(const void *ws, int plane, void *stream, double *t_c, double *R)
 {
     if (!ws || plane < 0) return BF_ERR_INVALID_ARG;
@@ -1176,7 +1186,7 @@ bf_status bf_gp_batched_plane_stats(const bf_gp_plan *plan, void *ws, size_t ws_
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     bf_status st = upload_tables(plan, wsb, s);
     if (st != BF_OK) return st;
-    BF_CUDA(cudaMemsetAsync(wsb, 0, sizeof(uint32_t), s));
+    BF_CUDA(cudaMemsetAsync(wsb, 0, 8 + sizeof(unsigned long long) * NCOUNTERS, s));  // status word and counters
     BatchArgs b = batch_args(plan, wsb);
     batched_stats_partial<<<plan->total_stats, 256, 0, s>>>(b);
     batched_stats_finalize<<<plan->n, 256, 0, s>>>(b);

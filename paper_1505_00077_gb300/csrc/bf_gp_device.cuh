@@ -347,6 +347,26 @@ __device__ __forceinline__ float envelope(const PlaneParams &P, float u)
 
 // ------------------------------------------------------------------ stats
 
+// Counters after the status word in the workspace header (byte 8 on), zeroed
+// with it by the statistics pass of every call:
+//   [0] pixels whose Q <= 0 (set to NaN), [1] non-finite input values,
+//   [2] planes whose exponentials leave the FP32 range, [3] bounded waits that gave up.
+constexpr int NCOUNTERS = 4;
+__device__ __forceinline__ unsigned long long *status_counters(uint32_t *status)
+{
+    return reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(status) + 8);
+}
+// Adds a warp's pixels with Q <= 0 to the counter and raises the flag (every lane calls).
+__device__ __noinline__ void count_nonpos(uint32_t *status, int nonpos)
+{
+    const unsigned n = __reduce_add_sync(0xffffffffu, (unsigned)nonpos);
+    if (n && (threadIdx.x & 31) == 0) {
+        atomicOr(status, 0x1u);
+        atomicAdd(status_counters(status), (unsigned long long)n);
+    }
+}
+
+
 // grid (nblk, planes), block 256.  Each block reduces a band of rows.  Block
 // (0, 0) also zeroes the status word of this call.
 // COPY: f is host memory mapped into the device's address space (read with
@@ -463,7 +483,10 @@ __global__ void __launch_bounds__(256) stats_partial(const float *__restrict__ f
                                                      int rows_per_block, StatPartial *__restrict__ part,
                                                      uint32_t *__restrict__ status, float *__restrict__ copy)
 {
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *status = 0u;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        *status = 0u;
+        for (int i = 0; i < NCOUNTERS; ++i) status_counters(status)[i] = 0ull;
+    }
     const size_t po = (size_t)blockIdx.y * H * pitch;
     stats_partial_body<COPY>(f + po, H, W, pitch, rows_per_block, blockIdx.x,
                              part + (size_t)blockIdx.y * gridDim.x + blockIdx.x, COPY ? copy + po : nullptr);
@@ -533,6 +556,7 @@ __device__ __forceinline__ void stats_finalize_body(const StatPartial *__restric
         const double tc = centre_given ? tc_given : S / (double)npix;
         double R = fmax((double)MX - tc, tc - (double)MN);
         int mode = BAD > 0 ? 2 : 0;  // 2: non-finite input (copy + flag)
+        if (BAD > 0) atomicAdd(status_counters(status) + 1, (unsigned long long)BAD);
         if (!(R > 0.0)) {
             // constant plane: the forward copies it; for training the filter runs
             // with R = 1 (the result is independent of R), which gives y = t_c = f
@@ -595,6 +619,7 @@ __device__ __forceinline__ void stats_finalize_body(const StatPartial *__restric
         q.tc_d = sh_tc;
         q.R_d = sh_R;
         if (flags) atomicOr(status, flags);
+        if (flags & 0x4u) atomicAdd(status_counters(status) + 2, 1ull);
     }
 }
 
@@ -1141,7 +1166,7 @@ struct AdjSums {
 // Writes the result for one pixel (r, x) of the plane.
 template <int RPT, int MODE, bool DSMEM>
 __device__ __forceinline__ void finish_pixel(const ColArgs &a, const PlaneParams &P, int plane, int r, int x,
-                                             const Combine<RPT, MODE, DSMEM> &cb, int j, bool &nonpos,
+                                             const Combine<RPT, MODE, DSMEM> &cb, int j, int &nonpos,
                                              AdjSums &sums)
 {
     const size_t pix = ((size_t)plane * a.H + r) * a.pitch + x;
@@ -1181,7 +1206,7 @@ __device__ __forceinline__ void finish_pixel(const ColArgs &a, const PlaneParams
     const float Q = cb.q[j];
     float out;
     if (!(Q > 0.f)) {
-        nonpos = true;
+        ++nonpos;
         out = __int_as_float(0x7fc00000);
     } else {
         out = fmaf(P.R, __fdiv_rn(cb.p[j], Q), P.tc);
@@ -1501,7 +1526,7 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
     }
     // no CTA may leave while a peer can still read its shared memory
     cl.sync();
-    bool nonpos = false;
+    int nonpos = 0;
     AdjSums sums = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int j = 0; j < C; ++j) {
@@ -1510,8 +1535,8 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
     }
     if (MODE == MODE_ADJ) {
         flush_sums(a, plane, sums);
-    } else if (__any_sync(0xffffffffu, nonpos) && lane == 0) {
-        atomicOr(a.status, 0x1u);
+    } else {
+        count_nonpos(a.status, nonpos);
     }
 }
 
@@ -1930,8 +1955,11 @@ __device__ __forceinline__ void col_tc5_body(const ColArgs &a, const IIRCoef &cf
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(tmem) : "memory");
     }
-    if (timed_out) atomicOr(a.status, 0x8u);
-    bool nonpos = false;
+    if (timed_out) {
+        atomicOr(a.status, 0x8u);
+        atomicAdd(status_counters(a.status) + 3, 1ull);
+    }
+    int nonpos = 0;
     AdjSums sums = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int j = 0; j < C; ++j) {
@@ -1940,8 +1968,8 @@ __device__ __forceinline__ void col_tc5_body(const ColArgs &a, const IIRCoef &cf
     }
     if (MODE == MODE_ADJ) {
         flush_sums(a, plane, sums);
-    } else if (__any_sync(0xffffffffu, nonpos) && lane == 0) {
-        atomicOr(a.status, 0x1u);
+    } else {
+        count_nonpos(a.status, nonpos);
     }
 }
 
@@ -2005,7 +2033,7 @@ __global__ void __launch_bounds__(256) col_fir(ColArgs a, FIRCoef g)
             cb.step(k, a.N, P.s2, y);
         }
     }
-    bool nonpos = false;
+    int nonpos = 0;
     AdjSums sums = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int j = 0; j < RPT; ++j) {
@@ -2014,8 +2042,8 @@ __global__ void __launch_bounds__(256) col_fir(ColArgs a, FIRCoef g)
     }
     if (MODE == MODE_ADJ) {
         flush_sums(a, plane, sums);
-    } else if (__any_sync(0xffffffffu, nonpos) && tx == 0) {
-        atomicOr(a.status, 0x1u);
+    } else {
+        count_nonpos(a.status, nonpos);
     }
 }
 
@@ -2183,8 +2211,9 @@ __global__ void __launch_bounds__(256) fir_fused(ColArgs a, FIRCoef g)
         if (yo < a.H && xo < a.W) {
             const float Q = fmaf(P.s2 * ou[j], qacc[j], psi0[j]);
             float out;
-            if (!(Q > 0.f)) {
+            if (!(Q > 0.f)) {  // rare: counted one pixel at a time
                 nonpos = true;
+                atomicAdd(status_counters(a.status), 1ull);
                 out = __int_as_float(0x7fc00000);
             } else {
                 out = fmaf(P.R, __fdiv_rn(pacc[j], Q), P.tc);
@@ -2738,7 +2767,7 @@ __device__ __forceinline__ void col_tc_body(const ColArgs &a, const IIRCoef &cf,
         cb.step(k, a.N, P.s2, y16);
     }
     cl.sync();  // no CTA may leave while a peer can still read its shared memory
-    bool nonpos = false;
+    int nonpos = 0;
     AdjSums sums = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int q = 0; q < 4; ++q)
@@ -2749,8 +2778,8 @@ __device__ __forceinline__ void col_tc_body(const ColArgs &a, const IIRCoef &cf,
         }
     if (MODE == MODE_ADJ) {
         flush_sums(a, plane, sums);
-    } else if (__any_sync(0xffffffffu, nonpos) && lane == 0) {
-        atomicOr(a.status, 0x1u);
+    } else {
+        count_nonpos(a.status, nonpos);
     }
 }
 
@@ -2821,17 +2850,38 @@ __global__ void __launch_bounds__(256) batched_stats_finalize(BatchArgs b)
 // launches have all finished: this kernel follows the join on the stream).
 __global__ void gather_status(uint32_t *dst, const char *ws, const unsigned long long *ofs, int n)
 {
+    // OR of the planes' status words and sums of their counters
     uint32_t bits = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) bits |= *reinterpret_cast<const uint32_t *>(ws + ofs[i]);
+    unsigned long long c[NCOUNTERS] = {};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        bits |= *reinterpret_cast<const uint32_t *>(ws + ofs[i]);
+        const unsigned long long *pc = reinterpret_cast<const unsigned long long *>(ws + ofs[i] + 8);
 #pragma unroll
-    for (int o = 16; o; o >>= 1) bits |= __shfl_down_sync(0xffffffffu, bits, o);
-    __shared__ uint32_t w[8];
-    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = bits;
+        for (int q = 0; q < NCOUNTERS; ++q) c[q] += pc[q];
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        bits |= __shfl_down_sync(0xffffffffu, bits, o);
+#pragma unroll
+        for (int q = 0; q < NCOUNTERS; ++q) c[q] += __shfl_down_sync(0xffffffffu, c[q], o);
+    }
+    __shared__ uint32_t w[32];
+    __shared__ unsigned long long wc[32][NCOUNTERS];
+    if ((threadIdx.x & 31) == 0) {
+        w[threadIdx.x >> 5] = bits;
+#pragma unroll
+        for (int q = 0; q < NCOUNTERS; ++q) wc[threadIdx.x >> 5][q] = c[q];
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t b = 0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) b |= w[i];
+        unsigned long long t[NCOUNTERS] = {};
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            b |= w[i];
+            for (int q = 0; q < NCOUNTERS; ++q) t[q] += wc[i][q];
+        }
         *dst = b;
+        for (int q = 0; q < NCOUNTERS; ++q) status_counters(dst)[q] = t[q];
     }
 }
 

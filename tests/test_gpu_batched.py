@@ -56,6 +56,10 @@ def test_batched_graph_matches_single_and_oracle(bf):
     g.replay()
     torch.cuda.synchronize()
     assert (bfilt.status() & ~bf.BF_DEV_NONPOS_Q) == 0
+    # the batch's counters are the sums over its planes: NaN pixels are the Q <= 0 ones
+    n_nan = sum(int(torch.isnan(y).sum()) for x, y, *_ in planes)
+    assert bfilt.counters() == [n_nan, 0, 0, 0]
+    assert ((bfilt.status() & bf.BF_DEV_NONPOS_Q) != 0) == (n_nan > 0)
     for i, (x, y, ss, sr, order) in enumerate(planes):
         # the batch runs each plane through the single-image launches: the same result bit for bit
         o = bf.make_opts(order, "iir")

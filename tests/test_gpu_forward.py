@@ -191,6 +191,15 @@ def test_range_flag_beyond_fp32(bf):
     img[:, 32:] = 255.0
     _, bits = run_gpu(bf, img, 3.0, 3.0, 20, "fir", status=True)  # s^2 = (127.5 / 3)^2 = 1806
     assert bits & bf.BF_DEV_RANGE
+    # two planes beyond the range, one inside it: the counter counts planes
+    x = torch.from_numpy(np.stack([img, img, np.full_like(img, 7.0)])).cuda()
+    o = bf.make_opts(20, "fir")
+    need = bf.bf_gp_workspace_size(3, 64, 64, 3.0, o)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    y = torch.empty_like(x)
+    s = torch.cuda.current_stream().cuda_stream
+    bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 3, 64, 64, 64, 3.0, 3.0, o, ws.data_ptr(), need, s)
+    assert bf.bf_gp_get_device_counters(ws.data_ptr(), s)[2] == 2
 
 
 # ---------------------------------------------------------------- 4096^2 rectangles, sigma_s 10, sigma_r 20
@@ -271,21 +280,29 @@ def test_device_stats_readback(bf):
     assert bf.bf_gp_get_device_status(ws.data_ptr(), s) == 0
 
 
-def test_odd_order_flags_nonpositive_denominator(bf):
+@pytest.mark.parametrize("spatial,two_pass", [("fir", False), ("fir", True), ("iir", False)])
+def test_odd_order_flags_and_counts_nonpositive_denominator(bf, spatial, two_pass):
+    """Odd N: pixels with Q <= 0 become NaN, the flag is raised and the
+    counter holds exactly the number of such pixels (fused FIR kernel, FIR
+    column pass, recursive column pass)."""
     img = np.zeros((16, 16), np.float32)
     img[:, 8] = 255.0
     x = torch.from_numpy(img).cuda()
-    o = bf.make_opts(5, "fir")
+    o = bf.make_opts(5, spatial, fir_two_pass=two_pass)
     need = bf.bf_gp_workspace_size(1, 16, 16, 3.0, o)
     ws = torch.empty(need, dtype=torch.uint8, device="cuda")
     y = torch.empty_like(x)
     s = torch.cuda.current_stream().cuda_stream
     bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, 16, 16, 16, 3.0, 20.0, o, ws.data_ptr(), need, s)
     bits = bf.bf_gp_get_device_status(ws.data_ptr(), s)
-    assert bits & bf.BF_DEV_NONPOS_Q
+    counters = bf.bf_gp_get_device_counters(ws.data_ptr(), s)
     out = y.cpu().numpy()
-    ref = oracle.gp_bf(img.astype(np.float64), 3.0, 20.0, 5, "fir")
-    assert np.array_equal(np.isnan(out), np.isnan(ref))
+    nan = int(np.isnan(out).sum())
+    assert nan > 0 and bits & bf.BF_DEV_NONPOS_Q
+    assert counters == [nan, 0, 0, 0]
+    if spatial == "fir":
+        ref = oracle.gp_bf(img.astype(np.float64), 3.0, 20.0, 5, "fir")
+        assert np.array_equal(np.isnan(out), np.isnan(ref))
 
 
 def test_nonfinite_input_is_passed_through_and_flagged(bf):
@@ -299,8 +316,14 @@ def test_nonfinite_input_is_passed_through_and_flagged(bf):
     s = torch.cuda.current_stream().cuda_stream
     bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, 20, 20, 20, 3.0, 30.0, o, ws.data_ptr(), need, s)
     assert bf.bf_gp_get_device_status(ws.data_ptr(), s) & bf.BF_DEV_NONFINITE_IN
+    assert bf.bf_gp_get_device_counters(ws.data_ptr(), s) == [0, 1, 0, 0]
     out = y.cpu().numpy()
     assert np.array_equal(out, img, equal_nan=True)
+    # the next call on the same workspace starts from zero counts
+    x.copy_(torch.from_numpy(synthetic.make_image(20, 20, 3, 10.0, 0.0, 5)))
+    bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, 20, 20, 20, 3.0, 30.0, o, ws.data_ptr(), need, s)
+    assert bf.bf_gp_get_device_status(ws.data_ptr(), s) == 0
+    assert bf.bf_gp_get_device_counters(ws.data_ptr(), s) == [0, 0, 0, 0]
 
 
 @pytest.mark.parametrize("inp", ["pinned", "pageable"])
