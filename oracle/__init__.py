@@ -17,6 +17,9 @@ Functions (each cites the passage of Chaudhury's paper it follows):
   1-D spatial operators and the recursive filter's impulse response.
 * :func:`gp_adjoint` -- O3, the reverse-mode derivative of O2 (w.r.t. f and sigma_r).
 * :func:`gp_kernel` -- Eq. (5), the Gauss-polynomial range kernel.
+* :func:`gp_tangent`, :func:`kappa_input` -- the first-order change of O2 under
+  relative perturbations of the centred intensity (forward-mode derivative of
+  Eqs. (7)-(11)), and the part of the conditioning number kappa it gives.
 * :func:`window` -- W = ceil(3 sigma_s) (Sec. 1).
 """
 from __future__ import annotations
@@ -60,13 +63,18 @@ def _load():
     i, d = ctypes.c_int, ctypes.c_double
     lib.bfo_direct.argtypes = [dp, i, i, d, d, i, i, i, i, i, dp]
     lib.bfo_direct.restype = None
-    lib.bfo_gp.argtypes = [dp, i, i, d, d, i, d, i, i, i, i, i, i, i, dp, dp]
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.bfo_gp.argtypes = [dp, i, i, d, d, i, ip, d, i, i, i, i, i, i, dp, dp, dp]
+    lib.bfo_gp_tangent.argtypes = [dp, dp, i, i, d, d, i, ip, d, i, i, i, i, i, i, dp, i, dp, dp, dp, dp, dp]
+    lib.bfo_gp_tangent.restype = i
+    lib.bfo_gp_probe_sign.argtypes = [ctypes.c_ulonglong, ctypes.c_long, i]
+    lib.bfo_gp_probe_sign.restype = d
     lib.bfo_gp.restype = i
-    lib.bfo_line_filter.argtypes = [dp, i, i, d, i, i, i, dp]
+    lib.bfo_line_filter.argtypes = [dp, i, i, d, i, i, dp]
     lib.bfo_line_filter.restype = None
-    lib.bfo_deriche_response.argtypes = [d, i, i, dp]
+    lib.bfo_deriche_response.argtypes = [d, i, dp]
     lib.bfo_deriche_response.restype = None
-    lib.bfo_deriche_coefs.argtypes = [d, i, dp]
+    lib.bfo_deriche_coefs.argtypes = [d, dp]
     lib.bfo_deriche_coefs.restype = None
     lib.bfo_max_threads.argtypes = []
     lib.bfo_max_threads.restype = i
@@ -80,7 +88,7 @@ def _load():
     lib.bfo_gp_kernel.restype = d
     lib.bfo_direct_joint.argtypes = [dp, dp, i, i, d, d, i, i, i, i, i, dp]
     lib.bfo_direct_joint.restype = None
-    lib.bfo_gp_joint.argtypes = [dp, dp, i, i, d, d, i, d, i, i, i, i, i, i, i, dp, dp]
+    lib.bfo_gp_joint.argtypes = [dp, dp, i, i, d, d, i, d, i, i, i, i, i, i, dp, dp, dp]
     lib.bfo_gp_joint.restype = i
     _lib = lib
     return lib
@@ -88,6 +96,16 @@ def _load():
 
 def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _orders(N):
+    """(increasing orders as a C int array, count, whether N was a single order)."""
+    single = np.isscalar(N)
+    ns = [int(N)] if single else [int(n) for n in N]
+    if not ns or any(n < 0 for n in ns) or any(b <= a for a, b in zip(ns, ns[1:])):
+        raise ValueError(f"orders must be increasing and >= 0: {N}")
+    arr = (ctypes.c_int * len(ns))(*ns)
+    return arr, len(ns), single
 
 
 def window(sigma_s: float) -> int:
@@ -98,8 +116,14 @@ def window(sigma_s: float) -> int:
 BOX = 10  # BOX + P: P passes of a box of half-width r (window half-width P r)
 
 
+IIR_ERR = 3  # line_filter only: the recursive filter's tap error scale sum_m |A_m| |p_m|^d
+
+
 def _spatial(spatial, sigma_s, w, box):
-    """(operator code, window half-width) for 'fir', 'iir' or 'box' (box = (r, passes))."""
+    """(operator code, window half-width) for 'fir', 'iir', 'iir_err' (line_filter only) or 'box'
+    (box = (r, passes))."""
+    if spatial == "iir_err":
+        return IIR_ERR, 0
     if spatial == "box":
         r, passes = (int(v) for v in box)
         if not (r >= 1 and 1 <= passes <= 3):
@@ -141,8 +165,81 @@ def mean(f) -> float:
     return float(_load().bfo_mean(_ptr(f), f.size))
 
 
-def gp_bf(f, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop=None, round_coef_f32=False,
-          return_kappa=False, box=None):
+# Probes of the input's part of kappa: four with independent random signs at every pixel
+# (delta, eta, xi = +-1), then one each with the same sign everywhere (delta = 1; eta = 1; xi = 1).
+_RANDOM_PROBES = [(0.0, 1.0, 0.0, 1.0, 0.0, 1.0, float(seed)) for seed in (11, 12, 13, 14)]
+_SYSTEMATIC_PROBES = [(1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0), (0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 0.0),
+                      (0.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0)]
+
+
+def gp_tangent(f, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop=None, box=None, g=None,
+               delta=None, eta=None, xi=None, lam=None, probes=None):
+    """First-order change of gp_bf (g given: of gp_bf_joint with guide g) on the
+    crop under relative perturbations, per pixel, of the centred intensity
+    (delta: in the exponential and the power of Eq. (7) and in G_n = H^n),
+    of the argument of the exponential of Eq. (7) alone (eta), and of the
+    centred data (xi, joint filter only).  Either explicit [H, W] patterns
+    (None = zero), or probes = [(d0, d1, e0, e1, x0, x1, seed), ...] drawn
+    with signs s = probe_sign(seed, y W + x, k): delta = d0 + d1 s(k = 0),
+    eta = e0 + e1 s(k = 1), xi = x0 + x1 s(k = 2).  lam: per-pixel factor on
+    the exponential's argument (None = 1), the point the derivative is taken at.
+    N: an order or a list of increasing orders (one pass).  Returns [crop]
+    (explicit patterns) or [len(probes), crop], with an order axis after the
+    probe axis when N is a list."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    H, W = f.shape
+    gg = None if g is None else np.ascontiguousarray(g, dtype=np.float64)
+    sp, w = _spatial(spatial, sigma_s, w, box)
+    r0, r1, c0, c1 = _crop(crop, H, W)
+
+    def arr(a):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(a, np.float64), (H, W)))
+        return a
+
+    pats = [arr(delta), arr(eta), arr(xi)]
+    lam_a = arr(lam)
+    explicit = any(a is not None for a in pats)
+    if explicit == (probes is not None):
+        raise ValueError("give either explicit patterns or probes")
+    npr = 1 if explicit else len(probes)
+    spec = None if explicit else np.ascontiguousarray(np.array(probes, np.float64).reshape(npr, 7))
+    ns, nN, single = _orders(N)
+    out = np.empty((npr, nN, r1 - r0, c1 - c0), np.float64)
+    tc = float("nan") if t_c is None else float(t_c)
+    P = lambda a: _ptr(a) if a is not None else None
+    rc = _load().bfo_gp_tangent(_ptr(f), P(gg), H, W, float(sigma_s), float(sigma_r), nN, ns, tc, sp, w,
+                                r0, r1, c0, c1, P(lam_a), npr, P(spec), P(pats[0]), P(pats[1]), P(pats[2]),
+                                _ptr(out))
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    if single:
+        out = out[:, 0]
+    return out[0] if explicit else out
+
+
+def probe_sign(seed, pixel, k):
+    """The sign gp_tangent draws at pixel index y W + x for component k (0 delta, 1 eta, 2 xi)."""
+    return float(_load().bfo_gp_probe_sign(int(seed), int(pixel), int(k)))
+
+
+def kappa_input(f, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop=None, box=None, g=None):
+    """The input's part of kappa: how far relative errors eps in the centred
+    intensity at every pixel (and in the argument of the exponential of
+    Eq. (7), and in the centred data for the joint filter) move the result,
+    per eps: the root mean square over four probes with independent random
+    signs at every pixel (the size of a sum of independent roundings) plus the
+    changes under the same sign everywhere (a rounding shared by every pixel,
+    such as that of the scale).  N: an order or a list of increasing orders."""
+    probes = _RANDOM_PROBES + _SYSTEMATIC_PROBES[:2] + (_SYSTEMATIC_PROBES[2:] if g is not None else [])
+    d = gp_tangent(f, sigma_s, sigma_r, N, spatial, t_c=t_c, w=w, crop=crop, box=box, g=g, probes=probes)
+    nr = len(_RANDOM_PROBES)
+    return np.sqrt(np.mean(d[:nr] ** 2, axis=0)) + np.abs(d[nr:]).sum(axis=0)
+
+
+def gp_bf(f, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop=None, return_kappa=False, box=None,
+          lam=None):
     """O2: Algorithm 1 (GPF) in FP64.
 
     spatial: 'fir' (window sum of Eq. (8), zero extension), 'iir' (Deriche's
@@ -150,24 +247,40 @@ def gp_bf(f, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop=None, ro
     the window sum with the passes-fold iterated box of half-width r in place
     of the Gaussian (the paper's constant-time alternative).  t_c: centre (None = image mean,
     the algorithm's first step).  crop: (r0, r1, c0, c1) output region; the
-    operator still reads every sample it needs from the full image.
-    return_kappa: also return kappa = sigma_r (sum|p_n| + |P/Q| sum|q_n|) / |Q|,
-    the bound on how far relative errors eps in the terms of Eqs. (9)-(10) can
-    move the result (error <= kappa * eps); inf where Q <= 0.
+    operator still reads every sample it needs from the full image.  lam:
+    per-pixel factor on the argument of the exponential of Eq. (7) (None = 1).
+    return_kappa: also return kappa, how far relative errors eps in the
+    arithmetic move the result (error about kappa * eps; inf where Q <= 0):
+    the terms' part sigma_r (sum|p_n| + |P/Q| sum|q_n|) / |Q| (a relative
+    error in every product entering Eqs. (9)-(10)) plus kappa_input (the
+    rounding of the centred intensity itself).  return_kappa="parts" returns
+    (y, kappa, terms' part, input's part).  Where Q <= 0, Eq. (11) is undefined
+    and the pixel keeps its own value (kappa = inf there).  N: an order, or a
+    list of increasing orders computed in one pass (results stacked on a first
+    axis): the terms of order N are a prefix of Algorithm 1's loop.
     """
     f = np.ascontiguousarray(f, dtype=np.float64)
     H, W = f.shape
     sp, w = _spatial(spatial, sigma_s, w, box)
     r0, r1, c0, c1 = _crop(crop, H, W)
-    out = np.empty((r1 - r0, c1 - c0), np.float64)
+    ns, nN, single = _orders(N)
+    out = np.empty((nN, r1 - r0, c1 - c0), np.float64)
     kap = np.empty_like(out) if return_kappa else None
     tc = float("nan") if t_c is None else float(t_c)
-    rc = _load().bfo_gp(_ptr(f), H, W, float(sigma_s), float(sigma_r), int(N), tc, sp, w,
-                        1 if round_coef_f32 else 0, r0, r1, c0, c1, _ptr(out),
+    lam_a = None if lam is None else np.ascontiguousarray(np.broadcast_to(np.asarray(lam, np.float64), (H, W)))
+    rc = _load().bfo_gp(_ptr(f), H, W, float(sigma_s), float(sigma_r), nN, ns, tc, sp, w,
+                        r0, r1, c0, c1, _ptr(lam_a) if lam_a is not None else None, _ptr(out),
                         _ptr(kap) if kap is not None else None)
     if rc != 0:
         raise MemoryError("oracle allocation failed")
-    return (out, kap) if return_kappa else out
+    if single:
+        out = out[0]
+        kap = kap[0] if kap is not None else None
+    if not return_kappa:
+        return out
+    ku = kappa_input(f, sigma_s, sigma_r, N, spatial, t_c=t_c, w=w, crop=crop, box=box)
+    total = np.where(np.isfinite(kap), kap + ku, np.inf)
+    return (out, total, kap, ku) if return_kappa == "parts" else (out, total)
 
 
 def direct_bf_joint(f, g, sigma_s, sigma_r, w=None, crop=None):
@@ -184,12 +297,13 @@ def direct_bf_joint(f, g, sigma_s, sigma_r, w=None, crop=None):
     return out
 
 
-def gp_bf_joint(f, g, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop=None, round_coef_f32=False,
-                return_kappa=False, box=None):
+def gp_bf_joint(f, g, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop=None, return_kappa=False,
+                box=None, lam=None):
     """Joint (cross) bilateral filter by the Gauss-polynomial decomposition in
     FP64: Algorithm 1 with the range kernel on the centred guide g (t_c = None:
     the guide's mean), 2 (N + 1) filterings (F_n and F_n (f - t_c)).  Arguments
-    as gp_bf; kappa without the sigma_r factor."""
+    as gp_bf; kappa without the sigma_r factor, its input's part also counting
+    a relative error in the centred data."""
     f = np.ascontiguousarray(f, dtype=np.float64)
     g = np.ascontiguousarray(g, dtype=np.float64)
     assert f.shape == g.shape
@@ -199,12 +313,17 @@ def gp_bf_joint(f, g, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop
     out = np.empty((r1 - r0, c1 - c0), np.float64)
     kap = np.empty_like(out) if return_kappa else None
     tc = float("nan") if t_c is None else float(t_c)
+    lam_a = None if lam is None else np.ascontiguousarray(np.broadcast_to(np.asarray(lam, np.float64), (H, W)))
     rc = _load().bfo_gp_joint(_ptr(f), _ptr(g), H, W, float(sigma_s), float(sigma_r), int(N), tc, sp, w,
-                              1 if round_coef_f32 else 0, r0, r1, c0, c1, _ptr(out),
+                              r0, r1, c0, c1, _ptr(lam_a) if lam_a is not None else None, _ptr(out),
                               _ptr(kap) if kap is not None else None)
     if rc != 0:
         raise MemoryError("oracle allocation failed")
-    return (out, kap) if return_kappa else out
+    if not return_kappa:
+        return out
+    ku = kappa_input(f, sigma_s, sigma_r, N, spatial, t_c=t_c, w=w, crop=crop, box=box, g=g)
+    total = np.where(np.isfinite(kap), kap + ku, np.inf)
+    return (out, total, kap, ku) if return_kappa == "parts" else (out, total)
 
 
 def gp_adjoint(f, sigma_s, sigma_r, N, ybar, spatial="fir", t_c=None, w=None, box=None):
@@ -229,20 +348,20 @@ def gp_adjoint(f, sigma_s, sigma_r, N, ybar, spatial="fir", t_c=None, w=None, bo
     return fb, float(srb[0])
 
 
-def line_filter(x, sigma_s, spatial="fir", w=None, round_coef_f32=False, box=None):
+def line_filter(x, sigma_s, spatial="fir", w=None, box=None):
     """The 1-D spatial operator applied to each row of x (zero extension)."""
     x = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
     count, n = x.shape
     sp, w = _spatial(spatial, sigma_s, w, box)
     y = np.empty_like(x)
-    _load().bfo_line_filter(_ptr(x), count, n, float(sigma_s), sp, w, 1 if round_coef_f32 else 0, _ptr(y))
+    _load().bfo_line_filter(_ptr(x), count, n, float(sigma_s), sp, w, _ptr(y))
     return y
 
 
-def deriche_response(sigma_s, n, round_coef_f32=False):
+def deriche_response(sigma_s, n):
     """h(d), d = 0..n-1, of the recursive Gaussian at scale sigma_s."""
     h = np.empty(int(n), np.float64)
-    _load().bfo_deriche_response(float(sigma_s), 1 if round_coef_f32 else 0, int(n), _ptr(h))
+    _load().bfo_deriche_response(float(sigma_s), int(n), _ptr(h))
     return h
 
 
@@ -254,8 +373,8 @@ def gp_kernel(t, tau, sigma_r, N):
     return np.array(flat, np.float64).reshape(t.shape)
 
 
-def deriche_coefs(sigma_s, round_coef_f32=False):
+def deriche_coefs(sigma_s):
     """(poles[2], residues[2]) as complex numpy arrays."""
     o = np.empty(8, np.float64)
-    _load().bfo_deriche_coefs(float(sigma_s), 1 if round_coef_f32 else 0, _ptr(o))
+    _load().bfo_deriche_coefs(float(sigma_s), _ptr(o))
     return o[0:4:2] + 1j * o[1:4:2], o[4:8:2] + 1j * o[5:8:2]

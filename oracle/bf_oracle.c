@@ -48,6 +48,7 @@
 
 #define BFO_FIR 1
 #define BFO_IIR 2
+#define BFO_IIR_ERR 3 /* line filter only: the recursive filter's tap error scale (modal_abs_line) */
 #define BFO_BOX 10 /* BFO_BOX + P: P passes of a box of half-width w / P (window of half-width w) */
 
 typedef struct {
@@ -55,7 +56,7 @@ typedef struct {
     double complex A[2]; /* residues */
 } deriche_t;
 
-static void deriche_design(double sigma, int round_f32, deriche_t *D)
+static void deriche_design(double sigma, deriche_t *D)
 {
     const double a0 = 1.680, a1 = 3.735, b0 = 1.783, b1 = 1.723;
     const double c0 = -0.6803, c1 = -0.2598, w0 = 0.6318, w1 = 1.997;
@@ -63,12 +64,6 @@ static void deriche_design(double sigma, int round_f32, deriche_t *D)
     D->p[1] = cexp((-b1 + I * w1) / sigma);
     D->A[0] = a0 - I * a1;
     D->A[1] = c0 - I * c1;
-    if (round_f32) {
-        for (int m = 0; m < 2; ++m) {
-            D->p[m] = (double)(float)creal(D->p[m]) + I * (double)(float)cimag(D->p[m]);
-            D->A[m] = (double)(float)creal(D->A[m]) + I * (double)(float)cimag(D->A[m]);
-        }
-    }
 }
 
 /* FIR: y[i] = sum_{d=-w..w} taps[|d|] x[i-d], samples outside [0, n) are zero. */
@@ -102,6 +97,33 @@ static void iir_line(const double *x, long xs, int n, const deriche_t *D,
         for (int i = n - 2; i >= 0; --i) {
             v = D->p[m] * (x[(long)(i + 1) * xs] + v);
             y[(long)i * ys] += creal(D->A[m] * v);
+        }
+    }
+}
+
+/*
+ * Error scale of the recursive filter's taps: M(d) = sum_m |A_m| |p_m|^d.  The
+ * filter forms h(d) = Re sum_m A_m p_m^d from its modal terms, each carried with
+ * a relative error of the order of the arithmetic's, so the error of an
+ * effective tap is of the order of eps M(d); in the tail the terms cancel and
+ * |h(d)| is far below them.  y[i] = sum_j M(|i - j|) x[j] over the line (zero
+ * extension), computed as two first-order recursions per pole with the real
+ * factors |p_m|, |A_m| (the same form as iir_line).
+ */
+static void modal_abs_line(const double *x, long xs, int n, const deriche_t *D, double *y, long ys)
+{
+    for (int i = 0; i < n; ++i) y[(long)i * ys] = 0.0;
+    for (int m = 0; m < 2; ++m) {
+        const double r = cabs(D->p[m]), a = cabs(D->A[m]);
+        double z = 0.0;
+        for (int i = 0; i < n; ++i) {
+            z = x[(long)i * xs] + r * z;
+            y[(long)i * ys] += a * z;
+        }
+        double v = 0.0;
+        for (int i = n - 2; i >= 0; --i) {
+            v = r * (x[(long)(i + 1) * xs] + v);
+            y[(long)i * ys] += a * v;
         }
     }
 }
@@ -169,10 +191,10 @@ void bfo_set_threads(int n)
 }
 
 /* Impulse response of the recursive filter: h[d] for d = 0..n-1. */
-void bfo_deriche_response(double sigma, int round_f32, int n, double *h)
+void bfo_deriche_response(double sigma, int n, double *h)
 {
     deriche_t D;
-    deriche_design(sigma, round_f32, &D);
+    deriche_design(sigma, &D);
     for (int d = 0; d < n; ++d) {
         double acc = 0.0;
         for (int m = 0; m < 2; ++m) acc += creal(D.A[m] * cpow(D.p[m], (double)d));
@@ -181,10 +203,10 @@ void bfo_deriche_response(double sigma, int round_f32, int n, double *h)
 }
 
 /* Poles and residues as (re, im) pairs: out[0..3] = p0, p1; out[4..7] = A0, A1. */
-void bfo_deriche_coefs(double sigma, int round_f32, double *out)
+void bfo_deriche_coefs(double sigma, double *out)
 {
     deriche_t D;
-    deriche_design(sigma, round_f32, &D);
+    deriche_design(sigma, &D);
     for (int m = 0; m < 2; ++m) {
         out[2 * m] = creal(D.p[m]);
         out[2 * m + 1] = cimag(D.p[m]);
@@ -195,7 +217,7 @@ void bfo_deriche_coefs(double sigma, int round_f32, double *out)
 
 /* 1-D spatial operator on `count` independent lines of length n (row-major). */
 void bfo_line_filter(const double *x, int count, int n, double sigma_s, int spatial,
-                     int w, int round_f32, double *y)
+                     int w, double *y)
 {
     /* box variant: P passes of a flat kernel, evaluated as its window sum */
     const int box = spatial > BFO_BOX ? spatial - BFO_BOX : 0;
@@ -209,9 +231,13 @@ void bfo_line_filter(const double *x, int count, int n, double sigma_s, int spat
         free(taps);
     } else {
         deriche_t D;
-        deriche_design(sigma_s, round_f32, &D);
+        deriche_design(sigma_s, &D);
+        const int err = spatial == BFO_IIR_ERR;
 #pragma omp parallel for schedule(static)
-        for (int l = 0; l < count; ++l) iir_line(x + (long)l * n, 1, n, &D, y + (long)l * n, 1);
+        for (int l = 0; l < count; ++l) {
+            if (err) modal_abs_line(x + (long)l * n, 1, n, &D, y + (long)l * n, 1);
+            else iir_line(x + (long)l * n, 1, n, &D, y + (long)l * n, 1);
+        }
     }
 }
 
@@ -269,7 +295,7 @@ typedef struct {
     int spatial, w;
     const double *taps;
     const deriche_t *D;
-    const double *abs_h; /* |h(d)|, d = 0..abs_D: the kernel's absolute values (for kappa) */
+    const double *abs_h; /* window taps' error scale, d = 0..abs_D (for kappa; the recursive filter uses modal_abs_line) */
     int abs_D;
 } spatial_op;
 
@@ -285,7 +311,8 @@ static void apply_S_impl(const spatial_op *S, int absk, const double *a, int W, 
 #pragma omp for schedule(static)
         for (int y = ylo; y < yhi; ++y) {
             const double *src = a + (long)(y - ylo) * W;
-            if (absk) absconv_line(src, 1, W, S->abs_h, S->abs_D < W - 1 ? S->abs_D : W - 1, line, 1);
+            if (absk && S->spatial != BFO_FIR) modal_abs_line(src, 1, W, S->D, line, 1);
+            else if (absk) absconv_line(src, 1, W, S->abs_h, S->abs_D < W - 1 ? S->abs_D : W - 1, line, 1);
             else if (S->spatial == BFO_FIR) fir_line(src, 1, W, S->taps, S->w, line, 1);
             else iir_line(src, 1, W, S->D, line, 1);
             memcpy(rowtmp + (long)(y - ylo) * cw, line + c0, sizeof(double) * (size_t)cw);
@@ -298,7 +325,8 @@ static void apply_S_impl(const spatial_op *S, int absk, const double *a, int W, 
         double *col = malloc(sizeof(double) * (size_t)nr);
 #pragma omp for schedule(static)
         for (int x = 0; x < cw; ++x) {
-            if (absk) absconv_line(rowtmp + x, cw, nr, S->abs_h, S->abs_D < nr - 1 ? S->abs_D : nr - 1, col, 1);
+            if (absk && S->spatial != BFO_FIR) modal_abs_line(rowtmp + x, cw, nr, S->D, col, 1);
+            else if (absk) absconv_line(rowtmp + x, cw, nr, S->abs_h, S->abs_D < nr - 1 ? S->abs_D : nr - 1, col, 1);
             else if (S->spatial == BFO_FIR) fir_line(rowtmp + x, cw, nr, S->taps, S->w, col, 1);
             else iir_line(rowtmp + x, cw, nr, S->D, col, 1);
             for (int y = r0; y < r1; ++y) out[(long)(y - r0) * cw + x] = col[y - ylo];
@@ -315,30 +343,43 @@ static void apply_S(const spatial_op *S, const double *a, int W, int ylo, int yh
 
 /*
  * O2 -- Algorithm 1 (GPF).  f is the full H x W image; the result is produced
- * on the crop [r0, r1) x [c0, c1).  t_c: the centre of Sec. 2 (NaN selects the
+ * on the crop [r0, r1) x [c0, c1), for each of the nN increasing orders Ns
+ * (out and kappa: [nN][crop]; the terms of order N are a prefix of the loop).  t_c: the centre of Sec. 2 (NaN selects the
  * image mean of the algorithm's first step).  spatial: BFO_FIR (window w) or
- * BFO_IIR.  round_f32 rounds the recursive filter's poles and residues to
- * single precision before use (the values a single-precision implementation
- * holds).  Returns 0 on success, -1 on allocation failure.
+ * BFO_IIR.  Returns 0 on success, -1 on allocation failure.
  *
  * sigma_r = +inf is taken as its limit: every G_n, n >= 1, vanishes and the
- * result is S(h)/S(1) + t_c, the normalised spatial filter.  A pixel whose
- * denominator Q is not positive is returned as NaN (with the window sum this
- * needs odd N, where the truncated exponential has a real root; the recursive
- * filter's small negative tail can also do it when (R / sigma_r)^2 is large).
+ * result is S(h)/S(1) + t_c, the normalised spatial filter.  Where the
+ * denominator Q is not positive, Eq. (11) is undefined and the pixel keeps its
+ * own value f (with the window sum this needs odd N, where the truncated
+ * exponential has a real root; the recursive filter's small negative tail also
+ * does it when (R / sigma_r)^2 is large).
+ *
+ * lam (may be NULL): a per-pixel factor on the argument of the exponential
+ * of Eq. (7), E = exp(-lam h^2 / 2 sigma_r^2) (1 everywhere when NULL); it
+ * only serves to pin the sensitivity to that argument (bfo_gp_tangent).
  *
  * kappa (may be NULL): first-order bound on how far relative errors eps in
  * every product entering P and Q (the spatial sums of Eq. (8) and the terms
  * of Eqs. (9)-(10)) can move the result:
  *     kappa = sigma_r (sum_n |G_n| (|h| * |F_{n+1}|) / n! + |P/Q| sum_n |G_n| (|h| * |F_n|) / n!) / |Q|,
- * where |h| * |F| filters |F| with the absolute spatial kernel (explicitly,
- * out to 40 sigma_s for the recursive one); the result moves by at most
- * about kappa * eps.  Infinite where Q <= 0.
+ * where |h| * |F| filters |F| with the error scale of the spatial kernel's
+ * taps: the window taps themselves, or, for the recursive filter, the
+ * magnitude sum_m |A_m| |p_m|^d of its modal terms (modal_abs_line); the
+ * result moves by at most about kappa * eps.  The sensitivity to rounding the centred intensity itself is
+ * bfo_gp_tangent's.
+ * Infinite where Q <= 0.
  */
-int bfo_gp(const double *f, int H, int W, double sigma_s, double sigma_r, int N,
-           double t_c, int spatial, int w, int round_f32,
-           int r0, int r1, int c0, int c1, double *out, double *kappa)
+int bfo_gp(const double *f, int H, int W, double sigma_s, double sigma_r, int nN, const int *Ns,
+           double t_c, int spatial, int w, int r0, int r1, int c0, int c1, const double *lam, double *out,
+           double *kappa)
 {
+    /* orders: Ns[0] < Ns[1] < ... ; the loop runs to the last one and the result of each is taken when
+       the loop has added its terms (P and Q of order N are the sums over n <= N) */
+    if (nN < 1) return -1;
+    for (int q = 0; q < nN; ++q)
+        if (Ns[q] < 0 || (q > 0 && Ns[q] <= Ns[q - 1])) return -1;
+    const int N = Ns[nN - 1];
     /* box variant: P passes of a flat kernel, evaluated as its window sum */
     const int box = spatial > BFO_BOX ? spatial - BFO_BOX : 0;
     if (box) spatial = BFO_FIR;
@@ -361,28 +402,17 @@ int bfo_gp(const double *f, int H, int W, double sigma_s, double sigma_r, int N,
         else make_taps(sigma_s, w, taps);
         S.taps = taps;
     } else {
-        deriche_design(sigma_s, round_f32, &D);
+        deriche_design(sigma_s, &D);
         S.D = &D;
     }
-    /* |h(d)| for kappa: the window taps, or the recursive kernel out to 40 sigma (|h| < 1e-29 there) */
+    /* the error scale of each tap for kappa: the window taps (the recursive filter's is modal_abs_line) */
     double *abs_h = NULL;
-    if (kappa) {
-        int Dn = spatial == BFO_FIR ? w : (int)ceil(40.0 * sigma_s);
-        const int nmax = (H > W ? H : W) - 1;
-        if (spatial != BFO_FIR && Dn > nmax) Dn = nmax;
-        if (Dn < 0) Dn = 0;
-        abs_h = malloc(sizeof(double) * (size_t)(Dn + 1));
+    if (kappa && spatial == BFO_FIR) {
+        abs_h = malloc(sizeof(double) * (size_t)(w + 1));
         if (!abs_h) { free(taps); return -1; }
-        for (int d = 0; d <= Dn; ++d) {
-            if (spatial == BFO_FIR) abs_h[d] = taps[d];
-            else {
-                double acc = 0.0;
-                for (int m = 0; m < 2; ++m) acc += creal(D.A[m] * cpow(D.p[m], (double)d));
-                abs_h[d] = fabs(acc);
-            }
-        }
+        for (int d = 0; d <= w; ++d) abs_h[d] = taps[d];
         S.abs_h = abs_h;
-        S.abs_D = Dn;
+        S.abs_D = w;
     }
 
     /* F and Hs live on the full-width rows [ylo, yhi) (offset so that row y is at (y - ylo) * W) */
@@ -417,10 +447,11 @@ int bfo_gp(const double *f, int H, int W, double sigma_s, double sigma_r, int N,
             apply_S_impl(&S, 1, Fa, W, ylo, yhi, r0, r1, c0, c1, rowtmp, Pa);
             apply_S_impl(&S, 1, Hs, W, ylo, yhi, r0, r1, c0, c1, rowtmp, Qa);
         }
-        for (long i = 0; i < ncrop; ++i) {
-            out[i] = P[i] / Q[i] + t_c;
-            if (kappa) kappa[i] = (Pa[i] + fabs(P[i] / Q[i]) * Qa[i]) / fabs(Q[i]);
-        }
+        for (int q = 0; q < nN; ++q)
+            for (long i = 0; i < ncrop; ++i) {
+                out[(long)q * ncrop + i] = P[i] / Q[i] + t_c;
+                if (kappa) kappa[(long)q * ncrop + i] = (Pa[i] + fabs(P[i] / Q[i]) * Qa[i]) / fabs(Q[i]);
+            }
         goto done;
     }
 
@@ -428,7 +459,7 @@ int bfo_gp(const double *f, int H, int W, double sigma_s, double sigma_r, int N,
 #pragma omp parallel for schedule(static)
     for (long i = 0; i < nreg; ++i) {
         const double h = f[(long)ylo * W + i] - t_c;
-        F[i] = exp(-h * h / (2.0 * sigma_r * sigma_r));
+        F[i] = exp(-(lam ? lam[(long)ylo * W + i] : 1.0) * h * h / (2.0 * sigma_r * sigma_r));
         Hs[i] = h / sigma_r;
     }
     for (int y = r0; y < r1; ++y)
@@ -465,11 +496,18 @@ int bfo_gp(const double *f, int H, int W, double sigma_s, double sigma_r, int N,
         }
         for (long i = 0; i < ncrop; ++i) G[i] *= Hc[i];
         c /= (double)(n + 1);
-    }
-    /* step 18: Eq. (11) with the sigma_r of Eq. (9), then undo the centring (Eq. (6)) */
-    for (long i = 0; i < ncrop; ++i) {
-        out[i] = Q[i] > 0.0 ? sigma_r * (P[i] / Q[i]) + t_c : NAN;
-        if (kappa) kappa[i] = Q[i] > 0.0 ? sigma_r * (Pa[i] + fabs(P[i] / Q[i]) * Qa[i]) / Q[i] : INFINITY;
+        /* step 18 for every requested order n: Eq. (11) with the sigma_r of Eq. (9), then undo the
+           centring (Eq. (6)) */
+        for (int q = 0; q < nN; ++q) {
+            if (Ns[q] != n) continue;
+            double *o = out + (long)q * ncrop, *k = kappa ? kappa + (long)q * ncrop : NULL;
+            for (long i = 0; i < ncrop; ++i) {
+                /* Q <= 0: Eq. (11) is undefined; the pixel keeps its own value */
+                const double fi = f[(long)(r0 + i / cw) * W + c0 + i % cw];
+                o[i] = Q[i] > 0.0 ? sigma_r * (P[i] / Q[i]) + t_c : fi;
+                if (k) k[i] = Q[i] > 0.0 ? sigma_r * (Pa[i] + fabs(P[i] / Q[i]) * Qa[i]) / Q[i] : INFINITY;
+            }
+        }
     }
 
 done:
@@ -523,11 +561,11 @@ void bfo_direct_joint(const double *f, const double *g, int H, int W, double sig
  * with G_n = H^n at the output pixel (Eqs. (9)-(10) with the data f in place
  * of h in the numerator).  With g = f this is Algorithm 1 (P here is sigma_r
  * times the P of Eq. (9)).  t_c: NaN selects the guide's mean.  Other
- * arguments and kappa as bfo_gp (kappa without the sigma_r factor).
+ * arguments, lam and kappa as bfo_gp (kappa without the sigma_r factor).
  */
 int bfo_gp_joint(const double *f, const double *g, int H, int W, double sigma_s, double sigma_r, int N,
-                 double t_c, int spatial, int w, int round_f32,
-                 int r0, int r1, int c0, int c1, double *out, double *kappa)
+                 double t_c, int spatial, int w, int r0, int r1, int c0, int c1, const double *lam, double *out,
+                 double *kappa)
 {
     /* box variant: P passes of a flat kernel, evaluated as its window sum */
     const int box = spatial > BFO_BOX ? spatial - BFO_BOX : 0;
@@ -551,27 +589,16 @@ int bfo_gp_joint(const double *f, const double *g, int H, int W, double sigma_s,
         else make_taps(sigma_s, w, taps);
         S.taps = taps;
     } else {
-        deriche_design(sigma_s, round_f32, &D);
+        deriche_design(sigma_s, &D);
         S.D = &D;
     }
     double *abs_h = NULL;
-    if (kappa) {
-        int Dn = spatial == BFO_FIR ? w : (int)ceil(40.0 * sigma_s);
-        const int nmax = (H > W ? H : W) - 1;
-        if (spatial != BFO_FIR && Dn > nmax) Dn = nmax;
-        if (Dn < 0) Dn = 0;
-        abs_h = malloc(sizeof(double) * (size_t)(Dn + 1));
+    if (kappa && spatial == BFO_FIR) {
+        abs_h = malloc(sizeof(double) * (size_t)(w + 1));
         if (!abs_h) { free(taps); return -1; }
-        for (int d = 0; d <= Dn; ++d) {
-            if (spatial == BFO_FIR) abs_h[d] = taps[d];
-            else {
-                double acc = 0.0;
-                for (int m = 0; m < 2; ++m) acc += creal(D.A[m] * cpow(D.p[m], (double)d));
-                abs_h[d] = fabs(acc);
-            }
-        }
+        for (int d = 0; d <= w; ++d) abs_h[d] = taps[d];
         S.abs_h = abs_h;
-        S.abs_D = Dn;
+        S.abs_D = w;
     }
 
     double *F = malloc(sizeof(double) * (size_t)nreg);   /* F_n on the rows the operator reads */
@@ -601,7 +628,7 @@ int bfo_gp_joint(const double *f, const double *g, int H, int W, double sigma_s,
 #pragma omp parallel for schedule(static)
     for (long i = 0; i < nreg; ++i) {
         const double h = g[(long)ylo * W + i] - t_c;
-        F[i] = inf_r ? 1.0 : exp(-h * h / (2.0 * sigma_r * sigma_r));
+        F[i] = inf_r ? 1.0 : exp(-(lam ? lam[(long)ylo * W + i] : 1.0) * h * h / (2.0 * sigma_r * sigma_r));
         Hs[i] = inf_r ? 0.0 : h / sigma_r;
         Dc[i] = f[(long)ylo * W + i] - t_c;
     }
@@ -640,12 +667,286 @@ int bfo_gp_joint(const double *f, const double *g, int H, int W, double sigma_s,
         c /= (double)(n + 1);
     }
     for (long i = 0; i < ncrop; ++i) {
-        out[i] = Q[i] > 0.0 ? P[i] / Q[i] + t_c : NAN;
+        /* Q <= 0: the ratio is undefined; the pixel keeps its data value */
+        const double fi = f[(long)(r0 + i / cw) * W + c0 + i % cw];
+        out[i] = Q[i] > 0.0 ? P[i] / Q[i] + t_c : fi;
         if (kappa) kappa[i] = Q[i] > 0.0 ? (Pa[i] + fabs(P[i] / Q[i]) * Qa[i]) / Q[i] : INFINITY;
     }
     free(F); free(FD); free(Hs); free(Dc); free(rowtmp); free(Fbar); free(G); free(Hc); free(P); free(Q);
     free(Pa); free(Qa); free(Fa); free(FbarA); free(taps); free(abs_h);
     return 0;
+}
+
+/*
+ * Probe signs for bfo_gp_tangent: the top bit of splitmix64 (Steele, Lea and
+ * Flood, "Fast splittable pseudorandom number generators", 2014) applied to
+ * the seed mixed with a per-pixel counter.
+ */
+static unsigned long long bfo_splitmix64(unsigned long long z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static double bfo_probe_sign(unsigned long long seed, long counter)
+{
+    return (bfo_splitmix64(seed ^ bfo_splitmix64((unsigned long long)counter)) >> 63) ? -1.0 : 1.0;
+}
+
+/* the sign bfo_gp_tangent draws for pixel index y W + x, component k (0: delta, 1: eta, 2: xi) */
+double bfo_gp_probe_sign(unsigned long long seed, long pixel, int k)
+{
+    return bfo_probe_sign(seed, 3 * pixel + k);
+}
+
+/*
+ * First-order change of O2 (bfo_gp; with a guide g: bfo_gp_joint) on the crop
+ * under relative perturbations, at every pixel j of the image, of
+ *   delta_j: the centred intensity H_j = (g_j - t_c) / sigma_r (g = f for the
+ *            plain filter) in all its uses: the exponential and the power of
+ *            Eq. (7) where j is an input, G_n = H^n where j is the output pixel;
+ *   eta_j:   the argument lam_j H_j^2 / 2 of the exponential of Eq. (7) alone;
+ *   xi_j:    the centred data f_j - t_c (joint filter only).
+ * This is the derivative of Eqs. (7)-(11), taken in forward mode:
+ *   dF_n = F_n ((n - lam H^2) delta - lam (H^2 / 2) eta),   dG_n = n G_n delta,
+ *   dQ = sum_n (dG_n S F_n + G_n S dF_n) / n!,   dP the same with F_{n+1}
+ *   (joint: with F_n (f - t_c), whose change also has F_n (f - t_c) xi),
+ *   dy = sigma_r (dP - (P / Q) dQ) / Q   (joint: without sigma_r),
+ * and for sigma_r = inf (y = S(h) / S(1) + t_c)  dy = S(h delta) / S(1)
+ * (joint: S((f - t_c) xi) / S(1)).
+ * npr probes: either one explicit probe (delta, eta, xi are [H][W] arrays or
+ * NULL for zero; spec unused) or, when all three are NULL, npr drawn ones:
+ * spec[7p .. 7p+6] = {d0, d1, e0, e1, x0, x1, seed} gives delta_j = d0 + d1 s_j,
+ * eta_j = e0 + e1 s'_j, xi_j = x0 + x1 s''_j with the signs of
+ * bfo_gp_probe_sign(seed, y W + x, 0 / 1 / 2).  dy: [npr][nN][crop] for the
+ * increasing orders Ns; where Q <= 0
+ * (the pixel keeps its value) the change of that value.  t_c: NaN selects the
+ * mean (of g for the joint filter).  Returns 0,
+ * or -1 on allocation failure or bad arguments.
+ */
+int bfo_gp_tangent(const double *f, const double *g, int H, int W, double sigma_s, double sigma_r, int nN,
+                   const int *Ns, double t_c, int spatial, int w, int r0, int r1, int c0, int c1, const double *lam,
+                   int npr, const double *spec, const double *delta, const double *eta, const double *xi, double *dy)
+{
+    if (nN < 1) return -1;
+    for (int q = 0; q < nN; ++q)
+        if (Ns[q] < 0 || (q > 0 && Ns[q] <= Ns[q - 1])) return -1;
+    const int N = Ns[nN - 1];
+    const int joint = g != NULL;
+    const int explicit_probe = delta || eta || xi;
+    if (npr < 1 || (explicit_probe && npr != 1) || (!explicit_probe && !spec)) return -1;
+    const int box = spatial > BFO_BOX ? spatial - BFO_BOX : 0;
+    if (box) spatial = BFO_FIR;
+    const int cw = c1 - c0, ch = r1 - r0;
+    const long ncrop = (long)cw * ch;
+    int ylo = 0, yhi = H;
+    if (spatial == BFO_FIR) {
+        ylo = r0 - w < 0 ? 0 : r0 - w;
+        yhi = r1 + w > H ? H : r1 + w;
+    }
+    const long nreg = (long)(yhi - ylo) * W;
+    const int inf_r = isinf(sigma_r);
+    /* channels: F_n, n = 0..N+1 (plain); F_n and F_n (f - t_c), n = 0..N (joint) */
+    const int K = joint ? 2 * (N + 1) : (inf_r ? 2 : N + 2);
+
+    double *taps = NULL;
+    deriche_t D;
+    spatial_op S = {spatial, w, NULL, NULL, NULL, 0};
+    if (spatial == BFO_FIR) {
+        taps = malloc(sizeof(double) * (size_t)(w + 1));
+        if (!taps) return -1;
+        if (box) make_box_taps(box, w / box, taps);
+        else make_taps(sigma_s, w, taps);
+        S.taps = taps;
+    } else {
+        deriche_design(sigma_s, &D);
+        S.D = &D;
+    }
+    double *E = malloc(sizeof(double) * (size_t)nreg);      /* exp(-lam H^2 / 2) */
+    double *Hs = malloc(sizeof(double) * (size_t)nreg);     /* H on the operator's rows */
+    double *L2 = malloc(sizeof(double) * (size_t)nreg);     /* lam H^2 */
+    double *Dc = malloc(sizeof(double) * (size_t)nreg);     /* f - t_c */
+    double *Fn = malloc(sizeof(double) * (size_t)nreg);
+    double *dF = malloc(sizeof(double) * (size_t)nreg);
+    double *pd = malloc(sizeof(double) * (size_t)nreg);     /* the probe's delta, eta, xi on the rows */
+    double *pe = malloc(sizeof(double) * (size_t)nreg);
+    double *px = malloc(sizeof(double) * (size_t)nreg);
+    double *rowtmp = malloc(sizeof(double) * (size_t)((long)(yhi - ylo) * cw));
+    double *Fb = malloc(sizeof(double) * (size_t)ncrop * K);  /* S of every channel on the crop */
+    double *dFb = malloc(sizeof(double) * (size_t)ncrop);
+    double *Hc = malloc(sizeof(double) * (size_t)ncrop);
+    double *P = calloc((size_t)ncrop * nN, sizeof(double)); /* [order][crop] */
+    double *Q = calloc((size_t)ncrop * nN, sizeof(double));
+    double *dP = malloc(sizeof(double) * (size_t)ncrop * nN);
+    double *dQ = malloc(sizeof(double) * (size_t)ncrop * nN);
+    double *Gc = malloc(sizeof(double) * (size_t)ncrop);
+    double *dc = malloc(sizeof(double) * (size_t)ncrop);    /* delta at the crop's output pixels */
+    double *Wp = malloc(sizeof(double) * (size_t)ncrop);
+    int rc = -1;
+    if (!E || !Hs || !L2 || !Dc || !Fn || !dF || !pd || !pe || !px || !rowtmp || !Fb || !dFb || !Hc || !P || !Q ||
+        !dP || !dQ || !Gc || !dc || !Wp)
+        goto out;
+    rc = 0;
+    const double *rng_src = joint ? g : f;
+    if (isnan(t_c)) t_c = bfo_mean(rng_src, (long)H * W);
+    for (long i = 0; i < nreg; ++i) {
+        const double h = rng_src[(long)ylo * W + i] - t_c;
+        const double l = lam ? lam[(long)ylo * W + i] : 1.0;
+        Hs[i] = inf_r ? 0.0 : h / sigma_r;
+        L2[i] = l * Hs[i] * Hs[i];
+        E[i] = exp(-0.5 * L2[i]);
+        Dc[i] = (joint ? f[(long)ylo * W + i] : rng_src[(long)ylo * W + i]) - t_c;
+    }
+    for (int y = r0; y < r1; ++y)
+        for (int x = c0; x < c1; ++x)
+            Hc[(long)(y - r0) * cw + (x - c0)] = inf_r ? 0.0 : (rng_src[(long)y * W + x] - t_c) / sigma_r;
+
+    /* forward: every filtered channel on the crop (Fb), then P and Q */
+    if (!joint && inf_r) {
+        /* plain filter, sigma_r = inf: channel 0 = 1, channel 1 = h */
+        for (long i = 0; i < nreg; ++i) Fn[i] = 1.0;
+        apply_S(&S, Fn, W, ylo, yhi, r0, r1, c0, c1, rowtmp, Fb);
+        apply_S(&S, Dc, W, ylo, yhi, r0, r1, c0, c1, rowtmp, Fb + ncrop);
+        for (int q = 0; q < nN; ++q)
+            for (long i = 0; i < ncrop; ++i) {
+                Q[(long)q * ncrop + i] = Fb[i];
+                P[(long)q * ncrop + i] = Fb[ncrop + i];
+            }
+    } else {
+        for (long i = 0; i < nreg; ++i) Fn[i] = E[i];
+        const int nch = joint ? N + 1 : N + 2; /* powers n = 0..nch-1 */
+        for (int n = 0; n < nch; ++n) {
+            if (n > 0)
+                for (long i = 0; i < nreg; ++i) Fn[i] *= Hs[i];
+            if (joint) {
+                apply_S(&S, Fn, W, ylo, yhi, r0, r1, c0, c1, rowtmp, Fb + (long)(2 * n) * ncrop);
+                for (long i = 0; i < nreg; ++i) dF[i] = Fn[i] * Dc[i];
+                apply_S(&S, dF, W, ylo, yhi, r0, r1, c0, c1, rowtmp, Fb + (long)(2 * n + 1) * ncrop);
+            } else {
+                apply_S(&S, Fn, W, ylo, yhi, r0, r1, c0, c1, rowtmp, Fb + (long)n * ncrop);
+            }
+        }
+        /* Eqs. (9)-(10): Q = sum_{n<=N} G_n Fbar_n / n!, P = sum_{n<=N} G_n Fbar_{n+1} / n!
+           (joint: P with the data channel of power n) */
+        for (long i = 0; i < ncrop; ++i) {
+            double gn = 1.0, c = 1.0, sq = 0.0, spp = 0.0;
+            for (int n = 0, q = 0; n <= N; ++n) {
+                if (joint) {
+                    sq += c * gn * Fb[(long)(2 * n) * ncrop + i];
+                    spp += c * gn * Fb[(long)(2 * n + 1) * ncrop + i];
+                } else {
+                    sq += c * gn * Fb[(long)n * ncrop + i];
+                    spp += c * gn * Fb[(long)(n + 1) * ncrop + i];
+                }
+                if (n == Ns[q]) {
+                    Q[(long)q * ncrop + i] = sq;
+                    P[(long)q * ncrop + i] = spp;
+                    ++q;
+                }
+                gn *= Hc[i];
+                c /= (double)(n + 1);
+            }
+        }
+    }
+
+    /* probes */
+    for (int p = 0; p < npr; ++p) {
+        const double *sp = spec ? spec + 7 * p : NULL;
+        const unsigned long long seed = sp ? (unsigned long long)sp[6] : 0ull;
+        for (int y = ylo; y < yhi; ++y)
+            for (int x = 0; x < W; ++x) {
+                const long j = (long)y * W + x, i = (long)(y - ylo) * W + x;
+                if (explicit_probe) {
+                    pd[i] = delta ? delta[j] : 0.0;
+                    pe[i] = eta ? eta[j] : 0.0;
+                    px[i] = xi ? xi[j] : 0.0;
+                } else {
+                    pd[i] = sp[0] + sp[1] * bfo_gp_probe_sign(seed, j, 0);
+                    pe[i] = sp[2] + sp[3] * bfo_gp_probe_sign(seed, j, 1);
+                    px[i] = sp[4] + sp[5] * bfo_gp_probe_sign(seed, j, 2);
+                }
+            }
+        for (int y = r0; y < r1; ++y)
+            for (int x = c0; x < c1; ++x)
+                dc[(long)(y - r0) * cw + (x - c0)] = pd[(long)(y - ylo) * W + x];
+        double *out = dy + (long)p * nN * ncrop;
+        if (!joint && inf_r) {
+            /* dy = S(h delta) / S(1), the same for every order */
+            for (long i = 0; i < nreg; ++i) dF[i] = Dc[i] * pd[i];
+            apply_S(&S, dF, W, ylo, yhi, r0, r1, c0, c1, rowtmp, dFb);
+            for (int q = 0; q < nN; ++q)
+                for (long i = 0; i < ncrop; ++i) out[(long)q * ncrop + i] = dFb[i] / Q[i];
+            continue;
+        }
+        /* output-pixel part: dG_n = n G_n delta */
+        for (long i = 0; i < ncrop; ++i) {
+            double gn = 1.0, c = 1.0, sq = 0.0, spp = 0.0;
+            for (int n = 0, q = 0; n <= N; ++n) {
+                if (joint) {
+                    sq += c * n * gn * Fb[(long)(2 * n) * ncrop + i];
+                    spp += c * n * gn * Fb[(long)(2 * n + 1) * ncrop + i];
+                } else {
+                    sq += c * n * gn * Fb[(long)n * ncrop + i];
+                    spp += c * n * gn * Fb[(long)(n + 1) * ncrop + i];
+                }
+                if (n == Ns[q]) {
+                    dQ[(long)q * ncrop + i] = sq * dc[i];
+                    dP[(long)q * ncrop + i] = spp * dc[i];
+                    ++q;
+                }
+                gn *= Hc[i];
+                c /= (double)(n + 1);
+            }
+        }
+        /* input part: dF_n = F_n ((n - lam H^2) delta - lam (H^2 / 2) eta), filtered; channel n enters Q
+           with weight G_n / n! (n <= N) and P with G_{n-1} / (n-1)! (n >= 1; joint: its data channel, G_n / n!) */
+        for (long i = 0; i < nreg; ++i) Fn[i] = E[i];
+        for (long i = 0; i < ncrop; ++i) {
+            Gc[i] = 1.0; /* G_n / n! */
+            Wp[i] = 0.0; /* G_{n-1} / (n-1)! */
+        }
+        const int nch = joint ? N + 1 : N + 2;
+        for (int n = 0; n < nch; ++n) {
+            if (n > 0)
+                for (long i = 0; i < nreg; ++i) Fn[i] *= Hs[i];
+            for (long i = 0; i < nreg; ++i) dF[i] = Fn[i] * ((n - L2[i]) * pd[i] - 0.5 * L2[i] * pe[i]);
+            apply_S(&S, dF, W, ylo, yhi, r0, r1, c0, c1, rowtmp, dFb);
+            /* order N takes channel n into Q when n <= N and into P when n <= N + 1 (joint: n <= N) */
+            for (int q = 0; q < nN; ++q) {
+                double *dq = dQ + (long)q * ncrop, *dp = dP + (long)q * ncrop;
+                for (long i = 0; i < ncrop; ++i) {
+                    if (n <= Ns[q]) dq[i] += Gc[i] * dFb[i];
+                    if (!joint && n >= 1 && n <= Ns[q] + 1) dp[i] += Wp[i] * dFb[i];
+                }
+            }
+            if (joint) {
+                /* data channel F_n (f - t_c): the same change times (f - t_c), plus F_n (f - t_c) xi */
+                for (long i = 0; i < nreg; ++i) dF[i] = (dF[i] + Fn[i] * px[i]) * Dc[i];
+                apply_S(&S, dF, W, ylo, yhi, r0, r1, c0, c1, rowtmp, dFb);
+                for (int q = 0; q < nN; ++q)
+                    if (n <= Ns[q])
+                        for (long i = 0; i < ncrop; ++i) dP[(long)q * ncrop + i] += Gc[i] * dFb[i];
+            }
+            for (long i = 0; i < ncrop; ++i) {
+                Wp[i] = Gc[i];
+                Gc[i] *= Hc[i] / (double)(n + 1);
+            }
+        }
+        const double pref = joint ? 1.0 : sigma_r;
+        for (long e = 0; e < (long)nN * ncrop; ++e) {
+            /* Q <= 0: y is the pixel's own (data) value, which moves with its own perturbation */
+            const long i = e % ncrop;
+            const long j = (long)(r0 + i / cw - ylo) * W + c0 + i % cw;
+            out[e] = Q[e] > 0.0 ? pref * (dP[e] - (P[e] / Q[e]) * dQ[e]) / Q[e] : Dc[j] * (joint ? px[j] : pd[j]);
+        }
+    }
+out:
+    free(taps); free(E); free(Hs); free(L2); free(Dc); free(Fn); free(dF); free(pd); free(pe); free(px);
+    free(rowtmp); free(Fb); free(dFb); free(Hc); free(P); free(Q); free(dP); free(dQ); free(Gc); free(dc);
+    free(Wp);
+    return rc;
 }
 
 /*
@@ -680,6 +981,7 @@ double bfo_gp_kernel(double t, double tau, double sigma_r, int N)
  *          hbar                                 when t_c is given.
  *   sigma_r: y depends on it through the explicit factor, H (dH/dsigma_r = -H/sigma_r)
  *   and E (dE/dsigma_r = E h^2 / sigma_r^3).
+ *   A pixel whose Q <= 0 keeps its value (y = f): it passes ybar to its own input only.
  * Full image only (no crop).  Returns 0, or -1 on allocation failure.
  */
 int bfo_gp_adjoint(const double *f, int H_, int W, double sigma_s, double sigma_r, int N, double t_c_given,
@@ -700,7 +1002,7 @@ int bfo_gp_adjoint(const double *f, int H_, int W, double sigma_s, double sigma_
         else make_taps(sigma_s, w, taps);
         S.taps = taps;
     } else {
-        deriche_design(sigma_s, 0, &D);
+        deriche_design(sigma_s, &D);
         S.D = &D;
     }
     double *h = malloc(sizeof(double) * (size_t)n);
@@ -742,6 +1044,13 @@ int bfo_gp_adjoint(const double *f, int H_, int W, double sigma_s, double sigma_
             Q[i] += c * g * Fb[(long)k * n + i];
             g *= Hh[i];
             c /= (double)(k + 1);
+        }
+        if (!(Q[i] > 0.0)) {
+            /* Q <= 0: y = f (the pixel keeps its value), so dL/df gets ybar directly; written as
+               y = t_c + h, its t_c part cancels in the centring term below */
+            Pb[i] = Qb[i] = 0.0;
+            hb[i] += ybar[i];
+            continue;
         }
         Pb[i] = ybar[i] * sigma_r / Q[i];
         Qb[i] = -ybar[i] * sigma_r * P[i] / (Q[i] * Q[i]);

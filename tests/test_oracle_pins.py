@@ -114,6 +114,23 @@ def test_iir_line_operator_is_symmetric_toeplitz(sigma, n):
     np.testing.assert_allclose(M, ref, rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("sigma,n", [(2.0, 40), (7.5, 90)])
+def test_iir_error_scale_is_the_modal_magnitude(sigma, n):
+    """The recursive filter's tap error scale used by kappa, M(d) = sum_m |A_m| |p_m|^d
+    (the magnitudes of the modal terms that h(d) is formed from), filtered by its
+    recursions, equals the explicit convolution with M; M >= |h| everywhere, and far
+    above it where the terms cancel (around the kernel's negative lobe)."""
+    p, A = oracle.deriche_coefs(sigma)
+    d = np.arange(n)
+    M = sum(abs(A[m]) * abs(p[m]) ** d for m in range(2))
+    x = np.random.default_rng(8).normal(size=(3, n))
+    y = oracle.line_filter(x, sigma, "iir_err")
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    np.testing.assert_allclose(y, x @ M[np.abs(i - j)].T, rtol=1e-12, atol=1e-12)
+    h = np.abs(oracle.deriche_response(sigma, n))
+    assert np.all(M >= h) and np.max(M[1:] / h[1:]) > 5
+
+
 @pytest.mark.parametrize("sigma", [1.0, 3.0, 4.5])
 def test_fir_line_matches_scipy(sigma):
     x = np.random.default_rng(5).normal(size=(3, 50))
@@ -279,12 +296,39 @@ def test_crop_equals_full_slice(sp):
 
 
 def test_odd_order_can_give_non_positive_denominator():
-    """Odd N: the truncated exponential has a real root; pixels whose Q <= 0 are NaN."""
+    """Odd N: the truncated exponential has a real root, so Q <= 0 can happen; Eq. (11)
+    is undefined there and the pixel keeps its own value (the reading for that case).
+    Even N with the window sum never has Q <= 0."""
     f = np.zeros((16, 16))
     f[:, 8] = 255.0  # a thin bright line: its pixels see mostly negative weights
-    y = oracle.gp_bf(f, 3.0, 20.0, 5, "fir")
-    assert np.isnan(y[:, 8]).all() and not np.isnan(np.delete(y, 8, axis=1)).any()
-    assert not np.isnan(oracle.gp_bf(f, 3.0, 20.0, 6, "fir")).any()
+    y, k = oracle.gp_bf(f, 3.0, 20.0, 5, "fir", return_kappa=True)
+    assert np.all(y[:, 8] == 255.0) and np.all(np.isinf(k[:, 8]))
+    others = np.delete(y, 8, axis=1)
+    assert np.all(np.isfinite(np.delete(k, 8, axis=1))) and np.all(others < 255.0)
+    _, k6 = oracle.gp_bf(f, 3.0, 20.0, 6, "fir", return_kappa=True)
+    assert np.all(np.isfinite(k6))
+
+
+def test_adjoint_where_the_denominator_is_not_positive():
+    """O3 with pixels whose Q <= 0 (odd N): they pass dL/dy to their own input,
+    against central differences of O2 (which keeps their value there)."""
+    f = np.zeros((9, 10))
+    f[:, 5] = 255.0
+    f += synthetic.make_image(9, 10, 2, 4.0, 0.0, synthetic.seed_for(9, 47)).astype(np.float64) * 0.05
+    _, k = oracle.gp_bf(f, 1.5, 20.0, 5, "fir", return_kappa=True)
+    assert np.isinf(k).sum() >= 5  # some pixels take the Q <= 0 branch
+    yb = np.random.default_rng(7).normal(size=f.shape)
+    g, gs = oracle.gp_adjoint(f, 1.5, 20.0, 5, yb, "fir")
+    L = lambda ff, sr=20.0: float((yb * oracle.gp_bf(ff, 1.5, sr, 5, "fir")).sum())
+    eps = 1e-5
+    fd = np.empty_like(f)
+    for idx in np.ndindex(f.shape):
+        e = np.zeros_like(f)
+        e[idx] = eps
+        fd[idx] = (L(f + e) - L(f - e)) / (2 * eps)
+    np.testing.assert_allclose(g, fd, rtol=0, atol=1e-6 * max(1.0, np.abs(fd).max()))
+    fds = (L(f, 20.0 + 1e-4) - L(f, 20.0 - 1e-4)) / 2e-4
+    assert abs(gs - fds) <= 1e-6 * max(1.0, abs(fds))
 
 
 # ------------------------------------------------------- Eq. (5) and Fig. 1-3
@@ -338,15 +382,115 @@ def test_error_grows_with_abs_tau():
 
 @pytest.mark.parametrize("sp", ["fir", "iir"])
 def test_kappa_lower_bound_and_equality(sp):
-    """kappa >= 2 |y - t_c| by the triangle inequality; with non-negative terms
-    (f >= t_c = 0 and the positive window weights) it is equal."""
+    """The terms' part of kappa is >= 2 |y - t_c| by the triangle inequality; with
+    non-negative terms (f >= t_c = 0 and the positive window weights) it is equal.
+    The total adds the input's part, which is non-negative."""
     f = small_image(30, 26, 31)
-    y, k = oracle.gp_bf(f, 2.0, 30.0, 20, sp, return_kappa=True)
+    y, k, kt, ku = oracle.gp_bf(f, 2.0, 30.0, 20, sp, return_kappa="parts")
     tc = f.mean()
-    assert np.all(k >= 2 * np.abs(y - tc) * (1 - 1e-12))
+    assert np.all(kt >= 2 * np.abs(y - tc) * (1 - 1e-12))
+    assert np.all(ku >= 0) and np.array_equal(k, kt + ku)
     if sp == "fir":
-        y0, k0 = oracle.gp_bf(f, 2.0, 30.0, 20, sp, t_c=0.0, return_kappa=True)
+        y0, _, k0, _ = oracle.gp_bf(f, 2.0, 30.0, 20, sp, t_c=0.0, return_kappa="parts")
         np.testing.assert_allclose(k0, 2 * np.abs(y0), rtol=1e-12)
+
+
+@pytest.mark.parametrize("sp", ["fir", "iir"])
+def test_several_orders_in_one_pass(sp):
+    """The terms of order N are a prefix of Algorithm 1's loop: a list of orders in
+    one pass gives, bit for bit, what each order gives alone (result, kappa, tangent)."""
+    f = small_image(40, 33, 48, n_rect=6)
+    Ns = [0, 3, 4, 10, 20]
+    ys, ks = oracle.gp_bf(f, 2.0, 25.0, Ns, sp, return_kappa=True)
+    for q, n in enumerate(Ns):
+        y, k = oracle.gp_bf(f, 2.0, 25.0, n, sp, return_kappa=True)
+        assert np.array_equal(y, ys[q]) and np.allclose(k, ks[q], rtol=1e-12, atol=0)
+
+
+# ------------------------------------------- first-order sensitivity to the input's rounding
+
+
+def _pm1(shape, seed):
+    return np.random.default_rng(seed).choice([-1.0, 1.0], size=shape)
+
+
+@pytest.mark.parametrize("sp,ss,sr", [("fir", 1.5, 25.0), ("fir", 2.0, 10.0), ("iir", 2.0, 25.0), ("iir", 3.0, 10.0),
+                                      ("fir", 1.5, math.inf), ("iir", 2.0, math.inf)])
+def test_tangent_matches_central_differences(sp, ss, sr):
+    """gp_tangent is the derivative of Eqs. (7)-(11): against central differences of
+    O2 under h -> h (1 + e delta) (the centred intensity, given centre) and under a
+    per-pixel factor 1 + e eta on the exponential's argument."""
+    f = small_image(14, 11, 44, n_rect=5)
+    tc = float(f.mean())
+    d, e = _pm1(f.shape, 1), _pm1(f.shape, 2)
+    t = oracle.gp_tangent(f, ss, sr, 12, sp, t_c=tc, delta=d, eta=e)
+    eps = 1e-6
+    yp = oracle.gp_bf(tc + (f - tc) * (1 + eps * d), ss, sr, 12, sp, t_c=tc, lam=1 + eps * e)
+    ym = oracle.gp_bf(tc + (f - tc) * (1 - eps * d), ss, sr, 12, sp, t_c=tc, lam=1 - eps * e)
+    fd = (yp - ym) / (2 * eps)
+    np.testing.assert_allclose(t, fd, rtol=0, atol=1e-9 * max(1.0, np.abs(fd).max()) + 1e-7)
+    # each part alone (a dropped term in either would show here)
+    td = oracle.gp_tangent(f, ss, sr, 12, sp, t_c=tc, delta=d)
+    te = oracle.gp_tangent(f, ss, sr, 12, sp, t_c=tc, eta=e)
+    np.testing.assert_allclose(td + te, t, rtol=1e-12, atol=1e-12)
+    fde = (oracle.gp_bf(f, ss, sr, 12, sp, t_c=tc, lam=1 + eps * e)
+           - oracle.gp_bf(f, ss, sr, 12, sp, t_c=tc, lam=1 - eps * e)) / (2 * eps)
+    np.testing.assert_allclose(te, fde, rtol=0, atol=1e-9 * max(1.0, np.abs(fde).max()) + 1e-7)
+
+
+@pytest.mark.parametrize("sp,ss", [("fir", 1.5), ("iir", 2.5)])
+def test_joint_tangent_matches_central_differences(sp, ss):
+    """The joint filter's tangent: guide intensity (delta), exponential's argument (eta)
+    and data (xi), against central differences of its O2."""
+    f = small_image(14, 11, 45, n_rect=5)
+    g = small_image(14, 11, 46, n_rect=4)
+    tc = float(g.mean())
+    d, e, x = _pm1(f.shape, 3), _pm1(f.shape, 4), _pm1(f.shape, 5)
+    t = oracle.gp_tangent(f, ss, 25.0, 12, sp, t_c=tc, g=g, delta=d, eta=e, xi=x)
+    eps = 1e-6
+    yp = oracle.gp_bf_joint(tc + (f - tc) * (1 + eps * x), tc + (g - tc) * (1 + eps * d), ss, 25.0, 12, sp, t_c=tc,
+                            lam=1 + eps * e)
+    ym = oracle.gp_bf_joint(tc + (f - tc) * (1 - eps * x), tc + (g - tc) * (1 - eps * d), ss, 25.0, 12, sp, t_c=tc,
+                            lam=1 - eps * e)
+    fd = (yp - ym) / (2 * eps)
+    np.testing.assert_allclose(t, fd, rtol=0, atol=1e-9 * max(1.0, np.abs(fd).max()) + 1e-7)
+
+
+def test_probe_signs_are_balanced_and_independent():
+    """The drawn probe signs: +-1, mean near 0, no correlation between the three
+    components or between seeds (Rademacher probes)."""
+    n = 200000
+    s = np.array([[oracle.probe_sign(seed, j, k) for j in range(0, n, 97)] for seed in (11, 12) for k in (0, 1, 2)])
+    assert set(np.unique(s)) == {-1.0, 1.0}
+    assert np.all(np.abs(s.mean(axis=1)) < 0.03)
+    c = np.corrcoef(s)
+    assert np.all(np.abs(c[~np.eye(len(c), dtype=bool)]) < 0.05)
+
+
+@pytest.mark.parametrize("sp,ss,sr", [("fir", 2.0, 30.0), ("iir", 3.0, 10.0)])
+def test_kappa_input_predicts_the_change_under_rounding(sp, ss, sr):
+    """kappa_input * eps is the size of the change of O2 when every pixel's centred
+    intensity and exponential argument carry an independent relative error of up to
+    eps (as rounding gives): over 6 such random perturbations the change stays below
+    3 kappa_input eps everywhere, and reaches a fair share of it (the prediction is not
+    vacuous).  And a perturbation by the same factor everywhere moves O2 by at most
+    kappa_input eps."""
+    f = synthetic.make_image(40, 36, 8, 10.0, 30.0, synthetic.seed_for(9, 46)).astype(np.float64)
+    tc = float(f.mean())
+    y = oracle.gp_bf(f, ss, sr, 20, sp, t_c=tc)
+    ku = oracle.kappa_input(f, ss, sr, 20, sp, t_c=tc)
+    eps = 1e-7
+    rng = np.random.default_rng(6)
+    ratios = []
+    for _ in range(6):
+        d, e = rng.uniform(-1, 1, size=(2,) + f.shape)
+        dy = oracle.gp_bf(tc + (f - tc) * (1 + eps * d), ss, sr, 20, sp, t_c=tc, lam=1 + eps * e) - y
+        ratios.append(np.abs(dy) / (ku * eps))
+    r = np.max(ratios, axis=0)
+    assert r.max() <= 3.0, r.max()
+    assert np.median(r) >= 0.1, np.median(r)
+    dy = oracle.gp_bf(tc + (f - tc) * (1 + eps), ss, sr, 20, sp, t_c=tc) - y
+    assert np.all(np.abs(dy) <= ku * eps * (1 + 1e-3) + 1e-12)
 
 
 # --------------------------------------------------------------- O3 adjoint
