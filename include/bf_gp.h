@@ -59,7 +59,7 @@ typedef enum {
 } bf_status;
 
 /* Bits of the device status word, set by the kernels of the last call. */
-#define BF_DEV_NONPOS_Q 0x1u      /* some pixel had Q <= 0 (odd N, or FP32 cancellation when (R/sigma_r)^2 is large); it was set to NaN */
+#define BF_DEV_NONPOS_Q 0x1u      /* some pixel had Q <= 0, where Eq. (11) is undefined (odd N; with the recursive filter, whose kernel has a slightly negative tail, also large (R/sigma_r)^2): it kept its own value */
 #define BF_DEV_NONFINITE_IN 0x2u  /* the input held NaN/Inf; the plane was passed through unchanged */
 #define BF_DEV_RANGE 0x4u         /* (R/sigma_r)^2 / 2 > 80: exp(-s^2 u^2 / 2) underflows FP32 */
 #define BF_DEV_TIMEOUT 0x8u       /* a bounded inter-block wait gave up */
@@ -98,7 +98,10 @@ typedef struct {
                            HBM), 1 = the separate row and column passes (what bf_gp_phase_rows /
                            bf_gp_phase_cols always run) */
     int box_passes;     /* BF_SPATIAL_BOX: passes of the flat kernel, 1..3 (0 selects 3) */
-    int reserved[5];    /* must be zero */
+    int tc5_wait_test;  /* engine 3 only, to test its bounded wait: 0 = normal; n > 0 = the column pass
+                           issues no tensor-core product and gives up each wait for one after n polls:
+                           the call reports BF_DEV_TIMEOUT and writes every plane as copied */
+    int reserved[4];    /* must be zero */
 } bf_gp_opts;
 
 /* Fill *opts with the defaults: N = 20, AUTO spatial operator, mean centre. */
@@ -201,7 +204,8 @@ bf_status bf_gp_forward_joint(const float *f, const float *g, float *y, int plan
  *   the forward's workspace; its contents are not needed).  The derivative of
  *   the centre t_c (the plane mean, Algorithm 1 step 1) is included; a given
  *   centre is held fixed.  R gets no derivative (the result does not depend
- *   on it).  Pixels whose forward result was NaN (Q <= 0) pass no gradient.
+ *   on it).  A pixel whose forward kept its own value (Q <= 0) passes dL/dy
+ *   to its own input (dy/df = 1 there) and nothing else.
  *   Enqueues four kernels: stats, adjoint row pass, adjoint column pass
  *   (the same spatial operator, which is symmetric), finish.
  */
@@ -254,7 +258,8 @@ bf_status bf_gp_forward_host(const float *f_host, float *y_host, int planes, int
  *    pixels per call (e.g. one 512 x 512 plane, or three 256 x 256 planes).
  *  - Set-up: the first call on a device looks up the array's device address
  *    (with that device current) and caches it; make that first call before
- *    any stream capture.
+ *    any stream capture.  Later calls check the cached address against the
+ *    current context and look it up again after a cudaDeviceReset.
  *  - Sharing: every call on a device uses the same array, which keeps the
  *    previous call's contents; the filter writes every scratch byte it reads
  *    before reading it, so nothing needs clearing.  Calls that overlap on the
@@ -370,7 +375,7 @@ bf_status bf_gp_get_device_status(const void *ws, void *stream, uint32_t *bits);
 /*
  * Counts behind the status bits of the last call that used `ws` (for a batch:
  * summed over its planes), into counters[BF_GP_NCOUNTERS]:
- *   [0] pixels whose Q <= 0 (set to NaN; BF_DEV_NONPOS_Q)
+ *   [0] pixels whose Q <= 0 (they kept their own value; BF_DEV_NONPOS_Q)
  *   [1] non-finite input values (BF_DEV_NONFINITE_IN)
  *   [2] planes whose exponentials leave the FP32 range (BF_DEV_RANGE)
  *   [3] bounded waits that gave up (BF_DEV_TIMEOUT)

@@ -253,7 +253,8 @@ def gp_bf(f, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop=None, re
     arithmetic move the result (error about kappa * eps; inf where Q <= 0):
     the terms' part sigma_r (sum|p_n| + |P/Q| sum|q_n|) / |Q| (a relative
     error in every product entering Eqs. (9)-(10)) plus kappa_input (the
-    rounding of the centred intensity itself).  return_kappa="parts" returns
+    rounding of the centred intensity itself) plus |y| (the rounding of the
+    result itself when the centre is added back).  return_kappa="parts" returns
     (y, kappa, terms' part, input's part).  Where Q <= 0, Eq. (11) is undefined
     and the pixel keeps its own value (kappa = inf there).  N: an order, or a
     list of increasing orders computed in one pass (results stacked on a first
@@ -279,7 +280,8 @@ def gp_bf(f, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop=None, re
     if not return_kappa:
         return out
     ku = kappa_input(f, sigma_s, sigma_r, N, spatial, t_c=t_c, w=w, crop=crop, box=box)
-    total = np.where(np.isfinite(kap), kap + ku, np.inf)
+    # the last operation, adding the centre back (Eq. (6)), rounds the result itself: eps |y|
+    total = np.where(np.isfinite(kap), kap + ku + np.abs(out), np.inf)
     return (out, total, kap, ku) if return_kappa == "parts" else (out, total)
 
 
@@ -322,7 +324,8 @@ def gp_bf_joint(f, g, sigma_s, sigma_r, N, spatial="fir", t_c=None, w=None, crop
     if not return_kappa:
         return out
     ku = kappa_input(f, sigma_s, sigma_r, N, spatial, t_c=t_c, w=w, crop=crop, box=box, g=g)
-    total = np.where(np.isfinite(kap), kap + ku, np.inf)
+    # the last operation, adding the centre back (Eq. (6)), rounds the result itself: eps |y|
+    total = np.where(np.isfinite(kap), kap + ku + np.abs(out), np.inf)
     return (out, total, kap, ku) if return_kappa == "parts" else (out, total)
 
 

@@ -52,7 +52,8 @@ class BFError(RuntimeError):
 class bf_gp_opts(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("spatial", ctypes.c_int), ("centre", ctypes.c_int),
                 ("fir_halfwidth", ctypes.c_int), ("t_c", ctypes.c_double), ("engine", ctypes.c_int),
-                ("fir_two_pass", ctypes.c_int), ("box_passes", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("fir_two_pass", ctypes.c_int), ("box_passes", ctypes.c_int), ("tc5_wait_test", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 class bf_gp_plane(ctypes.Structure):
@@ -154,15 +155,17 @@ ENGINE_TCGEN05 = 3     # half-chunk products on tcgen05 where a pass has such a 
 
 
 def make_opts(order: int = 20, spatial="auto", t_c=None, fir_halfwidth: int = 0, engine: int = ENGINE_AUTO,
-              fir_two_pass: bool = False, box_passes: int = 0) -> bf_gp_opts:
+              fir_two_pass: bool = False, box_passes: int = 0, tc5_wait_test: int = 0) -> bf_gp_opts:
     """spatial 'box': box_passes passes (0 = 3) of a flat kernel of half-width
-    fir_halfwidth (0 = matched to sigma_s)."""
+    fir_halfwidth (0 = matched to sigma_s).  tc5_wait_test: see bf_gp_opts
+    (testing the tcgen05 column pass's bounded wait only)."""
     o = bf_gp_opts()
     _load().bf_gp_default_opts(ctypes.byref(o))
     o.order = int(order)
     o.engine = int(engine)
     o.fir_two_pass = int(bool(fir_two_pass))
     o.box_passes = int(box_passes)
+    o.tc5_wait_test = int(tc5_wait_test)
     o.spatial = _SPATIAL[spatial] if isinstance(spatial, str) else int(spatial)
     o.fir_halfwidth = int(fir_halfwidth)
     if t_c is not None:

@@ -80,7 +80,8 @@ bf_status check_opts(const bf_gp_opts *o)
     if (o->engine < 0 || o->engine > 3) return BF_ERR_INVALID_ARG;
     if (o->fir_two_pass < 0 || o->fir_two_pass > 1) return BF_ERR_INVALID_ARG;
     if (o->box_passes < 0 || o->box_passes > 3) return BF_ERR_INVALID_ARG;
-    for (int i = 0; i < 5; ++i)
+    if (o->tc5_wait_test < 0) return BF_ERR_INVALID_ARG;
+    for (int i = 0; i < 4; ++i)
         if (o->reserved[i] != 0) return BF_ERR_INVALID_ARG;
     return BF_OK;
 }
@@ -345,6 +346,8 @@ bf_status prepare(const float *f, float *out, int planes, int H, int W, int pitc
     ca.Wp = c->p.Wp;
     ca.K = c->p.K;
     ca.N = c->p.N;
+    ca.wait_limit = opts->tc5_wait_test > 0 ? opts->tc5_wait_test : MBAR_LIMIT;
+    ca.no_mma = opts->tc5_wait_test > 0 ? 1 : 0;
     return BF_OK;
 }
 
@@ -761,7 +764,9 @@ bf_status bf_gp_backward(const float *f, const float *grad_y, const float *saved
 // Scratch for bf_gp_forward_noalloc: a static device array, so the entry
 // point needs neither a caller workspace nor an allocation.  Host code may
 // not use the symbol itself as a device pointer; its device address is looked
-// up once per device with cudaGetSymbolAddress (that device current) and cached.
+// up once per device with cudaGetSymbolAddress (that device current) and cached,
+// and looked up again when the cached one no longer names device memory of that
+// device (a new context after cudaDeviceReset).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[BF_GP_NOALLOC_SCRATCH_BYTES];
 
 namespace {
@@ -791,6 +796,16 @@ bf_status bf_gp_forward_noalloc(const float *f, float *y, int planes, int H, int
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
         base = g_noalloc_ptr[dev];
+        if (base) {
+            // the cached address belongs to the context it was looked up in: after a
+            // cudaDeviceReset the module is loaded again and the array may move
+            cudaPointerAttributes at;
+            if (cudaPointerGetAttributes(&at, base) != cudaSuccess || at.type != cudaMemoryTypeDevice ||
+                at.device != dev || at.devicePointer != base) {
+                (void)cudaGetLastError();
+                base = nullptr;
+            }
+        }
         if (!base) {
             BF_CUDA(cudaGetSymbolAddress(&base, g_noalloc_scratch));
             g_noalloc_ptr[dev] = base;

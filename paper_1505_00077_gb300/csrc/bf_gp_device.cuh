@@ -349,7 +349,7 @@ __device__ __forceinline__ float envelope(const PlaneParams &P, float u)
 
 // Counters after the status word in the workspace header (byte 8 on), zeroed
 // with it by the statistics pass of every call:
-//   [0] pixels whose Q <= 0 (set to NaN), [1] non-finite input values,
+//   [0] pixels whose Q <= 0 (they keep their own value), [1] non-finite input values,
 //   [2] planes whose exponentials leave the FP32 range, [3] bounded waits that gave up.
 constexpr int NCOUNTERS = 4;
 __device__ __forceinline__ unsigned long long *status_counters(uint32_t *status)
@@ -1061,6 +1061,8 @@ struct ColArgs {
     uint32_t *status;
     double *acc;      // MODE_ADJ
     int H, W, pitch, Wp, K, N;
+    int wait_limit;   // tcgen05 column pass: polls before a wait for the tensor core gives up
+    int no_mma;       // tcgen05 column pass, testing only: issue no product (every wait gives up)
 };
 
 // Per-pixel combine over descending channel m for RPT pixels.
@@ -1192,7 +1194,9 @@ __device__ __forceinline__ void finish_pixel(const ColArgs &a, const PlaneParams
         const float E = envelope(P, u);
         const float gind = E * fmaf(-P.s2 * u, cb.q[j], cb.p[j]);
         const float gu = gind + gdir;
-        const float gh = gu * P.invR;
+        float gh = gu * P.invR;
+        // where the forward kept the pixel's value (Q <= 0), dL/dy reaches its own input directly
+        if (!(Qt > 0.f) && isfinite(g)) gh += g;
         a.y[pix] = gh;
         sums.gy += isfinite(g) ? g : 0.f;
         sums.gh += gh;
@@ -1206,8 +1210,9 @@ __device__ __forceinline__ void finish_pixel(const ColArgs &a, const PlaneParams
     const float Q = cb.q[j];
     float out;
     if (!(Q > 0.f)) {
+        // Eq. (11) is undefined where Q <= 0: the pixel keeps its own (data) value
         ++nonpos;
-        out = __int_as_float(0x7fc00000);
+        out = __ldg((MODE == MODE_JOINT ? a.gy : a.f) + pix);
     } else {
         out = fmaf(P.R, __fdiv_rn(cb.p[j], Q), P.tc);
     }
@@ -1781,20 +1786,30 @@ __device__ __forceinline__ void col_tc5_body(const ColArgs &a, const IIRCoef &cf
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 16 * atile;
-    if (tid == 0) issue_mma(tmem + 64 * ((a.K - 1) & 1));
+    if (tid == 0 && !a.no_mma) issue_mma(tmem + 64 * ((a.K - 1) & 1));
     uint32_t phase = 0;
-    bool timed_out = false;
+    // stop: a wait for the tensor core gave up (CTA-uniform).  From then on no product is
+    // issued and tensor memory is not read; the CTA keeps its place in every cluster barrier
+    // (its peers wait on them), and before freeing tensor memory it waits once more, again
+    // bounded, for the products it gave up on.
+    bool stop = false;
 #pragma unroll 1
     for (int k = a.K - 1; k >= 0; --k) {
         // a. half sums of channel k
-        if (!mbar_wait(mb, phase, MBAR_LIMIT)) timed_out = true;
-        phase ^= 1u;
-        tc_fence_after();
+        const bool ok = stop || mbar_wait(mb, phase, a.wait_limit);
+        stop = __syncthreads_or(!ok) != 0;
         const uint32_t tk = trow + 64 * (k & 1);  // D of channel k: tensor-memory columns 64 (k & 1) ..
         float d0[8], d1[8];                       // half sums of the two halves (outputs 8..15)
-        tmem_ld8(tk + 8, d0);
-        tmem_ld8(tk + 16 + 8, d1);
-        tmem_wait_ld();
+        if (!stop) {
+            phase ^= 1u;
+            tc_fence_after();
+            tmem_ld8(tk + 8, d0);
+            tmem_ld8(tk + 16 + 8, d1);
+            tmem_wait_ld();
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) d0[j] = d1[j] = 0.f;
+        }
         if (k >= 2) issue_tile(k - 2);
         cp_async_commit();
 
@@ -1877,12 +1892,12 @@ __device__ __forceinline__ void col_tc5_body(const ColArgs &a, const IIRCoef &cf
         cluster_wait_acquire();
 
         // c. MMAs of channel k - 1, running while this thread finishes channel k
-        if (k >= 1) {
+        if (k >= 1 && !stop) {
             split_tile(k - 1);
             if (warp == 0) {
                 // every row of A written and fenced; D of channel k + 1 (same columns) read by every thread
                 bar_sync_named(3, 256);
-                if (lane == 0) {
+                if (lane == 0 && !a.no_mma) {
                     tc_fence_after();
                     issue_mma(tmem + 64 * ((k - 1) & 1));
                 }
@@ -1934,9 +1949,14 @@ __device__ __forceinline__ void col_tc5_body(const ColArgs &a, const IIRCoef &cf
         float y[C];
         {
             float l0[8], l1[8];  // in-half responses (outputs 0..7)
-            tmem_ld8(tk, l0);
-            tmem_ld8(tk + 16, l1);
-            tmem_wait_ld();
+            if (!stop) {
+                tmem_ld8(tk, l0);
+                tmem_ld8(tk + 16, l1);
+                tmem_wait_ld();
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) l0[j] = l1[j] = 0.f;
+            }
             tc_fence_before();  // D of channel k is read before this thread reaches barrier 3 again
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -1952,10 +1972,13 @@ __device__ __forceinline__ void col_tc5_body(const ColArgs &a, const IIRCoef &cf
     tc_fence_before();
     cl.sync();
     if (warp == 0) {
+        // after a give-up the products of the channel waited for may still be running: wait for
+        // them once more (bounded) before their accumulators are freed
+        if (stop) (void)mbar_wait(mb, phase, a.wait_limit);
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(tmem) : "memory");
     }
-    if (timed_out) {
+    if (stop && tid == 0) {
         atomicOr(a.status, 0x8u);
         atomicAdd(status_counters(a.status) + 3, 1ull);
     }
@@ -1964,7 +1987,13 @@ __device__ __forceinline__ void col_tc5_body(const ColArgs &a, const IIRCoef &cf
 #pragma unroll
     for (int j = 0; j < C; ++j) {
         const int r = row0 + j;
-        if (r < a.H && x < a.W) finish_pixel<C, MODE>(a, P, plane, r, x, cb, j, nonpos, sums);
+        if (!(r < a.H && x < a.W)) continue;
+        if (stop) {  // no result: the plane is written as copied (the backward: no gradient)
+            const size_t pix = ((size_t)plane * a.H + r) * a.pitch + x;
+            a.y[pix] = MODE == MODE_ADJ ? 0.f : __ldg((MODE == MODE_JOINT ? a.gy : a.f) + pix);
+        } else {
+            finish_pixel<C, MODE>(a, P, plane, r, x, cb, j, nonpos, sums);
+        }
     }
     if (MODE == MODE_ADJ) {
         flush_sums(a, plane, sums);
@@ -2211,10 +2240,10 @@ __global__ void __launch_bounds__(256) fir_fused(ColArgs a, FIRCoef g)
         if (yo < a.H && xo < a.W) {
             const float Q = fmaf(P.s2 * ou[j], qacc[j], psi0[j]);
             float out;
-            if (!(Q > 0.f)) {  // rare: counted one pixel at a time
+            if (!(Q > 0.f)) {  // rare: counted one pixel at a time; the pixel keeps its value
                 nonpos = true;
                 atomicAdd(status_counters(a.status), 1ull);
-                out = __int_as_float(0x7fc00000);
+                out = __ldg(a.f + ((size_t)plane * a.H + yo) * a.pitch + xo);
             } else {
                 out = fmaf(P.R, __fdiv_rn(pacc[j], Q), P.tc);
             }

@@ -6,13 +6,13 @@ import numpy as np
 import pytest
 
 import oracle
+import parity
 import synthetic
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-3
-KAPPA_GATE = 8e-4 / (16 * 2.0 ** -24)
+TOL = parity.TOL
 
 
 @pytest.fixture(scope="module")
@@ -25,9 +25,7 @@ def bf():
 
 
 def _gated_max_err(gpu, ref, kap):
-    gated = np.isfinite(ref) & (kap <= KAPPA_GATE)
-    assert gated.mean() >= 0.999
-    return float(np.max(np.abs(gpu[gated] - ref[gated])))
+    return parity.gate(gpu, ref, kap, min_gated=0.99, label="autotuned")["max_err_gated"]
 
 
 def _setup(bf, H, W, ss, spatial):
@@ -57,7 +55,8 @@ def test_autotune_recursive_times_every_engine_and_stores_the_fastest(bf):
     y.fill_(float("nan"))
     bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, sr, o, ws.data_ptr(), need, s)
     assert bf.bf_gp_get_device_status(ws.data_ptr(), s) == 0
-    ref, kap = oracle.gp_bf(img.astype(np.float64), ss, sr, 20, "iir", return_kappa=True)
+    ref, kap = oracle.gp_bf(img.astype(np.float64), ss, sr, 20, "iir", t_c=parity.gpu_centre(bf, ws.data_ptr(), 0, s),
+                            return_kappa=True)
     assert _gated_max_err(y.cpu().numpy().astype(np.float64), ref, kap) <= TOL
     # forgetting the choice times again
     bf.bf_gp_autotune_clear()
@@ -75,7 +74,8 @@ def test_autotune_fir_chooses_between_fused_and_two_pass(bf):
     assert ms[0] > 0 and ms[1] > 0 and ms[2] == -1.0 and ms[3] == -1.0
     assert o.fir_two_pass == int(np.argmin(ms[:2]))
     bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, sr, o, ws.data_ptr(), need, s)
-    ref, kap = oracle.gp_bf(img.astype(np.float64), ss, sr, 20, "fir", return_kappa=True)
+    ref, kap = oracle.gp_bf(img.astype(np.float64), ss, sr, 20, "fir", t_c=parity.gpu_centre(bf, ws.data_ptr(), 0, s),
+                            return_kappa=True)
     assert _gated_max_err(y.cpu().numpy().astype(np.float64), ref, kap) <= TOL
 
 

@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
+import parity
 import synthetic
 
 torch = pytest.importorskip("torch")
@@ -133,3 +134,100 @@ def test_autograd_function(bf):
     ref_g, ref_s = oracle.gp_adjoint(img.astype(np.float64), 4.0, 25.0, 20, w.cpu().numpy().astype(np.float64), "iir")
     check_grad(x.grad.cpu().numpy().astype(np.float64), ref_g, "autograd dL/df")
     assert abs(float(sr.grad) - ref_s) <= RTOL * abs(ref_s)
+
+
+def test_backward_where_the_denominator_is_not_positive(bf):
+    """Odd N: the pixels whose Q <= 0 keep their value in the forward pass and pass
+    dL/dy straight to their own input in the backward pass, as in O3."""
+    img = np.zeros((40, 36), np.float32)
+    img[:, 17] = 255.0
+    img += synthetic.make_image(40, 36, 3, 3.0, 0.0, synthetic.seed_for(5, 7100)) * 0.05
+    gy = np.random.default_rng(13).normal(size=img.shape).astype(np.float32)
+    for spatial, ss in (("fir", 2.0), ("iir", 2.5)):
+        y, gx, gsr, bits = gpu_fwd_bwd(bf, img[None], gy[None], ss, 20.0, 5, spatial)
+        assert bits == 0  # the backward call's own status (the forward's flag is reset by it)
+        _, kap = oracle.gp_bf(img.astype(np.float64), ss, 20.0, 5, spatial, return_kappa=True)
+        assert parity.kept_value_pixels(y[0], img, kap) > 0
+        ref_g, ref_s = oracle.gp_adjoint(img.astype(np.float64), ss, 20.0, 5, gy.astype(np.float64), spatial)
+        check_grad(gx[0], ref_g, f"{spatial} dL/df")
+        assert abs(gsr[0] - ref_s) <= RTOL * max(abs(ref_s), 1e-6 * np.abs(ref_g).max() * img.size), (gsr[0], ref_s)
+
+
+# ------------------------------------------- finite differences at the 16 x 512^2 workload's settings
+
+FD_STEP = 1e-2          # central differences of the FP64 forward (O2)
+FD_SS, FD_SR, FD_N = 5.0, 25.0, 20
+CROP = 32
+HALO = 30               # 6 sigma_s: the recursive kernel is below 1e-4 of its peak there
+
+
+def _fd_subproblem():
+    """The 32 x 32 crop of image 0 (centre rows/columns 240..271) with a 30-pixel halo,
+    as a standalone image, and the centre t_c of the full image (FP32 value), held fixed."""
+    full = synthetic.batch512(1)[0, 0].astype(np.float64)
+    r0 = c0 = 240 - HALO
+    sub = full[r0:r0 + CROP + 2 * HALO, c0:c0 + CROP + 2 * HALO].copy()
+    tc = float(np.float32(full.mean()))
+    return sub, tc
+
+
+def _fd_gradients(f, ybar, tc, pixels):
+    """Central differences (step 1e-2) of L = sum(ybar * O2(f)) for every pixel in `pixels`,
+    and for sigma_r; t_c is held at tc (None: the image mean, its derivative included)."""
+    L = lambda ff, sr=FD_SR: float((ybar * oracle.gp_bf(ff, FD_SS, sr, FD_N, "iir", t_c=tc)).sum())
+    g = np.zeros_like(f)
+    for idx in pixels:
+        e = np.zeros_like(f)
+        e[idx] = FD_STEP
+        g[idx] = (L(f + e) - L(f - e)) / (2 * FD_STEP)
+    gs = (L(f, FD_SR + FD_STEP) - L(f, FD_SR - FD_STEP)) / (2 * FD_STEP)
+    return g, gs, L
+
+
+def test_finite_differences_on_a_32x32_crop(bf):
+    """Every pixel of the 32 x 32 crop (2048 forward evaluations, t_c fixed) and 16
+    random directions supported on the crop: central differences of O2 against O3 and
+    against the GPU's bf_gp_backward on the same sub-problem (centre given)."""
+    f, tc = _fd_subproblem()
+    rng = np.random.default_rng(16)
+    ybar = rng.normal(size=f.shape)
+    crop = [(r, c) for r in range(HALO, HALO + CROP) for c in range(HALO, HALO + CROP)]
+    fd, fds, L = _fd_gradients(f, ybar, tc, crop)
+    o3, o3s = oracle.gp_adjoint(f, FD_SS, FD_SR, FD_N, ybar, "iir", t_c=tc)
+    _, gx, gsr, bits = gpu_fwd_bwd(bf, f.astype(np.float32)[None], ybar.astype(np.float32)[None], FD_SS, FD_SR, FD_N,
+                                   "iir", t_c=tc)
+    assert bits == 0
+    sl = np.s_[HALO:HALO + CROP, HALO:HALO + CROP]
+    scale = np.abs(fd[sl]).max()
+    # FP64 O3 against FP64 differences (truncation error of the 1e-2 step only)
+    assert np.abs(o3[sl] - fd[sl]).max() <= 1e-5 * scale
+    assert abs(o3s - fds) <= 1e-5 * abs(fds)
+    # the GPU adjoint (FP32) against both
+    assert np.abs(gx[0][sl] - fd[sl]).max() <= RTOL * scale
+    assert np.abs(gx[0] - o3).max() <= RTOL * np.abs(o3).max()
+    assert abs(gsr[0] - fds) <= RTOL * abs(fds)
+    # directional derivatives along 16 random directions supported on the crop
+    for _ in range(16):
+        v = np.zeros_like(f)
+        v[sl] = rng.normal(size=(CROP, CROP))
+        dd = (L(f + FD_STEP * v) - L(f - FD_STEP * v)) / (2 * FD_STEP)
+        assert abs((o3 * v).sum() - dd) <= 1e-5 * max(1.0, abs(dd))
+        assert abs((gx[0] * v).sum() - dd) <= RTOL * np.abs(gx[0][sl] * v[sl]).sum()
+
+
+def test_finite_differences_standalone_32x32_with_mean_centre(bf):
+    """A standalone 32 x 32 image (the crop of image 0) with the mean centre of
+    Algorithm 1's first step: the centring term of the derivative, every pixel, by
+    central differences (step 1e-2) against O3 and the GPU."""
+    f, _ = _fd_subproblem()
+    f = f[HALO:HALO + CROP, HALO:HALO + CROP].copy()
+    ybar = np.random.default_rng(17).normal(size=f.shape)
+    fd, fds, _ = _fd_gradients(f, ybar, None, list(np.ndindex(f.shape)))
+    o3, o3s = oracle.gp_adjoint(f, FD_SS, FD_SR, FD_N, ybar, "iir")
+    _, gx, gsr, bits = gpu_fwd_bwd(bf, f.astype(np.float32)[None], ybar.astype(np.float32)[None], FD_SS, FD_SR, FD_N,
+                                   "iir")
+    assert bits == 0
+    scale = np.abs(fd).max()
+    assert np.abs(o3 - fd).max() <= 1e-5 * scale and abs(o3s - fds) <= 1e-5 * abs(fds)
+    assert np.abs(gx[0] - fd).max() <= RTOL * scale
+    assert abs(gsr[0] - fds) <= RTOL * abs(fds)

@@ -2,7 +2,10 @@
 
 Every case runs the CUDA path through the C ABI (bf_gp_forward) and compares
 element by element with oracle.gp_bf on the same seeded image, with the same
-spatial operator.  Bar: max |GPU - oracle| <= 1e-3 on the 0..255 scale.
+spatial operator and the centre the GPU used.  Bar (tests/parity.py): max
+|GPU - oracle| <= 1e-3 on the 0..255 scale on every pixel the FP32 arithmetic
+resolves; every other pixel finite and, for an even order with the window
+sum, inside its window's range; where Q <= 0 both keep the pixel's value.
 """
 import math
 
@@ -10,18 +13,13 @@ import numpy as np
 import pytest
 
 import oracle
+import parity
 import synthetic
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-3
-# A pixel is held to TOL when its conditioning kappa (oracle.gp_bf(..., return_kappa=True): the
-# first-order bound on how far relative errors eps in every product entering P and Q move the
-# result) predicts an FP32 error below 8e-4 with an effective eps of 16 units of roundoff
-# (the FP32 recursions accumulate up to ~13 ulp; measured max |err| / kappa = 7.8e-7):
-# 16 * 2^-24 * kappa <= 8e-4.
-KAPPA_GATE = 8e-4 * 2.0 ** 24 / 16
+TOL = parity.TOL
 
 
 @pytest.fixture(scope="module")
@@ -34,6 +32,7 @@ def bf():
 
 
 def run_gpu(bf, img, ss, sr, N, spatial, status=False, **kw):
+    """GPU result (FP64 copy), and with status=True also (status bits, counters, centre used)."""
     x = torch.from_numpy(np.ascontiguousarray(img, dtype=np.float32)).cuda()
     H, W = x.shape[-2], x.shape[-1]
     planes = max(1, x.numel() // (H * W))
@@ -41,43 +40,46 @@ def run_gpu(bf, img, ss, sr, N, spatial, status=False, **kw):
     need = bf.bf_gp_workspace_size(planes, H, W, ss, o)
     ws = torch.empty(need, dtype=torch.uint8, device="cuda")
     y = bf.bilateral_gp(x, ss, sr, N, spatial, ws=ws, **kw)
-    bits = bf.bf_gp_get_device_status(ws.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    s = torch.cuda.current_stream().cuda_stream
+    bits = bf.bf_gp_get_device_status(ws.data_ptr(), s)
     out = y.cpu().numpy().astype(np.float64)
-    return (out, bits) if status else out
+    if not status:
+        return out
+    return out, bits, bf.bf_gp_get_device_counters(ws.data_ptr(), s), parity.gpu_centre(bf, ws.data_ptr(), 0, s)
 
 
-def check(gpu, ref, tol=TOL, kappa=None, min_gated=1.0):
-    """Max-abs gate on the pixels the FP32 arithmetic can resolve (all of
-    them unless a kappa map says otherwise)."""
-    assert gpu.shape == ref.shape
-    gated = np.isfinite(ref)
-    if kappa is not None:
-        gated &= kappa <= KAPPA_GATE
-    frac = gated.mean()
-    assert frac >= min_gated, f"only {frac:.5f} of the pixels are well conditioned"
-    if min_gated >= 1.0:
-        assert np.isfinite(ref).all()
-    g, r = gpu[gated], ref[gated]
-    assert np.isfinite(g).all(), "non-finite GPU output on a well-conditioned pixel"
-    err = np.abs(g - r)
-    assert err.max() <= tol, f"max err {err.max():.3e}"
-    return err.max()
+def compare(bf, img, ss, sr, N, spatial, min_gated=1.0, label="", **kw):
+    """GPU vs oracle (with kappa) on the whole image, at the GPU's centre."""
+    out, bits, counters, tc = run_gpu(bf, img, ss, sr, N, spatial, status=True, **kw)
+    f64 = np.asarray(img, np.float64)
+    ref, kap = oracle.gp_bf(f64, ss, sr, N, spatial, t_c=kw.get("t_c", tc), return_kappa=True)
+    even_fir = spatial == "fir" and N % 2 == 0
+    rec = parity.gate(out, ref, kap, min_gated=min_gated, f=f64 if even_fir else None,
+                      window=oracle.window(ss) if even_fir else None, label=label or f"{f64.shape} {spatial} "
+                      f"ss={ss:g} sr={sr:g} N={N}")
+    n_q0 = parity.kept_value_pixels(out, f64, kap)
+    assert counters[0] == n_q0 and bool(bits & bf.BF_DEV_NONPOS_Q) == (n_q0 > 0)
+    assert (bits & ~bf.BF_DEV_NONPOS_Q) == 0
+    return rec
 
 
 # ---------------------------------------------------------------- 256^2 rectangles, sigma_s 3, sigma_r 30
 
-@pytest.mark.parametrize("N", [20, 34])
+@pytest.mark.parametrize("N", [20, 34, 38])
 def test_rects256_fir(bf, N):
-    img = synthetic.rects256_image()
-    f64 = img.astype(np.float64)
-    ref = oracle.gp_bf(f64, 3.0, 30.0, N, "fir")
-    check(run_gpu(bf, img, 3.0, 30.0, N, "fir"), ref)
+    """The paper's setting (N = 20), the order the kernel-error rule gives for sigma_r 30
+    over this image's range (N = 38, bf_gp_order_for_tol at 1e-3), and one between."""
+    compare(bf, synthetic.rects256_image(), 3.0, 30.0, N, "fir")
+
+
+def test_rects256_order_from_the_error_rule_is_38(bf):
+    img = synthetic.rects256_image().astype(np.float64)
+    R = float(np.max(np.abs(img - img.mean())))
+    assert bf.bf_gp_order_for_tol(30.0, R, 1e-3) == 38
 
 
 def test_rects256_iir(bf):
-    img = synthetic.rects256_image()
-    ref = oracle.gp_bf(img.astype(np.float64), 3.0, 30.0, 20, "iir")
-    check(run_gpu(bf, img, 3.0, 30.0, 20, "iir"), ref)
+    compare(bf, synthetic.rects256_image(), 3.0, 30.0, 20, "iir", min_gated=0.999)
 
 
 # ---------------------------------------------------------------- ragged shapes
@@ -91,8 +93,8 @@ SHAPES = [(1, 1), (1, 7), (5, 1), (2, 3), (17, 33), (31, 64), (65, 129), (300, 2
 def test_ragged_shapes(bf, shape, spatial, ss):
     H, W = shape
     img = synthetic.make_image(H, W, 6, 10.0, 0.0, synthetic.seed_for(9, H * 7 + W))
-    ref = oracle.gp_bf(img.astype(np.float64), ss, 30.0, 12, spatial)
-    check(run_gpu(bf, img, ss, 30.0, 12, spatial), ref)
+    # floors: the oracle's own resolvable fraction on these inputs (>= 0.91; >= 0.6 below 10 pixels)
+    compare(bf, img, ss, 30.0, 12, spatial, min_gated=0.5 if H * W < 10 else 0.9)
 
 
 @pytest.mark.parametrize("H", [511, 512, 513, 1024, 2047, 2049, 3000, 4096, 4097, 6000, 8192])
@@ -100,8 +102,7 @@ def test_iir_column_cluster_sizes(bf, H):
     """Columns spanning 1..16 CTAs of the clustered column pass (more than 8:
     the non-portable cluster size)."""
     img = synthetic.make_image(H, 24, 8, 10.0, 30.0, synthetic.seed_for(9, H))
-    ref = oracle.gp_bf(img.astype(np.float64), 7.0, 40.0, 10, "iir")
-    check(run_gpu(bf, img, 7.0, 40.0, 10, "iir"), ref)
+    compare(bf, img, 7.0, 40.0, 10, "iir", min_gated=0.8)  # the oracle's fraction here: >= 0.84
 
 
 @pytest.mark.parametrize("engine", [0, 1])
@@ -112,7 +113,6 @@ def test_iir_tall_columns_engines_and_training(bf, H, engine):
     the most shared memory per CTA)."""
     W = 40
     img = synthetic.make_image(H, W, 8, 10.0, 30.0, synthetic.seed_for(9, H + engine))
-    ref = oracle.gp_bf(img.astype(np.float64), 9.0, 40.0, 10, "iir")
     o = bf.make_opts(10, "iir", engine=engine)
     x = torch.from_numpy(img).cuda()
     need = bf.bf_gp_workspace_size(1, H, W, 9.0, o)
@@ -121,75 +121,70 @@ def test_iir_tall_columns_engines_and_training(bf, H, engine):
     y = torch.full_like(x, float("nan"))
     bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, H, W, W, 9.0, 40.0, o, ws.data_ptr(), need, s)
     assert bf.bf_gp_get_device_status(ws.data_ptr(), s) == 0
-    check(y.cpu().numpy().astype(np.float64), ref)
+    tc = parity.gpu_centre(bf, ws.data_ptr(), 0, s)
+    ref, kap = oracle.gp_bf(img.astype(np.float64), 9.0, 40.0, 10, "iir", t_c=tc, return_kappa=True)
+    parity.gate(y.cpu().numpy(), ref, kap, min_gated=0.9, label=f"tall {H} engine {engine}")  # oracle: >= 0.92
     saved = torch.empty((1, 4, H, W), dtype=torch.float32, device="cuda")
     y2 = torch.full_like(x, float("nan"))
     bf.bf_gp_forward_train(x.data_ptr(), y2.data_ptr(), saved.data_ptr(), 1, H, W, W, 9.0, 40.0, o, ws.data_ptr(),
                            need, s)
-    check(y2.cpu().numpy().astype(np.float64), ref)
+    parity.gate(y2.cpu().numpy(), ref, kap, min_gated=0.9, label=f"tall {H} engine {engine} training")
 
 
 @pytest.mark.parametrize("W", [511, 512, 513, 1024, 4095, 4096, 4097, 8192])
 def test_iir_long_rows(bf, W):
     img = synthetic.make_image(12, W, 8, 10.0, 30.0, synthetic.seed_for(9, W))
-    ref = oracle.gp_bf(img.astype(np.float64), 11.0, 40.0, 10, "iir")
-    check(run_gpu(bf, img, 11.0, 40.0, 10, "iir"), ref)
+    compare(bf, img, 11.0, 40.0, 10, "iir", min_gated=0.75)  # the oracle's fraction here: >= 0.79
 
 
-# ---------------------------------------------------------------- 1024^2 rectangles + ramp, sweeps
+# ---------------------------------------------------------------- 1024^2 rectangles + ramp: the full sweep
 
-@pytest.mark.parametrize("ss,sr,N,spatial", [
-    (2.0, 30.0, 20, "fir"), (2.0, 10.0, 20, "fir"), (2.0, 50.0, 8, "fir"), (3.0, 10.0, 12, "fir"),
-    (5.0, 30.0, 20, "iir"), (5.0, 50.0, 4, "iir"), (10.0, 30.0, 20, "iir"), (10.0, 50.0, 12, "iir"),
-    (20.0, 30.0, 20, "iir"), (20.0, 50.0, 16, "iir"), (20.0, 30.0, 6, "iir"),
-])
-def test_rects_ramp1024_sweep(bf, ss, sr, N, spatial):
+# sigma_s in {2, 5, 10, 20} x sigma_r in {10, 30, 50} x every even order 4..20, on the full
+# 1024^2 image: the recursive filter for every sigma_s, the window sum also for sigma_s = 2.
+# The oracle computes every order of one (sigma_s, sigma_r, operator) in one pass.
+SWEEP_ORDERS = list(range(4, 21, 2))
+SWEEP = [(ss, sr, "iir") for ss in (2.0, 5.0, 10.0, 20.0) for sr in (10.0, 30.0, 50.0)] + \
+        [(2.0, sr, "fir") for sr in (10.0, 30.0, 50.0)]
+# the smallest resolvable fraction kappa gives on this image (sigma_r = 10: (R / sigma_r)^2 = 234)
+SWEEP_MIN_GATED = {10.0: 0.92, 30.0: 0.996, 50.0: 0.999}
+_sweep_cache = {}
+
+
+def _sweep_oracle(img, ss, sr, spatial, tc):
+    key = (ss, sr, spatial, tc)
+    if key not in _sweep_cache:
+        _sweep_cache.clear()
+        _sweep_cache[key] = oracle.gp_bf(img.astype(np.float64), ss, sr, SWEEP_ORDERS, spatial, t_c=tc,
+                                         return_kappa=True)
+    return _sweep_cache[key]
+
+
+@pytest.mark.parametrize("N", SWEEP_ORDERS)
+@pytest.mark.parametrize("ss,sr,spatial", SWEEP)
+def test_rects_ramp1024_sweep(bf, ss, sr, spatial, N):
     img = synthetic.rects_ramp1024_image()
-    ref, kap = oracle.gp_bf(img.astype(np.float64), ss, sr, N, spatial, return_kappa=True)
-    out, bits = run_gpu(bf, img, ss, sr, N, spatial, status=True)
-    assert bits == 0
-    check(out, ref, kappa=kap, min_gated=0.9999)
-
-
-@pytest.mark.parametrize("ss", [5.0, 10.0, 20.0])
-def test_rects_ramp1024_recursive_small_sigma_r(bf, ss):
-    """sigma_r = 10 on the 1024^2 image gives s^2 = 234.  With the recursive
-    Gaussian, whose kernel dips to -1.4e-4 of its peak far out, the N = 20
-    approximation breaks down here: Q <= 0 on 0.2-1.4% of the pixels even in
-    FP64 (NaN on both sides) and outputs leave [0, 255] around them.  FP32
-    rounding of u is amplified ~s^2-fold through exp(-s^2 u^2 / 2), which kappa
-    does not model, so in this regime the gate is: NaN sets agree wherever
-    the pixel is conditioned, 99.99% of the conditioned pixels are within
-    1e-3 and all of them within 1e-2."""
-    img = synthetic.rects_ramp1024_image()
-    ref, kap = oracle.gp_bf(img.astype(np.float64), ss, 10.0, 20, "iir", return_kappa=True)
-    out, bits = run_gpu(bf, img, ss, 10.0, 20, "iir", status=True)
+    out, bits, counters, tc = run_gpu(bf, img, ss, sr, N, spatial, status=True)
+    refs, kaps = _sweep_oracle(img, ss, sr, spatial, tc)
+    q = SWEEP_ORDERS.index(N)
+    f64 = img.astype(np.float64)
+    fir = spatial == "fir"
+    parity.gate(out, refs[q], kaps[q], min_gated=SWEEP_MIN_GATED[sr], f=f64 if fir else None,
+                window=oracle.window(ss) if fir else None, label=f"1024^2 {spatial} ss={ss:g} sr={sr:g} N={N}")
+    n_q0 = parity.kept_value_pixels(out, f64, kaps[q])
+    assert counters[0] == n_q0 and bool(bits & bf.BF_DEV_NONPOS_Q) == (n_q0 > 0)
     assert (bits & ~bf.BF_DEV_NONPOS_Q) == 0
-    assert bool(bits & bf.BF_DEV_NONPOS_Q) == bool(np.isnan(ref).any())
-    cond = kap <= KAPPA_GATE
-    assert cond.mean() >= 0.95
-    assert np.array_equal(np.isnan(out)[cond], np.isnan(ref)[cond])
-    g = cond & np.isfinite(ref)
-    err = np.abs(out[g] - ref[g])
-    assert np.isfinite(err).all()
-    assert (err <= TOL).mean() >= 0.9999, f"{(err > TOL).sum()} pixels above {TOL}"
-    assert err.max() <= 10 * TOL, f"max err {err.max():.3e}"
 
 
 def test_large_s2_stays_in_fp32_range(bf):
     """(R / sigma_r)^2 = 234 on the 1024^2 image (R = 153, sigma_r = 10): exp(-s^2 u^2 / 2)
     would underflow FP32 at |u| = 1 without the common power-of-two channel scale."""
-    img = synthetic.rects_ramp1024_image()
-    out, bits = run_gpu(bf, img, 2.0, 10.0, 20, "fir", status=True)
-    assert bits == 0
-    ref, kap = oracle.gp_bf(img.astype(np.float64), 2.0, 10.0, 20, "fir", return_kappa=True)
-    check(out, ref, kappa=kap)
+    compare(bf, synthetic.rects_ramp1024_image(), 2.0, 10.0, 20, "fir", min_gated=0.999)
 
 
 def test_range_flag_beyond_fp32(bf):
     img = np.zeros((64, 64), np.float32)
     img[:, 32:] = 255.0
-    _, bits = run_gpu(bf, img, 3.0, 3.0, 20, "fir", status=True)  # s^2 = (127.5 / 3)^2 = 1806
+    _, bits, _, _ = run_gpu(bf, img, 3.0, 3.0, 20, "fir", status=True)  # s^2 = (127.5 / 3)^2 = 1806
     assert bits & bf.BF_DEV_RANGE
     # two planes beyond the range, one inside it: the counter counts planes
     x = torch.from_numpy(np.stack([img, img, np.full_like(img, 7.0)])).cuda()
@@ -206,16 +201,15 @@ def test_range_flag_beyond_fp32(bf):
 
 def test_rects4096_crop(bf):
     """4096^2, sigma_s 10, sigma_r 20, N 20, recursive filter: a 512^2 crop of the
-    GPU output against the oracle run on full lines of the full image."""
+    GPU output against the oracle run on full lines of the full image, and a
+    border crop (the zero extension at the image edge)."""
     img = synthetic.rects4096_image()
     f64 = img.astype(np.float64)
-    gpu = run_gpu(bf, img, 10.0, 20.0, 20, "iir")
-    r0, c0 = 1792, 2304
-    ref = oracle.gp_bf(f64, 10.0, 20.0, 20, "iir", crop=(r0, r0 + 512, c0, c0 + 512))
-    check(gpu[r0:r0 + 512, c0:c0 + 512], ref)  # every pixel: kappa <= 182 on this crop
-    # border crop (zero-extension path at the image edge)
-    ref2 = oracle.gp_bf(f64, 10.0, 20.0, 20, "iir", crop=(4096 - 64, 4096, 0, 64))
-    check(gpu[4096 - 64:, :64], ref2)
+    gpu, bits, _, tc = run_gpu(bf, img, 10.0, 20.0, 20, "iir", status=True)
+    assert bits == 0
+    for r0, r1, c0, c1 in ((1792, 2304, 2304, 2816), (4096 - 64, 4096, 0, 64)):
+        ref, kap = oracle.gp_bf(f64, 10.0, 20.0, 20, "iir", t_c=tc, crop=(r0, r1, c0, c1), return_kappa=True)
+        parity.gate(gpu[r0:r1, c0:c1], ref, kap, min_gated=0.99, label=f"4096^2 crop {r0}:{r1},{c0}:{c1}")
 
 
 # ---------------------------------------------------------------- special cases
@@ -229,22 +223,30 @@ def test_constant_image_exact(bf):
 def test_sigma_r_infinite(bf):
     img = synthetic.make_image(96, 80, 6, 10.0, 0.0, synthetic.seed_for(9, 1))
     for sp, ss in (("fir", 2.0), ("iir", 6.0)):
-        ref = oracle.gp_bf(img.astype(np.float64), ss, math.inf, 20, sp)
-        check(run_gpu(bf, img, ss, math.inf, 20, sp), ref)
+        compare(bf, img, ss, math.inf, 20, sp)
 
 
 def test_given_centre(bf):
     img = synthetic.make_image(64, 64, 6, 10.0, 0.0, synthetic.seed_for(9, 2))
-    ref = oracle.gp_bf(img.astype(np.float64), 2.0, 30.0, 20, "fir", t_c=127.5)
-    check(run_gpu(bf, img, 2.0, 30.0, 20, "fir", t_c=127.5), ref)
+    compare(bf, img, 2.0, 30.0, 20, "fir", t_c=127.5)
 
 
 def test_multi_plane_independent_centres(bf):
     imgs = np.stack([synthetic.make_image(50, 70, 5, 10.0, 0.0, synthetic.seed_for(9, 10 + i)) for i in range(3)])
     imgs[1] *= 0.3
-    gpu = run_gpu(bf, imgs, 2.0, 25.0, 20, "fir")
+    x = torch.from_numpy(imgs).cuda()
+    o = bf.make_opts(20, "fir")
+    need = bf.bf_gp_workspace_size(3, 50, 70, 2.0, o)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    y = torch.empty_like(x)
+    s = torch.cuda.current_stream().cuda_stream
+    bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 3, 50, 70, 70, 2.0, 25.0, o, ws.data_ptr(), need, s)
+    gpu = y.cpu().numpy()
     for i in range(3):
-        check(gpu[i], oracle.gp_bf(imgs[i].astype(np.float64), 2.0, 25.0, 20, "fir"))
+        tc = parity.gpu_centre(bf, ws.data_ptr(), i, s)
+        assert abs(tc - imgs[i].astype(np.float64).mean()) < 1e-3  # each plane its own mean
+        ref, kap = oracle.gp_bf(imgs[i].astype(np.float64), 2.0, 25.0, 20, "fir", t_c=tc, return_kappa=True)
+        parity.gate(gpu[i], ref, kap, f=imgs[i], window=oracle.window(2.0), label=f"plane {i}")
 
 
 def test_pitched_input(bf):
@@ -256,11 +258,12 @@ def test_pitched_input(bf):
     o = bf.make_opts(20, "fir")
     need = bf.bf_gp_workspace_size(1, 40, 50, 2.0, o)
     ws = torch.empty(need, dtype=torch.uint8, device="cuda")
-    bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, 40, 50, 53, 2.0, 30.0, o, ws.data_ptr(), need,
-                     torch.cuda.current_stream().cuda_stream)
-    torch.cuda.synchronize()
+    s = torch.cuda.current_stream().cuda_stream
+    bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, 40, 50, 53, 2.0, 30.0, o, ws.data_ptr(), need, s)
+    tc = parity.gpu_centre(bf, ws.data_ptr(), 0, s)
     out = y.cpu().numpy()
-    check(out[:, :50].astype(np.float64), oracle.gp_bf(img.astype(np.float64), 2.0, 30.0, 20, "fir"))
+    ref, kap = oracle.gp_bf(img.astype(np.float64), 2.0, 30.0, 20, "fir", t_c=tc, return_kappa=True)
+    parity.gate(out[:, :50], ref, kap, f=img, window=oracle.window(2.0), label="pitched")
     assert np.all(out[:, 50:] == -7.0)  # padding untouched
 
 
@@ -282,27 +285,55 @@ def test_device_stats_readback(bf):
 
 @pytest.mark.parametrize("spatial,two_pass", [("fir", False), ("fir", True), ("iir", False)])
 def test_odd_order_flags_and_counts_nonpositive_denominator(bf, spatial, two_pass):
-    """Odd N: pixels with Q <= 0 become NaN, the flag is raised and the
-    counter holds exactly the number of such pixels (fused FIR kernel, FIR
-    column pass, recursive column pass)."""
+    """Odd N: pixels with Q <= 0 keep their own value (Eq. (11) is undefined
+    there), the flag is raised and the counter holds exactly the number of
+    such pixels (fused FIR kernel, FIR column pass, recursive column pass)."""
     img = np.zeros((16, 16), np.float32)
     img[:, 8] = 255.0
     x = torch.from_numpy(img).cuda()
     o = bf.make_opts(5, spatial, fir_two_pass=two_pass)
     need = bf.bf_gp_workspace_size(1, 16, 16, 3.0, o)
     ws = torch.empty(need, dtype=torch.uint8, device="cuda")
-    y = torch.empty_like(x)
+    y = torch.full_like(x, float("nan"))
     s = torch.cuda.current_stream().cuda_stream
     bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, 16, 16, 16, 3.0, 20.0, o, ws.data_ptr(), need, s)
     bits = bf.bf_gp_get_device_status(ws.data_ptr(), s)
     counters = bf.bf_gp_get_device_counters(ws.data_ptr(), s)
     out = y.cpu().numpy()
-    nan = int(np.isnan(out).sum())
-    assert nan > 0 and bits & bf.BF_DEV_NONPOS_Q
-    assert counters == [nan, 0, 0, 0]
-    if spatial == "fir":
-        ref = oracle.gp_bf(img.astype(np.float64), 3.0, 20.0, 5, "fir")
-        assert np.array_equal(np.isnan(out), np.isnan(ref))
+    assert np.isfinite(out).all()
+    assert counters[0] > 0 and bits & bf.BF_DEV_NONPOS_Q and counters[1:] == [0, 0, 0]
+    assert np.all(out[:, 8] == 255.0)  # the line's pixels (Q <= 0) keep their value
+    tc = parity.gpu_centre(bf, ws.data_ptr(), 0, s)
+    ref, kap = oracle.gp_bf(img.astype(np.float64), 3.0, 20.0, 5, spatial, t_c=tc, return_kappa=True)
+    assert parity.kept_value_pixels(out, img, kap) == counters[0]
+    parity.gate(out, ref, kap, min_gated=0.5, label=f"odd N {spatial} two_pass={two_pass}")
+
+
+def test_tcgen05_wait_gives_up_cleanly(bf):
+    """The tcgen05 column pass told to issue no tensor-core product and to give up
+    each wait for one after 2000 polls: nothing is in flight when it gives up, so it
+    frees its tensor memory and returns; the call reports BF_DEV_TIMEOUT with one
+    count per CTA, writes the plane as copied, and the context stays usable."""
+    H, W, ss = 1030, 64, 6.0
+    img = synthetic.make_image(H, W, 8, 10.0, 0.0, synthetic.seed_for(9, 9100))
+    x = torch.from_numpy(img).cuda()
+    s = torch.cuda.current_stream().cuda_stream
+    o = bf.make_opts(20, "iir", engine=3, tc5_wait_test=2000)
+    need = bf.bf_gp_workspace_size(1, H, W, ss, o)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    y = torch.full_like(x, float("nan"))
+    bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, 30.0, o, ws.data_ptr(), need, s)
+    bits = bf.bf_gp_get_device_status(ws.data_ptr(), s)
+    counters = bf.bf_gp_get_device_counters(ws.data_ptr(), s)
+    assert bits & bf.BF_DEV_TIMEOUT and (bits & ~bf.BF_DEV_TIMEOUT) == 0
+    ctas = (W // 8) * ((H + 511) // 512)
+    assert counters == [0, 0, 0, ctas]
+    assert np.array_equal(y.cpu().numpy(), img)
+    # the same context, the normal engine-3 call: no timeout, the oracle's result
+    compare(bf, img, ss, 30.0, 20, "iir", min_gated=0.95, label="engine 3 after a timed-out call")
+    o3 = bf.make_opts(20, "iir", engine=3)
+    bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, 30.0, o3, ws.data_ptr(), need, s)
+    assert bf.bf_gp_get_device_status(ws.data_ptr(), s) == 0
 
 
 def test_nonfinite_input_is_passed_through_and_flagged(bf):
@@ -399,13 +430,14 @@ def test_engines_agree_with_oracle(bf, engine, shape, ss):
     s = torch.cuda.current_stream().cuda_stream
     bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, 30.0, o, ws.data_ptr(), need, s)
     assert bf.bf_gp_get_device_status(ws.data_ptr(), s) == 0
-    ref, kap = oracle.gp_bf(img.astype(np.float64), ss, 30.0, 20, "iir", return_kappa=True)
-    check(y.cpu().numpy().astype(np.float64), ref, kappa=kap, min_gated=0.999)
+    tc = parity.gpu_centre(bf, ws.data_ptr(), 0, s)
+    ref, kap = oracle.gp_bf(img.astype(np.float64), ss, 30.0, 20, "iir", t_c=tc, return_kappa=True)
+    parity.gate(y.cpu().numpy(), ref, kap, min_gated=0.9, label=f"engine {engine} {shape} ss={ss:g}")
 
 
 # ---------------------------------------------------------------- fused FIR forward
 
-def _forward(bf, img, ss, sr, N, two_pass):
+def _forward(bf, img, ss, sr, N, two_pass, centre=False):
     x = torch.from_numpy(np.ascontiguousarray(img, dtype=np.float32)).cuda()
     H, W = x.shape
     o = bf.make_opts(N, "fir", fir_two_pass=two_pass)
@@ -414,7 +446,8 @@ def _forward(bf, img, ss, sr, N, two_pass):
     y = torch.full_like(x, float("nan"))
     s = torch.cuda.current_stream().cuda_stream
     bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, sr, o, ws.data_ptr(), need, s)
-    return y.cpu().numpy().astype(np.float64), bf.bf_gp_get_device_status(ws.data_ptr(), s)
+    out = (y.cpu().numpy().astype(np.float64), bf.bf_gp_get_device_status(ws.data_ptr(), s))
+    return out + (parity.gpu_centre(bf, ws.data_ptr(), 0, s),) if centre else out
 
 
 @pytest.mark.parametrize("shape,ss", [((1, 1), 1.0), ((7, 300), 0.4), ((33, 65), 2.0), ((256, 256), 3.0),
@@ -425,12 +458,13 @@ def test_fir_fused_matches_two_pass_and_oracle(bf, shape, ss):
     every image edge, windows from W = 2 to 12."""
     H, W = shape
     img = synthetic.make_image(H, W, 6, 10.0, 20.0, synthetic.seed_for(9, 7000 + H + W))
-    fused, b1 = _forward(bf, img, ss, 30.0, 20, False)
+    fused, b1, tc = _forward(bf, img, ss, 30.0, 20, False, centre=True)
     two, b2 = _forward(bf, img, ss, 30.0, 20, True)
     assert b1 == 0 and b2 == 0
     assert np.abs(fused - two).max() <= 2e-4
-    ref, kap = oracle.gp_bf(img.astype(np.float64), ss, 30.0, 20, "fir", return_kappa=True)
-    check(fused, ref, kappa=kap, min_gated=0.999)
+    ref, kap = oracle.gp_bf(img.astype(np.float64), ss, 30.0, 20, "fir", t_c=tc, return_kappa=True)
+    parity.gate(fused, ref, kap, min_gated=0.999, f=img, window=oracle.window(ss), label=f"fused {shape} ss={ss:g}")
+    parity.gate(two, ref, kap, min_gated=0.999, f=img, window=oracle.window(ss), label=f"two-pass {shape} ss={ss:g}")
 
 
 def test_fir_fused_copy_planes(bf):
@@ -462,8 +496,11 @@ def test_box_variant_matches_oracle(bf, shape, r, passes):
     s = torch.cuda.current_stream().cuda_stream
     bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, H, W, W, 1.0, 30.0, o, ws.data_ptr(), need, s)
     assert bf.bf_gp_get_device_status(ws.data_ptr(), s) == 0
-    ref, kap = oracle.gp_bf(img.astype(np.float64), 1.0, 30.0, 20, "box", box=(r, passes), return_kappa=True)
-    check(y.cpu().numpy().astype(np.float64), ref, kappa=kap, min_gated=0.999)
+    tc = parity.gpu_centre(bf, ws.data_ptr(), 0, s)
+    ref, kap = oracle.gp_bf(img.astype(np.float64), 1.0, 30.0, 20, "box", box=(r, passes), t_c=tc,
+                            return_kappa=True)
+    parity.gate(y.cpu().numpy(), ref, kap, min_gated=0.999, f=img, window=r * passes,
+                label=f"box {shape} r={r} passes={passes}")
 
 
 def test_box_variant_radius_from_sigma_and_limits(bf):
@@ -471,10 +508,14 @@ def test_box_variant_radius_from_sigma_and_limits(bf):
     closest to sigma_s^2); wider windows than 12 and the two-pass form are refused."""
     img = synthetic.make_image(120, 140, 6, 10.0, 0.0, synthetic.seed_for(9, 8100))
     x = torch.from_numpy(img).cuda()
-    y = bf.bilateral_gp(x, 3.0, 30.0, 20, "box").cpu().numpy().astype(np.float64)
+    o0 = bf.make_opts(20, "box")
+    need0 = bf.bf_gp_workspace_size(1, 120, 140, 3.0, o0)
+    ws0 = torch.empty(need0, dtype=torch.uint8, device="cuda")
+    y = bf.bilateral_gp(x, 3.0, 30.0, 20, "box", ws=ws0).cpu().numpy().astype(np.float64)
+    tc = parity.gpu_centre(bf, ws0.data_ptr(), 0, torch.cuda.current_stream().cuda_stream)
     r = int(round((np.sqrt(12 * 9.0 / 3 + 1) - 1) / 2))
-    ref, kap = oracle.gp_bf(img.astype(np.float64), 3.0, 30.0, 20, "box", box=(r, 3), return_kappa=True)
-    check(y, ref, kappa=kap, min_gated=0.999)
+    ref, kap = oracle.gp_bf(img.astype(np.float64), 3.0, 30.0, 20, "box", box=(r, 3), t_c=tc, return_kappa=True)
+    parity.gate(y, ref, kap, min_gated=0.999, f=img, window=3 * r, label="box radius from sigma")
     with pytest.raises(bf.BFError):
         bf.bf_gp_workspace_size(1, 64, 64, 1.0, bf.make_opts(20, "box", fir_halfwidth=5, box_passes=3))
     o = bf.make_opts(20, "box", fir_halfwidth=2, box_passes=2, fir_two_pass=True)

@@ -5,13 +5,13 @@ import numpy as np
 import pytest
 
 import oracle
+import parity
 import synthetic
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-3
-KAPPA_GATE = 8e-4 * 2 ** 24 / 16
+TOL = parity.TOL
 
 
 @pytest.fixture(scope="module")
@@ -35,14 +35,8 @@ def run_joint(bf, f, g, ss, sr, N, spatial):
     s = torch.cuda.current_stream().cuda_stream
     bf.bf_gp_forward_joint(ft.data_ptr(), gt.data_ptr(), y.data_ptr(), planes, H, W, W, ss, sr, o, ws.data_ptr(), need, s)
     bits = bf.bf_gp_get_device_status(ws.data_ptr(), s)
-    return y.cpu().numpy().astype(np.float64), bits
-
-
-def gate(out, ref, kap, min_gated=0.999):
-    g = np.isfinite(ref) & (kap <= KAPPA_GATE)
-    assert g.mean() >= min_gated
-    err = np.abs(out[g] - ref[g])
-    assert err.max() <= TOL, f"max err {err.max():.3e}"
+    tcs = [parity.gpu_centre(bf, ws.data_ptr(), c, s) for c in range(planes)]
+    return y.cpu().numpy().astype(np.float64), bits, tcs
 
 
 @pytest.mark.parametrize("shape,ss,sr,N,spatial", [
@@ -53,15 +47,19 @@ def test_joint_matches_oracle(bf, shape, ss, sr, N, spatial):
     H, W = shape
     f = synthetic.make_image(H, W, 6, 10.0, 30.0, synthetic.seed_for(10, H * 7 + W))
     g = synthetic.make_image(H, W, 5, 8.0, 0.0, synthetic.seed_for(10, H * 11 + W))
-    out, bits = run_joint(bf, f, g, ss, sr, N, spatial)
-    assert bits == 0
-    ref, kap = oracle.gp_bf_joint(f.astype(np.float64), g.astype(np.float64), ss, sr, N, spatial, return_kappa=True)
-    gate(out, ref, kap)
+    out, bits, tcs = run_joint(bf, f, g, ss, sr, N, spatial)
+    assert (bits & ~bf.BF_DEV_NONPOS_Q) == 0
+    ref, kap = oracle.gp_bf_joint(f.astype(np.float64), g.astype(np.float64), ss, sr, N, spatial, t_c=tcs[0],
+                                  return_kappa=True)
+    even_fir = spatial == "fir" and N % 2 == 0
+    parity.gate(out, ref, kap, min_gated=0.99, f=f if even_fir else None, window=oracle.window(ss) if even_fir else None,
+                label=f"joint {shape} {spatial} ss={ss:g} sr={sr:g} N={N}")
+    assert parity.kept_value_pixels(out, f, kap) == 0 or bits & bf.BF_DEV_NONPOS_Q
 
 
 def test_joint_with_guide_equal_to_data_is_the_single_image_filter(bf):
     img = synthetic.make_image(150, 170, 6, 10.0, 20.0, synthetic.seed_for(10, 9))
-    out, bits = run_joint(bf, img, img, 5.0, 30.0, 20, "iir")
+    out, bits, _ = run_joint(bf, img, img, 5.0, 30.0, 20, "iir")
     assert bits == 0
     x = torch.from_numpy(img).cuda()
     single = bf.bilateral_gp(x, 5.0, 30.0, 20, "iir").cpu().numpy().astype(np.float64)
@@ -71,13 +69,13 @@ def test_joint_with_guide_equal_to_data_is_the_single_image_filter(bf):
 def test_joint_constant_guide_and_nonfinite_guide(bf):
     f = synthetic.make_image(80, 90, 6, 10.0, 0.0, synthetic.seed_for(10, 10))
     g = np.full_like(f, 42.0)
-    out, bits = run_joint(bf, f, g, 3.0, 30.0, 12, "fir")
+    out, bits, tcs = run_joint(bf, f, g, 3.0, 30.0, 12, "fir")
     assert bits == 0
-    ref = oracle.gp_bf_joint(f.astype(np.float64), g.astype(np.float64), 3.0, 30.0, 12, "fir")
-    assert np.abs(out - ref).max() <= TOL
+    ref = oracle.gp_bf_joint(f.astype(np.float64), g.astype(np.float64), 3.0, 30.0, 12, "fir", t_c=tcs[0])
+    parity.gate(out, ref, label="joint constant guide")
     g2 = synthetic.make_image(80, 90, 6, 10.0, 0.0, synthetic.seed_for(10, 11))
     g2[5, 5] = np.inf
-    out2, bits2 = run_joint(bf, f, g2, 3.0, 30.0, 12, "fir")
+    out2, bits2, _ = run_joint(bf, f, g2, 3.0, 30.0, 12, "fir")
     assert bits2 & bf.BF_DEV_NONFINITE_IN
     assert np.array_equal(out2, f.astype(np.float64))
 
@@ -87,10 +85,11 @@ def test_joint_batch_of_planes_and_convenience_call(bf):
     g = synthetic.make_image(70, 66, 4, 10.0, 0.0, synthetic.seed_for(10, 13), planes=3)
     y = bf.bilateral_gp_joint(torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda(), 4.0, 35.0, 18, "iir")
     y = y.cpu().numpy().astype(np.float64)
+    _, _, tcs = run_joint(bf, f, g, 4.0, 35.0, 18, "iir")
     for c in range(3):
         ref, kap = oracle.gp_bf_joint(f[c].astype(np.float64), g[c].astype(np.float64), 4.0, 35.0, 18, "iir",
-                                      return_kappa=True)
-        gate(y[c], ref, kap)
+                                      t_c=tcs[c], return_kappa=True)
+        parity.gate(y[c], ref, kap, min_gated=0.99, label=f"joint plane {c}")
 
 
 def test_joint_order_limit(bf):

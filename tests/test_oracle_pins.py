@@ -384,12 +384,13 @@ def test_error_grows_with_abs_tau():
 def test_kappa_lower_bound_and_equality(sp):
     """The terms' part of kappa is >= 2 |y - t_c| by the triangle inequality; with
     non-negative terms (f >= t_c = 0 and the positive window weights) it is equal.
-    The total adds the input's part, which is non-negative."""
+    The total adds the input's part, which is non-negative, and |y| (the final
+    rounding)."""
     f = small_image(30, 26, 31)
     y, k, kt, ku = oracle.gp_bf(f, 2.0, 30.0, 20, sp, return_kappa="parts")
     tc = f.mean()
     assert np.all(kt >= 2 * np.abs(y - tc) * (1 - 1e-12))
-    assert np.all(ku >= 0) and np.array_equal(k, kt + ku)
+    assert np.all(ku >= 0) and np.array_equal(k, kt + ku + np.abs(y))
     if sp == "fir":
         y0, _, k0, _ = oracle.gp_bf(f, 2.0, 30.0, 20, sp, t_c=0.0, return_kappa="parts")
         np.testing.assert_allclose(k0, 2 * np.abs(y0), rtol=1e-12)
