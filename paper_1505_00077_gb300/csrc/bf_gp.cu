@@ -538,7 +538,7 @@ bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
         TCMat tm;
         if (tcore) tc_mats((double)sigma_s, &tm);
         // the CUDA-core pass: the channel tiles, and for the saving forward its dp, dq ([2 C][256])
-        const size_t smem = tcore ? sizeof(float) * 2 * 512 * 8
+        const size_t smem = tcore ? sizeof(float) * COL_TILE_BUFS * COL_TILE_FLOATS
                                   : sizeof(float) * (COL_TILE_BUFS * COL_TILE_FLOATS +
                                                      (MODE == MODE_SAVE ? 2 * COL_C * 256 : 0));
         if constexpr (MODE != MODE_JOINT) {

@@ -2640,19 +2640,35 @@ __global__ void __launch_bounds__(512) row_tc(RowArgs a, IIRCoef cf, TCMat tm)
     row_tc_body<MODE>(a, cf, tm, blockIdx.x, blockIdx.y);
 }
 
-// Column pass, tensor cores.  A cluster of CL CTAs covers an 8-column strip's
-// full height; CTA rank r owns rows [512 r, 512 r + 512) = 64 chunks of 8 rows
-// per column; warp w owns chunks [8 w, 8 w + 8) of every column; its group q
-// has MMA row g = (column g, chunk 8w + 2q), row g + 8 = (column g, chunk
-// 8w + 2q + 1).  Thread (g, t) thus holds combo t of column g for 8
-// consecutive chunks: the chunk scan runs in registers.
+// Column pass, tensor cores (mma.sync, TF32 x 3).  The cluster structure is
+// col_iir's: a cluster of CL <= 8 CTAs covers an 8-column strip's full height,
+// CTA rank r owns rows [512 r, 512 r + 512); channel tiles are staged by
+// cp.async two channels ahead in four buffers; warp 0 turns the warp totals
+// into the carry entering each warp and pushes the CTA total, already carried
+// across the CTAs in between, into the CTAs it enters; a split cluster barrier
+// publishes them.  The products are row_tc's: warp w owns rows
+// [64 w, 64 w + 64) of the CTA, 8 chunks of 8 rows per column; in group q its
+// MMA row g is (column g, chunk 2q) and row g + 8 is (column g, chunk 2q + 1).
+// Thread (g, t) thus holds combo t (pole t & 1, direction t >> 1) of column g
+// for the warp's 8 chunks, so the chunk scan runs in its registers, and its 16
+// outputs are column g, rows 64 w + 16 q + 8 h + 2 t + {0, 1} (h = 0, 1).
+// grid (strips * CL, planes), block 256, cluster (CL, 1, 1).
 template <int MODE>
 __device__ __forceinline__ void col_tc_body(const ColArgs &a, const IIRCoef &cf, const TCMat &tm, int strip,
                                             int plane)
 {
-    extern __shared__ __align__(16) float tiles[];  // [2][512][8]
-    __shared__ float2 wtot[8][8][4];                 // [warp][column][combo]
-    __shared__ float2 ctot[2][8][4];                 // [channel parity][column][combo] CTA totals
+    extern __shared__ __align__(16) float tiles[];  // [COL_TILE_BUFS][COL_TILE_FLOATS], col_iir's tile layout
+    // [channel parity][warp][column][combo]: warp totals; warp 0 replaces them by the carry entering each warp
+    __shared__ float2 wt[2][8][8][4];
+    // [channel parity][source rank][column][combo]: CTA totals pushed by the other CTAs of the cluster
+    // (causal combos by lower ranks, anticausal ones by higher ranks), each already carried across the
+    // CTAs in between; slots no CTA writes stay zero
+    __shared__ float2 inc[2][8][8][4];
+    // the B fragments of every lane, split (TF32 high and low parts): loc, sum, cor
+    __shared__ uint4 sbf[3][32];
+    // forward: u of this thread's pixel pairs (j = 2e, 2e + 1), kept out of registers
+    constexpr bool FWD = MODE == MODE_FWD;
+    __shared__ float2 su[FWD ? 8 : 1][FWD ? 256 : 1];
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t = lane & 3;
@@ -2660,29 +2676,37 @@ __device__ __forceinline__ void col_tc_body(const ColArgs &a, const IIRCoef &cf,
     const int rank = (int)cl.block_rank();
     const int CL = (int)cl.num_blocks();
     const int x = strip * 8 + g;
-    const int rbase = rank * 512;
+    const int rbase = rank * COL_ROWS;
     const PlaneParams &P = a.pp[plane];
     const bool filt = (P.mode == 0);
     const float *wsp = a.ws + (size_t)plane * a.K * a.H * a.Wp + strip * 8;
-    constexpr int TILE = 512 * 8;
 
-    auto issue_tile = [&](int k, int buf) {
-        const float *src = wsp + (size_t)k * a.H * a.Wp;
-        float *dst = tiles + buf * TILE;
+    // tile copy: every warp copies the 64 rows it reads itself (rows 64 w + lane/2 + 16 i, i < 4, two
+    // 16-byte halves), so a tile needs no CTA-wide barrier: the warp's own wait and __syncwarp
+    const size_t plane_stride = (size_t)a.H * a.Wp;
+    const int lrow = 64 * warp + (lane >> 1);
+    const int gr0 = rbase + lrow;
+    const int src0 = gr0 * a.Wp + (lane & 1) * 4;
+    const unsigned dst0 = smem_u32(tiles + tile_off(lrow) + (lane & 1) * 4);
+    auto issue_tile = [&](int k) {
+        const float *src = wsp + (size_t)k * plane_stride + src0;
+        const unsigned dst = dst0 + (unsigned)((k & (COL_TILE_BUFS - 1)) * COL_TILE_FLOATS * sizeof(float));
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const int idx = tid + i * 256;
-            const int r = idx >> 1, half = idx & 1;
-            const int gr = rbase + r;
-            const bool ok = filt && gr < a.H;
-            cp_async16(dst + r * 8 + half * 4, src + (size_t)(ok ? gr : 0) * a.Wp + half * 4, ok);
+            const bool ok = filt && gr0 + 16 * i < a.H;
+            // tile_off(r + 16) = tile_off(r) + 17 * 8
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst + i * 17 * 8 * 4),
+                         "l"(ok ? src + (size_t)i * 16 * a.Wp : wsp), "r"(ok ? 16 : 0)
+                         : "memory");
         }
-        cp_async_commit();
     };
 
-    // pixel j = 4 q + i of this lane: group q, D slot i
-    auto prow = [&](int q, int i) { return rbase + 8 * (8 * warp + 2 * q + (i >> 1)) + 2 * t + (i & 1); };
+    // pixel j = 4 q + i of this thread: row 64 w + 16 q + 8 (i >> 1) + 2 t + (i & 1) of the CTA
+    auto prow = [&](int q, int i) { return rbase + 64 * warp + 16 * q + 8 * (i >> 1) + 2 * t + (i & 1); };
+    // the per-pixel sums: for the forward p and q in registers and u in shared memory (the same
+    // Horner steps as Combine), otherwise Combine
     Combine<16, MODE> cb;
+    float fp[FWD ? 16 : 1], fq[FWD ? 16 : 1];
     const float *fcol = a.f + (size_t)plane * a.H * a.pitch;
 #pragma unroll
     for (int q = 0; q < 4; ++q)
@@ -2691,99 +2715,171 @@ __device__ __forceinline__ void col_tc_body(const ColArgs &a, const IIRCoef &cf,
             const int r = prow(q, i);
             const bool in = (r < a.H) && (x < a.W);
             const float fv = in ? __ldg(fcol + (size_t)r * a.pitch + x) : 0.f;
-            cb.init((fv - P.tc) * P.invR, q * 4 + i);
+            const float uu = (fv - P.tc) * P.invR;
+            if constexpr (FWD) {
+                const int j = q * 4 + i;
+                if (j & 1)
+                    su[j >> 1][tid].y = uu;
+                else
+                    su[j >> 1][tid].x = uu;
+                fp[j] = fq[j] = 0.f;
+            } else {
+                cb.init(uu, q * 4 + i);
+            }
         }
-    BFrag bl, bs, bc;
-    bl.load(tm.loc, g, t);
-    bs.load(tm.sum, g, t);
-    bc.load(tm.cor, g, t);
+    if (tid < 32) {
+        BFrag b;
+        b.load(tm.loc, g, t);
+        sbf[0][lane] = make_uint4(b.h0, b.h1, b.l0, b.l1);
+        b.load(tm.sum, g, t);
+        sbf[1][lane] = make_uint4(b.h0, b.h1, b.l0, b.l1);
+        b.load(tm.cor, g, t);
+        sbf[2][lane] = make_uint4(b.h0, b.h1, b.l0, b.l1);
+    }
+    auto bfrag = [&](int which) {
+        const uint4 v = sbf[which][lane];
+        BFrag b;
+        b.h0 = v.x;
+        b.h1 = v.y;
+        b.l0 = v.z;
+        b.l1 = v.w;
+        return b;
+    };
     const int m = t & 1;
-    const bool rev = (t >> 1) != 0;
+    const bool rev = (t >> 1) != 0;                      // anticausal combo: scan order reversed
     const float P1r = cf.Pr[m][0], P1i = cf.Pi[m][0];    // p^8: one chunk
-    const float P8r = cf.Pr[m][3], P8i = cf.Pi[m][3];    // p^64: one warp (8 chunks)
-    const float P64r = cf.Pr[m][6], P64i = cf.Pi[m][6];  // p^512: one CTA
-    float Phr, Phi;  // p^{64 hops}: the CTA carry crosses the warps before (causal) / after (anticausal) this one
+    float Phr, Phi;  // p^{64 w'}: a carry from outside the CTA crosses the warps before (causal) / after this one
     cpow_tab(Phr, Phi, cf, m, 8 * (rev ? 7 - warp : warp));
+    {
+        float2 *z = &inc[0][0][0][0];
+        for (int e = tid; e < 2 * 8 * 8 * 4; e += blockDim.x) z[e] = make_float2(0.f, 0.f);
+    }
+    cl.sync();  // zeroed before any peer pushes
 
-    issue_tile(a.K - 1, (a.K - 1) & 1);
-#pragma unroll 1
-    for (int k = a.K - 1; k >= 0; --k) {
-        cp_async_wait_all();
-        __syncthreads();  // tile k visible; all threads done with the tile of channel k+1
-        if (k > 0) issue_tile(k - 1, (k - 1) & 1);
-        const float *tl = tiles + (k & 1) * TILE + g;
-        float D[4][4], S[4][4];
+    issue_tile(a.K - 1);
+    cp_async_commit();
+    if (a.K >= 2) issue_tile(a.K - 2);
+    cp_async_commit();
+    cp_async_wait_1();
+    __syncthreads();
+    // this warp's rows in a tile: tile_off(64 w + 16 q + r) = (68 w + 17 q + r) * 8 for r < 16
+    const int toff = 68 * 8 * warp + g;
+    // the A values of the next channel's tile, loaded as soon as the tile is visible
+    float xa[4][4];
+    auto load_a = [&](int k) {
+        const float *tl = tiles + (k & (COL_TILE_BUFS - 1)) * COL_TILE_FLOATS + toff;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int r0 = 8 * (8 * warp + 2 * q) + t, r1 = r0 + 8;
+            const float *tq = tl + 17 * 8 * q;
+            xa[q][0] = tq[t * 8];
+            xa[q][1] = tq[(t + 8) * 8];
+            xa[q][2] = tq[(t + 4) * 8];
+            xa[q][3] = tq[(t + 12) * 8];
+        }
+    };
+    load_a(a.K - 1);
+#pragma unroll 1
+    for (int k = a.K - 1; k >= 0; --k) {
+        // tile k's A values are in xa (loaded after the warp's copies landed); the buffer of tile
+        // k - 2 last held tile k + 2, which this warp finished reading before issuing this copy
+        float D[4][4], S[4][4];
+        const BFrag bl = bfrag(0), bs = bfrag(1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            AFrag af;
+            af.set(xa[q][0], xa[q][1], xa[q][2], xa[q][3]);
 #pragma unroll
             for (int i = 0; i < 4; ++i) D[q][i] = S[q][i] = 0.f;
-            AFrag af;
-            af.set(tl[r0 * 8], tl[r1 * 8], tl[(r0 + 4) * 8], tl[(r1 + 4) * 8]);
             mma3f(D[q], af, bl);
             mma3f(S[q], af, bs);
         }
+        if (k >= 2) issue_tile(k - 2);
+        cp_async_commit();
+
+        // the warp total of combo t of column g (zero state at the warp's start, in scan order)
         Seq8 sq;
         sq.from_chunks(S, rev);
-        float totr = 0.f, toti = 0.f;
+        float tr = 0.f, ti = 0.f;
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
-            float nr, ni;
-            cmul(nr, ni, P1r, P1i, totr, toti);
-            totr = nr + sq.r[s];
-            toti = ni + sq.i[s];
+            float nr = sq.r[s], ni = sq.i[s];
+            cmadd(nr, ni, P1r, P1i, tr, ti);
+            tr = nr;
+            ti = ni;
         }
-        wtot[warp][g][t] = make_float2(totr, toti);
-        __syncthreads();
-        // carry entering this warp from the other warps of the CTA (p^64 per warp)
-        float Wr = 0.f, Wi = 0.f;
-        for (int s = 0; s < 8; ++s) {
-            const int w = rev ? 7 - s : s;
-            if ((!rev && w >= warp) || (rev && w <= warp)) continue;
-            const float2 tt = wtot[w][g][t];
-            float nr, ni;
-            cmul(nr, ni, P8r, P8i, Wr, Wi);
-            Wr = nr + tt.x;
-            Wi = ni + tt.y;
+        const int par = k & 1;
+        wt[par][warp][g][t] = make_float2(tr, ti);
+        if (warp == 0) {
+            bar_sync_named(1, 256);  // all warp totals of this channel written
+            // lane (g, t): fold the 8 warp totals in scan order; each slot becomes the carry entering its warp
+            const float P8r = m == 0 ? cf.Pr[0][3] : cf.Pr[1][3], P8i = m == 0 ? cf.Pi[0][3] : cf.Pi[1][3];  // p^64
+            float Wr = 0.f, Wi = 0.f;
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                const int w = rev ? 7 - s : s;
+                const float2 tt = wt[par][w][g][t];
+                wt[par][w][g][t] = make_float2(Wr, Wi);
+                float nr = tt.x, ni = tt.y;
+                cmadd(nr, ni, P8r, P8i, Wr, Wi);
+                Wr = nr;
+                Wi = ni;
+            }
+            // push the CTA total to the CTAs it enters, later ranks (causal) or earlier ones
+            // (anticausal), times p^512 per CTA crossed on the way
+            float2 *own = &inc[par][rank][g][t];
+            const int nd = rev ? rank : CL - 1 - rank;
+            const float P64r = m == 0 ? cf.Pr[0][6] : cf.Pr[1][6], P64i = m == 0 ? cf.Pi[0][6] : cf.Pi[1][6];  // p^512
+            for (int d = 1; d <= nd; ++d) {
+                *cl.map_shared_rank(own, rev ? rank - d : rank + d) = make_float2(Wr, Wi);
+                float nr, ni;
+                cmul(nr, ni, P64r, P64i, Wr, Wi);
+                Wr = nr;
+                Wi = ni;
+            }
+        } else {
+            bar_arrive_named(1, 256);
         }
-        // CTA total: the last warp in scan order extends its incoming carry by its own total
-        if ((!rev && warp == 7) || (rev && warp == 0)) {
-            float cr2 = totr, ci2 = toti;
-            cmadd(cr2, ci2, P8r, P8i, Wr, Wi);
-            ctot[k & 1][g][t] = make_float2(cr2, ci2);
+        cp_async_wait_1();  // this thread's part of tile k - 1
+        __syncwarp();       // the warp's rows of tile k - 1 visible to the warp
+        // releases the carries and the pushed CTA totals
+        cluster_arrive_release();
+        cluster_wait_acquire();
+        if (k >= 1) load_a(k - 1);  // their latency runs under the rest of channel k
+
+        // the carry entering this warp: from the warps before it in the CTA, and from the other CTAs
+        float Wr, Wi;
+        {
+            const float2 w2 = wt[par][warp][g][t];
+            Wr = w2.x;
+            Wi = w2.y;
         }
-        // CTA totals of the cluster written.  ctot is double-buffered by channel parity: a
-        // peer may still read this channel's totals until it reaches the next cluster barrier.
-        cl.sync();
         if (CL > 1) {
             float Xr = 0.f, Xi = 0.f;
-            const int nsteps = rev ? CL - 1 - rank : rank;
-            for (int s = 0; s < nsteps; ++s) {
-                const int r = rev ? CL - 1 - s : s;
-                const float2 tt = *cl.map_shared_rank(&ctot[k & 1][g][t], r);
-                float nr, ni;
-                cmul(nr, ni, P64r, P64i, Xr, Xi);
-                Xr = nr + tt.x;
-                Xi = ni + tt.y;
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                const float2 tt = inc[par][s][g][t];
+                Xr += tt.x;
+                Xi += tt.y;
             }
             cmadd(Wr, Wi, Phr, Phi, Xr, Xi);
         }
-        // incoming state of each chunk in scan order, the correction products in chunk order
-        float inr_s[8], ini_s[8];
+        // incoming state of each chunk in scan order (written over the chunk sums), then the
+        // correction products in chunk order
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
-            inr_s[s] = Wr;
-            ini_s[s] = Wi;
-            float nr, ni;
-            cmul(nr, ni, P1r, P1i, Wr, Wi);
-            Wr = nr + sq.r[s];
-            Wi = ni + sq.i[s];
+            float nr = sq.r[s], ni = sq.i[s];
+            sq.r[s] = Wr;
+            sq.i[s] = Wi;
+            cmadd(nr, ni, P1r, P1i, Wr, Wi);
+            Wr = nr;
+            Wi = ni;
         }
+        const BFrag bc = bfrag(2);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int c0 = 2 * q, c1 = 2 * q + 1;
-            const float r0 = rev ? inr_s[7 - c0] : inr_s[c0], i0 = rev ? ini_s[7 - c0] : ini_s[c0];
-            const float r1 = rev ? inr_s[7 - c1] : inr_s[c1], i1 = rev ? ini_s[7 - c1] : ini_s[c1];
+            const float r0 = rev ? sq.r[7 - c0] : sq.r[c0], i0 = rev ? sq.i[7 - c0] : sq.i[c0];
+            const float r1 = rev ? sq.r[7 - c1] : sq.r[c1], i1 = rev ? sq.i[7 - c1] : sq.i[c1];
             AFrag cfr;
             cfr.set(r0, r1, i0, i1);
             mma3f(D[q], cfr, bc);
@@ -2793,9 +2889,45 @@ __device__ __forceinline__ void col_tc_body(const ColArgs &a, const IIRCoef &cf,
         for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int i = 0; i < 4; ++i) y16[4 * q + i] = D[q][i];
-        cb.step(k, a.N, P.s2, y16);
+        if constexpr (FWD) {
+            // Combine::step of the forward, u from shared memory
+            if (k == 0) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const float2 uu = su[e][tid];
+                    fq[2 * e] = fmaf(P.s2 * uu.x, fq[2 * e], y16[2 * e]);
+                    fq[2 * e + 1] = fmaf(P.s2 * uu.y, fq[2 * e + 1], y16[2 * e + 1]);
+                }
+            } else {
+                const float mk = (float)k;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int j = 2 * e;
+                    const float2 uu = su[e][tid];
+                    if (k <= a.N) fma2r(fq[j], fq[j + 1], uu.x, uu.y, fq[j], fq[j + 1], y16[j], y16[j + 1]);
+                    float t0, t1;
+                    mul2(t0, t1, mk, mk, y16[j], y16[j + 1]);
+                    fma2r(fp[j], fp[j + 1], uu.x, uu.y, fp[j], fp[j + 1], t0, t1);
+                }
+            }
+        } else {
+            cb.step(k, a.N, P.s2, y16);
+        }
     }
     cl.sync();  // no CTA may leave while a peer can still read its shared memory
+    if constexpr (FWD) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const float2 uu = su[e][tid];
+            cb.u[2 * e] = uu.x;
+            cb.u[2 * e + 1] = uu.y;
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            cb.p[j] = fp[j];
+            cb.q[j] = fq[j];
+        }
+    }
     int nonpos = 0;
     AdjSums sums = {0.f, 0.f, 0.f};
 #pragma unroll
