@@ -659,7 +659,11 @@ def run_extra(args, rank, world, local):
     ms_fwd = timed(fwd, steps)
     ms_plain = timed(plain_fwd, steps)
     px = B * H * W
-    bytes_step = ((8 * K + 32) + (8 * K + 60)) * px  # forward with saves + backward (see DESIGN)
+    # algorithmic bytes per pixel: the forward that saves its sums, 8K + 16 plus 16 (P~, Q~ and the two
+    # derivative sums written); the backward, 8K + 56: statistics 4, the adjoint row pass reads f, dL/dy and
+    # two saved sums (16) and writes K planes, the adjoint column pass reads the K planes, f, dL/dy and the
+    # four saved sums (24) and writes dL/dh (4), the finish reads and writes the gradient (8)
+    bytes_step = ((8 * K + 32) + (8 * K + 56)) * px
     line = {"metric": "Mpixel/s", "value": px / (ms / 1e3) / 1e6, "unit": "Mpixel/s", "n_gpus": 1, "steps": steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
