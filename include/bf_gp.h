@@ -101,7 +101,10 @@ typedef struct {
     int tc5_wait_test;  /* engine 3 only, to test its bounded wait: 0 = normal; n > 0 = the column pass
                            issues no tensor-core product and gives up each wait for one after n polls:
                            the call reports BF_DEV_TIMEOUT and writes every plane as copied */
-    int reserved[4];    /* must be zero */
+    int row_threads;    /* threads per CTA of the row pass (recursive filter, two-pass FIR): 0 = the
+                           default (256, or one row when a row needs more); 256 or 512.  A CTA holds
+                           row_threads / (threads per row) rows.  The autotuner chooses it */
+    int reserved[3];    /* must be zero */
 } bf_gp_opts;
 
 /* Fill *opts with the defaults: N = 20, AUTO spatial operator, mean centre. */
@@ -349,8 +352,10 @@ bf_status bf_gp_batched_plane_stats(const bf_gp_plan *plan, void *ws, size_t ws_
  *     on the caller's f, y and ws (y is overwritten), and waits for them;
  *     later calls return the stored choice without launching anything.  ms
  *     (NULL, or BF_GP_TUNE_CANDIDATES floats) gets each candidate's mean time
- *     in milliseconds in candidate order (recursive: engines 0..3; FIR: fused,
- *     two-pass), -1 where nothing was timed.  Not capturable into a graph.
+ *     in milliseconds in candidate order (recursive: engine e with row_threads
+ *     256 at 2 e and 512 at 2 e + 1; FIR: fused, two-pass with 256 and with
+ *     512 row threads), -1 where nothing was timed.  The choice (engine or FIR
+ *     form, and row_threads) is written into opts.  Not capturable into a graph.
  *     BF_ERR_UNSUPPORTED if no candidate runs.
  *   bf_gp_autotune_clear: forgets every stored choice.
  *   bf_gp_batched_plan_tune: runs bf_gp_autotune for every plane of an
@@ -358,7 +363,7 @@ bf_status bf_gp_batched_plane_stats(const bf_gp_plan *plan, void *ws, size_t ws_
  *     outputs are overwritten) and makes bf_gp_batched use each plane's choice.
  *   bf_gp_batched_plan_engines: the engine each plane runs with (n entries).
  */
-#define BF_GP_TUNE_CANDIDATES 4
+#define BF_GP_TUNE_CANDIDATES 8
 bf_status bf_gp_autotune(const float *f, float *y, int planes, int H, int W, int pitch, float sigma_s,
                          float sigma_r, bf_gp_opts *opts, void *ws, size_t ws_bytes, void *stream, int reps,
                          float *ms);

@@ -53,7 +53,7 @@ class bf_gp_opts(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("spatial", ctypes.c_int), ("centre", ctypes.c_int),
                 ("fir_halfwidth", ctypes.c_int), ("t_c", ctypes.c_double), ("engine", ctypes.c_int),
                 ("fir_two_pass", ctypes.c_int), ("box_passes", ctypes.c_int), ("tc5_wait_test", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("row_threads", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class bf_gp_plane(ctypes.Structure):
@@ -155,7 +155,8 @@ ENGINE_TCGEN05 = 3     # half-chunk products on tcgen05 where a pass has such a 
 
 
 def make_opts(order: int = 20, spatial="auto", t_c=None, fir_halfwidth: int = 0, engine: int = ENGINE_AUTO,
-              fir_two_pass: bool = False, box_passes: int = 0, tc5_wait_test: int = 0) -> bf_gp_opts:
+              fir_two_pass: bool = False, box_passes: int = 0, tc5_wait_test: int = 0,
+              row_threads: int = 0) -> bf_gp_opts:
     """spatial 'box': box_passes passes (0 = 3) of a flat kernel of half-width
     fir_halfwidth (0 = matched to sigma_s).  tc5_wait_test: see bf_gp_opts
     (testing the tcgen05 column pass's bounded wait only)."""
@@ -166,6 +167,7 @@ def make_opts(order: int = 20, spatial="auto", t_c=None, fir_halfwidth: int = 0,
     o.fir_two_pass = int(bool(fir_two_pass))
     o.box_passes = int(box_passes)
     o.tc5_wait_test = int(tc5_wait_test)
+    o.row_threads = int(row_threads)
     o.spatial = _SPATIAL[spatial] if isinstance(spatial, str) else int(spatial)
     o.fir_halfwidth = int(fir_halfwidth)
     if t_c is not None:
@@ -263,12 +265,12 @@ def bf_gp_batched(plan, ws_ptr, ws_bytes, stream=0) -> None:
     _check(_load().bf_gp_batched(_vp(plan), _vp(ws_ptr), int(ws_bytes), _vp(stream)), "bf_gp_batched")
 
 
-BF_GP_TUNE_CANDIDATES = 4
+BF_GP_TUNE_CANDIDATES = 8
 
 
 def bf_gp_autotune(f_ptr, y_ptr, planes, H, W, pitch, sigma_s, sigma_r, opts, ws_ptr, ws_bytes, stream=0, reps=0):
-    """Fastest engine (recursive filter) or FIR form for this shape class,
-    written into opts (a bf_gp_opts, modified in place and returned) with each
+    """Fastest engine (recursive filter) or FIR form, and row-pass CTA size, for
+    this shape class, written into opts (a bf_gp_opts, modified in place and returned) with each
     candidate's mean time in ms (-1: not timed, e.g. a stored choice).  Times
     on the given buffers (y is overwritten) and synchronises; see include/bf_gp.h."""
     ms = (ctypes.c_float * BF_GP_TUNE_CANDIDATES)()

@@ -57,6 +57,7 @@ struct Plan {
     int T;                     // row threads per row
     int CL;                    // column cluster size (IIR)
     int row_tc, col_tc;        // recursive filter: row / column pass engine (0 CUDA cores, 1 mma.sync, 2 tcgen05)
+    int row_block;             // threads per CTA of the row pass asked for (0 = default)
     int engine_auto;           // opts.engine == 0 (the adjoint row pass then runs on CUDA cores)
     int joint;                 // joint filter: K = 2 (N + 1), CUDA-core passes
     int box_passes, box_r;     // box variant: passes of a flat kernel of half-width box_r (w = passes * box_r)
@@ -81,7 +82,8 @@ bf_status check_opts(const bf_gp_opts *o)
     if (o->fir_two_pass < 0 || o->fir_two_pass > 1) return BF_ERR_INVALID_ARG;
     if (o->box_passes < 0 || o->box_passes > 3) return BF_ERR_INVALID_ARG;
     if (o->tc5_wait_test < 0) return BF_ERR_INVALID_ARG;
-    for (int i = 0; i < 4; ++i)
+    if (o->row_threads != 0 && o->row_threads != 256 && o->row_threads != 512) return BF_ERR_INVALID_ARG;
+    for (int i = 0; i < 3; ++i)
         if (o->reserved[i] != 0) return BF_ERR_INVALID_ARG;
     return BF_OK;
 }
@@ -126,6 +128,7 @@ bf_status make_plan(int planes, int H, int W, float sigma_s, const bf_gp_opts *o
     p->engine_auto = o->engine == 0 ? 1 : 0;
     p->col_tc = joint ? 0 : (o->engine == 2 ? 1 : (o->engine == 3 ? 2 : 0));
     p->wpr = next_pow2((W + 511) / 512);
+    p->row_block = o->row_threads;
     if (sp == BF_SPATIAL_IIR && p->row_tc && p->wpr > 16) return BF_ERR_UNSUPPORTED;
     // columns longer than 8192 (CUDA-core column pass) or 4096 (tensor-core column passes)
     if (sp == BF_SPATIAL_IIR && p->CL > (p->col_tc ? COL_MAX_CLUSTER_TC : COL_MAX_CTAS)) return BF_ERR_UNSUPPORTED;
@@ -244,10 +247,11 @@ void fir_coefs(double sigma, int w, FIRCoef *g)
 // ---------------------------------------------------------------- launches
 
 template <int WH, int MODE>
-bf_status launch_row_fir_w(const RowArgs &ra, const FIRCoef &g, int planes, cudaStream_t s)
+bf_status launch_row_fir_w(const RowArgs &ra, const FIRCoef &g, int planes, cudaStream_t s, int row_block)
 {
     const int T = ra.T;
-    const int block = T > 256 ? T : 256;
+    const int want = row_block ? row_block : 256;
+    const int block = T > want ? T : want;
     const int rows_per_cta = block / T;
     const size_t smem = sizeof(float) * 2 * rows_per_cta * (size_t)(T * ROW_C + 2 * WH);
     BF_CUDA(cudaFuncSetAttribute(row_fir<ROW_C, WH, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -379,7 +383,8 @@ bf_status run_rows(const Call &c, int planes, float sigma_s)
 {
     if (c.p.spatial == BF_SPATIAL_BOX) return BF_ERR_UNSUPPORTED;  // the box variant runs fused only
     const int T = c.ra.T;
-    const int block = T > 256 ? T : 256;
+    const int want = c.p.row_block ? c.p.row_block : 256;  // threads per CTA asked for
+    const int block = T > want ? T : want;
     const int rows_per_cta = block / T;
     if (c.p.spatial == BF_SPATIAL_FIR) {
         FIRCoef g;
@@ -387,7 +392,7 @@ bf_status run_rows(const Call &c, int planes, float sigma_s)
         bf_status st = BF_ERR_UNSUPPORTED;
         switch (c.p.w) {
 #define BF_CASE(WW) \
-    case WW: st = launch_row_fir_w<WW, MODE>(c.ra, g, planes, c.s); break;
+    case WW: st = launch_row_fir_w<WW, MODE>(c.ra, g, planes, c.s, c.p.row_block); break;
             BF_CASE(1) BF_CASE(2) BF_CASE(3) BF_CASE(4) BF_CASE(5) BF_CASE(6)
             BF_CASE(7) BF_CASE(8) BF_CASE(9) BF_CASE(10) BF_CASE(11) BF_CASE(12)
 #undef BF_CASE
@@ -402,7 +407,7 @@ bf_status run_rows(const Call &c, int planes, float sigma_s)
         tc_mats((double)sigma_s, &tm);
         RowArgs ra = c.ra;
         ra.T = c.p.wpr;  // warps per row
-        const int tblock = 32 * c.p.wpr > 256 ? 32 * c.p.wpr : 256;
+        const int tblock = 32 * c.p.wpr > want ? 32 * c.p.wpr : want;
         const int trows = (tblock / 32) / c.p.wpr;
         dim3 grid((c.ra.H + trows - 1) / trows, planes);
         if constexpr (MODE != MODE_JOINT) row_tc<MODE><<<grid, tblock, 0, c.s>>>(ra, cr, tm);
@@ -984,7 +989,8 @@ struct bf_gp_plan {
     // off_planes + sub_off[i]), spread over the plan's streams
     std::vector<bf_gp_plane> specs;
     bf_gp_opts base;
-    std::vector<int> engine;  // per plane: base.engine, or the autotuner's choice (bf_gp_batched_plan_tune)
+    std::vector<int> engine;       // per plane: base.engine, or the autotuner's choice (bf_gp_batched_plan_tune)
+    std::vector<int> row_threads;  // per plane: base.row_threads, or the autotuner's choice
     std::vector<size_t> sub_off, sub_bytes;
     size_t off_statusofs = 0;  // in the tables: byte offset of every plane's status word, n x uint64
     int nstreams = 0;
@@ -1064,6 +1070,7 @@ bf_status bf_gp_batched_plan_create(const bf_gp_plane *planes, int n, const bf_g
     pl->specs.assign(planes, planes + n);
     pl->base = *opts;
     pl->engine.assign(n, opts->engine);
+    pl->row_threads.assign(n, opts->row_threads);
     pl->sub_off = pl->plane_off;
     pl->sub_bytes.resize(n);
     for (int i = 0; i < n; ++i)
@@ -1234,6 +1241,7 @@ bf_status bf_gp_batched(const bf_gp_plan *plan, void *ws, size_t ws_bytes, void 
         o.order = q.order;
         o.spatial = BF_SPATIAL_IIR;
         o.engine = plan->engine[i];
+        o.row_threads = plan->row_threads[i];
         cudaStream_t si = plan->streams[i % plan->nstreams];
         Call c;
         st = prepare(q.f, q.y, 1, q.H, q.W, q.pitch, q.sigma_s, q.sigma_r, &o, wsb + plan->off_planes + plan->sub_off[i],
@@ -1307,21 +1315,29 @@ bf_status bf_gp_autotune(const float *f, float *y, int planes, int H, int W, int
         if (it != g_tune.end()) {
             opts->engine = it->second.engine;
             opts->fir_two_pass = it->second.fir_two_pass;
+            opts->row_threads = it->second.row_threads;
             return BF_OK;
         }
     }
-    // candidates, in the order their times are reported
+    // candidates, in the order their times are reported: the recursive filter's engines, each with
+    // 256- and 512-thread row-pass CTAs; the window sum fused, or two-pass with either row-pass CTA
     bf_gp_opts cand[BF_GP_TUNE_CANDIDATES];
     int nc = 0;
     if (p.spatial == BF_SPATIAL_IIR) {
-        for (int e = 0; e < 4; ++e) {
-            cand[nc] = *opts;
-            cand[nc++].engine = e;
-        }
+        for (int e = 0; e < 4; ++e)
+            for (int rt = 256; rt <= 512; rt += 256) {
+                cand[nc] = *opts;
+                cand[nc].engine = e;
+                cand[nc++].row_threads = rt;
+            }
     } else if (p.spatial == BF_SPATIAL_FIR) {
-        for (int t = 0; t < 2; ++t) {
+        cand[nc] = *opts;
+        cand[nc].fir_two_pass = 0;
+        cand[nc++].row_threads = 0;
+        for (int rt = 256; rt <= 512; rt += 256) {
             cand[nc] = *opts;
-            cand[nc++].fir_two_pass = t;
+            cand[nc].fir_two_pass = 1;
+            cand[nc++].row_threads = rt;
         }
     } else {
         cand[nc++] = *opts;
@@ -1358,6 +1374,7 @@ bf_status bf_gp_autotune(const float *f, float *y, int planes, int H, int W, int
     if (best < 0) return BF_ERR_UNSUPPORTED;
     opts->engine = cand[best].engine;
     opts->fir_two_pass = cand[best].fir_two_pass;
+    opts->row_threads = cand[best].row_threads;
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     g_tune[key] = *opts;
     return BF_OK;
@@ -1384,6 +1401,7 @@ bf_status bf_gp_batched_plan_tune(bf_gp_plan *plan, void *ws, size_t ws_bytes, v
                                       nullptr);
         if (st != BF_OK) return st;
         plan->engine[i] = o.engine;
+        plan->row_threads[i] = o.row_threads;
     }
     return BF_OK;
 }

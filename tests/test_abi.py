@@ -67,7 +67,7 @@ def test_bad_options_rejected():
         with pytest.raises(bfgp.BFError):
             bfgp.bf_gp_workspace_size(1, 32, 32, 2.0, o)
     o = bfgp.make_opts()
-    o.reserved[3] = 1
+    o.reserved[2] = 1
     with pytest.raises(bfgp.BFError):
         bfgp.bf_gp_workspace_size(1, 32, 32, 2.0, o)
 

@@ -45,12 +45,13 @@ def test_autotune_recursive_times_every_engine_and_stores_the_fastest(bf):
     s = torch.cuda.current_stream().cuda_stream
     bf.bf_gp_autotune_clear()
     o, ms = bf.bf_gp_autotune(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, sr, o, ws.data_ptr(), need, s, reps=3)
-    assert all(t > 0 for t in ms), ms
-    assert o.engine == int(np.argmin(ms))
-    # the stored choice: nothing timed, same engine
+    assert all(t > 0 for t in ms), ms  # engines 0..3, each with 256- and 512-thread row-pass CTAs
+    best = int(np.argmin(ms))
+    assert o.engine == best // 2 and o.row_threads == (256, 512)[best % 2]
+    # the stored choice: nothing timed, same engine and row-pass CTA
     o2 = bf.make_opts(20, "iir", engine=0)
     o2, ms2 = bf.bf_gp_autotune(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, sr, o2, ws.data_ptr(), need, s)
-    assert ms2 == [-1.0] * 4 and o2.engine == o.engine
+    assert ms2 == [-1.0] * 8 and o2.engine == o.engine and o2.row_threads == o.row_threads
     # the tuned filter still agrees with the oracle
     y.fill_(float("nan"))
     bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, sr, o, ws.data_ptr(), need, s)
@@ -71,8 +72,9 @@ def test_autotune_fir_chooses_between_fused_and_two_pass(bf):
     s = torch.cuda.current_stream().cuda_stream
     bf.bf_gp_autotune_clear()
     o, ms = bf.bf_gp_autotune(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, sr, o, ws.data_ptr(), need, s, reps=3)
-    assert ms[0] > 0 and ms[1] > 0 and ms[2] == -1.0 and ms[3] == -1.0
-    assert o.fir_two_pass == int(np.argmin(ms[:2]))
+    assert all(t > 0 for t in ms[:3]) and ms[3:] == [-1.0] * 5  # fused; two-pass with 256 / 512 row threads
+    best = int(np.argmin(ms[:3]))
+    assert o.fir_two_pass == (best > 0) and o.row_threads == (0, 256, 512)[best]
     bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, sr, o, ws.data_ptr(), need, s)
     ref, kap = oracle.gp_bf(img.astype(np.float64), ss, sr, 20, "fir", t_c=parity.gpu_centre(bf, ws.data_ptr(), 0, s),
                             return_kappa=True)
@@ -113,3 +115,24 @@ def test_batched_plan_tune_gives_the_single_image_bytes_per_plane(bf):
                          torch.cuda.current_stream().cuda_stream)
         torch.cuda.synchronize()
         assert torch.equal(y, y1)
+
+
+@pytest.mark.parametrize("spatial,engine,ss", [("iir", 0, 6.0), ("iir", 1, 6.0), ("iir", 2, 6.0), ("fir", 0, 2.0)])
+def test_row_threads_change_nothing_but_the_launch(bf, spatial, engine, ss):
+    """The row pass's CTA size (one knob the autotuner turns) regroups rows into CTAs;
+    every row is filtered the same way, so the result is the same bit for bit."""
+    H, W = 301, 700
+    img = synthetic.make_image(H, W, 8, 10.0, 20.0, synthetic.seed_for(11, 77))
+    x = torch.from_numpy(img).cuda()
+    s = torch.cuda.current_stream().cuda_stream
+    outs = []
+    for rt in (0, 256, 512):
+        o = bf.make_opts(20, spatial, engine=engine, fir_two_pass=True, row_threads=rt)
+        need = bf.bf_gp_workspace_size(1, H, W, ss, o)
+        ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+        y = torch.full_like(x, float("nan"))
+        bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, 30.0, o, ws.data_ptr(), need, s)
+        outs.append(y.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    with pytest.raises(bf.BFError):
+        bf.bf_gp_workspace_size(1, H, W, ss, bf.make_opts(20, spatial, row_threads=384))
