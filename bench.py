@@ -592,6 +592,14 @@ def run_extra(args, rank, world, local):
             g.replay()
         ms, clocks = _clock_wrap(local, lambda: timed(g.replay, steps))
         status = bfilt.status()
+        # the same batch as one persistent launch (engine 0 for every plane), captured and replayed
+        gp = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gp):
+            bfilt.run_persistent()
+        for _ in range(2):
+            gp.replay()
+        ms_pers = timed(gp.replay, max(1, min(args.steps, 20)))
+        status_pers = bfilt.status()
         # plain form: the single-image path plane by plane (same kernels, 4 launches per plane)
         popts = [bf.make_opts(o, "iir", engine=e) for (x, y, ss, sr, o), e in zip(planes, engines)]
         maxws = max(bf.bf_gp_workspace_size(1, p[0].shape[0], p[0].shape[1], p[2], po) for p, po in zip(planes, popts))
@@ -613,6 +621,11 @@ def run_extra(args, rank, world, local):
                            "engine_choice": "bf_gp_batched_plan_tune (per plane, before the timed region)"},
                 "plain_loop": {"value": px / (ms_plain / 1e3) / 1e6, "unit": "Mpixel/s", "ms_per_step": ms_plain,
                                "how": "bf_gp_forward plane by plane, same kernels and engines, no graph"},
+                "persistent": {"value": px / (ms_pers / 1e3) / 1e6, "unit": "Mpixel/s", "ms_per_step": ms_pers,
+                               "device_status": status_pers,
+                               "how": "CUDA graph of bf_gp_batched_persistent: one launch of resident 4-CTA clusters "
+                                      "taking statistics, row and column items from a counter (engine 0 kernels' "
+                                      "arithmetic for every plane), replayed"},
                 "step_roofline": {"bound": "hbm", "algorithmic_bytes_per_step": bytes_step,
                                   "achieved": bytes_step / (ms / 1e3) / 1e9, "peak": peak,
                                   "frac": bytes_step / (ms / 1e3) / 1e9 / peak, "peak_kind": peak_kind},

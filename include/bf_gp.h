@@ -372,6 +372,40 @@ bf_status bf_gp_batched_plan_tune(bf_gp_plan *plan, void *ws, size_t ws_bytes, v
 bf_status bf_gp_batched_plan_engines(const bf_gp_plan *plan, int *engines);
 
 /*
+ * Batched filtering in one persistent launch.  The same per-plane forward as
+ * bf_gp_batched with engine 0 (tensor-core row pass, CUDA-core column pass,
+ * the recursive Gaussian of Sec. 3 applied along rows then columns, Algorithm
+ * 1), run by one launch of resident thread-block clusters that take work
+ * items from a counter in ws: every plane's statistics partials, then its
+ * centre and scale, its row groups, its column strips, in that order.  An
+ * item that needs an earlier one (the row pass needs the plane's centre, the
+ * column pass all of its rows) waits on that plane's readiness counter in ws
+ * for at most a bounded number of clock cycles; a wait that gives up sets
+ * BF_DEV_TIMEOUT in the plane's status word, counts one in its counter 3 and
+ * skips the item (its output is then not written), so the launch always
+ * ends.  Each plane's status word and counters are then gathered into ws's,
+ * as bf_gp_batched does.
+ *
+ *   bf_gp_batched_persistent: enqueues a zeroing of the counters, the
+ *     persistent launch and the gather on `stream`; no host synchronisation,
+ *     graph-capturable.  ws must be the workspace the plan was uploaded to
+ *     (bf_gp_batched_plan_upload), at least bf_gp_batched_plan_workspace
+ *     bytes (BF_ERR_WORKSPACE otherwise).  BF_ERR_UNSUPPORTED when a plane
+ *     has rows of more than 4096 samples or more than 4096 rows (the one
+ *     launch's CTA and cluster shapes), or when no cluster fits on the device.
+ *     The per-plane results equal bf_gp_batched's with engine 0 bit for bit
+ *     (same kernels' arithmetic in the same order).  Calls on one plan must
+ *     not overlap, nor overlap bf_gp_batched on the same workspace.
+ *   bf_gp_batched_plan_set_wait: the wait budget of one readiness wait in SM
+ *     clock cycles (>= 1; the plan starts with 2^32, about two seconds), and,
+ *     for testing the timeout, a plane (0..n-1; -1 for none) whose column
+ *     items wait for one row group more than the plane has, so that they give
+ *     up.  BF_ERR_INVALID_ARG for a budget < 1 or a plane out of range.
+ */
+bf_status bf_gp_batched_persistent(const bf_gp_plan *plan, void *ws, size_t ws_bytes, void *stream);
+bf_status bf_gp_batched_plan_set_wait(bf_gp_plan *plan, long long wait_cycles, int starve_plane);
+
+/*
  * Read the device status word written by the last call that used `ws`
  * (BF_DEV_* bits).  Synchronises `stream` first.
  */

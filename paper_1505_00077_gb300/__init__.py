@@ -118,6 +118,8 @@ def _load():
         "bf_gp_autotune_clear": (None, []),
         "bf_gp_batched_plan_tune": (c_int, [c_void_p, c_void_p, c_size_t, c_void_p, c_int]),
         "bf_gp_batched_plan_engines": (c_int, [c_void_p, P(c_int)]),
+        "bf_gp_batched_persistent": (c_int, [c_void_p, c_void_p, c_size_t, c_void_p]),
+        "bf_gp_batched_plan_set_wait": (c_int, [c_void_p, ctypes.c_longlong, c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -137,7 +139,8 @@ def exported_symbols():
             "bf_gp_host_workspace_size", "bf_gp_forward_host",
             "bf_gp_get_device_status", "bf_gp_get_device_counters", "bf_gp_get_plane_stats", "bf_gp_order_for_tol", "bf_gp_order_fp32_limit",
             "bf_gp_joint_workspace_size", "bf_gp_forward_joint", "bf_gp_autotune", "bf_gp_autotune_clear",
-            "bf_gp_batched_plan_tune", "bf_gp_batched_plan_engines"]
+            "bf_gp_batched_plan_tune", "bf_gp_batched_plan_engines", "bf_gp_batched_persistent",
+            "bf_gp_batched_plan_set_wait"]
 
 
 def status_string(status: int) -> str:
@@ -265,6 +268,17 @@ def bf_gp_batched(plan, ws_ptr, ws_bytes, stream=0) -> None:
     _check(_load().bf_gp_batched(_vp(plan), _vp(ws_ptr), int(ws_bytes), _vp(stream)), "bf_gp_batched")
 
 
+def bf_gp_batched_persistent(plan, ws_ptr, ws_bytes, stream=0) -> None:
+    """The whole batched forward as one persistent launch (see include/bf_gp.h)."""
+    _check(_load().bf_gp_batched_persistent(_vp(plan), _vp(ws_ptr), int(ws_bytes), _vp(stream)),
+           "bf_gp_batched_persistent")
+
+
+def bf_gp_batched_plan_set_wait(plan, wait_cycles, starve_plane=-1) -> None:
+    _check(_load().bf_gp_batched_plan_set_wait(_vp(plan), int(wait_cycles), int(starve_plane)),
+           "bf_gp_batched_plan_set_wait")
+
+
 BF_GP_TUNE_CANDIDATES = 8
 
 
@@ -383,6 +397,12 @@ class BatchedFilter:
         import torch
         s = torch.cuda.current_stream().cuda_stream if stream is None else stream
         bf_gp_batched(self.plan, self.ws.data_ptr(), self.ws_bytes, s)
+
+    def run_persistent(self, stream=None):
+        """The same forward (engine 0) as one persistent launch."""
+        import torch
+        s = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        bf_gp_batched_persistent(self.plan, self.ws.data_ptr(), self.ws_bytes, s)
 
     def status(self):
         import torch

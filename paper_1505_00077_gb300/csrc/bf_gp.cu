@@ -993,6 +993,19 @@ struct bf_gp_plan {
     std::vector<int> row_threads;  // per plane: base.row_threads, or the autotuner's choice
     std::vector<size_t> sub_off, sub_bytes;
     size_t off_statusofs = 0;  // in the tables: byte offset of every plane's status word, n x uint64
+    // persistent launch (bf_gp_batched_persistent): per-plane descriptors and coefficients, the work
+    // items in dependency order, the work and readiness counters; tables at off_ptables in ws
+    std::vector<PersistPlane> ppl;
+    std::vector<IIRCoef> pcrow, pccol;
+    std::vector<TCMat> ptm;
+    std::vector<int4> pitems;  // in the order of the launch (set at upload, when the grid is known)
+    std::vector<int4> pstats, pfinal, prows, pcols;  // per kind, plane by plane
+    int pcl = 1;               // cluster size of the persistent launch
+    bool persist_ok = false;   // every plane within its kernels' limits (rows of at most 4096 samples)
+    size_t off_ptables = 0, ptables_bytes = 0, off_pitems = 0, off_pcount = 0;
+    long long wait_cycles = 1ll << 32;  // about two seconds at 2 GHz
+    int starve_plane = -1;
+    int pclusters = 0;         // clusters resident at once (found at upload; 0: none fits)
     int nstreams = 0;
     cudaStream_t streams[BATCH_STREAMS] = {};
     cudaEvent_t ev_fork = nullptr, ev_join[BATCH_STREAMS] = {};
@@ -1005,6 +1018,218 @@ struct bf_gp_plan {
         if (ev_fork) cudaEventDestroy(ev_fork);
     }
 };
+
+extern "C" {
+
+}  // extern "C"
+
+namespace {
+
+// The persistent launch's tables: each plane's descriptor (offsets into its single-image
+// workspace), its coefficients, and the work items: every plane's statistics partials (one
+// per CTA, pcl per item), then its finalisation, its row groups (pcl per item), its column
+// strips (pcl / G per item, G CTAs per strip).  Planes whose rows exceed 4096 samples are
+// outside the row pass's 256-thread CTAs: the plan then has no persistent form.
+bf_status build_persistent(bf_gp_plan *pl, const bf_gp_plane *planes, const bf_gp_opts *opts)
+{
+    const int n = pl->n;
+    pl->persist_ok = true;
+    int clmax = 1;
+    for (int i = 0; i < n; ++i) {
+        if (planes[i].W > 4096) pl->persist_ok = false;
+        clmax = std::max(clmax, (planes[i].H + COL_ROWS_PER_CTA - 1) / COL_ROWS_PER_CTA);
+    }
+    if (clmax > 8) pl->persist_ok = false;
+    if (!pl->persist_ok) return BF_OK;
+    pl->pcl = next_pow2(clmax);
+    pl->ppl.resize(n);
+    pl->pcrow.resize(n);
+    pl->pccol.resize(n);
+    pl->ptm.resize(n);
+    std::vector<int4> stats, fin, rows, cols;
+    for (int i = 0; i < n; ++i) {
+        const bf_gp_plane &q = planes[i];
+        bf_gp_opts o = *opts;
+        o.order = q.order;
+        o.spatial = BF_SPATIAL_IIR;
+        o.engine = 0;
+        o.row_threads = 0;
+        Plan pp;
+        bf_status st = make_plan(1, q.H, q.W, q.sigma_s, &o, &pp);
+        if (st != BF_OK) return st;
+        PersistPlane &d = pl->ppl[i];
+        std::memset(&d, 0, sizeof d);
+        d.f = q.f;
+        d.y = q.y;
+        d.off_params = (long long)pp.off_params;
+        d.off_part = (long long)pp.off_part;
+        d.off_planes = (long long)pp.off_planes;
+        d.H = q.H;
+        d.W = q.W;
+        d.pitch = q.pitch;
+        d.Wp = pp.Wp;
+        d.K = pp.K;
+        d.N = pp.N;
+        d.wpr = pp.wpr;
+        d.nblk = pp.nblk;
+        d.rows_per_block = pp.rows_per_block;
+        const int rows_per_cta = 8 / pp.wpr;  // 256 threads: 8 warps, wpr per row
+        d.rowgroups = (q.H + rows_per_cta - 1) / rows_per_cta;
+        d.strips = (q.W + 7) / 8;
+        d.G = next_pow2(pp.CL);
+        // per item, a CTA takes about 32K pixels of statistics and 16K pixels of rows
+        const long long blk_px = (long long)pp.rows_per_block * q.W, grp_px = (long long)rows_per_cta * q.W;
+        d.stat_m = (int)std::min<long long>(64, std::max<long long>(1, (32768 + blk_px - 1) / blk_px));
+        d.row_m = (int)std::min<long long>(16, std::max<long long>(1, (16384 + grp_px - 1) / grp_px));
+        d.sigma_s = q.sigma_s;
+        d.sigma_r = q.sigma_r;
+        deriche_coefs((double)q.sigma_s, TC_C, &pl->pcrow[i]);
+        deriche_coefs((double)q.sigma_s, COL_C, &pl->pccol[i]);
+        tc_mats((double)q.sigma_s, &pl->ptm[i]);
+        const int c = pl->pcl;
+        const int su = c * d.stat_m, ru = c * d.row_m;  // units per item
+        for (int u = 0; u < d.nblk; u += su) stats.push_back(make_int4(PITEM_STATS, i, u, std::min(su, d.nblk - u)));
+        fin.push_back(make_int4(PITEM_FINAL, i, 0, 1));
+        for (int u = 0; u < d.rowgroups; u += ru)
+            rows.push_back(make_int4(PITEM_ROWS, i, u, std::min(ru, d.rowgroups - u)));
+        const int per = c / d.G;  // strips per column item
+        for (int u = 0; u < d.strips; u += per) cols.push_back(make_int4(PITEM_COLS, i, u, std::min(per, d.strips - u)));
+    }
+    pl->pstats = stats;
+    pl->pfinal = fin;
+    pl->prows = rows;
+    pl->pcols = cols;
+    pl->pitems.resize(stats.size() + fin.size() + rows.size() + cols.size());
+    size_t o = 0;
+    o += sizeof(PersistPlane) * n;
+    o = align_up(o, 16) + sizeof(IIRCoef) * n;
+    o = align_up(o, 16) + sizeof(IIRCoef) * n;
+    o = align_up(o, 16) + sizeof(TCMat) * n;
+    pl->off_pitems = align_up(o, 16);
+    o = pl->off_pitems + sizeof(int4) * pl->pitems.size();
+    pl->off_pcount = align_up(o, 16);
+    pl->ptables_bytes = pl->off_pcount + sizeof(int) * (1 + 3 * (size_t)n);
+    pl->off_ptables = align_up(pl->total, 256);
+    pl->total = pl->off_ptables + pl->ptables_bytes;
+    return BF_OK;
+}
+
+// The persistent launch's shape: one cluster of pcl CTAs of 256 threads (the grid is set by the caller).
+void persist_config(const bf_gp_plan *pl, cudaStream_t s, cudaLaunchConfig_t *cfg, cudaLaunchAttribute *attr)
+{
+    std::memset(cfg, 0, sizeof *cfg);
+    cfg->blockDim = dim3(256, 1, 1);
+    cfg->gridDim = dim3((unsigned)pl->pcl, 1, 1);
+    cfg->dynamicSmemBytes = sizeof(float) * COL_TILE_BUFS * COL_TILE_FLOATS;
+    cfg->stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)pl->pcl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg->attrs = attr;
+    cfg->numAttrs = 1;
+}
+
+// Copies the persistent tables (with this workspace's plane addresses) into ws, waits, and
+// finds how many clusters are resident at once.
+// The launch's item order: all statistics partials, all centres and scales, then the row items
+// plane after plane, each plane's column items following once `lag` row items have come after its
+// last one (or at the end).  Every item comes after the items it waits for.
+void order_items(bf_gp_plan *pl, int lag)
+{
+    std::vector<int4> &o = pl->pitems;
+    o.clear();
+    o.insert(o.end(), pl->pstats.begin(), pl->pstats.end());
+    o.insert(o.end(), pl->pfinal.begin(), pl->pfinal.end());
+    size_t r = 0, c = 0;
+    std::vector<std::pair<int, long long>> pending;  // (plane, row items placed when its rows ended)
+    long long placed = 0;
+    auto flush = [&](bool all) {
+        while (!pending.empty() && (all || placed - pending.front().second >= lag)) {
+            const int p = pending.front().first;
+            while (c < pl->pcols.size() && pl->pcols[c].y == p) o.push_back(pl->pcols[c++]);
+            pending.erase(pending.begin());
+        }
+    };
+    while (r < pl->prows.size()) {
+        const int p = pl->prows[r].y;
+        while (r < pl->prows.size() && pl->prows[r].y == p) {
+            o.push_back(pl->prows[r++]);
+            ++placed;
+            flush(false);
+        }
+        pending.emplace_back(p, placed);
+    }
+    flush(true);
+}
+
+bf_status upload_persistent(bf_gp_plan *pl, char *wsb, cudaStream_t s)
+{
+    if (!pl->persist_ok) return BF_OK;
+    const int n = pl->n;
+    std::vector<char> img(pl->off_pcount, 0);
+    std::vector<PersistPlane> d = pl->ppl;
+    for (int i = 0; i < n; ++i) d[i].ws = wsb + pl->off_planes + pl->sub_off[i];
+    size_t o = 0;
+    std::memcpy(img.data() + o, d.data(), sizeof(PersistPlane) * n);
+    o += sizeof(PersistPlane) * n;
+    o = align_up(o, 16);
+    std::memcpy(img.data() + o, pl->pcrow.data(), sizeof(IIRCoef) * n);
+    o += sizeof(IIRCoef) * n;
+    o = align_up(o, 16);
+    std::memcpy(img.data() + o, pl->pccol.data(), sizeof(IIRCoef) * n);
+    o += sizeof(IIRCoef) * n;
+    o = align_up(o, 16);
+    std::memcpy(img.data() + o, pl->ptm.data(), sizeof(TCMat) * n);
+    o += sizeof(TCMat) * n;
+    BF_CUDA(cudaMemcpyAsync(wsb + pl->off_ptables, img.data(), img.size(), cudaMemcpyHostToDevice, s));
+    BF_CUDA(cudaStreamSynchronize(s));
+    // how many clusters of the launch's shape are resident at once on this device
+    const size_t smem = sizeof(float) * COL_TILE_BUFS * COL_TILE_FLOATS;
+    BF_CUDA(cudaFuncSetAttribute(batched_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    persist_config(pl, s, &cfg, attr);
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, batched_persistent, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        nclusters = 0;
+    }
+    pl->pclusters = nclusters;
+    // column items two rounds of the grid after their plane's last row item
+    order_items(pl, 2ll * std::max(1, nclusters));
+    BF_CUDA(cudaMemcpyAsync(wsb + pl->off_ptables + pl->off_pitems, pl->pitems.data(),
+                            sizeof(int4) * pl->pitems.size(), cudaMemcpyHostToDevice, s));
+    BF_CUDA(cudaStreamSynchronize(s));
+    return BF_OK;
+}
+
+PersistArgs persist_args(const bf_gp_plan *pl, char *wsb)
+{
+    const int n = pl->n;
+    char *tb = wsb + pl->off_ptables;
+    PersistArgs a;
+    std::memset(&a, 0, sizeof a);
+    size_t o = 0;
+    a.pl = reinterpret_cast<const PersistPlane *>(tb + o);
+    o = align_up(o + sizeof(PersistPlane) * n, 16);
+    a.crow = reinterpret_cast<const IIRCoef *>(tb + o);
+    o = align_up(o + sizeof(IIRCoef) * n, 16);
+    a.ccol = reinterpret_cast<const IIRCoef *>(tb + o);
+    o = align_up(o + sizeof(IIRCoef) * n, 16);
+    a.tm = reinterpret_cast<const TCMat *>(tb + o);
+    a.items = reinterpret_cast<const int4 *>(tb + pl->off_pitems);
+    a.work = reinterpret_cast<int *>(tb + pl->off_pcount);
+    a.ready = a.work + 1;
+    a.nitems = (int)pl->pitems.size();
+    a.centre_given = pl->centre_given;
+    a.tc_given = pl->tc_given;
+    a.wait_cycles = pl->wait_cycles;
+    a.starve_plane = pl->starve_plane;
+    return a;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -1106,6 +1331,11 @@ bf_status bf_gp_batched_plan_create(const bf_gp_plane *planes, int n, const bf_g
     off = align_up(off + pl->tables_bytes, 256);
     pl->off_planes = off;
     pl->total = off + planes_bytes;
+    st = build_persistent(pl, planes, opts);
+    if (st != BF_OK) {
+        delete pl;
+        return st;
+    }
     pl->nstreams = std::min(n, BATCH_STREAMS);
     bool ok = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming) == cudaSuccess;
     for (int i = 0; ok && i < pl->nstreams; ++i)
@@ -1187,6 +1417,7 @@ bf_status bf_gp_batched_plan_upload(bf_gp_plan *plan, void *ws, size_t ws_bytes,
     if (!plan || !ws) return BF_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < plan->total) return BF_ERR_WORKSPACE;
     bf_status st = upload_tables(plan, static_cast<char *>(ws), reinterpret_cast<cudaStream_t>(stream));
+    if (st == BF_OK) st = upload_persistent(plan, static_cast<char *>(ws), reinterpret_cast<cudaStream_t>(stream));
     if (st != BF_OK) return st;
     plan->uploaded_ws = ws;
     return BF_OK;
@@ -1260,6 +1491,38 @@ bf_status bf_gp_batched(const bf_gp_plan *plan, void *ws, size_t ws_bytes, void 
         reinterpret_cast<const unsigned long long *>(wsb + plan->off_tables + plan->off_statusofs);
     gather_status<<<1, 256, 0, s>>>(reinterpret_cast<uint32_t *>(wsb), wsb, ofs, n);
     BF_CUDA(cudaGetLastError());
+    return BF_OK;
+}
+
+bf_status bf_gp_batched_persistent(const bf_gp_plan *plan, void *ws, size_t ws_bytes, void *stream)
+{
+    if (!plan || !ws) return BF_ERR_INVALID_ARG;
+    if (ws != plan->uploaded_ws || ws_bytes < plan->total) return BF_ERR_WORKSPACE;
+    if (!plan->persist_ok) return BF_ERR_UNSUPPORTED;
+    char *wsb = static_cast<char *>(ws);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    PersistArgs a = persist_args(plan, wsb);
+    if (plan->pclusters < 1) return BF_ERR_UNSUPPORTED;
+    const unsigned long long *ofs =
+        reinterpret_cast<const unsigned long long *>(wsb + plan->off_tables + plan->off_statusofs);
+    // the work counter, every plane's readiness counters, status word and counters start at zero
+    BF_CUDA(cudaMemsetAsync(a.work, 0, sizeof(int) * (1 + 3 * (size_t)plan->n), s));
+    zero_plane_status<<<(plan->n + 255) / 256, 256, 0, s>>>(wsb, ofs, plan->n);
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    persist_config(plan, s, &cfg, attr);
+    cfg.gridDim = dim3((unsigned)(plan->pclusters * plan->pcl), 1, 1);  // the clusters resident at once
+    BF_CUDA(cudaLaunchKernelEx(&cfg, batched_persistent, a));
+    gather_status<<<1, 256, 0, s>>>(reinterpret_cast<uint32_t *>(wsb), wsb, ofs, plan->n);
+    BF_CUDA(cudaGetLastError());
+    return BF_OK;
+}
+
+bf_status bf_gp_batched_plan_set_wait(bf_gp_plan *plan, long long wait_cycles, int starve_plane)
+{
+    if (!plan || wait_cycles < 1 || starve_plane < -1 || starve_plane >= plan->n) return BF_ERR_INVALID_ARG;
+    plan->wait_cycles = wait_cycles;
+    plan->starve_plane = starve_plane;
     return BF_OK;
 }
 

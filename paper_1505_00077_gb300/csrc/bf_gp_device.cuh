@@ -1296,8 +1296,18 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)_
 //      states, the out-of-half response and the Horner step.
 // grid (strips * CL, planes), block 256, cluster (CL, 1, 1), CL <= MAXCTA
 // (8: the portable cluster size; COL_MAX_CTAS: columns of up to 8192 rows).
+// The CTAs of a cluster that share one column strip: `size` CTAs from cluster
+// rank `base`, this CTA being the `rank`-th (a cluster may hold several groups,
+// each on its own strip: they meet at the cluster barriers, exchange nothing).
+// An inactive group has no strip: it loads and writes nothing but still meets
+// every barrier.
+struct ColGroup {
+    int size, rank, base, active;
+};
+
 template <int C, int MODE, int MAXCTA = 8>
-__device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf, int strip, int plane)
+__device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf, int strip, int plane,
+                                             ColGroup grp = {0, 0, 0, 1})
 {
     static_assert(C == 16, "column chunks are two halves of 8 rows");
     extern __shared__ __align__(16) float tiles[];  // [COL_TILE_BUFS][COL_TILE_FLOATS]
@@ -1313,14 +1323,16 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
     const int lane = tid & 31, warp = tid >> 5;
     const int col = lane & 7, l4 = lane >> 3;
     cg::cluster_group cl = cg::this_cluster();
-    const int rank = (int)cl.block_rank();
-    const int CL = (int)cl.num_blocks();
+    // the whole cluster on one strip unless a group is given
+    const int rank = grp.size ? grp.rank : (int)cl.block_rank();
+    const int CL = grp.size ? grp.size : (int)cl.num_blocks();
+    const int gbase = grp.size ? grp.base : 0;
     const int x = strip * 8 + col;
     const int chunk_cta = warp * 4 + l4;
     const int rbase = rank * COL_ROWS;
     const int row0 = rbase + chunk_cta * C;
     const PlaneParams &P = a.pp[plane];
-    const bool filt = (P.mode == 0);
+    const bool filt = (P.mode == 0) && grp.active;
     const float *wsp = a.ws + (size_t)plane * a.K * a.H * a.Wp + strip * 8;
 
     // tile copy: 512 rows x two 16-byte halves; thread copies rows tid/2 + 128 i, i < 4
@@ -1464,7 +1476,7 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
             float2 *own = &inc[par][rank][gcol][gm][gdir];
             const int nd = gdir == 0 ? CL - 1 - rank : rank;
             for (int d = 1; d <= nd; ++d) {
-                *cl.map_shared_rank(own, gdir == 0 ? rank + d : rank - d) = make_float2(totr, toti);
+                *cl.map_shared_rank(own, gbase + (gdir == 0 ? rank + d : rank - d)) = make_float2(totr, toti);
                 float nr, ni;
                 cmul(nr, ni, p32r, p32i, totr, toti);
                 totr = nr;
@@ -1536,7 +1548,7 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
 #pragma unroll
     for (int j = 0; j < C; ++j) {
         const int r = row0 + j;
-        if (r < a.H && x < a.W) finish_pixel(a, P, plane, r, x, cb, j, nonpos, sums);
+        if (grp.active && r < a.H && x < a.W) finish_pixel(a, P, plane, r, x, cb, j, nonpos, sums);
     }
     if (MODE == MODE_ADJ) {
         flush_sums(a, plane, sums);
@@ -3005,6 +3017,215 @@ __global__ void __launch_bounds__(256) batched_stats_finalize(BatchArgs b)
     const BatchPlane &d = b.bp[p];
     stats_finalize_body(b.part + b.pre_stats[p], d.nblk, (long long)d.H * d.W, b.centre_given, b.tc_given,
                         d.sigma_r, d.sigma_s, d.K, 0, p, b.pp, b.status);
+}
+
+// ------------------------------------------------------------------ persistent batched
+
+constexpr int COL_C_PERSIST = 16;  // the column pass's chunk length
+
+// One plane of a persistent batched launch: its buffers, its single-image
+// workspace (status word, PlaneParams, statistics partials, channel planes at
+// the offsets a single-image call of the same size uses) and its work units.
+struct PersistPlane {
+    const float *f;
+    float *y;
+    char *ws;
+    long long off_params, off_part, off_planes;
+    int H, W, pitch, Wp, K, N, wpr;
+    int nblk, rows_per_block, rowgroups, strips;
+    int G;  // CTAs per column strip: the power of two >= ceil(H / 512), at most the cluster size
+    int stat_m, row_m;  // statistics partials / row groups one CTA takes per item
+    double sigma_s, sigma_r;
+};
+
+enum { PITEM_STATS = 0, PITEM_FINAL = 1, PITEM_ROWS = 2, PITEM_COLS = 3 };
+
+struct PersistArgs {
+    const PersistPlane *pl;
+    const IIRCoef *crow;  // per plane: chunk length 8 (tensor-core row pass)
+    const TCMat *tm;      // per plane
+    const IIRCoef *ccol;  // per plane: chunk length 16 (column pass)
+    const int4 *items;    // {kind, plane, first unit, units}, in dependency order
+    int *work;            // next item to take (zeroed before the launch)
+    int *ready;           // per plane: partials done, finalized, row groups done (zeroed before the launch)
+    int nitems, centre_given;
+    double tc_given;
+    long long wait_cycles;  // budget of one wait for a plane's readiness counter
+    int starve_plane;       // testing: this plane's column items wait for one row group more than exists
+    int pad;
+};
+
+__device__ __forceinline__ int load_acquire(const int *c)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];\n" : "=r"(v) : "l"(c) : "memory");
+    return v;
+}
+
+// Waits until *c >= target (acquire), at most `budget` clock cycles; false if it gave up.
+__device__ __forceinline__ bool wait_count(const int *c, int target, long long budget)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        const int v = load_acquire(c);
+        if (v >= target) return true;
+        if (clock64() - t0 > budget) return false;
+        __nanosleep(256);
+    }
+}
+
+// Counts n finished units of a plane: every thread's writes are done, then one release.
+__device__ __forceinline__ void count_done(int *c, int n)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(c, n);
+    }
+}
+
+// The whole batched forward in one launch of resident clusters.  Cluster rank 0
+// takes the next item from a counter and hands it to the cluster.  Every item
+// comes after the items it needs (all planes' statistics partials, then their
+// centres and scales, then the row groups of plane after plane, with each
+// plane's column strips placed a few rounds of row items after its last row
+// group, so that they find its channel planes still partly in L2), so an item
+// only waits for items taken before it, by clusters that are running.  Rank 0 waits for the item's
+// prerequisite (a per-plane readiness counter, bounded by wait_cycles) and the
+// whole cluster follows its decision; a wait that gives up raises
+// BF_DEV_TIMEOUT in the plane's status word and the item is skipped (its own
+// count still advances, so nothing waits on it in turn).  Statistics and row
+// items give stat_m / row_m consecutive units to each CTA; a column item gives
+// one strip to each group of G CTAs (the cluster size / G strips at once).  Each plane's coefficients
+// are staged in shared memory for its items.  Same kernels' arithmetic as the
+// single-image forward with engine 0 (tensor-core rows, CUDA-core columns).
+// grid (clusters * cluster size), block 256, cluster (size <= 8).
+__global__ void __launch_bounds__(256, 2) batched_persistent(PersistArgs a)
+{
+    __shared__ int s_item, s_go;
+    __shared__ IIRCoef s_cf;
+    __shared__ TCMat s_tm;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int CLn = (int)cl.num_blocks();
+    const int tid = threadIdx.x;
+    auto stage = [&](const void *src, void *dst, int bytes) {
+        const int *sp = static_cast<const int *>(src);
+        int *dp = static_cast<int *>(dst);
+        for (int i = tid; i < bytes / 4; i += blockDim.x) dp[i] = __ldg(sp + i);
+    };
+    for (;;) {
+        if (rank == 0 && tid == 0) s_item = atomicAdd(a.work, 1);
+        cl.sync();
+        const int it = *cl.map_shared_rank(&s_item, 0);
+        if (it >= a.nitems) {
+            cl.sync();  // rank 0 leaves only after every peer has read its s_item
+            break;
+        }
+        const int4 w = a.items[it];
+        const int p = w.y;
+        const PersistPlane &d = a.pl[p];
+        int *rdy = a.ready + 3 * p;
+        if (rank == 0 && tid == 0) {
+            bool go = true;
+            if (w.x == PITEM_FINAL) go = wait_count(rdy + 0, d.nblk, a.wait_cycles);
+            if (w.x == PITEM_ROWS) go = wait_count(rdy + 1, 1, a.wait_cycles);
+            if (w.x == PITEM_COLS) go = wait_count(rdy + 2, d.rowgroups + (p == a.starve_plane), a.wait_cycles);
+            s_go = go ? 1 : 0;
+            if (!go) {
+                uint32_t *status = reinterpret_cast<uint32_t *>(d.ws);
+                atomicOr(status, 0x8u);
+                atomicAdd(status_counters(status) + 3, 1ull);
+            }
+        }
+        cl.sync();
+        const bool go = *cl.map_shared_rank(&s_go, 0) != 0;
+        if (go && tid == 0 && w.x != PITEM_STATS) {
+            // this CTA's own acquire of the counter rank 0 saw reach its target
+            load_acquire(rdy + (w.x == PITEM_FINAL ? 0 : w.x == PITEM_ROWS ? 1 : 2));
+        }
+        uint32_t *status = reinterpret_cast<uint32_t *>(d.ws);
+        PlaneParams *pp = reinterpret_cast<PlaneParams *>(d.ws + d.off_params);
+        StatPartial *part = reinterpret_cast<StatPartial *>(d.ws + d.off_part);
+        float *planes = reinterpret_cast<float *>(d.ws + d.off_planes);
+        if (w.x == PITEM_STATS) {
+            // units w.z + rank m .. of the item's w.w, m = stat_m per CTA
+            const int u0 = rank * d.stat_m, u1 = min(w.w, u0 + d.stat_m);
+            if (u0 < u1) {
+                for (int j = u0; j < u1; ++j)
+                    stats_partial_body(d.f, d.H, d.W, d.pitch, d.rows_per_block, w.z + j, part + w.z + j);
+                count_done(rdy + 0, u1 - u0);
+            }
+        } else if (w.x == PITEM_FINAL) {
+            if (rank == 0) {
+                if (go)
+                    stats_finalize_body(part, d.nblk, (long long)d.H * d.W, a.centre_given, a.tc_given, d.sigma_r,
+                                        d.sigma_s, d.K, 0, 0, pp, status);
+                count_done(rdy + 1, 1);
+            }
+        } else if (w.x == PITEM_ROWS) {
+            const int u0 = rank * d.row_m, u1 = min(w.w, u0 + d.row_m);
+            if (u0 < u1) {
+                stage(a.crow + p, &s_cf, (int)sizeof(IIRCoef));
+                stage(a.tm + p, &s_tm, (int)sizeof(TCMat));
+                __syncthreads();
+                if (go) {
+                    RowArgs ra;
+                    ra.f = d.f;
+                    ra.gy = nullptr;
+                    ra.fd = nullptr;
+                    ra.saved = nullptr;
+                    ra.ws = planes;
+                    ra.pp = pp;
+                    ra.acc = nullptr;
+                    ra.H = d.H;
+                    ra.W = d.W;
+                    ra.pitch = d.pitch;
+                    ra.Wp = d.Wp;
+                    ra.K = d.K;
+                    ra.T = d.wpr;
+                    ra.N = d.N;
+                    for (int j = u0; j < u1; ++j) row_tc_body<MODE_FWD>(ra, s_cf, s_tm, w.z + j, 0);
+                }
+                count_done(rdy + 2, u1 - u0);
+            }
+        } else {  // PITEM_COLS: every CTA of the cluster, G per strip
+            stage(a.ccol + p, &s_cf, (int)sizeof(IIRCoef));
+            __syncthreads();
+            const int G = d.G, g = rank / G;
+            const int strip = w.z + g;
+            const bool active = go && g < w.w && strip < d.strips;
+            ColArgs ca;
+            ca.ws = planes;
+            ca.f = d.f;
+            ca.y = d.y;
+            ca.gy = nullptr;
+            ca.saved = nullptr;
+            ca.pp = pp;
+            ca.status = status;
+            ca.acc = nullptr;
+            ca.H = d.H;
+            ca.W = d.W;
+            ca.pitch = d.pitch;
+            ca.Wp = d.Wp;
+            ca.K = d.K;
+            ca.N = d.N;
+            ca.wait_limit = 0;
+            ca.no_mma = 0;
+            col_iir_body<COL_C_PERSIST, MODE_FWD, 8>(ca, s_cf, active ? strip : 0, 0, ColGroup{G, rank % G, g * G, active ? 1 : 0});
+        }
+        __syncthreads();  // the staged coefficients are read before the next item replaces them
+    }
+}
+
+// Zeroes every plane's status word and counters (before a persistent launch).
+__global__ void zero_plane_status(char *ws, const unsigned long long *ofs, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t *st = reinterpret_cast<uint32_t *>(ws + ofs[i]);
+        *st = 0u;
+        for (int q = 0; q < NCOUNTERS; ++q) status_counters(st)[q] = 0ull;
+    }
 }
 
 // ORs the status word of every plane's workspace into the batch's (the planes'

@@ -139,3 +139,113 @@ def test_adaptive_order_per_plane(bf):
     exact = oracle.direct_bf(f64[i], specs[i][2], specs[i][3])
     out = planes[i][1].cpu().numpy().astype(np.float64)
     assert np.mean((out - exact) ** 2) < np.mean((ref20 - exact) ** 2)
+
+
+def _persistent_shape(planes):
+    """Cluster size of the persistent launch and each plane's column items."""
+    def p2(v):
+        return 1 << max(0, (v - 1).bit_length())
+    pcl = p2(max((x.shape[0] + 511) // 512 for x, *_ in planes))
+    items = []
+    for x, *_ in planes:
+        G = p2((x.shape[0] + 511) // 512)
+        strips = (x.shape[1] + 7) // 8
+        per = pcl // G
+        items.append((strips + per - 1) // per)
+    return pcl, items
+
+
+def _forked_outputs(bfilt, planes):
+    for _, y, *_ in planes:
+        y.fill_(float("nan"))
+    bfilt.run()
+    torch.cuda.synchronize()
+    return [y.clone() for _, y, *_ in planes], bfilt.status(), bfilt.counters()
+
+
+@pytest.mark.parametrize("n_images,lo,hi,seed", [(10, 33, 700, 4), (6, 256, 2048, 8)])
+def test_persistent_matches_forked_path(bf, n_images, lo, hi, seed):
+    """One persistent launch over the whole batch (work items taken from a
+    counter, per-plane readiness counters) gives every plane the forked
+    path's result bit for bit, the same status and counters, also when
+    captured into a graph and replayed.  The second batch has sides up to
+    2048: column strips of 1, 2 and 4 CTAs share clusters of 4."""
+    batch = make_batch(n_images, lo, hi, seed)
+    planes = []
+    for img, ss, sr in batch:
+        for c in range(3):
+            x = torch.from_numpy(np.ascontiguousarray(img[c])).cuda()
+            planes.append((x, torch.empty_like(x), ss, sr, 20 if c != 1 else 12))
+    bfilt = bf.BatchedFilter(planes)
+    ref, st_ref, cnt_ref = _forked_outputs(bfilt, planes)
+    for _, y, *_ in planes:
+        y.fill_(float("nan"))
+    bfilt.run_persistent()
+    torch.cuda.synchronize()
+    assert bfilt.status() == st_ref
+    assert bfilt.counters() == cnt_ref
+    for i, (r, (_, y, *_)) in enumerate(zip(ref, planes)):
+        assert torch.equal(r, y), i
+    # captured and replayed
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            bfilt.run_persistent()
+    torch.cuda.current_stream().wait_stream(s)
+    for rep in range(2):
+        for _, y, *_ in planes:
+            y.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert bfilt.status() == st_ref
+        for i, (r, (_, y, *_)) in enumerate(zip(ref, planes)):
+            assert torch.equal(r, y), (rep, i)
+
+
+def test_persistent_wait_gives_up_on_a_starved_counter(bf):
+    """The host makes one plane's column items wait for a row group that does
+    not exist: each of them gives up after its budget, raises BF_DEV_TIMEOUT
+    and counts one wait in counter 3; the launch ends, the plane's output is
+    left as it was, every other plane is still filtered, and the next launch
+    with the normal budget is clean."""
+    batch = make_batch(5, 64, 1200, 12)
+    planes = []
+    for img, ss, sr in batch:
+        for c in range(3):
+            x = torch.from_numpy(np.ascontiguousarray(img[c])).cuda()
+            planes.append((x, torch.empty_like(x), ss, sr, 16))
+    bfilt = bf.BatchedFilter(planes)
+    ref, st_ref, cnt_ref = _forked_outputs(bfilt, planes)
+    _, items = _persistent_shape(planes)
+    starved = 4
+    bf.bf_gp_batched_plan_set_wait(bfilt.plan, 1 << 20, starved)  # about half a millisecond per wait
+    for _, y, *_ in planes:
+        y.fill_(-7.0)
+    bfilt.run_persistent()
+    torch.cuda.synchronize()
+    assert bfilt.status() & bf.BF_DEV_TIMEOUT
+    assert bfilt.counters()[3] == items[starved]
+    for i, (r, (_, y, *_)) in enumerate(zip(ref, planes)):
+        if i == starved:
+            assert bool((y == -7.0).all())
+        else:
+            assert torch.equal(r, y), i
+    bf.bf_gp_batched_plan_set_wait(bfilt.plan, 1 << 32, -1)
+    bfilt.run_persistent()
+    torch.cuda.synchronize()
+    assert bfilt.status() == st_ref and bfilt.counters() == cnt_ref
+    for r, (_, y, *_) in zip(ref, planes):
+        assert torch.equal(r, y)
+    with pytest.raises(bf.BFError):
+        bf.bf_gp_batched_plan_set_wait(bfilt.plan, 0, -1)
+    with pytest.raises(bf.BFError):
+        bf.bf_gp_batched_plan_set_wait(bfilt.plan, 100, len(planes))
+
+
+def test_persistent_rejects_rows_longer_than_4096(bf):
+    x = torch.zeros((64, 5000), device="cuda")
+    bfilt = bf.BatchedFilter([(x, torch.empty_like(x), 3.0, 30.0, 8)])
+    with pytest.raises(bf.BFError):
+        bfilt.run_persistent()
