@@ -297,11 +297,21 @@ def main():
     x = torch.from_numpy(img).cuda()
     y = torch.empty_like(x)
     opts = bf.make_opts(N, spatial, engine={"auto": 0, "cuda-core": 1, "tensor": 2, "tcgen05": 3}[args.engine])
+    tune_fir = spatial == "fir" and args.engine == "auto"
     ws_bytes = bf.bf_gp_workspace_size(1, H, W, ss, opts)
+    if tune_fir:  # room for every candidate the autotuner times (the two-pass form is the largest)
+        ws_bytes = max(ws_bytes, bf.bf_gp_workspace_size(1, H, W, ss, bf.make_opts(N, spatial, fir_two_pass=True)))
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
     K = N + 2
+    tuned = None
+    if tune_fir:
+        # the window sum's form and fused tile height, from the autotuner, before the measured region
+        opts, _ = bf.bf_gp_autotune(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, sr, opts, ws.data_ptr(), ws_bytes,
+                                    sp, reps=20)
+        tuned = {"fir_two_pass": int(opts.fir_two_pass), "fir_tile": int(opts.fir_tile),
+                 "row_threads": int(opts.row_threads), "how": "bf_gp_autotune (20 timed runs per candidate)"}
 
     fused = spatial == "box" or (spatial == "fir" and not opts.fir_two_pass)
     working_set = (12 * H * W) if fused else (ws_bytes + 8 * H * W)
@@ -437,7 +447,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "H": H, "W": W, "planes_per_gpu": 1, "sigma_s": ss, "sigma_r": sr,
-                   "order": N, "channels": K, "spatial": spatial, "engine": args.engine,
+                   "order": N, "channels": K, "spatial": spatial, "engine": args.engine, "tuned": tuned,
                    "parallelism": f"replicas x{world}",
                    "l2": (f"working set {working_set / 1e6:.1f} MB < 2 x 129 MB L2: each step timed alone, "
                           "L2 flushed (512 MB written) between steps" if small else

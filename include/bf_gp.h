@@ -93,7 +93,7 @@ typedef struct {
                            2 = mma.sync tensor cores (TF32 x 3 products) for both passes,
                            3 = column pass on tcgen05 (TF32 x 3, accumulators in tensor memory),
                                row pass on CUDA cores */
-    int fir_two_pass;   /* FIR forward only: 0 = one fused kernel per 32 x 32 tile (channels, row and
+    int fir_two_pass;   /* FIR forward only: 0 = one fused kernel per output tile (channels, row and
                            column filters and combine in shared memory, no row-filtered planes in
                            HBM), 1 = the separate row and column passes (what bf_gp_phase_rows /
                            bf_gp_phase_cols always run) */
@@ -104,7 +104,10 @@ typedef struct {
     int row_threads;    /* threads per CTA of the row pass (recursive filter, two-pass FIR): 0 = the
                            default (256, or one row when a row needs more); 256 or 512.  A CTA holds
                            row_threads / (threads per row) rows.  The autotuner chooses it */
-    int reserved[3];    /* must be zero */
+    int fir_tile;       /* fused FIR forward: output tile height, 0 (= 32), 16, 32 or 64 rows, tile
+                           width 32; a taller tile shares its halo among more outputs, a shorter one
+                           gives small images more CTAs.  The autotuner chooses it */
+    int reserved[2];    /* must be zero */
 } bf_gp_opts;
 
 /* Fill *opts with the defaults: N = 20, AUTO spatial operator, mean centre. */
@@ -353,9 +356,10 @@ bf_status bf_gp_batched_plane_stats(const bf_gp_plan *plan, void *ws, size_t ws_
  *     later calls return the stored choice without launching anything.  ms
  *     (NULL, or BF_GP_TUNE_CANDIDATES floats) gets each candidate's mean time
  *     in milliseconds in candidate order (recursive: engine e with row_threads
- *     256 at 2 e and 512 at 2 e + 1; FIR: fused, two-pass with 256 and with
- *     512 row threads), -1 where nothing was timed.  The choice (engine or FIR
- *     form, and row_threads) is written into opts.  Not capturable into a graph.
+ *     256 at 2 e and 512 at 2 e + 1; FIR: fused with 32-row tiles, two-pass
+ *     with 256 and with 512 row threads, fused with 16- and with 64-row
+ *     tiles), -1 where nothing was timed.  The choice (engine or FIR form,
+ *     row_threads and fir_tile) is written into opts.  Not capturable into a graph.
  *     BF_ERR_UNSUPPORTED if no candidate runs.
  *   bf_gp_autotune_clear: forgets every stored choice.
  *   bf_gp_batched_plan_tune: runs bf_gp_autotune for every plane of an

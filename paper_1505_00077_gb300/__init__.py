@@ -53,7 +53,7 @@ class bf_gp_opts(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("spatial", ctypes.c_int), ("centre", ctypes.c_int),
                 ("fir_halfwidth", ctypes.c_int), ("t_c", ctypes.c_double), ("engine", ctypes.c_int),
                 ("fir_two_pass", ctypes.c_int), ("box_passes", ctypes.c_int), ("tc5_wait_test", ctypes.c_int),
-                ("row_threads", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("row_threads", ctypes.c_int), ("fir_tile", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class bf_gp_plane(ctypes.Structure):
@@ -159,7 +159,7 @@ ENGINE_TCGEN05 = 3     # half-chunk products on tcgen05 where a pass has such a 
 
 def make_opts(order: int = 20, spatial="auto", t_c=None, fir_halfwidth: int = 0, engine: int = ENGINE_AUTO,
               fir_two_pass: bool = False, box_passes: int = 0, tc5_wait_test: int = 0,
-              row_threads: int = 0) -> bf_gp_opts:
+              row_threads: int = 0, fir_tile: int = 0) -> bf_gp_opts:
     """spatial 'box': box_passes passes (0 = 3) of a flat kernel of half-width
     fir_halfwidth (0 = matched to sigma_s).  tc5_wait_test: see bf_gp_opts
     (testing the tcgen05 column pass's bounded wait only)."""
@@ -171,6 +171,7 @@ def make_opts(order: int = 20, spatial="auto", t_c=None, fir_halfwidth: int = 0,
     o.box_passes = int(box_passes)
     o.tc5_wait_test = int(tc5_wait_test)
     o.row_threads = int(row_threads)
+    o.fir_tile = int(fir_tile)
     o.spatial = _SPATIAL[spatial] if isinstance(spatial, str) else int(spatial)
     o.fir_halfwidth = int(fir_halfwidth)
     if t_c is not None:

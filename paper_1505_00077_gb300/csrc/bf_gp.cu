@@ -58,6 +58,7 @@ struct Plan {
     int CL;                    // column cluster size (IIR)
     int row_tc, col_tc;        // recursive filter: row / column pass engine (0 CUDA cores, 1 mma.sync, 2 tcgen05)
     int row_block;             // threads per CTA of the row pass asked for (0 = default)
+    int fir_tile;              // fused FIR: output tile height (16, 32 or 64 rows)
     int engine_auto;           // opts.engine == 0 (the adjoint row pass then runs on CUDA cores)
     int joint;                 // joint filter: K = 2 (N + 1), CUDA-core passes
     int box_passes, box_r;     // box variant: passes of a flat kernel of half-width box_r (w = passes * box_r)
@@ -83,7 +84,8 @@ bf_status check_opts(const bf_gp_opts *o)
     if (o->box_passes < 0 || o->box_passes > 3) return BF_ERR_INVALID_ARG;
     if (o->tc5_wait_test < 0) return BF_ERR_INVALID_ARG;
     if (o->row_threads != 0 && o->row_threads != 256 && o->row_threads != 512) return BF_ERR_INVALID_ARG;
-    for (int i = 0; i < 3; ++i)
+    if (o->fir_tile != 0 && o->fir_tile != 16 && o->fir_tile != 32 && o->fir_tile != 64) return BF_ERR_INVALID_ARG;
+    for (int i = 0; i < 2; ++i)
         if (o->reserved[i] != 0) return BF_ERR_INVALID_ARG;
     return BF_OK;
 }
@@ -129,6 +131,7 @@ bf_status make_plan(int planes, int H, int W, float sigma_s, const bf_gp_opts *o
     p->col_tc = joint ? 0 : (o->engine == 2 ? 1 : (o->engine == 3 ? 2 : 0));
     p->wpr = next_pow2((W + 511) / 512);
     p->row_block = o->row_threads;
+    p->fir_tile = o->fir_tile ? o->fir_tile : 32;
     if (sp == BF_SPATIAL_IIR && p->row_tc && p->wpr > 16) return BF_ERR_UNSUPPORTED;
     // columns longer than 8192 (CUDA-core column pass) or 4096 (tensor-core column passes)
     if (sp == BF_SPATIAL_IIR && p->CL > (p->col_tc ? COL_MAX_CLUSTER_TC : COL_MAX_CTAS)) return BF_ERR_UNSUPPORTED;
@@ -461,12 +464,29 @@ void umma_mats(double sigma, UMat *um)
         }
 }
 
+// The fused FIR kernel with tile height TH (window half-width from the plan).
+template <int TH>
+bf_status launch_fir_fused(const Call &c, int planes, const FIRCoef &g)
+{
+    dim3 grid((c.ca.W + 31) / 32, (c.ca.H + TH - 1) / TH, planes);
+    switch (c.p.w) {
+#define BF_CASE(WW) \
+    case WW: fir_fused<WW, 0, TH><<<grid, 256, 0, c.s>>>(c.ca, g); break;
+        BF_CASE(1) BF_CASE(2) BF_CASE(3) BF_CASE(4) BF_CASE(5) BF_CASE(6)
+        BF_CASE(7) BF_CASE(8) BF_CASE(9) BF_CASE(10) BF_CASE(11) BF_CASE(12)
+#undef BF_CASE
+    default: return BF_ERR_UNSUPPORTED;
+    }
+    BF_CUDA(cudaGetLastError());
+    return BF_OK;
+}
+
 bf_status run_fir_fused(const Call &c, int planes, float sigma_s)
 {
     FIRCoef g;
     fir_coefs((double)sigma_s, c.p.w, &g);
     dim3 grid((c.ca.W + 31) / 32, (c.ca.H + 31) / 32, planes);
-    if (c.p.box_passes) {
+    if (c.p.box_passes) {  // 32-row tiles
         const int key = c.p.box_passes * 16 + c.p.box_r;
         switch (key) {
 #define BF_BOX(P, R) \
@@ -481,16 +501,9 @@ bf_status run_fir_fused(const Call &c, int planes, float sigma_s)
         BF_CUDA(cudaGetLastError());
         return BF_OK;
     }
-    switch (c.p.w) {
-#define BF_CASE(WW) \
-    case WW: fir_fused<WW><<<grid, 256, 0, c.s>>>(c.ca, g); break;
-        BF_CASE(1) BF_CASE(2) BF_CASE(3) BF_CASE(4) BF_CASE(5) BF_CASE(6)
-        BF_CASE(7) BF_CASE(8) BF_CASE(9) BF_CASE(10) BF_CASE(11) BF_CASE(12)
-#undef BF_CASE
-    default: return BF_ERR_UNSUPPORTED;
-    }
-    BF_CUDA(cudaGetLastError());
-    return BF_OK;
+    if (c.p.fir_tile == 16) return launch_fir_fused<16>(c, planes, g);
+    if (c.p.fir_tile == 64) return launch_fir_fused<64>(c, planes, g);
+    return launch_fir_fused<32>(c, planes, g);
 }
 
 template <int MODE>
@@ -1579,11 +1592,13 @@ bf_status bf_gp_autotune(const float *f, float *y, int planes, int H, int W, int
             opts->engine = it->second.engine;
             opts->fir_two_pass = it->second.fir_two_pass;
             opts->row_threads = it->second.row_threads;
+            opts->fir_tile = it->second.fir_tile;
             return BF_OK;
         }
     }
     // candidates, in the order their times are reported: the recursive filter's engines, each with
-    // 256- and 512-thread row-pass CTAs; the window sum fused, or two-pass with either row-pass CTA
+    // 256- and 512-thread row-pass CTAs; the window sum fused (32-row tiles), two-pass with either
+    // row-pass CTA, fused with 16- and 64-row tiles
     bf_gp_opts cand[BF_GP_TUNE_CANDIDATES];
     int nc = 0;
     if (p.spatial == BF_SPATIAL_IIR) {
@@ -1596,11 +1611,19 @@ bf_status bf_gp_autotune(const float *f, float *y, int planes, int H, int W, int
     } else if (p.spatial == BF_SPATIAL_FIR) {
         cand[nc] = *opts;
         cand[nc].fir_two_pass = 0;
+        cand[nc].fir_tile = 32;
         cand[nc++].row_threads = 0;
         for (int rt = 256; rt <= 512; rt += 256) {
             cand[nc] = *opts;
             cand[nc].fir_two_pass = 1;
+            cand[nc].fir_tile = 0;
             cand[nc++].row_threads = rt;
+        }
+        for (int th = 16; th <= 64; th += 48) {
+            cand[nc] = *opts;
+            cand[nc].fir_two_pass = 0;
+            cand[nc].fir_tile = th;
+            cand[nc++].row_threads = 0;
         }
     } else {
         cand[nc++] = *opts;
@@ -1638,6 +1661,7 @@ bf_status bf_gp_autotune(const float *f, float *y, int planes, int H, int W, int
     opts->engine = cand[best].engine;
     opts->fir_two_pass = cand[best].fir_two_pass;
     opts->row_threads = cand[best].row_threads;
+    opts->fir_tile = cand[best].fir_tile;
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     g_tune[key] = *opts;
     return BF_OK;

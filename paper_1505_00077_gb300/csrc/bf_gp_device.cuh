@@ -2091,19 +2091,21 @@ __global__ void __launch_bounds__(256) col_fir(ColArgs a, FIRCoef g)
 // Fused forward for the FIR operator (Eq. (8) with the window of Eq. (1)), or
 // with BOXP > 0 for the box variant (BOXP passes of a flat kernel of
 // half-width WH / BOXP, by running sums: about 2 BOXP additions per sample
-// plus one window sum per 8 (rows) or 4 (columns) samples, instead of
+// plus one window sum per 8 (rows) or TH / 8 (columns) samples, instead of
 // 2 WH + 1 multiply-adds):
-// one CTA computes a 32 x 32 output tile for all K
+// one CTA computes a TH x 32 output tile (TH rows: 16, 32 or 64) for all K
 // channels without writing the row-filtered planes.  Per channel k (ascending):
 //   1. Phi_k = 2^e0 E u^k on the tile plus a WH halo (zero outside the image),
 //      by one multiply per sample from the previous channel, into shared memory;
-//   2. row filter of the (32 + 2 WH) rows x 32 columns (threads: row x strip of 8);
-//   3. column filter of the 32 x 32 outputs (threads: column x 4 rows), times beta_k,
+//   2. row filter of the (TH + 2 WH) rows x 32 columns (work items: row x strip of 8);
+//   3. column filter of the TH x 32 outputs (threads: column x TH / 8 rows), times beta_k,
 //      accumulated with running powers of u:
 //        p += k u^{k-1} Psi_k,  q += u^{k-1} Psi_k (1 <= k <= N),  Psi_0 kept;
 //   y = t_c + R p / (Psi_0 + s^2 u q).
-// The row-filtered tile is double-buffered by channel parity, so each channel
-// costs two barriers.  grid (ceil(W/32), ceil(H/32), planes), block 256.
+// A taller tile shares its halo columns among more outputs; a shorter one
+// gives small images more CTAs.  The row-filtered tile is double-buffered by
+// channel parity, so each channel costs two barriers.
+// grid (ceil(W/32), ceil(H/TH), planes), block 256.
 // Sum over j of win[j .. j + 2 R] for the LOUT outputs after BOXP passes of a
 // box of half-width R (running sums; each pass shortens the window by 2 R).
 template <int BOXP, int R, int LOUT>
@@ -2136,25 +2138,27 @@ __device__ __forceinline__ void box_passes(const float *win, float *out)
     for (int j = 0; j < LOUT; ++j) out[j] = cur[j];
 }
 
-template <int WH, int BOXP = 0>
+template <int WH, int BOXP = 0, int TH = 32>
 __global__ void __launch_bounds__(256) fir_fused(ColArgs a, FIRCoef g)
 {
-    constexpr int T = 32;
-    constexpr int RS = T + 2 * WH;              // side of the tile plus halo
-    constexpr int NR = (RS * RS + 255) / 256;   // halo samples per thread
-    __shared__ float phi[RS][RS + 1];
-    __shared__ float rf[2][RS][T + 1];
+    static_assert(TH == 16 || TH == 32 || TH == 64, "tile heights 16, 32, 64");
+    constexpr int T = 32;                          // tile width
+    constexpr int RPT = TH / 8;                    // output rows per thread
+    constexpr int RSW = T + 2 * WH, RSH = TH + 2 * WH;  // tile plus halo
+    constexpr int NR = (RSH * RSW + 255) / 256;    // halo samples per thread
+    __shared__ float phi[RSH][RSW + 1];
+    __shared__ float rf[2][RSH][T + 1];
     const int tid = threadIdx.x;
     const int plane = blockIdx.z;
-    const int x0 = blockIdx.x * T, y0 = blockIdx.y * T;
+    const int x0 = blockIdx.x * T, y0 = blockIdx.y * TH;
     const PlaneParams &P = a.pp[plane];
     const float *fp = a.f + (size_t)plane * a.H * a.pitch;
-    // output pixels of this thread: column c, rows r0 .. r0 + 3
-    const int c = tid & 31, r0 = (tid >> 5) * 4;
+    // output pixels of this thread: column c, rows r0 .. r0 + RPT - 1
+    const int c = tid & 31, r0 = (tid >> 5) * RPT;
     const int xo = x0 + c;
     if (P.mode != 0) {  // constant plane or non-finite input: the result is the input
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < RPT; ++j) {
             const int yo = y0 + r0 + j;
             if (yo < a.H && xo < a.W) {
                 const size_t pix = ((size_t)plane * a.H + yo) * a.pitch + xo;
@@ -2167,25 +2171,23 @@ __global__ void __launch_bounds__(256) fir_fused(ColArgs a, FIRCoef g)
 #pragma unroll
     for (int i = 0; i < NR; ++i) {
         const int idx = tid + 256 * i;
-        const int rr = idx / RS, cc = idx % RS;
+        const int rr = idx / RSW, cc = idx % RSW;
         const int gy = y0 - WH + rr, gx = x0 - WH + cc;
-        const bool in = idx < RS * RS && gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
+        const bool in = idx < RSH * RSW && gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
         const float uu = in ? (__ldg(fp + (size_t)gy * a.pitch + gx) - P.tc) * P.invR : 0.f;
         hu[i] = uu;
         hv[i] = in ? envelope(P, uu) : 0.f;
     }
-    float ou[4], pacc[4], qacc[4], psi0[4], w[4];
+    float ou[RPT], pacc[RPT], qacc[RPT], psi0[RPT], w[RPT];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < RPT; ++j) {
         const int yo = y0 + r0 + j;
         const bool in = yo < a.H && xo < a.W;
         ou[j] = in ? (__ldg(fp + (size_t)yo * a.pitch + xo) - P.tc) * P.invR : 0.f;
         pacc[j] = qacc[j] = psi0[j] = 0.f;
         w[j] = 1.f;
     }
-    // row-filter work item: row rr, columns 8 s .. 8 s + 7 (RS x 4 items)
-    const bool row_item = tid < 4 * RS;
-    const int rr_row = tid >> 2, cs = (tid & 3) * 8;
+    // row-filter work items: row rr, columns 8 s .. 8 s + 7 (RSH x 4 items, 256 at a time)
 #pragma unroll 1
     for (int k = 0; k < a.K; ++k) {
         const int buf = k & 1;
@@ -2193,10 +2195,12 @@ __global__ void __launch_bounds__(256) fir_fused(ColArgs a, FIRCoef g)
         for (int i = 0; i < NR; ++i) {
             const int idx = tid + 256 * i;
             if (k > 0) hv[i] *= hu[i];
-            if (idx < RS * RS) phi[idx / RS][idx % RS] = hv[i];
+            if (idx < RSH * RSW) phi[idx / RSW][idx % RSW] = hv[i];
         }
         __syncthreads();  // Phi_k on the halo tile; every thread is past the row filter of channel k - 1
-        if (row_item) {
+#pragma unroll
+        for (int item = tid; item < 4 * RSH; item += 256) {
+            const int rr_row = item >> 2, cs = (item & 3) * 8;
             float win[8 + 2 * WH];
 #pragma unroll
             for (int j = 0; j < 8 + 2 * WH; ++j) win[j] = phi[rr_row][cs + j];
@@ -2216,17 +2220,17 @@ __global__ void __launch_bounds__(256) fir_fused(ColArgs a, FIRCoef g)
             }
         }
         __syncthreads();  // row-filtered tile of channel k
-        float win[4 + 2 * WH];
+        float win[RPT + 2 * WH];
 #pragma unroll
-        for (int j = 0; j < 4 + 2 * WH; ++j) win[j] = rf[buf][r0 + j][c];
+        for (int j = 0; j < RPT + 2 * WH; ++j) win[j] = rf[buf][r0 + j][c];
         const float beta = P.beta[k];
         const float mk = (float)k;
-        float o4[4];
+        float o4[RPT];
         if constexpr (BOXP > 0) {
-            box_passes<BOXP, WH / (BOXP > 0 ? BOXP : 1), 4>(win, o4);
+            box_passes<BOXP, WH / (BOXP > 0 ? BOXP : 1), RPT>(win, o4);
         } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < RPT; ++j) {
                 float acc = g.g[0] * win[j + WH];
 #pragma unroll
                 for (int dd = 1; dd <= WH; ++dd) acc = fmaf(g.g[dd], win[j + WH - dd] + win[j + WH + dd], acc);
@@ -2234,7 +2238,7 @@ __global__ void __launch_bounds__(256) fir_fused(ColArgs a, FIRCoef g)
             }
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < RPT; ++j) {
             const float psi = o4[j] * beta;
             if (k == 0) {
                 psi0[j] = psi;
@@ -2247,7 +2251,7 @@ __global__ void __launch_bounds__(256) fir_fused(ColArgs a, FIRCoef g)
     }
     bool nonpos = false;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < RPT; ++j) {
         const int yo = y0 + r0 + j;
         if (yo < a.H && xo < a.W) {
             const float Q = fmaf(P.s2 * ou[j], qacc[j], psi0[j]);

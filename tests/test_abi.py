@@ -67,9 +67,14 @@ def test_bad_options_rejected():
         with pytest.raises(bfgp.BFError):
             bfgp.bf_gp_workspace_size(1, 32, 32, 2.0, o)
     o = bfgp.make_opts()
-    o.reserved[2] = 1
+    o.reserved[1] = 1
     with pytest.raises(bfgp.BFError):
         bfgp.bf_gp_workspace_size(1, 32, 32, 2.0, o)
+    for t in (8, 48, 128, -1):  # fused FIR tile heights are 16, 32 and 64 rows
+        with pytest.raises(bfgp.BFError):
+            bfgp.bf_gp_workspace_size(1, 32, 32, 2.0, bfgp.make_opts(20, "fir", fir_tile=t))
+    for t in (0, 16, 32, 64):
+        assert bfgp.bf_gp_workspace_size(1, 32, 32, 2.0, bfgp.make_opts(20, "fir", fir_tile=t)) > 0
 
 
 def test_unsupported_sizes_reported():

@@ -72,9 +72,11 @@ def test_autotune_fir_chooses_between_fused_and_two_pass(bf):
     s = torch.cuda.current_stream().cuda_stream
     bf.bf_gp_autotune_clear()
     o, ms = bf.bf_gp_autotune(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, sr, o, ws.data_ptr(), need, s, reps=3)
-    assert all(t > 0 for t in ms[:3]) and ms[3:] == [-1.0] * 5  # fused; two-pass with 256 / 512 row threads
-    best = int(np.argmin(ms[:3]))
-    assert o.fir_two_pass == (best > 0) and o.row_threads == (0, 256, 512)[best]
+    # fused (32-row tiles); two-pass with 256 / 512 row threads; fused with 16- / 64-row tiles
+    assert all(t > 0 for t in ms[:5]) and ms[5:] == [-1.0] * 3
+    best = int(np.argmin(ms[:5]))
+    assert o.fir_two_pass == (best in (1, 2)) and o.row_threads == (0, 256, 512, 0, 0)[best]
+    assert o.fir_tile == (32, 0, 0, 16, 64)[best]
     bf.bf_gp_forward(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, sr, o, ws.data_ptr(), need, s)
     ref, kap = oracle.gp_bf(img.astype(np.float64), ss, sr, 20, "fir", t_c=parity.gpu_centre(bf, ws.data_ptr(), 0, s),
                             return_kappa=True)

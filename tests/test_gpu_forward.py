@@ -437,10 +437,10 @@ def test_engines_agree_with_oracle(bf, engine, shape, ss):
 
 # ---------------------------------------------------------------- fused FIR forward
 
-def _forward(bf, img, ss, sr, N, two_pass, centre=False):
+def _forward(bf, img, ss, sr, N, two_pass, centre=False, fir_tile=0):
     x = torch.from_numpy(np.ascontiguousarray(img, dtype=np.float32)).cuda()
     H, W = x.shape
-    o = bf.make_opts(N, "fir", fir_two_pass=two_pass)
+    o = bf.make_opts(N, "fir", fir_two_pass=two_pass, fir_tile=fir_tile)
     need = bf.bf_gp_workspace_size(1, H, W, ss, o)
     ws = torch.empty(need, dtype=torch.uint8, device="cuda")
     y = torch.full_like(x, float("nan"))
@@ -465,6 +465,26 @@ def test_fir_fused_matches_two_pass_and_oracle(bf, shape, ss):
     ref, kap = oracle.gp_bf(img.astype(np.float64), ss, 30.0, 20, "fir", t_c=tc, return_kappa=True)
     parity.gate(fused, ref, kap, min_gated=0.999, f=img, window=oracle.window(ss), label=f"fused {shape} ss={ss:g}")
     parity.gate(two, ref, kap, min_gated=0.999, f=img, window=oracle.window(ss), label=f"two-pass {shape} ss={ss:g}")
+
+
+@pytest.mark.parametrize("shape,ss", [((1, 1), 1.0), ((7, 300), 0.4), ((33, 65), 2.0), ((70, 45), 4.0),
+                                      ((100, 1030), 3.7), ((129, 47), 3.2)])
+def test_fir_fused_tile_heights(bf, shape, ss):
+    """The fused kernel with 16- and 64-row output tiles (the autotuner's other
+    tile shapes) gives the 32-row result bit for bit: every output is the same
+    window sums of the same channel values; only which CTA forms it changes.
+    Windows up to W = 12 make the 64-row tile's halo 88 rows (two row-filter
+    items per thread)."""
+    H, W = shape
+    img = synthetic.make_image(H, W, 6, 10.0, 20.0, synthetic.seed_for(9, 7100 + H + W))
+    base, b0, tc = _forward(bf, img, ss, 30.0, 20, False, centre=True)
+    assert b0 == 0
+    for th in (16, 64):
+        out, b = _forward(bf, img, ss, 30.0, 20, False, fir_tile=th)
+        assert b == 0
+        assert np.array_equal(out, base), th
+    ref, kap = oracle.gp_bf(img.astype(np.float64), ss, 30.0, 20, "fir", t_c=tc, return_kappa=True)
+    parity.gate(out, ref, kap, min_gated=0.999, f=img, window=oracle.window(ss), label=f"fused 64-row tiles {shape} ss={ss:g}")
 
 
 def test_fir_fused_copy_planes(bf):
