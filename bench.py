@@ -297,20 +297,23 @@ def main():
     x = torch.from_numpy(img).cuda()
     y = torch.empty_like(x)
     opts = bf.make_opts(N, spatial, engine={"auto": 0, "cuda-core": 1, "tensor": 2, "tcgen05": 3}[args.engine])
-    tune_fir = spatial == "fir" and args.engine == "auto"
+    tune = spatial in ("fir", "iir") and args.engine == "auto"
     ws_bytes = bf.bf_gp_workspace_size(1, H, W, ss, opts)
-    if tune_fir:  # room for every candidate the autotuner times (the two-pass form is the largest)
-        ws_bytes = max(ws_bytes, bf.bf_gp_workspace_size(1, H, W, ss, bf.make_opts(N, spatial, fir_two_pass=True)))
+    if tune:  # room for every candidate the autotuner times (the two-pass FIR form is the largest)
+        ws_bytes = max([ws_bytes] + [bf.bf_gp_workspace_size(1, H, W, ss, bf.make_opts(N, spatial, engine=e,
+                                                                                       fir_two_pass=spatial == "fir"))
+                                     for e in range(4)])
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
     K = N + 2
     tuned = None
-    if tune_fir:
-        # the window sum's form and fused tile height, from the autotuner, before the measured region
+    if tune:
+        # recursive filter: engine and row-pass CTA size; window sum: fused tile height or the two-pass
+        # form; from the autotuner, before the measured region
         opts, _ = bf.bf_gp_autotune(x.data_ptr(), y.data_ptr(), 1, H, W, W, ss, sr, opts, ws.data_ptr(), ws_bytes,
                                     sp, reps=20)
-        tuned = {"fir_two_pass": int(opts.fir_two_pass), "fir_tile": int(opts.fir_tile),
+        tuned = {"engine": int(opts.engine), "fir_two_pass": int(opts.fir_two_pass), "fir_tile": int(opts.fir_tile),
                  "row_threads": int(opts.row_threads), "how": "bf_gp_autotune (20 timed runs per candidate)"}
 
     fused = spatial == "box" or (spatial == "fir" and not opts.fir_two_pass)
@@ -417,9 +420,10 @@ def main():
     peak, peak_kind = measured_peaks()
     bytes_rows = (4 + 4 * K) * H * W       # read f, write K row-filtered planes
     bytes_cols = (4 * K + 8) * H * W       # read K planes + f, write y
-    rtc = spatial == "iir" and args.engine in ("auto", "tensor")
-    rk = ("row_tc" if rtc else "row_iir") if spatial == "iir" else "row_fir"
-    ck = {"tensor": "col_tc", "tcgen05": "col_tc5"}.get(args.engine, "col_iir") if spatial == "iir" else "col_fir"
+    # the kernels of the engine that ran: 0 row_tc + col_iir, 1 row_iir + col_iir, 2 row_tc + col_tc,
+    # 3 row_iir + col_tc5
+    rk = ("row_tc" if opts.engine in (0, 2) else "row_iir") if spatial == "iir" else "row_fir"
+    ck = ("col_iir", "col_iir", "col_tc", "col_tc5")[opts.engine] if spatial == "iir" else "col_fir"
     if fused:
         # FP32 FMA per pixel of the separable filter (row + column, 2w + 1 taps each) and the combine,
         # against the FP32 FMA rate of the SMs (152 SMs x 128 lanes x the measured maximum SM clock)
