@@ -249,3 +249,32 @@ def test_persistent_rejects_rows_longer_than_4096(bf):
     bfilt = bf.BatchedFilter([(x, torch.empty_like(x), 3.0, 30.0, 8)])
     with pytest.raises(bf.BFError):
         bfilt.run_persistent()
+
+
+def test_persistent_edge_planes(bf):
+    """Edge planes through the persistent launch: a constant plane (copied), a
+    plane holding a NaN (copied, BF_DEV_NONFINITE_IN), 1 x 1, single rows and
+    columns, a column 3 CTAs tall run by a group of 4. Bit for bit the forked
+    path's output, status word and counters."""
+    rng = np.random.default_rng(31)
+    shapes = [(40, 70), (33, 33), (1, 1), (1, 7), (5, 1), (700, 3), (1300, 20), (257, 513)]
+    planes = []
+    for i, (H, W) in enumerate(shapes):
+        img = synthetic.make_image(H, W, 4, 10.0, 0.0, synthetic.seed_for(13, i))
+        if i == 0:
+            img[:] = 77.0
+        if i == 1:
+            img[5, 7] = np.nan
+        x = torch.from_numpy(np.ascontiguousarray(img)).cuda()
+        planes.append((x, torch.empty_like(x), float(rng.uniform(1, 12)), float(rng.uniform(15, 60)), 18))
+    bfilt = bf.BatchedFilter(planes)
+    ref, st_ref, cnt_ref = _forked_outputs(bfilt, planes)
+    assert st_ref & bf.BF_DEV_NONFINITE_IN and cnt_ref[1] == 1
+    for _, y, *_ in planes:
+        y.fill_(-3.0)
+    bfilt.run_persistent()
+    torch.cuda.synchronize()
+    assert bfilt.status() == st_ref and bfilt.counters() == cnt_ref
+    for i, (r, (x, y, *_)) in enumerate(zip(ref, planes)):
+        assert torch.equal(torch.nan_to_num(r, nan=-1.0), torch.nan_to_num(y, nan=-1.0)), i
+    assert torch.equal(planes[0][1], planes[0][0])  # the constant plane comes back unchanged
