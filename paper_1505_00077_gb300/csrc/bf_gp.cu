@@ -558,7 +558,8 @@ bf_status run_cols(const Call &c, int planes, int W, float sigma_s)
         // the CUDA-core pass: the channel tiles, and for the saving forward its dp, dq ([2 C][256])
         const size_t smem = tcore ? sizeof(float) * COL_TILE_BUFS * COL_TILE_FLOATS
                                   : sizeof(float) * (COL_TILE_BUFS * COL_TILE_FLOATS +
-                                                     (MODE == MODE_SAVE ? 2 * COL_C * 256 : 0));
+                                                     (MODE == MODE_SAVE ? 2 * COL_C * 256 : 0) +
+                                                     (MODE == MODE_FWD ? COL_U_FLOATS : 0));
         if constexpr (MODE != MODE_JOINT) {
             if (tcore)
                 BF_CUDA(cudaFuncSetAttribute(col_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1133,7 +1134,7 @@ void persist_config(const bf_gp_plan *pl, cudaStream_t s, cudaLaunchConfig_t *cf
     std::memset(cfg, 0, sizeof *cfg);
     cfg->blockDim = dim3(256, 1, 1);
     cfg->gridDim = dim3((unsigned)pl->pcl, 1, 1);
-    cfg->dynamicSmemBytes = sizeof(float) * COL_TILE_BUFS * COL_TILE_FLOATS;
+    cfg->dynamicSmemBytes = sizeof(float) * (COL_TILE_BUFS * COL_TILE_FLOATS + COL_U_FLOATS);
     cfg->stream = s;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)pl->pcl;
@@ -1198,7 +1199,7 @@ bf_status upload_persistent(bf_gp_plan *pl, char *wsb, cudaStream_t s)
     BF_CUDA(cudaMemcpyAsync(wsb + pl->off_ptables, img.data(), img.size(), cudaMemcpyHostToDevice, s));
     BF_CUDA(cudaStreamSynchronize(s));
     // how many clusters of the launch's shape are resident at once on this device
-    const size_t smem = sizeof(float) * COL_TILE_BUFS * COL_TILE_FLOATS;
+    const size_t smem = sizeof(float) * (COL_TILE_BUFS * COL_TILE_FLOATS + COL_U_FLOATS);
     BF_CUDA(cudaFuncSetAttribute(batched_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];

@@ -1073,14 +1073,24 @@ struct ColArgs {
 // DSMEM: dp and dq live in shared memory (sd[j * 256] and sd[(RPT + j) * 256],
 // sd pointing at this thread's column of a [2 RPT][256] block), which frees
 // 2 RPT registers per thread.
-template <int RPT, int MODE, bool DSMEM = false>
+// USMEM (forward, RPT a multiple of 4): the centred intensities u live in shared
+// memory, us pointing at this thread's column of a [RPT / 4][256] float4 block,
+// read back as float4 by every step; the RPT registers they free keep the
+// column pass's working set out of local memory.
+template <int RPT, int MODE, bool DSMEM = false, bool USMEM = false>
 struct Combine {
     static constexpr bool SAVE_REG = MODE == MODE_SAVE && !DSMEM;
-    float u[RPT], p[RPT], q[RPT], dp[SAVE_REG ? RPT : 1], dq[SAVE_REG ? RPT : 1];
+    static constexpr bool USM = USMEM && MODE == MODE_FWD && (RPT % 4) == 0;
+    float u[USM ? 1 : RPT], p[RPT], q[RPT], dp[SAVE_REG ? RPT : 1], dq[SAVE_REG ? RPT : 1];
     float *sd;
+    float *us;
+    __device__ __forceinline__ float getu(int j) const { return USM ? us[(j >> 2) * 1024 + (j & 3)] : u[USM ? 0 : j]; }
     __device__ __forceinline__ void init(float uu, int j)
     {
-        u[j] = uu;
+        if (USM)
+            us[(j >> 2) * 1024 + (j & 3)] = uu;
+        else
+            u[USM ? 0 : j] = uu;
         p[j] = q[j] = 0.f;
         if (MODE == MODE_SAVE) {
             if (DSMEM) {
@@ -1116,18 +1126,32 @@ struct Combine {
             for (int j = 0; j < RPT; ++j) q[j] = fmaf(u[j], q[j], y[j]);
             return;
         }
+        float uv[RPT];
+        if constexpr (USM) {
+#pragma unroll
+            for (int e = 0; e < RPT / 4; ++e) {
+                const float4 v = *reinterpret_cast<const float4 *>(us + e * 1024);
+                uv[4 * e] = v.x;
+                uv[4 * e + 1] = v.y;
+                uv[4 * e + 2] = v.z;
+                uv[4 * e + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < RPT; ++j) uv[j] = u[USM ? 0 : j];
+        }
         if (m == 0) {
 #pragma unroll
-            for (int j = 0; j < RPT; ++j) q[j] = fmaf(s2 * u[j], q[j], y[j]);  // Q~
+            for (int j = 0; j < RPT; ++j) q[j] = fmaf(s2 * uv[j], q[j], y[j]);  // Q~
             return;
         }
         if (MODE == MODE_FWD && (RPT & 1) == 0) {  // the same FMAs, two per instruction
 #pragma unroll
             for (int j = 0; j < RPT; j += 2) {
-                if (m <= N) fma2r(q[j], q[j + 1], u[j], u[j + 1], q[j], q[j + 1], y[j], y[j + 1]);
+                if (m <= N) fma2r(q[j], q[j + 1], uv[j], uv[j + 1], q[j], q[j + 1], y[j], y[j + 1]);
                 float t0, t1;
                 mul2(t0, t1, mk, mk, y[j], y[j + 1]);
-                fma2r(p[j], p[j + 1], u[j], u[j + 1], p[j], p[j + 1], t0, t1);
+                fma2r(p[j], p[j + 1], uv[j], uv[j + 1], p[j], p[j + 1], t0, t1);
             }
             return;
         }
@@ -1166,9 +1190,9 @@ struct AdjSums {
 };
 
 // Writes the result for one pixel (r, x) of the plane.
-template <int RPT, int MODE, bool DSMEM>
+template <int RPT, int MODE, bool DSMEM, bool USMEM>
 __device__ __forceinline__ void finish_pixel(const ColArgs &a, const PlaneParams &P, int plane, int r, int x,
-                                             const Combine<RPT, MODE, DSMEM> &cb, int j, int &nonpos,
+                                             const Combine<RPT, MODE, DSMEM, USMEM> &cb, int j, int &nonpos,
                                              AdjSums &sums)
 {
     const size_t pix = ((size_t)plane * a.H + r) * a.pitch + x;
@@ -1184,7 +1208,7 @@ __device__ __forceinline__ void finish_pixel(const ColArgs &a, const PlaneParams
         const float Qt = __ldg(a.saved + saved_idx(plane, 1, a.H, a.W, r, x));
         const float dpv = __ldg(a.saved + saved_idx(plane, 2, a.H, a.W, r, x));
         const float dqv = __ldg(a.saved + saved_idx(plane, 3, a.H, a.W, r, x));
-        const float u = cb.u[j];
+        const float u = cb.getu(j);
         float gdir = 0.f;
         if (Qt > 0.f && isfinite(g)) {
             const float al = __fdiv_rn(g * P.R, Qt);
@@ -1273,6 +1297,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 constexpr int COL_TILE_BUFS = 4;  // channel tiles in flight in the recursive column pass
+constexpr int COL_U_FLOATS = 16 * 256;  // the forward column pass's u (16 rows x 256 threads) after the tiles
 // CTAs of 512 rows in one column cluster of the recursive column pass (more
 // than 8 is a non-portable cluster size the launch has to opt into)
 constexpr int COL_MAX_CTAS = 16;
@@ -1353,9 +1378,10 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
         }
     };
 
-    // the saving forward keeps dp, dq in the dynamic shared memory after the tiles
-    Combine<C, MODE, MODE == MODE_SAVE> cb;
+    // after the tiles in the dynamic shared memory: the saving forward's dp, dq; the forward's u
+    Combine<C, MODE, MODE == MODE_SAVE, MODE == MODE_FWD> cb;
     cb.sd = tiles + COL_TILE_BUFS * COL_TILE_FLOATS + tid;
+    cb.us = tiles + COL_TILE_BUFS * COL_TILE_FLOATS + 4 * tid;
     const float *fcol = a.f + (size_t)plane * a.H * a.pitch;
 #pragma unroll
     for (int j = 0; j < C; ++j) {
