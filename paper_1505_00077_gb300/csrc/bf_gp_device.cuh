@@ -1390,18 +1390,29 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
         const float fv = in ? __ldg(fcol + (size_t)r * a.pitch + x) : 0.f;
         cb.init((fv - P.tc) * P.invR, j);
     }
-    float qcr[NP], qci[NP], qar[NP], qai[NP];  // p^{16 l4}, p^{16 (3 - l4)}
-#pragma unroll
-    for (int m = 0; m < NP; ++m) {
-        cpow_tab(qcr[m], qci[m], cf, m, l4);
-        cpow_tab(qar[m], qai[m], cf, m, 3 - l4);
+    // [l4][pole]: {p^{16 l4}, p^{16 (3 - l4)}} (re, im), read once per channel
+    __shared__ float4 qtab[4][NP];
+    if (tid < 4 * NP) {
+        const int ql = tid >> 1, qm = tid & 1;
+        float a0, a1, b0, b1;
+        cpow_tab(a0, a1, cf, qm, ql);
+        cpow_tab(b0, b1, cf, qm, 3 - ql);
+        qtab[ql][qm] = make_float4(a0, a1, b0, b1);
     }
     // cross-CTA roles: lane = (dir * 2 + pole) * 8 + column
     const int gcol = lane & 7, gq = lane >> 3, gm = gq & 1, gdir = gq >> 1;
-    float Phr, Phi;  // p^{64 w}: the CTA carry crosses the warps before (causal) / after (anticausal) this one
-    cpow_tab(Phr, Phi, cf, gm, 4 * (gdir == 0 ? warp : 7 - warp));
-    const float p4r = gm == 0 ? cf.Pr[0][2] : cf.Pr[1][2], p4i = gm == 0 ? cf.Pi[0][2] : cf.Pi[1][2];
-    const float p32r = gm == 0 ? cf.Pr[0][5] : cf.Pr[1][5], p32i = gm == 0 ? cf.Pi[0][5] : cf.Pi[1][5];
+    // [warp][dir][pole]: p^{64 w}, the CTA carry crosses the warps before (causal) / after (anticausal)
+    // warp w; [pole]: {p^64, p^512} for the leader's fold and pushes; read when used
+    __shared__ float2 phtab[8][2][NP];
+    __shared__ float4 lptab[NP];
+    if (tid < 8 * 2 * NP) {
+        const int pw = tid >> 2, pd = (tid >> 1) & 1, pm = tid & 1;
+        float a0, a1;
+        cpow_tab(a0, a1, cf, pm, 4 * (pd == 0 ? pw : 7 - pw));
+        phtab[pw][pd][pm] = make_float2(a0, a1);
+        if (tid < NP)
+            lptab[tid] = make_float4(cf.Pr[tid][2], cf.Pi[tid][2], cf.Pr[tid][5], cf.Pi[tid][5]);
+    }
     {
         float2 *z = &inc[0][0][0][0][0];
         for (int e = tid; e < 2 * MAXCTA * 8 * NP * 2; e += blockDim.x) z[e] = make_float2(0.f, 0.f);
@@ -1493,7 +1504,8 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
                 slot[0] = totr;
                 slot[1] = toti;
                 float nr, ni;
-                cmul(nr, ni, p4r, p4i, totr, toti);
+                const float4 lp = lptab[gm];
+                cmul(nr, ni, lp.x, lp.y, totr, toti);
                 totr = nr + tr;
                 toti = ni + ti;
             }
@@ -1504,7 +1516,8 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
             for (int d = 1; d <= nd; ++d) {
                 *cl.map_shared_rank(own, gbase + (gdir == 0 ? rank + d : rank - d)) = make_float2(totr, toti);
                 float nr, ni;
-                cmul(nr, ni, p32r, p32i, totr, toti);
+                const float4 lp = lptab[gm];
+                cmul(nr, ni, lp.z, lp.w, totr, toti);
                 totr = nr;
                 toti = ni;
             }
@@ -1543,7 +1556,8 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
                 Xr += t.x;
                 Xi += t.y;
             }
-            cmadd(Wr, Wi, Phr, Phi, Xr, Xi);
+            const float2 ph = phtab[warp][gdir][gm];
+            cmadd(Wr, Wi, ph.x, ph.y, Xr, Xi);
         }
         // the carries of this thread's column; states entering each half
         float cBr[NP], cBi[NP], aAr[NP], aAi[NP];
@@ -1553,8 +1567,9 @@ __device__ __forceinline__ void col_iir_body(const ColArgs &a, const IIRCoef &cf
             const float wci = __shfl_sync(0xffffffffu, Wi, (0 * 2 + m) * 8 + col);
             const float war = __shfl_sync(0xffffffffu, Wr, (1 * 2 + m) * 8 + col);
             const float wai = __shfl_sync(0xffffffffu, Wi, (1 * 2 + m) * 8 + col);
-            cmadd(cr[m], ci[m], qcr[m], qci[m], wcr, wci);
-            cmadd(ar[m], ai[m], qar[m], qai[m], war, wai);
+            const float4 qq = qtab[l4][m];
+            cmadd(cr[m], ci[m], qq.x, qq.y, wcr, wci);
+            cmadd(ar[m], ai[m], qq.z, qq.w, war, wai);
             // half B: causal p^8 c + cA; half A: anticausal aB + p^8 a
             cBr[m] = hAr[m];
             cBi[m] = hAi[m];
