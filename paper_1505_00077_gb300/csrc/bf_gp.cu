@@ -1040,10 +1040,12 @@ extern "C" {
 namespace {
 
 // The persistent launch's tables: each plane's descriptor (offsets into its single-image
-// workspace), its coefficients, and the work items: every plane's statistics partials (one
-// per CTA, pcl per item), then its finalisation, its row groups (pcl per item), its column
-// strips (pcl / G per item, G CTAs per strip).  Planes whose rows exceed 4096 samples are
-// outside the row pass's 256-thread CTAs: the plan then has no persistent form.
+// workspace), its coefficients, and its work items: statistics partials (stat_m per CTA,
+// pcl CTAs per item), its finalisation, its row groups (row_m per CTA), its column strips
+// (pcl / G per item, G CTAs per strip).  The launch order of the items is set at upload
+// (order_items).  Planes whose rows exceed 4096 samples are outside the row pass's 256-thread
+// CTAs, and columns longer than 4096 rows outside an 8-CTA cluster: the plan then has no
+// persistent form.
 bf_status build_persistent(bf_gp_plan *pl, const bf_gp_plane *planes, const bf_gp_opts *opts)
 {
     const int n = pl->n;

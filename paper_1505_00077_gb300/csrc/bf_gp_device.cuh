@@ -3135,15 +3135,17 @@ __device__ __forceinline__ void count_done(int *c, int n)
 // centres and scales, then the row groups of plane after plane, with each
 // plane's column strips placed a few rounds of row items after its last row
 // group, so that they find its channel planes still partly in L2), so an item
-// only waits for items taken before it, by clusters that are running.  Rank 0 waits for the item's
-// prerequisite (a per-plane readiness counter, bounded by wait_cycles) and the
-// whole cluster follows its decision; a wait that gives up raises
-// BF_DEV_TIMEOUT in the plane's status word and the item is skipped (its own
-// count still advances, so nothing waits on it in turn).  Statistics and row
-// items give stat_m / row_m consecutive units to each CTA; a column item gives
-// one strip to each group of G CTAs (the cluster size / G strips at once).  Each plane's coefficients
-// are staged in shared memory for its items.  Same kernels' arithmetic as the
-// single-image forward with engine 0 (tensor-core rows, CUDA-core columns).
+// only waits for items taken before it, by clusters that are running.  Rank 0
+// waits for the item's prerequisite (a per-plane readiness counter, bounded by
+// wait_cycles) and the whole cluster follows its decision; a wait that gives up
+// raises BF_DEV_TIMEOUT in the plane's status word and the item is skipped (its
+// own count still advances, so nothing waits on it in turn).  Statistics and
+// row items give stat_m / row_m consecutive units to each CTA; a column item
+// gives one strip to each group of G CTAs (the cluster size / G strips at
+// once).  Each plane's coefficients are staged in shared memory for its items.
+// Same kernels' arithmetic as the single-image forward with engine 0
+// (tensor-core rows, CUDA-core columns).  The statuses are zeroed before the
+// launch and gathered after it.
 // grid (clusters * cluster size), block 256, cluster (size <= 8).
 __global__ void __launch_bounds__(256, 2) batched_persistent(PersistArgs a)
 {
