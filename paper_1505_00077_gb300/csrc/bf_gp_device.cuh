@@ -3152,6 +3152,9 @@ __global__ void __launch_bounds__(256, 2) batched_persistent(PersistArgs a)
     __shared__ int s_item, s_go;
     __shared__ IIRCoef s_cf;
     __shared__ TCMat s_tm;
+    // the item's arguments, staged like its coefficients: read from shared memory where used
+    __shared__ RowArgs s_ra;
+    __shared__ ColArgs s_ca;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int CLn = (int)cl.num_blocks();
@@ -3215,51 +3218,53 @@ __global__ void __launch_bounds__(256, 2) batched_persistent(PersistArgs a)
             if (u0 < u1) {
                 stage(a.crow + p, &s_cf, (int)sizeof(IIRCoef));
                 stage(a.tm + p, &s_tm, (int)sizeof(TCMat));
+                if (tid == 0) {
+                    s_ra.f = d.f;
+                    s_ra.gy = nullptr;
+                    s_ra.fd = nullptr;
+                    s_ra.saved = nullptr;
+                    s_ra.ws = planes;
+                    s_ra.pp = pp;
+                    s_ra.acc = nullptr;
+                    s_ra.H = d.H;
+                    s_ra.W = d.W;
+                    s_ra.pitch = d.pitch;
+                    s_ra.Wp = d.Wp;
+                    s_ra.K = d.K;
+                    s_ra.T = d.wpr;
+                    s_ra.N = d.N;
+                }
                 __syncthreads();
                 if (go) {
-                    RowArgs ra;
-                    ra.f = d.f;
-                    ra.gy = nullptr;
-                    ra.fd = nullptr;
-                    ra.saved = nullptr;
-                    ra.ws = planes;
-                    ra.pp = pp;
-                    ra.acc = nullptr;
-                    ra.H = d.H;
-                    ra.W = d.W;
-                    ra.pitch = d.pitch;
-                    ra.Wp = d.Wp;
-                    ra.K = d.K;
-                    ra.T = d.wpr;
-                    ra.N = d.N;
-                    for (int j = u0; j < u1; ++j) row_tc_body<MODE_FWD>(ra, s_cf, s_tm, w.z + j, 0);
+                    for (int j = u0; j < u1; ++j) row_tc_body<MODE_FWD>(s_ra, s_cf, s_tm, w.z + j, 0);
                 }
                 count_done(rdy + 2, u1 - u0);
             }
         } else {  // PITEM_COLS: every CTA of the cluster, G per strip
             stage(a.ccol + p, &s_cf, (int)sizeof(IIRCoef));
+            if (tid == 0) {
+                s_ca.ws = planes;
+                s_ca.f = d.f;
+                s_ca.y = d.y;
+                s_ca.gy = nullptr;
+                s_ca.saved = nullptr;
+                s_ca.pp = pp;
+                s_ca.status = status;
+                s_ca.acc = nullptr;
+                s_ca.H = d.H;
+                s_ca.W = d.W;
+                s_ca.pitch = d.pitch;
+                s_ca.Wp = d.Wp;
+                s_ca.K = d.K;
+                s_ca.N = d.N;
+                s_ca.wait_limit = 0;
+                s_ca.no_mma = 0;
+            }
             __syncthreads();
             const int G = d.G, g = rank / G;
             const int strip = w.z + g;
             const bool active = go && g < w.w && strip < d.strips;
-            ColArgs ca;
-            ca.ws = planes;
-            ca.f = d.f;
-            ca.y = d.y;
-            ca.gy = nullptr;
-            ca.saved = nullptr;
-            ca.pp = pp;
-            ca.status = status;
-            ca.acc = nullptr;
-            ca.H = d.H;
-            ca.W = d.W;
-            ca.pitch = d.pitch;
-            ca.Wp = d.Wp;
-            ca.K = d.K;
-            ca.N = d.N;
-            ca.wait_limit = 0;
-            ca.no_mma = 0;
-            col_iir_body<COL_C_PERSIST, MODE_FWD, 8>(ca, s_cf, active ? strip : 0, 0, ColGroup{G, rank % G, g * G, active ? 1 : 0});
+            col_iir_body<COL_C_PERSIST, MODE_FWD, 8>(s_ca, s_cf, active ? strip : 0, 0, ColGroup{G, rank % G, g * G, active ? 1 : 0});
         }
         __syncthreads();  // the staged coefficients are read before the next item replaces them
     }
